@@ -1,0 +1,235 @@
+/*
+ * sg.h -- C ABI of the batched articulated-arm simulation step (libsg.so).
+ *
+ * The library steps thousands of independent robot environments on one
+ * GPU: each environment is one or two serial chains of revolute/prismatic
+ * joints on a fixed base under PD joint drives (Surgical Gym, Methods,
+ * "Simulation Setup": actors of rigid bodies joined by revolute/prismatic
+ * joints, PD position targets as actions; Results, "Multi-Tool Target
+ * Reaching": two arms per environment).  One step integrates the
+ * reduced-coordinate rigid-body dynamics with `substeps` implicit-drive
+ * semi-implicit Euler substeps (Methods, "Simulation Setup": the engine
+ * sub-steps every control step) and writes the per-environment
+ * observation, reward and done tensors (Methods, "Observation Space";
+ * Results, "Environments"; Methods, "Policy learning and control": time-outs
+ * reported apart from terminations).
+ *
+ * Conventions (all entry points):
+ *  - Pointers named *_dev are DEVICE pointers (e.g. torch tensor data_ptr()),
+ *    contiguous, row-major, caller-owned; pointers named *_host are host
+ *    pointers.  The library never frees caller memory.
+ *  - All device work is enqueued asynchronously on the context's stream
+ *    (sg_create / sg_set_stream); results are valid once that stream has
+ *    reached the call.  Host-side argument errors are reported
+ *    synchronously by the return code; nothing is enqueued then.
+ *  - Environment index i in every array is the caller's env i, whatever
+ *    internal packing the library uses.
+ *  - Device-side faults are never raised as traps: a non-finite state sets
+ *    done bit SG_DONE_NONFINITE for that env and a context error flag that
+ *    sg_sync_status() reports.
+ *  - No C++ exception crosses this ABI.  sg_last_error() describes the last
+ *    failing call of a context.
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sg_ctx sg_ctx;   /* opaque; owned by the library */
+
+typedef enum sg_status {
+  SG_OK = 0,
+  SG_ERR_INVALID_ARG = 1,   /* bad pointer, size, range or layout */
+  SG_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  SG_ERR_OOM = 3,           /* device or host allocation failed */
+  SG_ERR_NONFINITE = 4,     /* a kernel saw a non-finite state (sg_sync_status) */
+  SG_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up (sg_sync_status) */
+  SG_ERR_UNSUPPORTED = 6    /* valid request outside what this build implements */
+} sg_status;
+
+enum {
+  SG_TASK_REACH = 0,        /* Target Reaching / Multi-Tool Target Reaching */
+  SG_TASK_PATH = 1          /* Path Following (single-chain envs only) */
+};
+
+enum {
+  SG_JOINT_REVOLUTE = 0,
+  SG_JOINT_PRISMATIC = 1    /* translation along the joint frame's local z */
+};
+
+enum {
+  SG_DONE_TERMINATED = 1,   /* reserved: termination (never set by the tasks here) */
+  SG_DONE_TIMEOUT = 2,      /* step count since reset reached episode_len */
+  SG_DONE_NONFINITE = 4     /* q or qd became non-finite in this step */
+};
+
+enum {
+  SG_MAX_CHAINS = 2,        /* chains (arms) per environment */
+  SG_MAX_CHAIN_JOINTS = 7   /* joints per chain */
+};
+
+/*
+ * Robot and task description.  All pointers are HOST pointers read during
+ * sg_create / sg_plan only (the caller keeps ownership).  E = num_envs,
+ * J = max_joints (row stride of every per-joint array, >= the total DOF of
+ * every env).  Joint j of an env indexes chain 0's joints first, then
+ * chain 1's.  Per-joint arrays beyond an env's DOF are ignored.
+ *
+ * Geometry: joint i of a chain sits at (0, 0, link_len[i-1]) in the frame
+ * of link i-1 (at base_offset for i = 0, base axes aligned with the world);
+ * a revolute joint rotates about its local axis joint_axis (0=x, 1=y,
+ * 2=z); a prismatic joint translates along local z (joint_axis must be 2).
+ * Link i extends along its local +z; its centre of mass is at
+ * (0, 0, link_com[i]) with diagonal rotational inertia link_inertia[i]
+ * about the centre of mass.  The tool tip of a chain is (0, 0, link_len)
+ * of its last link.  Gravity is 9.81 m/s^2 along -z.
+ *
+ * Drive of joint i with target q*: tau = kp (q* - q) - (kd + damping) qd
+ * + tau_lim, where tau_lim = -k_limit (q - q_hi) above q_hi,
+ * -k_limit (q - q_lo) below q_lo, 0 inside.
+ */
+typedef struct sg_desc {
+  int32_t num_envs;                 /* E >= 1 */
+  int32_t max_joints;               /* J, 1..14 */
+  const int32_t *env_num_chains;    /* [E]     1 or 2 */
+  const int32_t *chain_num_joints;  /* [E][2]  1..7 (second entry unused for 1 chain) */
+  const int32_t *joint_type;        /* [E][J]  SG_JOINT_* */
+  const int32_t *joint_axis;        /* [E][J]  0=x 1=y 2=z */
+  const float *link_len;            /* [E][J]  m */
+  const float *link_mass;           /* [E][J]  kg, > 0 */
+  const float *link_inertia;        /* [E][J][3] Ixx, Iyy, Izz about the COM, > 0 */
+  const float *link_com;            /* [E][J]  COM offset along local z, m */
+  const float *q_lo, *q_hi;         /* [E][J]  joint limits (rad or m) */
+  const float *kp, *kd, *damping;   /* [E][J]  drive stiffness, drive damping, joint damping */
+  const float *k_limit;             /* [E][J]  limit-spring stiffness (0 = no spring) */
+  const float *base_offset;         /* [E][2][3] chain base positions (world) */
+  const float *q0;                  /* [E][J]  state after reset (qd = 0) */
+  int32_t episode_len;              /* steps until the time-out bit, >= 1 */
+  int32_t task;                     /* SG_TASK_* */
+  const float *goal;                /* [E][2][3] per-chain goal (SG_TASK_REACH) */
+  const float *path;                /* [E][path_len][3] waypoints (SG_TASK_PATH), else NULL */
+  int32_t path_len;                 /* W >= 4 for SG_TASK_PATH */
+  float alpha;                      /* path reward scale */
+} sg_desc;
+
+/*
+ * Observation layout of env e (n = its total DOF, nc = its chains), padded
+ * with zeros to D = sg_obs_dim():
+ *   SG_TASK_REACH: [q(n), qd(n), tip_c(3) per chain, q*(n), goal_c(3) per chain]
+ *   SG_TASK_PATH:  [q(n), qd(n), tip(3), quat(4) = (x, y, z, w) with w >= 0,
+ *                   waypoint[t+1](3), waypoint[t+2](3), waypoint[t+3](3)]
+ * where t = steps since reset after this step and waypoint indices clamp at
+ * path_len - 1.  Reward: REACH  -sum_c ||tip_c - goal_c||;
+ *                        PATH   -alpha ||tip - waypoint[t]||.
+ */
+
+typedef struct sg_plan_info {
+  int32_t obs_dim;        /* D */
+  int32_t num_slots;      /* internal chain slots (multiple of 32) */
+  int32_t num_chains;     /* real chains (sum of env_num_chains) */
+  int32_t class_slots[4]; /* slots per internal chain class: 7R, 7P, generic, 4R */
+} sg_plan_info;
+
+/* Validate a description and compute its packing plan on the host, with no
+ * CUDA call.  Returns SG_ERR_INVALID_ARG / SG_ERR_UNSUPPORTED with a message
+ * in err (NUL-terminated, truncated to err_len) when the description is
+ * rejected.  info may be NULL. */
+sg_status sg_plan(const sg_desc *desc, sg_plan_info *info, char *err, int32_t err_len);
+
+/* Create a context: validate and pack the description, allocate the device
+ * state and parameter slabs (cudaMalloc) and upload them on `stream`
+ * (cudaStream_t, NULL = legacy default stream).  All envs start reset
+ * (q = q0, qd = 0, step count 0).  On failure *out is NULL. */
+sg_status sg_create(const sg_desc *desc, void *stream, sg_ctx **out);
+
+/* Free a context and its device memory (synchronises its stream).  NULL is a no-op. */
+void sg_destroy(sg_ctx *ctx);
+
+/* Change the stream later calls enqueue on. */
+sg_status sg_set_stream(sg_ctx *ctx, void *stream);
+
+int32_t sg_obs_dim(const sg_ctx *ctx);
+int32_t sg_num_envs(const sg_ctx *ctx);
+int32_t sg_max_joints(const sg_ctx *ctx);
+
+/* Reset envs with env_mask_dev[e] != 0 (uint8 [E], device); NULL resets all.
+ * Reset envs get q = q0, qd = 0, step count 0; others are untouched. */
+sg_status sg_reset(sg_ctx *ctx, const uint8_t *env_mask_dev);
+
+/* One control step of every env.
+ *   actions_dev [E][J] float: PD position targets q* (padding ignored)
+ *   dt > 0 seconds, substeps 1..64 (substep length dt / substeps)
+ *   obs_dev [E][D] float, reward_dev [E] float, done_dev [E] uint8 (outputs)
+ * Does not reset envs: the caller passes done-derived masks to sg_reset. */
+sg_status sg_step(sg_ctx *ctx, const float *actions_dev, float dt, int32_t substeps,
+                  float *obs_dev, float *reward_dev, uint8_t *done_dev);
+
+/* Read / write the state in caller layout: q, qd [E][J] float (padding
+ * joints are written as 0 by sg_get_state and ignored by sg_set_state),
+ * step_count [E] int32.  Any of the three pointers may be NULL to skip it. */
+sg_status sg_get_state(sg_ctx *ctx, float *q_dev, float *qd_dev, int32_t *step_count_dev);
+sg_status sg_set_state(sg_ctx *ctx, const float *q_dev, const float *qd_dev,
+                       const int32_t *step_count_dev);
+
+/*
+ * Rollout of T control steps (the batched form of sg_step):
+ *   actions_dev [T][E][J], obs_dev [T][E][D], reward_dev [T][E], done_dev [T][E].
+ * Results are identical, bit for bit, to T successive sg_step calls.  The
+ * work is issued according to the context's launch plan:
+ *   SG_ROLLOUT_PERSISTENT  one kernel runs all T steps with the chain state
+ *                          held in registers (parameters staged once);
+ *   SG_ROLLOUT_STEP_GRAPH  T single-step kernels.
+ * Either way the launch sequence is captured once into a CUDA graph (on a
+ * private capture stream) and replayed on the context's stream while T, dt,
+ * substeps, the launch plan and all pointers stay the same; any change
+ * re-captures.  T is 1..4096.
+ */
+enum { SG_ROLLOUT_PERSISTENT = 0, SG_ROLLOUT_STEP_GRAPH = 1 };
+
+sg_status sg_rollout(sg_ctx *ctx, const float *actions_dev, int32_t T, float dt,
+                     int32_t substeps, float *obs_dev, float *reward_dev, uint8_t *done_dev);
+
+/* sg_rollout with HOST buffers (same shapes): copies actions to the device,
+ * runs the rollout and copies obs, reward and done back, all enqueued on
+ * the context's stream (the first call allocates device staging buffers with
+ * cudaMalloc).  Page-locked host memory gives asynchronous copies; the
+ * outputs are valid after sg_sync_status() or a stream synchronisation. */
+sg_status sg_rollout_host(sg_ctx *ctx, const float *actions_host, int32_t T, float dt,
+                          int32_t substeps, float *obs_host, float *reward_host,
+                          uint8_t *done_host);
+
+/* Launch plan: threads per block (32, 64, 128 or 256; each warp of 32
+ * threads integrates 32 chains) and the rollout mode.  Results do not
+ * depend on the plan. */
+sg_status sg_set_launch(sg_ctx *ctx, int32_t threads_per_block, int32_t rollout_mode);
+sg_status sg_get_launch(const sg_ctx *ctx, int32_t *threads_per_block, int32_t *rollout_mode);
+
+/* Autotuner: times every launch plan (threads per block x rollout mode) on
+ * a rollout with the given arguments (CUDA events, median of `repeats`
+ * timed runs after one warm-up run each), keeps the fastest and writes its
+ * time per rollout to *best_ms (may be NULL).  The environment state and
+ * step counts are restored afterwards; the output buffers hold the last
+ * trial's results.  Synchronises the stream; allocates a state snapshot. */
+sg_status sg_autotune(sg_ctx *ctx, const float *actions_dev, int32_t T, float dt,
+                      int32_t substeps, float *obs_dev, float *reward_dev, uint8_t *done_dev,
+                      int32_t repeats, float *best_ms);
+
+/* Synchronise the context's stream, then read and clear the device error
+ * flags: SG_ERR_NONFINITE if any env produced a non-finite state since the
+ * last call, SG_ERR_TIMEOUT if a bounded device wait gave up, else SG_OK
+ * (or SG_ERR_CUDA if the stream reports an error). */
+sg_status sg_sync_status(sg_ctx *ctx);
+
+/* Message of the last failing call on ctx (never NULL; "" if none).
+ * With ctx == NULL: the last sg_create failure of this thread. */
+const char *sg_last_error(const sg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SG_H */

@@ -1,0 +1,505 @@
+// C ABI of libsg.so (declared in include/sg.h): context management, argument
+// validation and kernel launches.  All device work goes to the context's
+// stream; no call synchronises except sg_create, sg_destroy and
+// sg_sync_status.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sg.h"
+#include "sg_internal.h"
+#include "sg_kernels.h"
+
+struct sg_ctx {
+  sg::Plan plan;
+  cudaStream_t stream = nullptr;
+  float* d_params = nullptr;
+  float* d_q = nullptr;
+  float* d_qd = nullptr;
+  float* d_q0 = nullptr;
+  float* d_path = nullptr;
+  int32_t* d_slot_env = nullptr;
+  int32_t* d_slot_info = nullptr;
+  int32_t* d_warp_class = nullptr;
+  int32_t* d_step_count = nullptr;
+  int32_t* d_err = nullptr;
+  int threads = 128;
+  int rollout_mode = SG_ROLLOUT_PERSISTENT;
+  std::string last_error;
+  // captured rollout (CUDA graph) and the arguments it was captured for
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  struct Key {
+    const float* actions;
+    float* obs;
+    float* reward;
+    uint8_t* done;
+    int T, substeps, threads, mode;
+    float dt;
+    bool operator==(const Key& o) const {
+      return actions == o.actions && obs == o.obs && reward == o.reward && done == o.done &&
+             T == o.T && substeps == o.substeps && threads == o.threads && mode == o.mode &&
+             dt == o.dt;
+    }
+  } graph_key{};
+  // device staging for sg_rollout_host
+  float* d_stage_act = nullptr;
+  float* d_stage_obs = nullptr;
+  float* d_stage_rew = nullptr;
+  uint8_t* d_stage_done = nullptr;
+  int stage_T = 0;
+  // state snapshot for the autotuner
+  float* d_snap_q = nullptr;
+  float* d_snap_qd = nullptr;
+  int32_t* d_snap_sc = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+sg_status set_err(sg_ctx* ctx, sg_status code, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return code;
+}
+
+sg_status cuda_err(sg_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return SG_OK;
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return set_err(ctx, e == cudaErrorMemoryAllocation ? SG_ERR_OOM : SG_ERR_CUDA, m);
+}
+
+template <class T>
+cudaError_t upload(T** dst, const T* src, size_t n, cudaStream_t s) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), sizeof(T) * (n ? n : 1));
+  if (e != cudaSuccess) return e;
+  if (n && src) return cudaMemcpyAsync(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice, s);
+  return cudaSuccess;
+}
+
+void free_ctx(sg_ctx* c) {
+  if (!c) return;
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  void* ptrs[] = {c->d_params, c->d_q, c->d_qd, c->d_q0, c->d_path, c->d_slot_env,
+                  c->d_slot_info, c->d_warp_class, c->d_step_count, c->d_err,
+                  c->d_stage_act, c->d_stage_obs, c->d_stage_rew, c->d_stage_done,
+                  c->d_snap_q, c->d_snap_qd, c->d_snap_sc};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+sg::StateArgs state_args(sg_ctx* c) {
+  sg::StateArgs s;
+  s.slot_env = c->d_slot_env;
+  s.slot_info = c->d_slot_info;
+  s.q = c->d_q;
+  s.qd = c->d_qd;
+  s.q0 = c->d_q0;
+  s.step_count = c->d_step_count;
+  s.num_slots = c->plan.num_slots;
+  s.max_joints = c->plan.max_joints;
+  return s;
+}
+
+sg::StepArgs step_args(sg_ctx* c, float dt, int substeps, int T) {
+  sg::StepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.params = c->d_params;
+  a.slot_env = c->d_slot_env;
+  a.slot_info = c->d_slot_info;
+  a.warp_class = c->d_warp_class;
+  a.q = c->d_q;
+  a.qd = c->d_qd;
+  a.step_count = c->d_step_count;
+  a.path = c->d_path;
+  a.err = c->d_err;
+  a.num_warps = c->plan.num_warps;
+  a.num_slots = c->plan.num_slots;
+  a.num_envs = c->plan.num_envs;
+  a.max_joints = c->plan.max_joints;
+  a.obs_dim = c->plan.obs_dim;
+  a.task = c->plan.task;
+  a.path_len = c->plan.path_len;
+  a.episode_len = c->plan.episode_len;
+  a.alpha = c->plan.alpha;
+  a.substeps = substeps;
+  a.T = T;
+  a.h = dt / (float)substeps;
+  return a;
+}
+
+sg_status check_step_args(sg_ctx* ctx, const void* actions, float dt, int substeps,
+                          const void* obs, const void* rew, const void* done) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  if (!actions || !obs || !rew || !done)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "actions, obs, reward and done must be non-NULL");
+  if (!(dt > 0.f) || !std::isfinite(dt)) return set_err(ctx, SG_ERR_INVALID_ARG, "dt must be > 0");
+  if (substeps < 1 || substeps > 64)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "substeps must be 1..64");
+  return SG_OK;
+}
+
+bool valid_threads(int t) { return t == 32 || t == 64 || t == 128 || t == 256; }
+
+// Enqueue (capturing first if needed) the rollout graph on the context's stream.
+sg_status run_rollout(sg_ctx* c, const float* actions, int T, float dt, int substeps, float* obs,
+                      float* rew, uint8_t* done) {
+  const sg_ctx::Key key{actions, obs, rew, done, T, substeps, c->threads, c->rollout_mode, dt};
+  if (!c->graph_exec || !(key == c->graph_key)) {
+    if (c->graph_exec) {
+      cudaGraphExecDestroy(c->graph_exec);
+      c->graph_exec = nullptr;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!c->capture_stream) e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_err(c, e, "sg_rollout: capture stream");
+    e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_err(c, e, "sg_rollout: begin capture");
+    cudaError_t le = cudaSuccess;
+    const size_t E = c->plan.num_envs, J = c->plan.max_joints, D = c->plan.obs_dim;
+    if (c->rollout_mode == SG_ROLLOUT_PERSISTENT) {
+      sg::StepArgs a = step_args(c, dt, substeps, T);
+      a.actions = actions;
+      a.obs = obs;
+      a.reward = rew;
+      a.done = done;
+      le = sg::launch_step(a, c->threads, c->capture_stream);
+    } else {
+      for (int t = 0; t < T && le == cudaSuccess; ++t) {
+        sg::StepArgs a = step_args(c, dt, substeps, 1);
+        a.actions = actions + (size_t)t * E * J;
+        a.obs = obs + (size_t)t * E * D;
+        a.reward = rew + (size_t)t * E;
+        a.done = done + (size_t)t * E;
+        le = sg::launch_step(a, c->threads, c->capture_stream);
+      }
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->capture_stream, &g);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->graph_exec = nullptr;
+      return cuda_err(c, e, "sg_rollout: capture");
+    }
+    c->graph_key = key;
+  }
+  return cuda_err(c, cudaGraphLaunch(c->graph_exec, c->stream), "sg_rollout: graph launch");
+}
+
+sg_status check_rollout_args(sg_ctx* ctx, const void* actions, int T, float dt, int substeps,
+                             const void* obs, const void* rew, const void* done) {
+  sg_status st = check_step_args(ctx, actions, dt, substeps, obs, rew, done);
+  if (st != SG_OK) return st;
+  if (T < 1 || T > 4096) return set_err(ctx, SG_ERR_INVALID_ARG, "T must be 1..4096");
+  return SG_OK;
+}
+
+template <class T>
+cudaError_t ensure(T** p, size_t n) {
+  if (*p) return cudaSuccess;
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * n);
+}
+
+cudaError_t snapshot(sg_ctx* c, bool save) {
+  const size_t n = (size_t)sg::kMaxLinks * c->plan.num_slots, E = c->plan.num_envs;
+  cudaError_t e = ensure(&c->d_snap_q, n);
+  if (e == cudaSuccess) e = ensure(&c->d_snap_qd, n);
+  if (e == cudaSuccess) e = ensure(&c->d_snap_sc, E);
+  if (e != cudaSuccess) return e;
+  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  if (save) {
+    e = cudaMemcpyAsync(c->d_snap_q, c->d_q, n * 4, k, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_snap_qd, c->d_qd, n * 4, k, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_snap_sc, c->d_step_count, E * 4, k, c->stream);
+  } else {
+    e = cudaMemcpyAsync(c->d_q, c->d_snap_q, n * 4, k, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_qd, c->d_snap_qd, n * 4, k, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_step_count, c->d_snap_sc, E * 4, k, c->stream);
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+sg_status sg_plan(const sg_desc* desc, sg_plan_info* info, char* err, int32_t err_len) {
+  sg::Plan p;
+  std::string msg;
+  sg_status st;
+  try {
+    st = sg::build_plan(desc, &p, &msg);
+  } catch (const std::bad_alloc&) {
+    st = SG_ERR_OOM;
+    msg = "host allocation failed";
+  }
+  if (err && err_len > 0) {
+    std::strncpy(err, msg.c_str(), (size_t)err_len - 1);
+    err[err_len - 1] = '\0';
+  }
+  if (st != SG_OK) return st;
+  if (info) {
+    info->obs_dim = p.obs_dim;
+    info->num_slots = p.num_slots;
+    info->num_chains = p.num_chains;
+    for (int k = 0; k < 4; ++k) info->class_slots[k] = p.class_slots[k];
+  }
+  return SG_OK;
+}
+
+sg_status sg_create(const sg_desc* desc, void* stream, sg_ctx** out) {
+  if (!out) {
+    g_create_error = "out is NULL";
+    return SG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  sg_ctx* c = new (std::nothrow) sg_ctx();
+  if (!c) {
+    g_create_error = "host allocation failed";
+    return SG_ERR_OOM;
+  }
+  std::string msg;
+  sg_status st;
+  try {
+    st = sg::build_plan(desc, &c->plan, &msg);
+  } catch (const std::bad_alloc&) {
+    st = SG_ERR_OOM;
+    msg = "host allocation failed";
+  }
+  if (st != SG_OK) {
+    g_create_error = msg;
+    free_ctx(c);
+    return st;
+  }
+  c->stream = static_cast<cudaStream_t>(stream);
+  const sg::Plan& P = c->plan;
+  const size_t NS = P.num_slots;
+  cudaError_t e = cudaSuccess;
+  auto step = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  step(upload(&c->d_params, P.params.data(), P.params.size(), c->stream));
+  step(upload(&c->d_slot_env, P.slot_env.data(), NS, c->stream));
+  step(upload(&c->d_slot_info, P.slot_info.data(), NS, c->stream));
+  step(upload(&c->d_warp_class, P.warp_class.data(), P.warp_class.size(), c->stream));
+  step(upload(&c->d_q0, P.q0.data(), P.q0.size(), c->stream));
+  step(upload<float>(&c->d_q, nullptr, (size_t)sg::kMaxLinks * NS, c->stream));
+  step(upload<float>(&c->d_qd, nullptr, (size_t)sg::kMaxLinks * NS, c->stream));
+  step(upload<int32_t>(&c->d_step_count, nullptr, (size_t)P.num_envs, c->stream));
+  step(upload<int32_t>(&c->d_err, nullptr, 1, c->stream));
+  step(upload(&c->d_path, P.path.empty() ? nullptr : P.path.data(), P.path.size(), c->stream));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_q, 0, sizeof(float) * sg::kMaxLinks * NS, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_qd, 0, sizeof(float) * sg::kMaxLinks * NS, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream);
+  if (e == cudaSuccess) e = sg::prepare_step_kernel();
+  if (e == cudaSuccess) e = sg::launch_reset(state_args(c), nullptr, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("sg_create: ") + cudaGetErrorString(e);
+    sg_status code = e == cudaErrorMemoryAllocation ? SG_ERR_OOM : SG_ERR_CUDA;
+    free_ctx(c);
+    return code;
+  }
+  *out = c;
+  return SG_OK;
+}
+
+void sg_destroy(sg_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  free_ctx(ctx);
+}
+
+sg_status sg_set_stream(sg_ctx* ctx, void* stream) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return SG_OK;
+}
+
+int32_t sg_obs_dim(const sg_ctx* ctx) { return ctx ? ctx->plan.obs_dim : 0; }
+int32_t sg_num_envs(const sg_ctx* ctx) { return ctx ? ctx->plan.num_envs : 0; }
+int32_t sg_max_joints(const sg_ctx* ctx) { return ctx ? ctx->plan.max_joints : 0; }
+
+sg_status sg_reset(sg_ctx* ctx, const uint8_t* env_mask_dev) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  return cuda_err(ctx, sg::launch_reset(state_args(ctx), env_mask_dev, ctx->stream), "sg_reset");
+}
+
+sg_status sg_step(sg_ctx* ctx, const float* actions_dev, float dt, int32_t substeps,
+                  float* obs_dev, float* reward_dev, uint8_t* done_dev) {
+  sg_status st = check_step_args(ctx, actions_dev, dt, substeps, obs_dev, reward_dev, done_dev);
+  if (st != SG_OK) return st;
+  sg::StepArgs a = step_args(ctx, dt, substeps, 1);
+  a.actions = actions_dev;
+  a.obs = obs_dev;
+  a.reward = reward_dev;
+  a.done = done_dev;
+  return cuda_err(ctx, sg::launch_step(a, ctx->threads, ctx->stream), "sg_step");
+}
+
+sg_status sg_rollout(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt,
+                     int32_t substeps, float* obs_dev, float* reward_dev, uint8_t* done_dev) {
+  sg_status st = check_rollout_args(ctx, actions_dev, T, dt, substeps, obs_dev, reward_dev, done_dev);
+  if (st != SG_OK) return st;
+  return run_rollout(ctx, actions_dev, T, dt, substeps, obs_dev, reward_dev, done_dev);
+}
+
+sg_status sg_rollout_host(sg_ctx* ctx, const float* actions_host, int32_t T, float dt,
+                          int32_t substeps, float* obs_host, float* reward_host,
+                          uint8_t* done_host) {
+  sg_status st =
+      check_rollout_args(ctx, actions_host, T, dt, substeps, obs_host, reward_host, done_host);
+  if (st != SG_OK) return st;
+  const size_t E = ctx->plan.num_envs, J = ctx->plan.max_joints, D = ctx->plan.obs_dim;
+  cudaError_t e = cudaSuccess;
+  if (T > ctx->stage_T) {
+    e = cudaStreamSynchronize(ctx->stream);
+    void* old[] = {ctx->d_stage_act, ctx->d_stage_obs, ctx->d_stage_rew, ctx->d_stage_done};
+    for (void* p : old)
+      if (p) cudaFree(p);
+    ctx->d_stage_act = ctx->d_stage_obs = ctx->d_stage_rew = nullptr;
+    ctx->d_stage_done = nullptr;
+    ctx->stage_T = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_stage_act, sizeof(float) * T * E * J);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_stage_obs, sizeof(float) * T * E * D);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_stage_rew, sizeof(float) * T * E);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_stage_done, (size_t)T * E);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "sg_rollout_host: staging");
+    ctx->stage_T = T;
+  }
+  e = cudaMemcpyAsync(ctx->d_stage_act, actions_host, sizeof(float) * T * E * J,
+                      cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "sg_rollout_host: copy in");
+  st = run_rollout(ctx, ctx->d_stage_act, T, dt, substeps, ctx->d_stage_obs, ctx->d_stage_rew,
+                   ctx->d_stage_done);
+  if (st != SG_OK) return st;
+  e = cudaMemcpyAsync(obs_host, ctx->d_stage_obs, sizeof(float) * T * E * D,
+                      cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(reward_host, ctx->d_stage_rew, sizeof(float) * T * E,
+                        cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(done_host, ctx->d_stage_done, (size_t)T * E, cudaMemcpyDeviceToHost,
+                        ctx->stream);
+  return cuda_err(ctx, e, "sg_rollout_host: copy out");
+}
+
+sg_status sg_set_launch(sg_ctx* ctx, int32_t threads_per_block, int32_t rollout_mode) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  if (!valid_threads(threads_per_block))
+    return set_err(ctx, SG_ERR_INVALID_ARG, "threads_per_block must be 32, 64, 128 or 256");
+  if (rollout_mode != SG_ROLLOUT_PERSISTENT && rollout_mode != SG_ROLLOUT_STEP_GRAPH)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "unknown rollout mode");
+  ctx->threads = threads_per_block;
+  ctx->rollout_mode = rollout_mode;
+  return SG_OK;
+}
+
+sg_status sg_get_launch(const sg_ctx* ctx, int32_t* threads_per_block, int32_t* rollout_mode) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  if (threads_per_block) *threads_per_block = ctx->threads;
+  if (rollout_mode) *rollout_mode = ctx->rollout_mode;
+  return SG_OK;
+}
+
+sg_status sg_autotune(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt,
+                      int32_t substeps, float* obs_dev, float* reward_dev, uint8_t* done_dev,
+                      int32_t repeats, float* best_ms) {
+  sg_status st = check_rollout_args(ctx, actions_dev, T, dt, substeps, obs_dev, reward_dev, done_dev);
+  if (st != SG_OK) return st;
+  if (repeats < 1 || repeats > 1000) return set_err(ctx, SG_ERR_INVALID_ARG, "repeats must be 1..1000");
+  cudaError_t e = snapshot(ctx, true);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "sg_autotune: snapshot");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "sg_autotune: events");
+  const int threads_list[] = {32, 64, 128, 256};
+  const int modes[] = {SG_ROLLOUT_PERSISTENT, SG_ROLLOUT_STEP_GRAPH};
+  float best = -1.f;
+  int best_t = ctx->threads, best_m = ctx->rollout_mode;
+  for (int m : modes) {
+    for (int th : threads_list) {
+      ctx->threads = th;
+      ctx->rollout_mode = m;
+      std::vector<float> times;
+      for (int r = -1; r < repeats && st == SG_OK; ++r) {
+        e = snapshot(ctx, false);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+        if (e != cudaSuccess) break;
+        st = run_rollout(ctx, actions_dev, T, dt, substeps, obs_dev, reward_dev, done_dev);
+        if (st != SG_OK) break;
+        e = cudaEventRecord(e1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        if (r >= 0) times.push_back(ms);
+      }
+      if (e != cudaSuccess || st != SG_OK) break;
+      std::sort(times.begin(), times.end());
+      const float med = times[times.size() / 2];
+      if (best < 0.f || med < best) {
+        best = med;
+        best_t = th;
+        best_m = m;
+      }
+    }
+    if (e != cudaSuccess || st != SG_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->threads = best_t;
+  ctx->rollout_mode = best_m;
+  if (st != SG_OK) return st;
+  if (e == cudaSuccess) e = snapshot(ctx, false);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "sg_autotune");
+  if (best_ms) *best_ms = best;
+  return SG_OK;
+}
+
+sg_status sg_get_state(sg_ctx* ctx, float* q_dev, float* qd_dev, int32_t* step_count_dev) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  return cuda_err(ctx, sg::launch_get_state(state_args(ctx), q_dev, qd_dev, step_count_dev,
+                                            ctx->stream),
+                  "sg_get_state");
+}
+
+sg_status sg_set_state(sg_ctx* ctx, const float* q_dev, const float* qd_dev,
+                       const int32_t* step_count_dev) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  return cuda_err(ctx, sg::launch_set_state(state_args(ctx), q_dev, qd_dev, step_count_dev,
+                                            ctx->stream),
+                  "sg_set_state");
+}
+
+sg_status sg_sync_status(sg_ctx* ctx) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "sg_sync_status");
+  int32_t flags = 0;
+  e = cudaMemcpy(&flags, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int32_t));
+  if (e != cudaSuccess) return cuda_err(ctx, e, "sg_sync_status");
+  if (flags & sg::DEVERR_TIMEOUT)
+    return set_err(ctx, SG_ERR_TIMEOUT, "a bounded device wait for a parameter copy gave up");
+  if (flags & sg::DEVERR_NONFINITE)
+    return set_err(ctx, SG_ERR_NONFINITE, "an environment produced a non-finite state");
+  return SG_OK;
+}
+
+const char* sg_last_error(const sg_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

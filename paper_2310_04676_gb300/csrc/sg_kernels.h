@@ -1,0 +1,31 @@
+// Kernel launchers (implemented in sg_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sg_internal.h"
+
+namespace sg {
+
+struct StateArgs {
+  const int32_t* slot_env;
+  const int32_t* slot_info;
+  float* q;
+  float* qd;
+  const float* q0;
+  int32_t* step_count;
+  int num_slots, max_joints;
+};
+
+constexpr int kMaxThreads = 256;   // largest step-kernel block
+
+size_t step_smem_bytes(int threads);
+cudaError_t prepare_step_kernel();   // one-time kernel attributes (not capturable)
+cudaError_t launch_step(const StepArgs& a, int threads, cudaStream_t stream);
+cudaError_t launch_reset(const StateArgs& s, const uint8_t* mask, cudaStream_t stream);
+cudaError_t launch_get_state(const StateArgs& s, float* q, float* qd, int32_t* sc,
+                             cudaStream_t stream);
+cudaError_t launch_set_state(const StateArgs& s, const float* q, const float* qd,
+                             const int32_t* sc, cudaStream_t stream);
+
+}  // namespace sg

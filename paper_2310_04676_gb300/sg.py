@@ -1,0 +1,305 @@
+"""Python binding of libsg.so (include/sg.h): argument marshalling only.
+
+Every step of the simulation runs in the library's CUDA kernels; PyTorch
+supplies device memory and the current CUDA stream.  There is no CPU
+fallback: if libsg.so is missing or no GPU is present, construction fails.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libsg.so")
+
+SG_OK, SG_ERR_INVALID_ARG, SG_ERR_CUDA, SG_ERR_OOM, SG_ERR_NONFINITE, SG_ERR_TIMEOUT, \
+    SG_ERR_UNSUPPORTED = range(7)
+STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_CUDA", 3: "SG_ERR_OOM",
+                4: "SG_ERR_NONFINITE", 5: "SG_ERR_TIMEOUT", 6: "SG_ERR_UNSUPPORTED"}
+DONE_TERMINATED, DONE_TIMEOUT, DONE_NONFINITE = 1, 2, 4
+ROLLOUT_PERSISTENT, ROLLOUT_STEP_GRAPH = 0, 1
+
+
+class SgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_c_i32p = ctypes.POINTER(ctypes.c_int32)
+_c_f32p = ctypes.POINTER(ctypes.c_float)
+
+
+class SgDesc(ctypes.Structure):
+    _fields_ = [
+        ("num_envs", ctypes.c_int32), ("max_joints", ctypes.c_int32),
+        ("env_num_chains", _c_i32p), ("chain_num_joints", _c_i32p),
+        ("joint_type", _c_i32p), ("joint_axis", _c_i32p),
+        ("link_len", _c_f32p), ("link_mass", _c_f32p), ("link_inertia", _c_f32p),
+        ("link_com", _c_f32p), ("q_lo", _c_f32p), ("q_hi", _c_f32p),
+        ("kp", _c_f32p), ("kd", _c_f32p), ("damping", _c_f32p), ("k_limit", _c_f32p),
+        ("base_offset", _c_f32p), ("q0", _c_f32p),
+        ("episode_len", ctypes.c_int32), ("task", ctypes.c_int32),
+        ("goal", _c_f32p), ("path", _c_f32p), ("path_len", ctypes.c_int32),
+        ("alpha", ctypes.c_float),
+    ]
+
+
+class SgPlanInfo(ctypes.Structure):
+    _fields_ = [("obs_dim", ctypes.c_int32), ("num_slots", ctypes.c_int32),
+                ("num_chains", ctypes.c_int32), ("class_slots", ctypes.c_int32 * 4)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libsg.so and declare its signatures (no GPU needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libsg.so not built (%s): run paper_2310_04676_gb300.build" % path)
+    lib = ctypes.CDLL(path)
+    vp, i32, f32, u8p = ctypes.c_void_p, ctypes.c_int32, ctypes.c_float, ctypes.c_void_p
+    sig = {
+        "sg_plan": (i32, [ctypes.POINTER(SgDesc), ctypes.POINTER(SgPlanInfo), ctypes.c_char_p, i32]),
+        "sg_create": (i32, [ctypes.POINTER(SgDesc), vp, ctypes.POINTER(vp)]),
+        "sg_destroy": (None, [vp]),
+        "sg_set_stream": (i32, [vp, vp]),
+        "sg_obs_dim": (i32, [vp]),
+        "sg_num_envs": (i32, [vp]),
+        "sg_max_joints": (i32, [vp]),
+        "sg_reset": (i32, [vp, u8p]),
+        "sg_step": (i32, [vp, vp, f32, i32, vp, vp, u8p]),
+        "sg_get_state": (i32, [vp, vp, vp, vp]),
+        "sg_set_state": (i32, [vp, vp, vp, vp]),
+        "sg_sync_status": (i32, [vp]),
+        "sg_rollout": (i32, [vp, vp, i32, f32, i32, vp, vp, u8p]),
+        "sg_rollout_host": (i32, [vp, vp, i32, f32, i32, vp, vp, u8p]),
+        "sg_set_launch": (i32, [vp, i32, i32]),
+        "sg_get_launch": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "sg_autotune": (i32, [vp, vp, i32, f32, i32, vp, vp, u8p, i32, ctypes.POINTER(f32)]),
+        "sg_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _arr(desc, key, dtype, shape):
+    a = np.ascontiguousarray(np.asarray(desc[key], dtype=dtype)).ravel()
+    need = int(np.prod(shape))
+    if a.size < need:
+        raise ValueError("desc[%r] has %d elements, needs %d" % (key, a.size, need))
+    return a
+
+
+def make_c_desc(desc):
+    """ctypes sg_desc over numpy copies of an ``sg_desc`` dictionary.
+    Returns (struct, keepalive list)."""
+    E, J = int(desc["num_envs"]), int(desc["max_joints"])
+    keep = []
+
+    def p(key, dtype, shape, ctype):
+        if desc.get(key) is None:
+            return ctypes.cast(None, ctype)
+        a = _arr(desc, key, dtype, shape)
+        keep.append(a)
+        return a.ctypes.data_as(ctype)
+
+    i32, f32 = np.int32, np.float32
+    d = SgDesc()
+    d.num_envs, d.max_joints = E, J
+    d.env_num_chains = p("env_num_chains", i32, (E,), _c_i32p)
+    d.chain_num_joints = p("chain_num_joints", i32, (E, 2), _c_i32p)
+    d.joint_type = p("joint_type", i32, (E, J), _c_i32p)
+    d.joint_axis = p("joint_axis", i32, (E, J), _c_i32p)
+    for k in ("link_len", "link_mass", "link_com", "q_lo", "q_hi", "kp", "kd", "damping",
+              "k_limit", "q0"):
+        setattr(d, k, p(k, f32, (E, J), _c_f32p))
+    d.link_inertia = p("link_inertia", f32, (E, J, 3), _c_f32p)
+    d.base_offset = p("base_offset", f32, (E, 2, 3), _c_f32p)
+    d.goal = p("goal", f32, (E, 2, 3), _c_f32p)
+    W = int(desc.get("path_len") or 0)
+    d.path = p("path", f32, (E, W, 3), _c_f32p) if W else ctypes.cast(None, _c_f32p)
+    d.path_len = W
+    d.episode_len = int(desc["episode_len"])
+    d.task = int(desc["task"])
+    d.alpha = float(desc.get("alpha", 1.0))
+    return d, keep
+
+
+def plan(desc):
+    """Host-only validation and packing plan (no GPU): dict or SgError."""
+    lib = load_library()
+    d, keep = make_c_desc(desc)
+    info = SgPlanInfo()
+    buf = ctypes.create_string_buffer(512)
+    st = lib.sg_plan(ctypes.byref(d), ctypes.byref(info), buf, 512)
+    if st != SG_OK:
+        raise SgError(st, buf.value.decode())
+    return dict(obs_dim=info.obs_dim, num_slots=info.num_slots, num_chains=info.num_chains,
+                class_slots=list(info.class_slots))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Env:
+    """A batch of environments on the current CUDA device.
+
+    ``desc`` is an ``sg_desc`` dictionary (see ``workloads.make_desc``).
+    Tensors passed in must be contiguous CUDA tensors of the documented
+    dtype and shape; outputs are allocated with torch and returned.
+    """
+
+    def __init__(self, desc, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA GPU is required (no CPU fallback)")
+        self._torch = torch
+        self.lib = load_library()
+        d, keep = make_c_desc(desc)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self._stream = s
+        ctx = ctypes.c_void_p()
+        st = self.lib.sg_create(ctypes.byref(d), ctypes.c_void_p(s.cuda_stream), ctypes.byref(ctx))
+        if st != SG_OK:
+            raise SgError(st, self.lib.sg_last_error(None).decode())
+        self.ctx = ctx
+        self.num_envs = self.lib.sg_num_envs(ctx)
+        self.max_joints = self.lib.sg_max_joints(ctx)
+        self.obs_dim = self.lib.sg_obs_dim(ctx)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.sg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers ----------------------------------------------------------
+    def _check(self, st):
+        if st != SG_OK:
+            raise SgError(st, self.lib.sg_last_error(self.ctx).decode())
+
+    def _sync_stream(self):
+        cur = self._torch.cuda.current_stream()
+        if cur.cuda_stream != self._stream.cuda_stream:
+            self._stream = cur
+            self._check(self.lib.sg_set_stream(self.ctx, ctypes.c_void_p(cur.cuda_stream)))
+
+    def _want(self, t, dtype, shape, name):
+        torch = self._torch
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != dtype \
+                or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous cuda %s tensor of shape %s" % (name, dtype, shape))
+        return t
+
+    def empty_outputs(self, T=None):
+        torch = self._torch
+        lead = () if T is None else (T,)
+        E, D = self.num_envs, self.obs_dim
+        return (torch.empty(lead + (E, D), dtype=torch.float32, device=self.device),
+                torch.empty(lead + (E,), dtype=torch.float32, device=self.device),
+                torch.empty(lead + (E,), dtype=torch.uint8, device=self.device))
+
+    # -- API ----------------------------------------------------------------
+    def reset(self, mask=None):
+        self._sync_stream()
+        if mask is not None:
+            self._want(mask, self._torch.uint8, (self.num_envs,), "mask")
+        self._check(self.lib.sg_reset(self.ctx, _ptr(mask)))
+
+    def step(self, actions, dt, substeps, out=None):
+        self._sync_stream()
+        torch = self._torch
+        self._want(actions, torch.float32, (self.num_envs, self.max_joints), "actions")
+        obs, rew, done = out if out is not None else self.empty_outputs()
+        self._check(self.lib.sg_step(self.ctx, _ptr(actions), float(dt), int(substeps),
+                                     _ptr(obs), _ptr(rew), _ptr(done)))
+        return obs, rew, done
+
+    def rollout(self, actions, dt, substeps, out=None):
+        """T steps in one call: actions [T, E, J] -> obs [T, E, D], reward
+        [T, E], done [T, E] (captured CUDA graph, see sg_rollout)."""
+        self._sync_stream()
+        torch = self._torch
+        T = int(actions.shape[0])
+        self._want(actions, torch.float32, (T, self.num_envs, self.max_joints), "actions")
+        obs, rew, done = out if out is not None else self.empty_outputs(T)
+        self._check(self.lib.sg_rollout(self.ctx, _ptr(actions), T, float(dt), int(substeps),
+                                        _ptr(obs), _ptr(rew), _ptr(done)))
+        return obs, rew, done
+
+    def rollout_host(self, actions, dt, substeps, out):
+        """Rollout on host tensors (ideally pinned): actions [T, E, J] float32
+        and preallocated host outputs (obs, reward, done); asynchronous on the
+        context's stream."""
+        self._sync_stream()
+        obs, rew, done = out
+        for t in (actions, obs, rew, done):
+            if t.device.type != "cpu" or not t.is_contiguous():
+                raise ValueError("rollout_host takes contiguous host tensors")
+        T = int(actions.shape[0])
+        self._check(self.lib.sg_rollout_host(self.ctx, _ptr(actions), T, float(dt), int(substeps),
+                                             _ptr(obs), _ptr(rew), _ptr(done)))
+
+    def set_launch(self, threads_per_block, mode):
+        self._check(self.lib.sg_set_launch(self.ctx, int(threads_per_block), int(mode)))
+
+    def get_launch(self):
+        t, m = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.sg_get_launch(self.ctx, ctypes.byref(t), ctypes.byref(m)))
+        return t.value, m.value
+
+    def autotune(self, actions, dt, substeps, out=None, repeats=3):
+        """Pick the fastest launch plan for this rollout shape; returns
+        (threads_per_block, mode, ms per rollout).  State is preserved."""
+        self._sync_stream()
+        torch = self._torch
+        T = int(actions.shape[0])
+        self._want(actions, torch.float32, (T, self.num_envs, self.max_joints), "actions")
+        obs, rew, done = out if out is not None else self.empty_outputs(T)
+        ms = ctypes.c_float()
+        self._check(self.lib.sg_autotune(self.ctx, _ptr(actions), T, float(dt), int(substeps),
+                                         _ptr(obs), _ptr(rew), _ptr(done), int(repeats),
+                                         ctypes.byref(ms)))
+        t, m = self.get_launch()
+        return t, m, ms.value
+
+    def get_state(self):
+        self._sync_stream()
+        torch = self._torch
+        E, J = self.num_envs, self.max_joints
+        q = torch.empty(E, J, dtype=torch.float32, device=self.device)
+        qd = torch.empty_like(q)
+        sc = torch.empty(E, dtype=torch.int32, device=self.device)
+        self._check(self.lib.sg_get_state(self.ctx, _ptr(q), _ptr(qd), _ptr(sc)))
+        return q, qd, sc
+
+    def set_state(self, q=None, qd=None, step_count=None):
+        self._sync_stream()
+        torch = self._torch
+        E, J = self.num_envs, self.max_joints
+        if q is not None:
+            self._want(q, torch.float32, (E, J), "q")
+        if qd is not None:
+            self._want(qd, torch.float32, (E, J), "qd")
+        if step_count is not None:
+            self._want(step_count, torch.int32, (E,), "step_count")
+        self._check(self.lib.sg_set_state(self.ctx, _ptr(q), _ptr(qd), _ptr(step_count)))
+
+    def sync_status(self):
+        """Synchronise and return the device status code (raises nothing)."""
+        return self.lib.sg_sync_status(self.ctx)

@@ -1,0 +1,99 @@
+"""The C-ABI library loads, exports every declared symbol, and validates
+descriptions on the host (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2310_04676_gb300 import sg, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(sg.LIB_PATH):
+        from paper_2310_04676_gb300 import build
+        build.build()
+    return sg.load_library()
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(sg_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_plan_counts_and_obs_dim(lib):
+    kinds = W.mixed_kinds(1000, W.C3_FRACTIONS)
+    d = W.make_desc(kinds)
+    info = sg.plan(d)
+    assert info["obs_dim"] == 54
+    n4 = kinds.count("4R")
+    n7 = kinds.count("7R")
+    n7p = kinds.count("7P")
+    nb = kinds.count("14B")
+    assert info["class_slots"] == [n7 + 2 * nb, n7p, 0, n4]
+    assert info["num_chains"] == n4 + n7 + n7p + 2 * nb
+    assert info["num_slots"] % 32 == 0
+
+
+def test_plan_generic_class_and_path_obs(lib):
+    from tests.helpers import chain_desc
+    d = chain_desc([([0, 1, 0], [0, 2, 1])], E=5)
+    info = sg.plan(d)
+    assert info["class_slots"] == [0, 0, 5, 0]
+    dp = W.make_desc(["7R"] * 3, task=1, path_len=8)
+    assert sg.plan(dp)["obs_dim"] == 30
+
+
+@pytest.mark.parametrize("mutate,code", [
+    (lambda d: d.__setitem__("num_envs", 0), sg.SG_ERR_INVALID_ARG),
+    (lambda d: d["env_num_chains"].__setitem__(0, 3), sg.SG_ERR_INVALID_ARG),
+    (lambda d: d["chain_num_joints"].__setitem__((0, 0), 8), sg.SG_ERR_INVALID_ARG),
+    (lambda d: d["joint_axis"].__setitem__((0, 1), 5), sg.SG_ERR_INVALID_ARG),
+    (lambda d: d["link_mass"].__setitem__((0, 2), 0.0), sg.SG_ERR_INVALID_ARG),
+    (lambda d: d["link_len"].__setitem__((0, 2), np.nan), sg.SG_ERR_INVALID_ARG),
+    (lambda d: d["kp"].__setitem__((0, 2), -1.0), sg.SG_ERR_INVALID_ARG),
+    (lambda d: (d["joint_type"].__setitem__((0, 1), 1), d["joint_axis"].__setitem__((0, 1), 1)),
+     sg.SG_ERR_UNSUPPORTED),
+    (lambda d: d.__setitem__("episode_len", 0), sg.SG_ERR_INVALID_ARG),
+    (lambda d: d.__setitem__("task", 7), sg.SG_ERR_INVALID_ARG),
+])
+def test_plan_rejects_bad_descriptions(lib, mutate, code):
+    d = W.make_desc(["7R", "4R"])
+    d = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in d.items()}
+    mutate(d)
+    with pytest.raises(sg.SgError) as ei:
+        sg.plan(d)
+    assert ei.value.status == code
+
+
+def test_path_task_rejects_two_arm_envs(lib):
+    d = W.make_desc(["7R", "14B"])
+    d["task"] = 1
+    d["path_len"] = 8
+    d["path"] = np.zeros((2, 8, 3), np.float32)
+    with pytest.raises(sg.SgError) as ei:
+        sg.plan(d)
+    assert ei.value.status == sg.SG_ERR_UNSUPPORTED
+
+
+def test_null_context_calls_are_rejected(lib):
+    assert lib.sg_step(None, None, ctypes.c_float(0.01), 1, None, None, None) == sg.SG_ERR_INVALID_ARG
+    assert lib.sg_reset(None, None) == sg.SG_ERR_INVALID_ARG
+    assert lib.sg_obs_dim(None) == 0
+    lib.sg_destroy(None)
