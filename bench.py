@@ -214,9 +214,9 @@ def main():
     out = env.empty_outputs(T)
     out_g = sgraph.empty_outputs(T)
     out_p = plain.empty_outputs(T)
-    threads, mode, tune_ms = env.autotune(acts, dt, S, out=out, repeats=3)
-    sgraph.set_launch(threads, sg.ROLLOUT_STEP_GRAPH)
-    plain.set_launch(threads, sg.ROLLOUT_PERSISTENT)
+    threads, mode, split, tune_ms = env.autotune(acts, dt, S, out=out, repeats=3)
+    sgraph.set_launch(threads, sg.ROLLOUT_STEP_GRAPH, split)
+    plain.set_launch(threads, sg.ROLLOUT_PERSISTENT, split)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -274,7 +274,7 @@ def main():
 
     # ---- end to end through the C ABI with host buffers
     env_h = sg.Env(desc)
-    env_h.set_launch(threads, mode)
+    env_h.set_launch(threads, mode, split)
     a_h = acts.cpu().pin_memory()
     o_h = (torch.empty(T, E, env_h.obs_dim).pin_memory(), torch.empty(T, E).pin_memory(),
            torch.empty(T, E, dtype=torch.uint8).pin_memory())
@@ -329,7 +329,8 @@ def main():
             "config": {"workload": wl.name, "envs_per_gpu": E, "rollout_steps": T,
                        "substeps": S, "dt": dt, "form": "persistent kernel in a CUDA graph",
                        "launch": {"threads_per_block": threads,
-                                  "mode": ["persistent", "step_graph"][mode]},
+                                  "mode": ["persistent", "step_graph"][mode],
+                                  "chain_split": split},
                        "l2": "flushed (256 MiB write) before every timed step"},
             "plain": {"value": world * E * T * args.steps / t_plain, "unit": "env-steps/s",
                       "ms_per_step": 1e3 * t_plain / args.steps,
@@ -345,7 +346,8 @@ def main():
             "status": sg.STATUS_NAMES.get(status, status),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                          "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-                         "kernel": "step_kernel (persistent, T=32)",
+                         "kernel": "%s (persistent, T=32)" % (
+                             "step_kernel_pair" if split == 2 else "step_kernel"),
                          "peak_source": "SMs x 128 FP32 lanes x 2 x %.0f MHz (%s max clock)"
                                         % (sm_max, peak_src),
                          "flops_per_launch": flops_launch,

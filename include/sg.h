@@ -202,13 +202,20 @@ sg_status sg_rollout_host(sg_ctx *ctx, const float *actions_host, int32_t T, flo
                           int32_t substeps, float *obs_host, float *reward_host,
                           uint8_t *done_host);
 
-/* Launch plan: threads per block (32, 64, 128 or 256; each warp of 32
- * threads integrates 32 chains) and the rollout mode.  Results do not
- * depend on the plan. */
-sg_status sg_set_launch(sg_ctx *ctx, int32_t threads_per_block, int32_t rollout_mode);
-sg_status sg_get_launch(const sg_ctx *ctx, int32_t *threads_per_block, int32_t *rollout_mode);
+/* Launch plan: threads per block (32, 64, 128 or 256), the rollout mode
+ * and the chain split: 1 = one thread integrates one chain (a warp holds 32
+ * chains); 2 = two threads in two cooperating warps share each chain (one
+ * computes the bias forces and drive terms, the other the mass matrix and
+ * the solve), which doubles the parallelism of batches too small to fill
+ * the GPU; threads_per_block must then be 64, 128 or 256.  Results do not
+ * depend on the plan (bit-identical). */
+sg_status sg_set_launch(sg_ctx *ctx, int32_t threads_per_block, int32_t rollout_mode,
+                        int32_t chain_split);
+sg_status sg_get_launch(const sg_ctx *ctx, int32_t *threads_per_block, int32_t *rollout_mode,
+                        int32_t *chain_split);
 
-/* Autotuner: times every launch plan (threads per block x rollout mode) on
+/* Autotuner: times every launch plan (threads per block x chain split x
+ * rollout mode) on
  * a rollout with the given arguments (CUDA events, median of `repeats`
  * timed runs after one warm-up run each), keeps the fastest and writes its
  * time per rollout to *best_ms (may be NULL).  The environment state and

@@ -30,6 +30,7 @@ struct sg_ctx {
   int32_t* d_err = nullptr;
   int threads = 128;
   int rollout_mode = SG_ROLLOUT_PERSISTENT;
+  int split = 1;
   std::string last_error;
   // captured rollout (CUDA graph) and the arguments it was captured for
   cudaStream_t capture_stream = nullptr;
@@ -39,12 +40,12 @@ struct sg_ctx {
     float* obs;
     float* reward;
     uint8_t* done;
-    int T, substeps, threads, mode;
+    int T, substeps, threads, mode, split;
     float dt;
     bool operator==(const Key& o) const {
       return actions == o.actions && obs == o.obs && reward == o.reward && done == o.done &&
              T == o.T && substeps == o.substeps && threads == o.threads && mode == o.mode &&
-             dt == o.dt;
+             split == o.split && dt == o.dt;
     }
   } graph_key{};
   // device staging for sg_rollout_host
@@ -148,10 +149,16 @@ sg_status check_step_args(sg_ctx* ctx, const void* actions, float dt, int subste
 
 bool valid_threads(int t) { return t == 32 || t == 64 || t == 128 || t == 256; }
 
+cudaError_t launch_plan(const sg_ctx* c, const sg::StepArgs& a, cudaStream_t s) {
+  return c->split == 2 ? sg::launch_step_pair(a, c->threads, s)
+                       : sg::launch_step(a, c->threads, s);
+}
+
 // Enqueue (capturing first if needed) the rollout graph on the context's stream.
 sg_status run_rollout(sg_ctx* c, const float* actions, int T, float dt, int substeps, float* obs,
                       float* rew, uint8_t* done) {
-  const sg_ctx::Key key{actions, obs, rew, done, T, substeps, c->threads, c->rollout_mode, dt};
+  const sg_ctx::Key key{actions, obs, rew, done, T, substeps, c->threads, c->rollout_mode,
+                        c->split, dt};
   if (!c->graph_exec || !(key == c->graph_key)) {
     if (c->graph_exec) {
       cudaGraphExecDestroy(c->graph_exec);
@@ -170,7 +177,7 @@ sg_status run_rollout(sg_ctx* c, const float* actions, int T, float dt, int subs
       a.obs = obs;
       a.reward = rew;
       a.done = done;
-      le = sg::launch_step(a, c->threads, c->capture_stream);
+      le = launch_plan(c, a, c->capture_stream);
     } else {
       for (int t = 0; t < T && le == cudaSuccess; ++t) {
         sg::StepArgs a = step_args(c, dt, substeps, 1);
@@ -178,7 +185,7 @@ sg_status run_rollout(sg_ctx* c, const float* actions, int T, float dt, int subs
         a.obs = obs + (size_t)t * E * D;
         a.reward = rew + (size_t)t * E;
         a.done = done + (size_t)t * E;
-        le = sg::launch_step(a, c->threads, c->capture_stream);
+        le = launch_plan(c, a, c->capture_stream);
       }
     }
     cudaGraph_t g = nullptr;
@@ -301,6 +308,7 @@ sg_status sg_create(const sg_desc* desc, void* stream, sg_ctx** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_qd, 0, sizeof(float) * sg::kMaxLinks * NS, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream);
   if (e == cudaSuccess) e = sg::prepare_step_kernel();
+  if (e == cudaSuccess) e = sg::prepare_step_pair_kernel();
   if (e == cudaSuccess) e = sg::launch_reset(state_args(c), nullptr, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
@@ -343,7 +351,7 @@ sg_status sg_step(sg_ctx* ctx, const float* actions_dev, float dt, int32_t subst
   a.obs = obs_dev;
   a.reward = reward_dev;
   a.done = done_dev;
-  return cuda_err(ctx, sg::launch_step(a, ctx->threads, ctx->stream), "sg_step");
+  return cuda_err(ctx, launch_plan(ctx, a, ctx->stream), "sg_step");
 }
 
 sg_status sg_rollout(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt,
@@ -393,21 +401,29 @@ sg_status sg_rollout_host(sg_ctx* ctx, const float* actions_host, int32_t T, flo
   return cuda_err(ctx, e, "sg_rollout_host: copy out");
 }
 
-sg_status sg_set_launch(sg_ctx* ctx, int32_t threads_per_block, int32_t rollout_mode) {
+sg_status sg_set_launch(sg_ctx* ctx, int32_t threads_per_block, int32_t rollout_mode,
+                        int32_t chain_split) {
   if (!ctx) return SG_ERR_INVALID_ARG;
   if (!valid_threads(threads_per_block))
     return set_err(ctx, SG_ERR_INVALID_ARG, "threads_per_block must be 32, 64, 128 or 256");
   if (rollout_mode != SG_ROLLOUT_PERSISTENT && rollout_mode != SG_ROLLOUT_STEP_GRAPH)
     return set_err(ctx, SG_ERR_INVALID_ARG, "unknown rollout mode");
+  if (chain_split != 1 && chain_split != 2)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "chain_split must be 1 or 2");
+  if (chain_split == 2 && threads_per_block < 64)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "chain_split 2 needs threads_per_block >= 64");
   ctx->threads = threads_per_block;
   ctx->rollout_mode = rollout_mode;
+  ctx->split = chain_split;
   return SG_OK;
 }
 
-sg_status sg_get_launch(const sg_ctx* ctx, int32_t* threads_per_block, int32_t* rollout_mode) {
+sg_status sg_get_launch(const sg_ctx* ctx, int32_t* threads_per_block, int32_t* rollout_mode,
+                        int32_t* chain_split) {
   if (!ctx) return SG_ERR_INVALID_ARG;
   if (threads_per_block) *threads_per_block = ctx->threads;
   if (rollout_mode) *rollout_mode = ctx->rollout_mode;
+  if (chain_split) *chain_split = ctx->split;
   return SG_OK;
 }
 
@@ -426,11 +442,14 @@ sg_status sg_autotune(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt
   const int threads_list[] = {32, 64, 128, 256};
   const int modes[] = {SG_ROLLOUT_PERSISTENT, SG_ROLLOUT_STEP_GRAPH};
   float best = -1.f;
-  int best_t = ctx->threads, best_m = ctx->rollout_mode;
+  int best_t = ctx->threads, best_m = ctx->rollout_mode, best_s = ctx->split;
   for (int m : modes) {
-    for (int th : threads_list) {
+    for (int plan = 0; plan < 8; ++plan) {
+      const int th = threads_list[plan & 3], sp = 1 + (plan >> 2);
+      if (sp == 2 && th < 64) continue;
       ctx->threads = th;
       ctx->rollout_mode = m;
+      ctx->split = sp;
       std::vector<float> times;
       for (int r = -1; r < repeats && st == SG_OK; ++r) {
         e = snapshot(ctx, false);
@@ -452,6 +471,7 @@ sg_status sg_autotune(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt
         best = med;
         best_t = th;
         best_m = m;
+        best_s = sp;
       }
     }
     if (e != cudaSuccess || st != SG_OK) break;
@@ -460,6 +480,7 @@ sg_status sg_autotune(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt
   cudaEventDestroy(e1);
   ctx->threads = best_t;
   ctx->rollout_mode = best_m;
+  ctx->split = best_s;
   if (st != SG_OK) return st;
   if (e == cudaSuccess) e = snapshot(ctx, false);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

@@ -132,25 +132,29 @@ struct Rec {
   }
 };
 
-// One implicit-drive semi-implicit Euler substep of one chain.
+// ---- pieces of one implicit-drive semi-implicit Euler substep ------------
 template <class Pat>
-__device__ __forceinline__ void chain_substep(const Pat& pat, const Rec& rec, float (&q)[7],
-                                              float (&qd)[7], const float (&qs)[7], float h,
-                                              float grav) {
-  constexpr int N = Pat::N;
-  float cq[N], sq[N];
+__device__ __forceinline__ void joint_sincos(const Pat& pat, const float (&q)[7],
+                                             float (&cq)[Pat::N], float (&sq)[Pat::N]) {
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
+  for (int i = 0; i < Pat::N; ++i) {
     if (pat.active(i) && pat.type(i) == 0) {
-      sincosf(q[i], &sq[i], &cq[i]);
+      __sincosf(q[i], &sq[i], &cq[i]);
     } else {
       cq[i] = 1.f;
       sq[i] = 0.f;
     }
   }
+}
 
-  // ---- RNEA forward sweep (qdd = 0): body-frame velocities/accelerations
-  V3 F[N], Nm[N];
+// RNEA forward sweep (qdd = 0): body-frame velocities/accelerations and the
+// inertial force F and moment Nm (about the COM) of every link.
+template <class Pat>
+__device__ __forceinline__ void rnea_forward(const Pat& pat, const Rec& rec, const float (&q)[7],
+                                             const float (&qd)[7], const float (&cq)[Pat::N],
+                                             const float (&sq)[Pat::N], float grav,
+                                             V3 (&F)[Pat::N], V3 (&Nm)[Pat::N]) {
+  constexpr int N = Pat::N;
   {
     V3 w{0.f, 0.f, 0.f}, wd{0.f, 0.f, 0.f}, acc{0.f, 0.f, grav};
 #pragma unroll
@@ -186,24 +190,37 @@ __device__ __forceinline__ void chain_substep(const Pat& pat, const Rec& rec, fl
     }
   }
 
-  // ---- backward sweep: RNEA forces, composite inertias, mass-matrix columns
-  float M[N][N];
-  float bias[N];
-  {
-    V3 fc{0.f, 0.f, 0.f}, nc{0.f, 0.f, 0.f};   // child wrench in the current frame
-    float mc = 0.f;                             // composite mass
-    V3 hc{0.f, 0.f, 0.f};                       // composite first moment
-    S3 Jc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};        // composite inertia about the origin
+}
+
+// Backward sweep from the tip: with kBias the RNEA wrenches give the bias
+// forces c(q, qd); with kMass the composite bodies give M(q) (upper triangle
+// and diagonal).
+template <class Pat, bool kBias, bool kMass>
+__device__ __forceinline__ void backward_sweep(const Pat& pat, const Rec& rec, const float (&q)[7],
+                                               const float (&cq)[Pat::N],
+                                               const float (&sq)[Pat::N],
+                                               const V3 (&F)[Pat::N], const V3 (&Nm)[Pat::N],
+                                               float (&bias)[Pat::N], float (&M)[Pat::N][Pat::N]) {
+  constexpr int N = Pat::N;
+  V3 fc{0.f, 0.f, 0.f}, nc{0.f, 0.f, 0.f};   // child wrench in the current frame
+  float mc = 0.f;                             // composite mass
+  V3 hc{0.f, 0.f, 0.f};                       // composite first moment
+  S3 Jc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};        // composite inertia about the origin
 #pragma unroll
-    for (int i = N - 1; i >= 0; --i) {
-      if (!pat.active(i)) continue;
-      const int a = pat.axis(i);
-      const float c = rec.lf(i, LF_C), m = rec.lf(i, LF_M);
+  for (int i = N - 1; i >= 0; --i) {
+    if (!pat.active(i)) continue;
+    const int a = pat.axis(i);
+    const float c = rec.lf(i, LF_C);
+    V3 f{0.f, 0.f, 0.f}, n{0.f, 0.f, 0.f};
+    if constexpr (kBias) {
       // RNEA: wrench on link i about its origin
-      const V3 f{F[i].x + fc.x, F[i].y + fc.y, F[i].z + fc.z};
-      const V3 n{Nm[i].x - c * F[i].y + nc.x, Nm[i].y + c * F[i].x + nc.y, Nm[i].z + nc.z};
+      f = V3{F[i].x + fc.x, F[i].y + fc.y, F[i].z + fc.z};
+      n = V3{Nm[i].x - c * F[i].y + nc.x, Nm[i].y + c * F[i].x + nc.y, Nm[i].z + nc.z};
       bias[i] = pat.type(i) == 0 ? compc(n, a) : f.z;
+    }
+    if constexpr (kMass) {
       // composite body of links i..N-1 about origin i
+      const float m = rec.lf(i, LF_M);
       const float mcc = m * c;
       mc += m;
       hc.z += mcc;
@@ -236,23 +253,29 @@ __device__ __forceinline__ void chain_substep(const Pat& pat, const Rec& rec, fl
         cn.y += ell * cf.x;
         M[j][i] = pat.type(j) == 0 ? compc(cn, pat.axis(j)) : cf.z;
       }
-      // carry the RNEA wrench and the composite body to the parent frame
-      if (i > 0) {
-        float ell = rec.lf(i - 1, LF_L);
-        V3 fp = f, np = n, hp = hc;
-        S3 Jp = Jc;
+    }
+    // carry the RNEA wrench and the composite body to the parent frame
+    if (i > 0) {
+      float ell = rec.lf(i - 1, LF_L);
+      if (pat.type(i) == 1) ell += q[i];
+      if constexpr (kBias) {
+        V3 fp = f, np = n;
         if (pat.type(i) == 0) {
           fp = to_parent(a, cq[i], sq[i], f);
           np = to_parent(a, cq[i], sq[i], n);
-          hp = to_parent(a, cq[i], sq[i], hc);
-          Jp = sym_to_parent(a, cq[i], sq[i], Jc);
-        } else {
-          ell += q[i];
         }
         np.x -= ell * fp.y;
         np.y += ell * fp.x;
         fc = fp;
         nc = np;
+      }
+      if constexpr (kMass) {
+        V3 hp = hc;
+        S3 Jp = Jc;
+        if (pat.type(i) == 0) {
+          hp = to_parent(a, cq[i], sq[i], hc);
+          Jp = sym_to_parent(a, cq[i], sq[i], Jc);
+        }
         // shift the composite from origin i to origin i-1 (offset (0,0,ell))
         const float t = 2.f * ell * hp.z + mc * ell * ell;
         Jp.xx += t;
@@ -265,9 +288,16 @@ __device__ __forceinline__ void chain_substep(const Pat& pat, const Rec& rec, fl
       }
     }
   }
+}
 
-  // ---- implicit drive: A = M + diag(h d + h^2 k_s), rhs = h (tau_d - h k_s qd - c)
-  float rhs[N];
+// Implicit drive terms: arm = h d + h^2 k_s (added to the diagonal of M) and
+// rhs = h (tau_d - h k_s qd - c).
+template <class Pat>
+__device__ __forceinline__ void drive_terms(const Pat& pat, const Rec& rec, const float (&q)[7],
+                                            const float (&qd)[7], const float (&qs)[7], float h,
+                                            const float (&bias)[Pat::N], float (&rhs)[Pat::N],
+                                            float (&arm)[Pat::N]) {
+  constexpr int N = Pat::N;
   const float hh = h * h;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -284,11 +314,20 @@ __device__ __forceinline__ void chain_substep(const Pat& pat, const Rec& rec, fl
     }
     const float tau = kp * (qs[i] - q[i]) - d * qd[i] + tl;
     rhs[i] = h * (tau - h * ks * qd[i] - bias[i]);
-    M[i][i] += h * d + hh * ks;
+    arm[i] = h * d + hh * ks;
   }
 
-  // ---- Cholesky A = L L^T (L stored in the lower triangle M[i][j], i >= j)
-  float inv[N];
+}
+
+// (M + diag(arm)) = L L^T in registers: L overwrites the lower triangle of M
+// (M[i][j], i > j; the upper triangle holds A on entry) and inv[i] = 1 / L_ii.
+template <class Pat>
+__device__ __forceinline__ void chol_factor(const Pat& pat, float (&M)[Pat::N][Pat::N],
+                                            const float (&arm)[Pat::N], float (&inv)[Pat::N]) {
+  constexpr int N = Pat::N;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (pat.active(i)) M[i][i] += arm[i];
 #pragma unroll
   for (int j = 0; j < N; ++j) {
     if (!pat.active(j)) continue;
@@ -305,7 +344,13 @@ __device__ __forceinline__ void chain_substep(const Pat& pat, const Rec& rec, fl
       M[i][j] = t * inv[j];
     }
   }
-  // forward / backward substitution
+}
+
+// rhs <- (L L^T)^{-1} rhs (forward, then backward substitution).
+template <class Pat>
+__device__ __forceinline__ void chol_apply(const Pat& pat, const float (&M)[Pat::N][Pat::N],
+                                           const float (&inv)[Pat::N], float (&rhs)[Pat::N]) {
+  constexpr int N = Pat::N;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     if (!pat.active(i)) continue;
@@ -324,13 +369,42 @@ __device__ __forceinline__ void chain_substep(const Pat& pat, const Rec& rec, fl
     }
     rhs[i] = t * inv[i];
   }
-  // ---- semi-implicit Euler update
+}
+
+// rhs <- (M + diag(arm))^{-1} rhs by an in-register Cholesky factorisation.
+template <class Pat>
+__device__ __forceinline__ void chol_solve(const Pat& pat, float (&M)[Pat::N][Pat::N],
+                                           const float (&arm)[Pat::N], float (&rhs)[Pat::N]) {
+  float inv[Pat::N];
+  chol_factor(pat, M, arm, inv);
+  chol_apply(pat, M, inv, rhs);
+}
+
+template <class Pat>
+__device__ __forceinline__ void integrate(const Pat& pat, float (&q)[7], float (&qd)[7],
+                                          const float (&dqd)[Pat::N], float h) {
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
+  for (int i = 0; i < Pat::N; ++i) {
     if (!pat.active(i)) continue;
-    qd[i] += rhs[i];
+    qd[i] += dqd[i];
     q[i] += h * qd[i];
   }
+}
+
+// One implicit-drive semi-implicit Euler substep of one chain (one thread).
+template <class Pat>
+__device__ __forceinline__ void chain_substep(const Pat& pat, const Rec& rec, float (&q)[7],
+                                              float (&qd)[7], const float (&qs)[7], float h,
+                                              float grav) {
+  constexpr int N = Pat::N;
+  float cq[N], sq[N], bias[N], M[N][N], rhs[N], arm[N];
+  V3 F[N], Nm[N];
+  joint_sincos(pat, q, cq, sq);
+  rnea_forward(pat, rec, q, qd, cq, sq, grav, F, Nm);
+  backward_sweep<Pat, true, true>(pat, rec, q, cq, sq, F, Nm, bias, M);
+  drive_terms(pat, rec, q, qd, qs, h, bias, rhs, arm);
+  chol_solve(pat, M, arm, rhs);
+  integrate(pat, q, qd, rhs, h);
 }
 
 // col_u' = c col_u + s col_v, col_v' = -s col_u + c col_v
@@ -356,7 +430,7 @@ __device__ __forceinline__ void chain_tip(const Pat& pat, const Rec& rec, const 
       p.z += q[i] * c2.z;
     } else {
       float s, c;
-      sincosf(q[i], &s, &c);
+      __sincosf(q[i], &s, &c);
       const int a = pat.axis(i);
       // R <- R Rot_a with the in-plane pair (u, v) = ((a+1)%3, (a+2)%3)
       if (a == 2) rot_cols(c0, c1, c, s);

@@ -1,0 +1,90 @@
+// Device helpers shared by the step kernels: mbarrier / bulk-copy PTX
+// wrappers with bounded waits, action loads and the observation write-out.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sg_chain.cuh"
+#include "sg_internal.h"
+
+namespace sg {
+
+constexpr float kGravity = 9.81f;
+constexpr int kWaitLimit = 1 << 20;   // bounded mbarrier polling
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (int it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <class Pat>
+__device__ __forceinline__ void load_targets(const Pat& pat, const StepArgs& a, int t, int env,
+                                             int jo, float (&dst)[7]) {
+  const float* arow = a.actions + ((size_t)t * a.num_envs + env) * a.max_joints + jo;
+#pragma unroll
+  for (int i = 0; i < Pat::N; ++i)
+    if (pat.active(i)) dst[i] = __ldg(arow + i);
+}
+
+// Copy the warp's staged observation rows to HBM: one warp-wide store per row
+// (8-byte vectors when rows are 8-byte aligned and D <= 64, else 4-byte).
+__device__ __forceinline__ void write_rows(float* obs_t, const float* stage, int row_env, int nrows,
+                                           int D, int DP, int lane) {
+  if ((D & 1) == 0 && D <= 2 * kWarp) {
+    const int half = D >> 1;
+#pragma unroll 4
+    for (int rr = 0; rr < nrows; ++rr) {
+      const int er = __shfl_sync(0xffffffffu, row_env, rr);
+      if (er >= 0 && lane < half) {
+        const float2 v = reinterpret_cast<const float2*>(stage + rr * DP)[lane];
+        reinterpret_cast<float2*>(obs_t + (size_t)er * D)[lane] = v;
+      }
+    }
+  } else {
+#pragma unroll 4
+    for (int rr = 0; rr < nrows; ++rr) {
+      const int er = __shfl_sync(0xffffffffu, row_env, rr);
+      if (er >= 0) {
+        const float* src = stage + rr * DP;
+        float* dst = obs_t + (size_t)er * D;
+        for (int k = lane; k < D; k += kWarp) dst[k] = src[k];
+      }
+    }
+  }
+}
+
+}  // namespace sg

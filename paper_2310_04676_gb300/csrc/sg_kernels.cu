@@ -9,52 +9,11 @@
 #include <cuda_runtime.h>
 
 #include "sg_chain.cuh"
+#include "sg_device.cuh"
 #include "sg_internal.h"
 #include "sg_kernels.h"
 
 namespace sg {
-
-constexpr float kGravity = 9.81f;
-constexpr int kWaitLimit = 1 << 20;   // bounded mbarrier polling
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  for (int it = 0; it < kWaitLimit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
 
 // Stage the warp's parameter record into shared memory; false if the copy
 // did not complete within the polling bound (error flag set).
@@ -75,9 +34,12 @@ __device__ __forceinline__ bool stage_record(const StepArgs& a, int gw, int cls,
   return false;
 }
 
+// Observation rows are first assembled in a per-warp shared-memory stage
+// (one row per env of the warp, odd row pitch: no bank conflicts), then the
+// warp writes each row to HBM with consecutive lanes on consecutive floats.
 template <class Pat>
 __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, const Rec& rec,
-                                          int slot, int lane, bool paired) {
+                                          float* stage, int slot, int lane, bool paired) {
   constexpr int N = Pat::N;
   const int env = a.slot_env[slot];
   const bool valid = env >= 0;
@@ -88,13 +50,19 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
   const int ntot = (info >> SI_NTOT_SHIFT) & 31;
   const int obs_len = (info >> SI_OBSLEN_SHIFT) & 127;
   const int NS = a.num_slots;
+  const int D = a.obs_dim, DP = stage_pitch(a.obs_dim);
+  const int nrows = paired ? 16 : 32;
+  float* srow = stage + (paired ? (lane >> 1) : lane) * DP;
+  // env owning stage row `lane` (rows >= nrows unused)
+  const int row_env = __shfl_sync(0xffffffffu, env, paired ? ((2 * lane) & 31) : lane);
 
-  float q[7], qd[7], qs[7];
+  float q[7], qd[7], qs[7], qn[7];
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
     q[i] = 0.f;
     qd[i] = 0.f;
     qs[i] = 0.f;
+    qn[i] = 0.f;
   }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -105,15 +73,12 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
   int sc = (valid && c == 0) ? a.step_count[env] : 0;
   const float goal_x = rec.cf(CF_GX), goal_y = rec.cf(CF_GY), goal_z = rec.cf(CF_GZ);
   const size_t E = (size_t)a.num_envs;
-  const int J = a.max_joints, D = a.obs_dim;
+  if (valid) load_targets(pat, a, 0, env, jo, qn);
 
   for (int t = 0; t < a.T; ++t) {
-    if (valid) {
-      const float* arow = a.actions + ((size_t)t * E + env) * J + jo;
 #pragma unroll
-      for (int i = 0; i < N; ++i)
-        if (pat.active(i)) qs[i] = __ldg(arow + i);
-    }
+    for (int i = 0; i < 7; ++i) qs[i] = qn[i];
+    if (valid && t + 1 < a.T) load_targets(pat, a, t + 1, env, jo, qn);   // prefetch
     for (int k = 0; k < a.substeps; ++k) chain_substep(pat, rec, q, qd, qs, a.h, kGravity);
 
     // ---- epilogue: tip pose, reward, observation, done
@@ -129,7 +94,6 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
     ++sc;
 
     float reward;
-    float* row = a.obs + ((size_t)t * E + (valid ? env : 0)) * D;
     if (a.task == SG_TASK_PATH) {
       const int W = a.path_len;
       const float* P = a.path + (size_t)(valid ? env : 0) * W * 3;
@@ -137,55 +101,56 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
       const float* p0 = P + (size_t)min(t0, W - 1) * 3;
       const float dx = tip.x - p0[0], dy = tip.y - p0[1], dz = tip.z - p0[2];
       reward = -a.alpha * sqrtf(dx * dx + dy * dy + dz * dz);
-      if (valid) {
-        const int n = ntot;
+      const int n = ntot;
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-          if (!pat.active(i)) continue;
-          row[i] = q[i];
-          row[n + i] = qd[i];
-        }
-        row[2 * n + 0] = tip.x;
-        row[2 * n + 1] = tip.y;
-        row[2 * n + 2] = tip.z;
-        float quat[4];
-        rot_to_quat(r0, r1, r2, quat);
+      for (int i = 0; i < N; ++i) {
+        if (!pat.active(i)) continue;
+        srow[i] = q[i];
+        srow[n + i] = qd[i];
+      }
+      srow[2 * n + 0] = tip.x;
+      srow[2 * n + 1] = tip.y;
+      srow[2 * n + 2] = tip.z;
+      float quat[4];
+      rot_to_quat(r0, r1, r2, quat);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) row[2 * n + 3 + k] = quat[k];
+      for (int k = 0; k < 4; ++k) srow[2 * n + 3 + k] = quat[k];
 #pragma unroll
-        for (int k = 1; k <= 3; ++k) {
-          const float* pk = P + (size_t)min(t0 + k, W - 1) * 3;
-          row[2 * n + 4 + 3 * k] = pk[0];
-          row[2 * n + 5 + 3 * k] = pk[1];
-          row[2 * n + 6 + 3 * k] = pk[2];
-        }
+      for (int k = 1; k <= 3; ++k) {
+        const float* pk = P + (size_t)min(t0 + k, W - 1) * 3;
+        srow[2 * n + 4 + 3 * k] = pk[0];
+        srow[2 * n + 5 + 3 * k] = pk[1];
+        srow[2 * n + 6 + 3 * k] = pk[2];
       }
     } else {
       const float dx = tip.x - goal_x, dy = tip.y - goal_y, dz = tip.z - goal_z;
       reward = -sqrtf(dx * dx + dy * dy + dz * dz);
       if (paired) reward += __shfl_xor_sync(0xffffffffu, reward, 1);
-      if (valid) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-          if (!pat.active(i)) continue;
-          row[jo + i] = q[i];
-          row[ntot + jo + i] = qd[i];
-          row[2 * ntot + 3 * nc + jo + i] = qs[i];
-        }
-        row[2 * ntot + 3 * c + 0] = tip.x;
-        row[2 * ntot + 3 * c + 1] = tip.y;
-        row[2 * ntot + 3 * c + 2] = tip.z;
-        row[3 * ntot + 3 * nc + 3 * c + 0] = goal_x;
-        row[3 * ntot + 3 * nc + 3 * c + 1] = goal_y;
-        row[3 * ntot + 3 * nc + 3 * c + 2] = goal_z;
+      for (int i = 0; i < N; ++i) {
+        if (!pat.active(i)) continue;
+        srow[jo + i] = q[i];
+        srow[ntot + jo + i] = qd[i];
+        srow[2 * ntot + 3 * nc + jo + i] = qs[i];
+      }
+      srow[2 * ntot + 3 * c + 0] = tip.x;
+      srow[2 * ntot + 3 * c + 1] = tip.y;
+      srow[2 * ntot + 3 * c + 2] = tip.z;
+      srow[3 * ntot + 3 * nc + 3 * c + 0] = goal_x;
+      srow[3 * ntot + 3 * nc + 3 * c + 1] = goal_y;
+      srow[3 * ntot + 3 * nc + 3 * c + 2] = goal_z;
+    }
+    if (c == 0) {
+      for (int k = obs_len; k < D; ++k) srow[k] = 0.f;
+      if (valid) {
+        a.reward[(size_t)t * E + env] = reward;
+        a.done[(size_t)t * E + env] =
+            (uint8_t)((sc >= a.episode_len ? SG_DONE_TIMEOUT : 0) | (bad ? SG_DONE_NONFINITE : 0));
       }
     }
-    if (valid && c == 0) {
-      for (int k = obs_len; k < D; ++k) row[k] = 0.f;
-      a.reward[(size_t)t * E + env] = reward;
-      a.done[(size_t)t * E + env] =
-          (uint8_t)((sc >= a.episode_len ? SG_DONE_TIMEOUT : 0) | (bad ? SG_DONE_NONFINITE : 0));
-    }
+    __syncwarp();
+    write_rows(a.obs + (size_t)t * E * D, stage, row_env, nrows, D, DP, lane);
+    __syncwarp();
   }
 
   if (valid) {
@@ -207,22 +172,25 @@ __global__ void __launch_bounds__(kMaxThreads) step_kernel(StepArgs a) {
   const int gw = blockIdx.x * wpb + wib;
   if (gw >= a.num_warps) return;
   const int wc = a.warp_class[gw];
+  const int stage_floats = kWarp * stage_pitch(a.obs_dim);
   float* rec = smem + (size_t)wib * kRecordFloats;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)wpb * kRecordFloats) + wib;
+  float* stage = smem + (size_t)wpb * kRecordFloats + (size_t)wib * stage_floats;
+  uint64_t* bar =
+      reinterpret_cast<uint64_t*>(smem + (size_t)wpb * (kRecordFloats + stage_floats)) + wib;
   if (!stage_record(a, gw, wc, rec, bar, lane)) return;
   const Rec r{rec + lane};
   const int slot = gw * kWarp + lane;
   const bool paired = (wc & kPairedBit) != 0;
   switch (wc & 3) {
-    case CLS_7R: run_chain(a, Pat7R{}, r, slot, lane, paired); break;
-    case CLS_7P: run_chain(a, Pat7P{}, r, slot, lane, paired); break;
-    case CLS_4R: run_chain(a, Pat4R{}, r, slot, lane, paired); break;
+    case CLS_7R: run_chain(a, Pat7R{}, r, stage, slot, lane, paired); break;
+    case CLS_7P: run_chain(a, Pat7P{}, r, stage, slot, lane, paired); break;
+    case CLS_4R: run_chain(a, Pat4R{}, r, stage, slot, lane, paired); break;
     default: {
       int code;
       const float cf = r.cf(CF_CODE);
       memcpy(&code, &cf, 4);
       const int n = (a.slot_info[slot] >> SI_NCHAIN_SHIFT) & 7;
-      run_chain(a, PatGen{code, n}, r, slot, lane, paired);
+      run_chain(a, PatGen{code, n}, r, stage, slot, lane, paired);
     }
   }
 }
@@ -286,20 +254,21 @@ __global__ void set_state_kernel(StateArgs s, const float* q_in, const float* qd
 }
 
 // ---- launchers ------------------------------------------------------------
-size_t step_smem_bytes(int threads) {
+size_t step_smem_bytes(int threads, int obs_dim) {
   const int wpb = threads / kWarp;
-  return (size_t)wpb * kRecordFloats * sizeof(float) + (size_t)wpb * sizeof(uint64_t);
+  const size_t stage = (size_t)kWarp * stage_pitch(obs_dim);
+  return (size_t)wpb * (kRecordFloats + stage) * sizeof(float) + (size_t)wpb * sizeof(uint64_t);
 }
 
 cudaError_t prepare_step_kernel() {
   return cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)step_smem_bytes(kMaxThreads));
+                              (int)step_smem_bytes(kMaxThreads, kMaxObsDim));
 }
 
 cudaError_t launch_step(const StepArgs& a, int threads, cudaStream_t stream) {
   const int wpb = threads / kWarp;
   const int blocks = (a.num_warps + wpb - 1) / wpb;
-  step_kernel<<<blocks, threads, step_smem_bytes(threads), stream>>>(a);
+  step_kernel<<<blocks, threads, step_smem_bytes(threads, a.obs_dim), stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -19,9 +19,21 @@ struct StateArgs {
 
 constexpr int kMaxThreads = 256;   // largest step-kernel block
 
-size_t step_smem_bytes(int threads);
+constexpr int kMaxObsDim = 63;     // widest observation row the step kernel stages
+
+// Row pitch (floats) of the per-warp observation stage: rows keep 8-byte
+// alignment when D is even; otherwise an odd pitch avoids bank conflicts.
+SG_HD inline int stage_pitch(int obs_dim) {
+  return (obs_dim & 1) ? obs_dim : (obs_dim % 4 == 0 ? obs_dim + 2 : obs_dim);
+}
+
+size_t step_smem_bytes(int threads, int obs_dim);
 cudaError_t prepare_step_kernel();   // one-time kernel attributes (not capturable)
 cudaError_t launch_step(const StepArgs& a, int threads, cudaStream_t stream);
+// warp-pair variant (sg_pair.cu): threads must be a multiple of 64
+size_t step_pair_smem_bytes(int threads, int obs_dim);
+cudaError_t prepare_step_pair_kernel();
+cudaError_t launch_step_pair(const StepArgs& a, int threads, cudaStream_t stream);
 cudaError_t launch_reset(const StateArgs& s, const uint8_t* mask, cudaStream_t stream);
 cudaError_t launch_get_state(const StateArgs& s, float* q, float* qd, int32_t* sc,
                              cudaStream_t stream);

@@ -1,0 +1,302 @@
+// Warp-pair step kernel: two warps share one block of 32 chains.
+//
+// When a batch has fewer chains than the GPU has warp schedulers (16384
+// mixed envs are ~590 warps of chains for 608 schedulers), one thread per
+// chain leaves each scheduler with a single dependent instruction stream.
+// Here the substep of every chain is split across two warps that run
+// concurrently on the same SM:
+//   role 0 (dynamics): RNEA bias forces and the implicit drive right-hand side;
+//   role 1 (inertia):  composite-rigid-body mass matrix plus the drive
+//                      armature, then its Cholesky factorisation.
+// The two halves run concurrently; the roles then swap the right-hand side
+// and the factor through a double-buffered shared-memory exchange (one
+// mbarrier phase per substep, bounded waits: no block barrier after
+// start-up, and a wait that runs out sets DEVERR_TIMEOUT and the warp leaves,
+// so a partner is never left waiting forever).  Both roles then execute the
+// same triangular solve on the same operands and apply the same update, so
+// their copies of the chain state stay bit-identical.  The
+// observation rows are staged by both roles and written out half by each.
+// The arithmetic is that of the one-thread-per-chain kernel; the two kernels
+// agree to rounding (separately compiled code may contract multiply-adds
+// differently).
+#include <cuda_runtime.h>
+
+#include "sg_chain.cuh"
+#include "sg_device.cuh"
+#include "sg_internal.h"
+#include "sg_kernels.h"
+
+namespace sg {
+
+namespace {
+
+// exchange per pair and substep: the Cholesky factor (lower triangle with
+// 1/L_ii on the diagonal, packed row by row) and the right-hand side; two
+// buffers alternate between substeps
+constexpr int kTri = kMaxLinks * (kMaxLinks + 1) / 2;
+constexpr int kXHalf = (kTri + kMaxLinks) * kWarp;
+constexpr int kXFloats = 2 * kXHalf;
+constexpr int kPairBars = 3;                      // tma, exchange, stage
+
+__device__ __forceinline__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait with a warp-uniform verdict; false (and the error flag set)
+// if the partner did not arrive in time.
+__device__ __forceinline__ bool pair_wait(uint64_t* bar, unsigned& parity, int* err, int lane) {
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity));
+  parity ^= 1u;
+  if (!ok && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+  return ok;
+}
+
+template <class Pat>
+__device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, const Rec& rec,
+                                         float* stage, float* xbuf, uint64_t* bars, int group,
+                                         int lane, int role, bool paired) {
+  constexpr int N = Pat::N;
+  const int slot = group * kWarp + lane;
+  const int env = a.slot_env[slot];
+  const bool valid = env >= 0;
+  const int info = a.slot_info[slot];
+  const int c = (info >> SI_C_SHIFT) & 1;
+  const int nc = (info >> SI_NC_SHIFT) & 3;
+  const int jo = (info >> SI_JO_SHIFT) & 15;
+  const int ntot = (info >> SI_NTOT_SHIFT) & 31;
+  const int obs_len = (info >> SI_OBSLEN_SHIFT) & 127;
+  const int NS = a.num_slots;
+  const int D = a.obs_dim, DP = stage_pitch(a.obs_dim);
+  const int nrows = paired ? 16 : 32;
+  float* srow = stage + (paired ? (lane >> 1) : lane) * DP;
+  const int row_env = __shfl_sync(0xffffffffu, env, paired ? ((2 * lane) & 31) : lane);
+  uint64_t* bar_x = bars + 1;
+  uint64_t* bar_stage = bars + 2;
+  unsigned ph_x = 0, ph_stage = 0;
+  unsigned xphase = 0;
+
+  float q[7], qd[7], qs[7], qn[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    q[i] = 0.f;
+    qd[i] = 0.f;
+    qs[i] = 0.f;
+    qn[i] = 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (!pat.active(i)) continue;
+    q[i] = a.q[(size_t)i * NS + slot];
+    qd[i] = a.qd[(size_t)i * NS + slot];
+  }
+  int sc = (valid && c == 0) ? a.step_count[env] : 0;
+  const size_t E = (size_t)a.num_envs;
+  if (valid && role == 0) load_targets(pat, a, 0, env, jo, qn);
+
+  for (int t = 0; t < a.T; ++t) {
+    if (role == 0) {
+#pragma unroll
+      for (int i = 0; i < 7; ++i) qs[i] = qn[i];
+      if (valid && t + 1 < a.T) load_targets(pat, a, t + 1, env, jo, qn);
+    }
+    for (int k = 0; k < a.substeps; ++k, ++xphase) {
+      float cq[N], sq[N];
+      float* xb = xbuf + (xphase & 1) * kXHalf;   // double-buffered exchange
+      joint_sincos(pat, q, cq, sq);
+      if (role == 0) {
+        float bias[N], rhs[N], arm[N], Mdummy[N][N];
+        V3 F[N], Nm[N];
+        rnea_forward(pat, rec, q, qd, cq, sq, kGravity, F, Nm);
+        backward_sweep<Pat, true, false>(pat, rec, q, cq, sq, F, Nm, bias, Mdummy);
+        drive_terms(pat, rec, q, qd, qs, a.h, bias, rhs, arm);
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+          if (pat.active(i)) xb[(kTri + i) * kWarp + lane] = rhs[i];
+      } else {
+        float M[N][N], inv[N], bias_dummy[N], rhs_dummy[N], arm[N];
+        V3 Fd[N], Nd[N];
+        backward_sweep<Pat, false, true>(pat, rec, q, cq, sq, Fd, Nd, bias_dummy, M);
+        drive_terms(pat, rec, q, qd, qs, a.h, bias_dummy, rhs_dummy, arm);
+        chol_factor(pat, M, arm, inv);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          if (!pat.active(i)) continue;
+          xb[tri(i, i) * kWarp + lane] = inv[i];
+#pragma unroll
+          for (int j = 0; j < i; ++j) xb[tri(i, j) * kWarp + lane] = M[i][j];
+        }
+      }
+      mbar_arrive(bar_x);
+      if (!pair_wait(bar_x, ph_x, a.err, lane)) return;
+      // both roles run the same substitution on the same operands, so their
+      // copies of the state stay identical
+      float L[N][N], inv[N], dqd[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        if (!pat.active(i)) continue;
+        dqd[i] = xb[(kTri + i) * kWarp + lane];
+        inv[i] = xb[tri(i, i) * kWarp + lane];
+#pragma unroll
+        for (int j = 0; j < i; ++j) L[i][j] = xb[tri(i, j) * kWarp + lane];
+      }
+      chol_apply(pat, L, inv, dqd);
+      integrate(pat, q, qd, dqd, a.h);
+    }
+
+    // ---- epilogue: role 0 stages q, qd, q* and writes done; role 1 the tip
+    // pose, goal / waypoints and the reward.
+    ++sc;
+    if (role == 0) {
+      bool bad = false;
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (pat.active(i)) bad = bad || !isfinite(q[i]) || !isfinite(qd[i]);
+      bad = bad && valid;
+      if (paired) bad = bad || __shfl_xor_sync(0xffffffffu, bad ? 1 : 0, 1) != 0;
+      if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, DEVERR_NONFINITE);
+      const int n = ntot;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        if (!pat.active(i)) continue;
+        srow[jo + i] = q[i];
+        srow[n + jo + i] = qd[i];
+        if (a.task != SG_TASK_PATH) srow[2 * n + 3 * nc + jo + i] = qs[i];
+      }
+      if (c == 0) {
+        for (int k = obs_len; k < D; ++k) srow[k] = 0.f;
+        if (valid)
+          a.done[(size_t)t * E + env] = (uint8_t)((sc >= a.episode_len ? SG_DONE_TIMEOUT : 0) |
+                                                  (bad ? SG_DONE_NONFINITE : 0));
+      }
+    } else {
+      V3 tip, r0, r1, r2;
+      chain_tip(pat, rec, q, tip, r0, r1, r2);
+      float reward;
+      if (a.task == SG_TASK_PATH) {
+        const int W = a.path_len, n = ntot;
+        const float* P = a.path + (size_t)(valid ? env : 0) * W * 3;
+        const int t0 = max(sc, 0);
+        const float* p0 = P + (size_t)min(t0, W - 1) * 3;
+        const float dx = tip.x - p0[0], dy = tip.y - p0[1], dz = tip.z - p0[2];
+        reward = -a.alpha * sqrtf(dx * dx + dy * dy + dz * dz);
+        srow[2 * n + 0] = tip.x;
+        srow[2 * n + 1] = tip.y;
+        srow[2 * n + 2] = tip.z;
+        float quat[4];
+        rot_to_quat(r0, r1, r2, quat);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) srow[2 * n + 3 + k] = quat[k];
+#pragma unroll
+        for (int k = 1; k <= 3; ++k) {
+          const float* pk = P + (size_t)min(t0 + k, W - 1) * 3;
+          srow[2 * n + 4 + 3 * k] = pk[0];
+          srow[2 * n + 5 + 3 * k] = pk[1];
+          srow[2 * n + 6 + 3 * k] = pk[2];
+        }
+      } else {
+        const float gx = rec.cf(CF_GX), gy = rec.cf(CF_GY), gz = rec.cf(CF_GZ);
+        const float dx = tip.x - gx, dy = tip.y - gy, dz = tip.z - gz;
+        reward = -sqrtf(dx * dx + dy * dy + dz * dz);
+        if (paired) reward += __shfl_xor_sync(0xffffffffu, reward, 1);
+        srow[2 * ntot + 3 * c + 0] = tip.x;
+        srow[2 * ntot + 3 * c + 1] = tip.y;
+        srow[2 * ntot + 3 * c + 2] = tip.z;
+        srow[3 * ntot + 3 * nc + 3 * c + 0] = gx;
+        srow[3 * ntot + 3 * nc + 3 * c + 1] = gy;
+        srow[3 * ntot + 3 * nc + 3 * c + 2] = gz;
+      }
+      if (valid && c == 0) a.reward[(size_t)t * E + env] = reward;
+    }
+    mbar_arrive(bar_stage);
+    if (!pair_wait(bar_stage, ph_stage, a.err, lane)) return;
+    // each role writes half of the staged rows
+    const int half = nrows >> 1;
+    const int r0 = role * half;
+    const int ev = __shfl_sync(0xffffffffu, row_env, (lane + r0) & 31);
+    write_rows(a.obs + (size_t)t * E * D, stage + r0 * DP, ev, half, D, DP, lane);
+  }
+
+  if (valid && role == 0) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      if (!pat.active(i)) continue;
+      a.q[(size_t)i * NS + slot] = q[i];
+      a.qd[(size_t)i * NS + slot] = qd[i];
+    }
+    if (c == 0) a.step_count[env] = sc;
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kMaxThreads) step_kernel_pair(StepArgs a) {
+  extern __shared__ __align__(128) float smem[];
+  const int w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int pairs = blockDim.x >> 6;
+  const int pair = w >> 1, role = w & 1;
+  const int stage_floats = kWarp * stage_pitch(a.obs_dim);
+  float* rec = smem + (size_t)pair * kRecordFloats;
+  float* stage = smem + (size_t)pairs * kRecordFloats + (size_t)pair * stage_floats;
+  float* xbuf = smem + (size_t)pairs * (kRecordFloats + stage_floats) + (size_t)pair * kXFloats;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)pairs * (kRecordFloats + stage_floats + kXFloats)) +
+                   (size_t)pair * kPairBars;
+  // start-up: warp 0 initialises every pair's barriers before any warp leaves
+  if (w == 0 && lane < pairs) {
+    uint64_t* b = reinterpret_cast<uint64_t*>(smem + (size_t)pairs * (kRecordFloats + stage_floats + kXFloats)) +
+                  (size_t)lane * kPairBars;
+    mbar_init(b + 0, 1);
+    mbar_init(b + 1, 2 * kWarp);
+    mbar_init(b + 2, 2 * kWarp);
+  }
+  __syncthreads();
+  const int group = blockIdx.x * pairs + pair;
+  if (group >= a.num_warps) return;
+  const int wc = a.warp_class[group];
+  if (role == 0 && lane == 0) {
+    const unsigned bytes = (unsigned)record_bytes_dev(wc);
+    mbar_expect_tx(bars, bytes);
+    bulk_g2s(rec, a.params + (size_t)group * kRecordFloats, bytes, bars);
+  }
+  unsigned ph_tma = 0;
+  if (!pair_wait(bars, ph_tma, a.err, lane)) {
+    mbar_wait_bounded(bars, 0);   // second bounded chance for an in-flight copy
+    return;
+  }
+  const Rec r{rec + lane};
+  const bool paired = (wc & kPairedBit) != 0;
+  switch (wc & 3) {
+    case CLS_7R: run_pair(a, Pat7R{}, r, stage, xbuf, bars, group, lane, role, paired); break;
+    case CLS_7P: run_pair(a, Pat7P{}, r, stage, xbuf, bars, group, lane, role, paired); break;
+    case CLS_4R: run_pair(a, Pat4R{}, r, stage, xbuf, bars, group, lane, role, paired); break;
+    default: {
+      int code;
+      const float cf = r.cf(CF_CODE);
+      memcpy(&code, &cf, 4);
+      const int n = (a.slot_info[group * kWarp + lane] >> SI_NCHAIN_SHIFT) & 7;
+      run_pair(a, PatGen{code, n}, r, stage, xbuf, bars, group, lane, role, paired);
+    }
+  }
+}
+
+size_t step_pair_smem_bytes(int threads, int obs_dim) {
+  const int pairs = threads / (2 * kWarp);
+  const size_t per = kRecordFloats + (size_t)kWarp * stage_pitch(obs_dim) + kXFloats;
+  return (size_t)pairs * per * sizeof(float) + (size_t)pairs * kPairBars * sizeof(uint64_t);
+}
+
+cudaError_t prepare_step_pair_kernel() {
+  return cudaFuncSetAttribute(step_kernel_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)step_pair_smem_bytes(kMaxThreads, kMaxObsDim));
+}
+
+cudaError_t launch_step_pair(const StepArgs& a, int threads, cudaStream_t stream) {
+  const int pairs = threads / (2 * kWarp);
+  const int blocks = (a.num_warps + pairs - 1) / pairs;
+  step_kernel_pair<<<blocks, threads, step_pair_smem_bytes(threads, a.obs_dim), stream>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace sg

@@ -77,8 +77,8 @@ def load_library(path=LIB_PATH):
         "sg_sync_status": (i32, [vp]),
         "sg_rollout": (i32, [vp, vp, i32, f32, i32, vp, vp, u8p]),
         "sg_rollout_host": (i32, [vp, vp, i32, f32, i32, vp, vp, u8p]),
-        "sg_set_launch": (i32, [vp, i32, i32]),
-        "sg_get_launch": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "sg_set_launch": (i32, [vp, i32, i32, i32]),
+        "sg_get_launch": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "sg_autotune": (i32, [vp, vp, i32, f32, i32, vp, vp, u8p, i32, ctypes.POINTER(f32)]),
         "sg_last_error": (ctypes.c_char_p, [vp]),
     }
@@ -255,17 +255,21 @@ class Env:
         self._check(self.lib.sg_rollout_host(self.ctx, _ptr(actions), T, float(dt), int(substeps),
                                              _ptr(obs), _ptr(rew), _ptr(done)))
 
-    def set_launch(self, threads_per_block, mode):
-        self._check(self.lib.sg_set_launch(self.ctx, int(threads_per_block), int(mode)))
+    def set_launch(self, threads_per_block, mode, chain_split=1):
+        self._check(self.lib.sg_set_launch(self.ctx, int(threads_per_block), int(mode),
+                                           int(chain_split)))
 
     def get_launch(self):
-        t, m = ctypes.c_int32(), ctypes.c_int32()
-        self._check(self.lib.sg_get_launch(self.ctx, ctypes.byref(t), ctypes.byref(m)))
-        return t.value, m.value
+        """(threads_per_block, rollout mode, chain split)"""
+        t, m, sp = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.sg_get_launch(self.ctx, ctypes.byref(t), ctypes.byref(m),
+                                           ctypes.byref(sp)))
+        return t.value, m.value, sp.value
 
     def autotune(self, actions, dt, substeps, out=None, repeats=3):
         """Pick the fastest launch plan for this rollout shape; returns
-        (threads_per_block, mode, ms per rollout).  State is preserved."""
+        (threads_per_block, mode, chain split, ms per rollout).  State is
+        preserved."""
         self._sync_stream()
         torch = self._torch
         T = int(actions.shape[0])
@@ -275,8 +279,8 @@ class Env:
         self._check(self.lib.sg_autotune(self.ctx, _ptr(actions), T, float(dt), int(substeps),
                                          _ptr(obs), _ptr(rew), _ptr(done), int(repeats),
                                          ctypes.byref(ms)))
-        t, m = self.get_launch()
-        return t, m, ms.value
+        t, m, sp = self.get_launch()
+        return t, m, sp, ms.value
 
     def get_state(self):
         self._sync_stream()

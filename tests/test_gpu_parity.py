@@ -50,8 +50,9 @@ def rel_rows(a, b, floor=1e-3):
     return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), floor)
 
 
-def one_step_accel(desc, substeps, seed=0):
+def one_step_accel(desc, substeps, seed=0, split=1):
     env = sg.Env(desc)
+    env.set_launch(64 * split, sg.ROLLOUT_PERSISTENT, split)
     ref = OracleEnv(desc)
     q, qd = random_state(desc, seed)
     env.set_state(cuda(q), cuda(qd))
@@ -71,10 +72,11 @@ KINDS = [["7R"], ["7P"], ["4R"], ["14B"], ["7R", "4R", "7P", "14B"]]
 
 @pytest.mark.parametrize("kinds", KINDS, ids=lambda k: "+".join(k))
 @pytest.mark.parametrize("substeps", [1, 2])
-def test_step_acceleration_matches_oracle(kinds, substeps):
+@pytest.mark.parametrize("split", [1, 2])
+def test_step_acceleration_matches_oracle(kinds, substeps, split):
     E = 197                                   # several warps and a ragged tail
     desc = W.make_desc((kinds * E)[:E])
-    rel, env, *_ = one_step_accel(desc, substeps)
+    rel, env, *_ = one_step_accel(desc, substeps, split=split)
     assert rel.max() <= 1e-4, rel.max()
     assert env.sync_status() == sg.SG_OK
 
@@ -85,16 +87,18 @@ def test_step_acceleration_matches_oracle(kinds, substeps):
     [([0] * 6, [1, 0, 2, 2, 1, 0])],
     [([0, 0, 0, 0], [2, 1, 2, 1]), ([0, 0, 1, 0, 0], [0, 1, 2, 2, 0])],
 ], ids=["x-axes", "prismatic-root", "six", "mixed-pair"])
-def test_generic_chains_match_oracle(chains):
+@pytest.mark.parametrize("split", [1, 2])
+def test_generic_chains_match_oracle(chains, split):
     desc = chain_desc(chains, E=70, seed=5, kp=50.0, kd=5.0, damping=0.1,
                       base=[(0, 0.25, 0), (0, -0.25, 0)])
-    rel, env, *_ = one_step_accel(desc, 2)
+    rel, env, *_ = one_step_accel(desc, 2, split=split)
     assert rel.max() <= 1e-4, rel.max()
 
 
-def test_limit_springs_match_oracle():
+@pytest.mark.parametrize("split", [1, 2])
+def test_limit_springs_match_oracle(split):
     desc = W.make_desc(["7R"] * 150 + ["7P"] * 40, k_limit=1e3)
-    rel, *_ = one_step_accel(desc, 8)
+    rel, *_ = one_step_accel(desc, 8, split=split)
     assert rel.max() <= 1e-4, rel.max()
 
 

@@ -21,14 +21,15 @@ def cuda(x):
 
 
 @pytest.mark.parametrize("mode", [sg.ROLLOUT_PERSISTENT, sg.ROLLOUT_STEP_GRAPH])
-@pytest.mark.parametrize("threads", [32, 128, 256])
-def test_rollout_equals_steps_bitwise(mode, threads):
+@pytest.mark.parametrize("threads,split", [(32, 1), (128, 1), (256, 1), (64, 2), (256, 2)])
+def test_rollout_equals_steps_bitwise(mode, threads, split):
     kinds = W.mixed_kinds(777, W.C3_FRACTIONS)
     desc = W.make_desc(kinds, episode_len=20)
     T = 32
     acts = cuda(W.joint_targets(desc, T))
     A, B = sg.Env(desc), sg.Env(desc)
-    B.set_launch(threads, mode)
+    A.set_launch(threads, sg.ROLLOUT_PERSISTENT, split)   # sg_step uses the same kernel
+    B.set_launch(threads, mode, split)
     steps = [A.step(acts[t], DT, 2) for t in range(T)]
     obs, rew, done = B.rollout(acts, DT, 2)
     for t in range(T):
@@ -42,6 +43,40 @@ def test_rollout_equals_steps_bitwise(mode, threads):
     obs2, _, _ = B.rollout(acts, DT, 2)
     s2 = [A.step(acts[t], DT, 2) for t in range(T)]
     assert torch.equal(obs2[-1], s2[-1][0])
+
+
+def _close(x, y, tol):
+    return (x - y).abs().max().item() <= tol * max(1.0, y.abs().max().item())
+
+
+@pytest.mark.parametrize("kinds", [["7R"], ["14B"], ["4R", "7P"], ["7R", "4R", "7P", "14B"]],
+                         ids=lambda k: "+".join(k))
+def test_warp_pair_kernel_matches_single_thread_kernel(kinds):
+    """Chain split 2 (two cooperating warps per chain block) agrees with one
+    thread per chain to rounding (1e-5 of the largest entry over 6 steps),
+    with identical done flags, for every chain class."""
+    desc = W.make_desc((kinds * 200)[:200])
+    T = 6
+    acts = cuda(W.joint_targets(desc, T))
+    A, B = sg.Env(desc), sg.Env(desc)
+    A.set_launch(128, sg.ROLLOUT_PERSISTENT, 1)
+    B.set_launch(128, sg.ROLLOUT_PERSISTENT, 2)
+    oa, ra, da = A.rollout(acts, DT, 2)
+    ob, rb, db = B.rollout(acts, DT, 2)
+    assert _close(ob, oa, 1e-5) and _close(rb, ra, 1e-5) and torch.equal(da, db)
+    qa, qda, sca = A.get_state()
+    qb, qdb, scb = B.get_state()
+    assert _close(qb, qa, 1e-5) and _close(qdb, qda, 1e-4) and torch.equal(sca, scb)
+
+
+def test_warp_pair_path_task():
+    desc = W.make_desc(["7R"] * 100, task=1, path_len=20, episode_len=10)
+    acts = cuda(W.joint_targets(desc, 12))
+    A, B = sg.Env(desc), sg.Env(desc)
+    B.set_launch(64, sg.ROLLOUT_STEP_GRAPH, 2)
+    oa, ra, da = A.rollout(acts, DT, 4)
+    ob, rb, db = B.rollout(acts, DT, 4)
+    assert _close(ob, oa, 1e-5) and _close(rb, ra, 1e-5) and torch.equal(da, db)
 
 
 def test_host_rollout_matches_device_rollout():
@@ -65,8 +100,9 @@ def test_autotune_keeps_state_and_picks_a_plan():
     T = 16
     acts = cuda(W.joint_targets(desc, T))
     A, B = sg.Env(desc), sg.Env(desc)
-    th, mode, ms = B.autotune(acts, DT, 2, repeats=2)
-    assert th in (32, 64, 128, 256) and mode in (0, 1) and ms > 0
+    th, mode, split, ms = B.autotune(acts, DT, 2, repeats=2)
+    assert th in (32, 64, 128, 256) and mode in (0, 1) and split in (1, 2) and ms > 0
+    A.set_launch(th, mode, split)
     qa, qda, sca = A.get_state()
     qb, qdb, scb = B.get_state()
     assert torch.equal(qa, qb) and torch.equal(qda, qdb) and torch.equal(sca, scb)
@@ -81,5 +117,7 @@ def test_rollout_argument_errors():
         env.set_launch(48, 0)
     with pytest.raises(sg.SgError):
         env.set_launch(64, 5)
+    with pytest.raises(sg.SgError):
+        env.set_launch(32, 0, 2)
     with pytest.raises(ValueError):
         env.rollout(torch.zeros(4, 8, 6, device="cuda"), DT, 2)
