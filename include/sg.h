@@ -225,6 +225,38 @@ sg_status sg_autotune(sg_ctx *ctx, const float *actions_dev, int32_t T, float dt
                       int32_t substeps, float *obs_dev, float *reward_dev, uint8_t *done_dev,
                       int32_t repeats, float *best_ms);
 
+/*
+ * Differentiation of tool-tip trajectories (a hand-written adjoint of the
+ * step; no counterpart in the paper, whose engine is not differentiable).
+ *
+ * sg_diff_forward: T control steps from the current state with
+ * actions_dev [T][E][J], writing the tool-tip position of every chain after
+ * every step to ee_dev [T][E][2][3] (chain 1 entries are 0 for one-chain
+ * envs).  The state (q, qd) is checkpointed every ckpt_every steps
+ * (1..32) in context scratch memory (cudaMalloc on first use or growth);
+ * the context's own state and step counts are NOT changed.  substeps 1..16.
+ *
+ * sg_diff_backward: the reverse pass of the last sg_diff_forward on this
+ * context.  Given dl_dee_dev [T][E][2][3] = dL/d(ee) it writes
+ * dactions_dev [T][E][J] = dL/d(actions) and dmass_dev [E][J] = dL/d(link
+ * mass) (link inertias scale with the mass, centre of mass fixed); dq0_dev
+ * and dqd0_dev [E][J] (either may be NULL) receive dL/d(initial q, qd).
+ * actions_dev must hold the same values as in the forward call.  Each
+ * segment between checkpoints is recomputed from its checkpoint.  Joint
+ * limit springs switch on and off at the limits; the gradient is that of
+ * the active branch.
+ */
+sg_status sg_diff_forward(sg_ctx *ctx, const float *actions_dev, int32_t T, float dt,
+                          int32_t substeps, int32_t ckpt_every, float *ee_dev);
+sg_status sg_diff_backward(sg_ctx *ctx, const float *actions_dev, const float *dl_dee_dev,
+                           float *dactions_dev, float *dmass_dev, float *dq0_dev,
+                           float *dqd0_dev);
+
+/* Replace the link masses with mass_dev [E][J] (device, > 0); each link's
+ * rotational inertia is rescaled by new mass / description mass (the link's
+ * box dimensions and centre of mass stay fixed). */
+sg_status sg_set_link_mass(sg_ctx *ctx, const float *mass_dev);
+
 /* Synchronise the context's stream, then read and clear the device error
  * flags: SG_ERR_NONFINITE if any env produced a non-finite state since the
  * last call, SG_ERR_TIMEOUT if a bounded device wait gave up, else SG_OK

@@ -13,6 +13,7 @@
 
 #include "sg.h"
 #include "sg_internal.h"
+#include "sg_diff.h"
 #include "sg_kernels.h"
 
 struct sg_ctx {
@@ -54,6 +55,15 @@ struct sg_ctx {
   float* d_stage_rew = nullptr;
   uint8_t* d_stage_done = nullptr;
   int stage_T = 0;
+  // description masses / inertias (for sg_set_link_mass)
+  float* d_mass0 = nullptr;
+  float* d_inertia0 = nullptr;
+  // differentiable rollout: checkpoint scratch and the last forward's shape
+  float* d_ckpt = nullptr;
+  size_t ckpt_floats = 0;
+  bool diff_ready = false;
+  int diff_T = 0, diff_substeps = 0, diff_every = 0;
+  float diff_dt = 0.f;
   // state snapshot for the autotuner
   float* d_snap_q = nullptr;
   float* d_snap_qd = nullptr;
@@ -90,7 +100,8 @@ void free_ctx(sg_ctx* c) {
   void* ptrs[] = {c->d_params, c->d_q, c->d_qd, c->d_q0, c->d_path, c->d_slot_env,
                   c->d_slot_info, c->d_warp_class, c->d_step_count, c->d_err,
                   c->d_stage_act, c->d_stage_obs, c->d_stage_rew, c->d_stage_done,
-                  c->d_snap_q, c->d_snap_qd, c->d_snap_sc};
+                  c->d_snap_q, c->d_snap_qd, c->d_snap_sc, c->d_mass0, c->d_inertia0,
+                  c->d_ckpt};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -299,6 +310,8 @@ sg_status sg_create(const sg_desc* desc, void* stream, sg_ctx** out) {
   step(upload(&c->d_slot_info, P.slot_info.data(), NS, c->stream));
   step(upload(&c->d_warp_class, P.warp_class.data(), P.warp_class.size(), c->stream));
   step(upload(&c->d_q0, P.q0.data(), P.q0.size(), c->stream));
+  step(upload(&c->d_mass0, P.mass0.data(), P.mass0.size(), c->stream));
+  step(upload(&c->d_inertia0, P.inertia0.data(), P.inertia0.size(), c->stream));
   step(upload<float>(&c->d_q, nullptr, (size_t)sg::kMaxLinks * NS, c->stream));
   step(upload<float>(&c->d_qd, nullptr, (size_t)sg::kMaxLinks * NS, c->stream));
   step(upload<int32_t>(&c->d_step_count, nullptr, (size_t)P.num_envs, c->stream));
@@ -309,6 +322,7 @@ sg_status sg_create(const sg_desc* desc, void* stream, sg_ctx** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream);
   if (e == cudaSuccess) e = sg::prepare_step_kernel();
   if (e == cudaSuccess) e = sg::prepare_step_pair_kernel();
+  if (e == cudaSuccess) e = sg::prepare_diff_kernels();
   if (e == cudaSuccess) e = sg::launch_reset(state_args(c), nullptr, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
@@ -502,6 +516,97 @@ sg_status sg_set_state(sg_ctx* ctx, const float* q_dev, const float* qd_dev,
   return cuda_err(ctx, sg::launch_set_state(state_args(ctx), q_dev, qd_dev, step_count_dev,
                                             ctx->stream),
                   "sg_set_state");
+}
+
+namespace {
+sg::DiffArgs diff_args(sg_ctx* c) {
+  sg::DiffArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.params = c->d_params;
+  a.slot_env = c->d_slot_env;
+  a.slot_info = c->d_slot_info;
+  a.warp_class = c->d_warp_class;
+  a.q = c->d_q;
+  a.qd = c->d_qd;
+  a.ckpt = c->d_ckpt;
+  a.err = c->d_err;
+  a.num_warps = c->plan.num_warps;
+  a.num_slots = c->plan.num_slots;
+  a.num_envs = c->plan.num_envs;
+  a.max_joints = c->plan.max_joints;
+  a.T = c->diff_T;
+  a.substeps = c->diff_substeps;
+  a.ckpt_every = c->diff_every;
+  a.nseg = (c->diff_T + c->diff_every - 1) / c->diff_every;
+  a.h = c->diff_dt / (float)c->diff_substeps;
+  return a;
+}
+}  // namespace
+
+sg_status sg_diff_forward(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt,
+                          int32_t substeps, int32_t ckpt_every, float* ee_dev) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  if (!actions_dev || !ee_dev)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "actions and ee must be non-NULL");
+  if (T < 1 || T > 4096) return set_err(ctx, SG_ERR_INVALID_ARG, "T must be 1..4096");
+  if (!(dt > 0.f) || !std::isfinite(dt)) return set_err(ctx, SG_ERR_INVALID_ARG, "dt must be > 0");
+  if (substeps < 1 || substeps > sg::kMaxDiffSubsteps)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "substeps must be 1..16 for the differentiable rollout");
+  if (ckpt_every < 1 || ckpt_every > sg::kMaxCkptEvery)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "ckpt_every must be 1..32");
+  const int nseg = (T + ckpt_every - 1) / ckpt_every;
+  const size_t need = (size_t)(nseg + 1) * 2 * sg::kMaxLinks * ctx->plan.num_slots;
+  if (need > ctx->ckpt_floats) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (ctx->d_ckpt) cudaFree(ctx->d_ckpt);
+    ctx->d_ckpt = nullptr;
+    ctx->ckpt_floats = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_ckpt, need * sizeof(float));
+    if (e != cudaSuccess) return cuda_err(ctx, e, "sg_diff_forward: checkpoint buffer");
+    ctx->ckpt_floats = need;
+  }
+  ctx->diff_T = T;
+  ctx->diff_dt = dt;
+  ctx->diff_substeps = substeps;
+  ctx->diff_every = ckpt_every;
+  ctx->diff_ready = true;
+  sg::DiffArgs a = diff_args(ctx);
+  a.actions = actions_dev;
+  a.ee = ee_dev;
+  return cuda_err(ctx, sg::launch_diff_forward(a, ctx->stream), "sg_diff_forward");
+}
+
+sg_status sg_diff_backward(sg_ctx* ctx, const float* actions_dev, const float* dl_dee_dev,
+                           float* dactions_dev, float* dmass_dev, float* dq0_dev,
+                           float* dqd0_dev) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  if (!ctx->diff_ready)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "sg_diff_backward needs a preceding sg_diff_forward");
+  if (!actions_dev || !dl_dee_dev || !dactions_dev || !dmass_dev)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "actions, dl_dee, dactions and dmass must be non-NULL");
+  sg::DiffArgs a = diff_args(ctx);
+  a.actions = actions_dev;
+  a.dl_dee = dl_dee_dev;
+  a.dactions = dactions_dev;
+  a.dmass = dmass_dev;
+  a.dq0 = dq0_dev;
+  a.dqd0 = dqd0_dev;
+  return cuda_err(ctx, sg::launch_diff_backward(a, ctx->stream), "sg_diff_backward");
+}
+
+sg_status sg_set_link_mass(sg_ctx* ctx, const float* mass_dev) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  if (!mass_dev) return set_err(ctx, SG_ERR_INVALID_ARG, "mass must be non-NULL");
+  sg::MassArgs m;
+  m.params = ctx->d_params;
+  m.slot_env = ctx->d_slot_env;
+  m.slot_info = ctx->d_slot_info;
+  m.mass = mass_dev;
+  m.mass0 = ctx->d_mass0;
+  m.inertia0 = ctx->d_inertia0;
+  m.num_slots = ctx->plan.num_slots;
+  m.max_joints = ctx->plan.max_joints;
+  return cuda_err(ctx, sg::launch_set_mass(m, ctx->stream), "sg_set_link_mass");
 }
 
 sg_status sg_sync_status(sg_ctx* ctx) {

@@ -1,0 +1,49 @@
+// Differentiable rollout kernels (implemented in sg_diff.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sg_internal.h"
+
+namespace sg {
+
+constexpr int kDiffThreads = 128;
+constexpr int kMaxCkptEvery = 32;      // checkpoint interval limit (thread-local segment buffer)
+constexpr int kMaxDiffSubsteps = 16;   // substeps limit of the differentiable rollout
+
+struct DiffArgs {
+  const float* params;
+  const int32_t* slot_env;
+  const int32_t* slot_info;
+  const int32_t* warp_class;
+  const float* q;          // start state [kMaxLinks][NS]
+  const float* qd;
+  float* ckpt;             // [nseg + 1][2 * kMaxLinks][NS]
+  const float* actions;    // [T][E][J]
+  float* ee;               // [T][E][2][3]      (forward output)
+  const float* dl_dee;     // [T][E][2][3]      (backward input)
+  float* dactions;         // [T][E][J]         (backward output)
+  float* dmass;            // [E][J]            (backward output)
+  float* dq0;              // [E][J] or null    (backward output)
+  float* dqd0;             // [E][J] or null    (backward output)
+  int32_t* err;
+  int num_warps, num_slots, num_envs, max_joints, T, substeps, ckpt_every, nseg;
+  float h;
+};
+
+struct MassArgs {
+  float* params;
+  const int32_t* slot_env;
+  const int32_t* slot_info;
+  const float* mass;       // caller [E][J]
+  const float* mass0;      // [kMaxLinks][NS] masses of the description
+  const float* inertia0;   // [3][kMaxLinks][NS] inertias of the description
+  int num_slots, max_joints;
+};
+
+cudaError_t prepare_diff_kernels();
+cudaError_t launch_diff_forward(const DiffArgs& a, cudaStream_t s);
+cudaError_t launch_diff_backward(const DiffArgs& a, cudaStream_t s);
+cudaError_t launch_set_mass(const MassArgs& m, cudaStream_t s);
+
+}  // namespace sg

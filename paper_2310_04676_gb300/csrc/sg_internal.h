@@ -65,6 +65,8 @@ struct Plan {
   std::vector<int32_t> warp_class;  // [NW]
   std::vector<float> params;        // [NW][kRecordFloats]
   std::vector<float> q0;            // [kMaxLinks][NS]
+  std::vector<float> mass0;         // [kMaxLinks][NS] link masses of the description
+  std::vector<float> inertia0;      // [3][kMaxLinks][NS] link inertias of the description
   std::vector<float> path;          // [E][W][3] (path task)
 };
 

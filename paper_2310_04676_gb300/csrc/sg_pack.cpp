@@ -166,6 +166,8 @@ sg_status build_plan(const sg_desc* d, Plan* P, std::string* err) {
   // ---- fill records, slot info and q0 ------------------------------------
   P->params.assign((size_t)P->num_warps * kRecordFloats, 0.f);
   P->q0.assign((size_t)kMaxLinks * NS, 0.f);
+  P->mass0.assign((size_t)kMaxLinks * NS, 1.f);
+  P->inertia0.assign((size_t)3 * kMaxLinks * NS, 1.f);
   P->slot_info.assign(NS, 0);
   for (int s = 0; s < NS; ++s) {
     const bool pad = P->slot_env[s] < 0;
@@ -203,6 +205,9 @@ sg_status build_plan(const sg_desc* d, Plan* P, std::string* err) {
       LF(i, LF_D) = d->kd[k] + d->damping[k];
       LF(i, LF_KLIM) = d->k_limit[k];
       P->q0[(size_t)i * NS + s] = d->q0[k];
+      P->mass0[(size_t)i * NS + s] = d->link_mass[k];
+      for (int a = 0; a < 3; ++a)
+        P->inertia0[((size_t)a * kMaxLinks + i) * NS + s] = d->link_inertia[3 * k + a];
     }
     std::memcpy(&CF(CF_CODE), &code, 4);
   }

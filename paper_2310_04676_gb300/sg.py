@@ -80,6 +80,9 @@ def load_library(path=LIB_PATH):
         "sg_set_launch": (i32, [vp, i32, i32, i32]),
         "sg_get_launch": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "sg_autotune": (i32, [vp, vp, i32, f32, i32, vp, vp, u8p, i32, ctypes.POINTER(f32)]),
+        "sg_diff_forward": (i32, [vp, vp, i32, f32, i32, i32, vp]),
+        "sg_diff_backward": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+        "sg_set_link_mass": (i32, [vp, vp]),
         "sg_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -282,6 +285,41 @@ class Env:
         t, m, sp = self.get_launch()
         return t, m, sp, ms.value
 
+    # -- differentiation -----------------------------------------------------
+    def set_link_mass(self, mass):
+        """Link masses [E, J] (inertias scale with them)."""
+        self._sync_stream()
+        self._want(mass, self._torch.float32, (self.num_envs, self.max_joints), "mass")
+        self._check(self.lib.sg_set_link_mass(self.ctx, _ptr(mass)))
+
+    def diff_forward(self, actions, dt, substeps, ckpt_every=8):
+        """Tool-tip trajectory [T, E, 2, 3] from the current state (state
+        unchanged); checkpoints kept for diff_backward."""
+        self._sync_stream()
+        torch = self._torch
+        T = int(actions.shape[0])
+        self._want(actions, torch.float32, (T, self.num_envs, self.max_joints), "actions")
+        ee = torch.empty(T, self.num_envs, 2, 3, dtype=torch.float32, device=self.device)
+        self._check(self.lib.sg_diff_forward(self.ctx, _ptr(actions), T, float(dt), int(substeps),
+                                             int(ckpt_every), _ptr(ee)))
+        return ee
+
+    def diff_backward(self, actions, dl_dee, initial_state=False):
+        """Gradients for the last diff_forward: (dactions [T, E, J],
+        dmass [E, J]) and, with initial_state, (dq0, dqd0) [E, J]."""
+        self._sync_stream()
+        torch = self._torch
+        T = int(actions.shape[0])
+        self._want(actions, torch.float32, (T, self.num_envs, self.max_joints), "actions")
+        self._want(dl_dee, torch.float32, (T, self.num_envs, 2, 3), "dl_dee")
+        da = torch.empty_like(actions)
+        dm = torch.empty(self.num_envs, self.max_joints, dtype=torch.float32, device=self.device)
+        dq0 = torch.empty_like(dm) if initial_state else None
+        dqd0 = torch.empty_like(dm) if initial_state else None
+        self._check(self.lib.sg_diff_backward(self.ctx, _ptr(actions), _ptr(dl_dee), _ptr(da),
+                                              _ptr(dm), _ptr(dq0), _ptr(dqd0)))
+        return (da, dm, dq0, dqd0) if initial_state else (da, dm)
+
     def get_state(self):
         self._sync_stream()
         torch = self._torch
@@ -307,3 +345,46 @@ class Env:
     def sync_status(self):
         """Synchronise and return the device status code (raises nothing)."""
         return self.lib.sg_sync_status(self.ctx)
+
+
+def _autograd_function():
+    import torch
+
+    class TipRollout(torch.autograd.Function):
+        """Differentiable tool-tip rollout through the library's adjoint
+        kernel: forward(env, actions [T,E,J], mass [E,J] or None, dt,
+        substeps, ckpt_every) -> ee [T,E,2,3]."""
+
+        @staticmethod
+        def forward(ctx, env, actions, mass, dt, substeps, ckpt_every):
+            if mass is not None:
+                env.set_link_mass(mass.detach().contiguous())
+            a = actions.detach().contiguous()
+            ee = env.diff_forward(a, dt, substeps, ckpt_every)
+            ctx.env = env
+            ctx.save_for_backward(a)
+            ctx.has_mass = mass is not None
+            return ee
+
+        @staticmethod
+        def backward(ctx, g):
+            (a,) = ctx.saved_tensors
+            da, dm = ctx.env.diff_backward(a, g.contiguous())
+            return None, da, (dm if ctx.has_mass else None), None, None, None
+
+    return TipRollout
+
+
+_TIP_ROLLOUT = None
+
+
+def tip_rollout(env, actions, dt, substeps, mass=None, ckpt_every=8):
+    """Tool-tip positions [T, E, 2, 3] as a differentiable function of the
+    actions (and optionally the link masses) -- backward runs the adjoint
+    kernel with checkpointing every ``ckpt_every`` steps.  One outstanding
+    forward per Env: a second call before backward overwrites the
+    checkpoints."""
+    global _TIP_ROLLOUT
+    if _TIP_ROLLOUT is None:
+        _TIP_ROLLOUT = _autograd_function()
+    return _TIP_ROLLOUT.apply(env, actions, mass, dt, substeps, ckpt_every)
