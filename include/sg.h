@@ -257,6 +257,46 @@ sg_status sg_diff_backward(sg_ctx *ctx, const float *actions_dev, const float *d
  * box dimensions and centre of mass stay fixed). */
 sg_status sg_set_link_mass(sg_ctx *ctx, const float *mass_dev);
 
+/*
+ * sg_diff_track_noalloc -- the paper has no counterpart (its engine is not
+ * differentiable); this is a no-allocation form of the differentiable
+ * rollout above, fused with the tracking loss
+ *     L_e = sum_t sum_c ||ee[t][e][c] - target[t][e][c]||^2 .
+ * It runs sg_diff_forward's forward kernel, the loss cotangent and
+ * sg_diff_backward's adjoint kernel in one call and writes ee_dev
+ * [T][E][2][3], loss_dev [E], dactions_dev [T][E][J] = dL/d(actions) and
+ * dmass_dev [E][J] = dL/d(link mass); target_dev is [T][E][2][3] (chain-1
+ * targets of one-chain envs are ignored).
+ *
+ * Who needs it: callers that cannot allocate device memory when they need
+ * gradients -- a training or control loop inside a host program that owns
+ * all device memory through its own pre-reserved pool and forbids further
+ * allocation, or one that must not stall on the implicit device
+ * synchronisation of cudaMalloc / cudaFree.  sg_diff_forward would
+ * cudaMalloc its checkpoints; this call allocates nothing: its scratch (the
+ * checkpoints and the loss cotangent) lives in a static __device__ array of
+ * 32 MiB compiled into libsg.so, which every GPU that loads the library
+ * holds until the process exits.  The context itself must have been created
+ * beforehand (sg_create allocates).
+ *
+ * Limits: substeps 1..16, ckpt_every 1..32, T 1..4096, and
+ * (ceil(T / ckpt_every) + 1) * 14 * sg_plan_info.num_slots + 6 * T * E
+ * floats must fit in the 32 MiB (8388608 floats); larger requests return
+ * SG_ERR_INVALID_ARG with a message and enqueue nothing.
+ * All calls on a device share the one array and it keeps the last call's
+ * contents (each call writes every entry it reads before reading it, so
+ * nothing needs clearing); calls whose GPU work overlaps -- other streams,
+ * other host threads, other contexts on the same device -- race on it, so
+ * the caller must serialise them.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  The context's
+ * own state and its sg_diff_forward checkpoints are not touched.
+ */
+sg_status sg_diff_track_noalloc(sg_ctx *ctx, const float *actions_dev, int32_t T, float dt,
+                                int32_t substeps, int32_t ckpt_every, const float *target_dev,
+                                float *ee_dev, float *loss_dev, float *dactions_dev,
+                                float *dmass_dev);
+
 /* Synchronise the context's stream, then read and clear the device error
  * flags: SG_ERR_NONFINITE if any env produced a non-finite state since the
  * last call, SG_ERR_TIMEOUT if a bounded device wait gave up, else SG_OK

@@ -543,6 +543,31 @@ sg::DiffArgs diff_args(sg_ctx* c) {
 }
 }  // namespace
 
+}  // extern "C"
+
+namespace sg {
+DiffArgs context_diff_args(sg_ctx* c) {
+  DiffArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.params = c->d_params;
+  a.slot_env = c->d_slot_env;
+  a.slot_info = c->d_slot_info;
+  a.warp_class = c->d_warp_class;
+  a.q = c->d_q;
+  a.qd = c->d_qd;
+  a.err = c->d_err;
+  a.num_warps = c->plan.num_warps;
+  a.num_slots = c->plan.num_slots;
+  a.num_envs = c->plan.num_envs;
+  a.max_joints = c->plan.max_joints;
+  return a;
+}
+void context_set_error(sg_ctx* c, const char* msg) { c->last_error = msg; }
+cudaStream_t context_stream(sg_ctx* c) { return c->stream; }
+}  // namespace sg
+
+extern "C" {
+
 sg_status sg_diff_forward(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt,
                           int32_t substeps, int32_t ckpt_every, float* ee_dev) {
   if (!ctx) return SG_ERR_INVALID_ARG;

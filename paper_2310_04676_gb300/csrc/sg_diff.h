@@ -41,6 +41,12 @@ struct MassArgs {
   int num_slots, max_joints;
 };
 
+// Context accessors for entry points implemented outside sg_api.cu:
+// the context's parameter/state/slot pointers and sizes (shape fields zero).
+DiffArgs context_diff_args(sg_ctx* ctx);
+void context_set_error(sg_ctx* ctx, const char* msg);
+cudaStream_t context_stream(sg_ctx* ctx);
+
 cudaError_t prepare_diff_kernels();
 cudaError_t launch_diff_forward(const DiffArgs& a, cudaStream_t s);
 cudaError_t launch_diff_backward(const DiffArgs& a, cudaStream_t s);

@@ -83,6 +83,7 @@ def load_library(path=LIB_PATH):
         "sg_diff_forward": (i32, [vp, vp, i32, f32, i32, i32, vp]),
         "sg_diff_backward": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "sg_set_link_mass": (i32, [vp, vp]),
+        "sg_diff_track_noalloc": (i32, [vp, vp, i32, f32, i32, i32, vp, vp, vp, vp, vp]),
         "sg_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
