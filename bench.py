@@ -1,23 +1,31 @@
 #!/usr/bin/env python
 """Benchmark of the batched articulated-arm step on one GB300 (or N replicas).
 
-Workload (default): 16384 heterogeneous environments -- 25% 4-DOF revolute
+Default workload: 16384 heterogeneous environments -- 25% 4-DOF revolute
 arms, 40% 7-DOF revolute, 20% 7-DOF with a prismatic insertion joint, 15%
 14-DOF two-arm robots -- reach task, dt = 1/60 s, 2 substeps.  One bench
 step is one 32-step rollout of every env (32 x 16384 env-steps), issued as
-the autotuned persistent kernel captured in a CUDA graph.  The plain
-one-kernel-per-step launch runs the same rollout on the same inputs from
-the same state and is reported beside it; both produce identical bits.
+the autotuned persistent kernel captured in a CUDA graph.  The same rollout
+on the same inputs from the same state is also timed as 32 single-step
+kernels replayed from a CUDA graph and as 32 sg_step calls (the plain
+one-kernel-per-step launch); all three produce identical bits.
 
 Metric: env-steps/s (aggregate over all ranks).  Timing: CUDA events on the
 launching stream, W warm-up steps, K timed steps, L2 flushed (a 256 MiB
-write) before every timed step, max over ranks.
+write, outside the events) before every timed step, max over ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config C1|C2|C3|C4|C5] [--envs E ...]
+
+--config selects one of the other workloads (C1: 64 envs, latency; C2: 8192
+envs path following; C4: adjoint of a 64-step rollout of 2048 envs; C5: the
+limit-spring 7-DOF sweep over --envs sizes); each prints one line.
 """
 import argparse
+import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import time
@@ -28,31 +36,59 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "env-steps/s at 16k mixed-DOF envs, batched vs plain; % FP32 roofline; grad err"
-T_ROLLOUT = 32
+ROLLOUT_T = {"C1": 50, "C2": 50, "C3": 32, "C5": 50}
 
 # Algorithmic FP32 operations of the step's formulation (an FMA counts 2),
 # counted by a counting-scalar run of the chain code: per substep of one
 # chain, and per step for the tool-tip kinematics of one chain.
 FLOP_SUBSTEP = {"4R": 774, "7R": 1697, "7P": 1580}
 FLOP_TIP = {"4R": 96, "7R": 168, "7P": 156}
-FLOP_REWARD = 9        # distance to the goal (per chain)
+FLOP_REWARD = 9          # distance to the goal (per chain)
+FLOP_QUAT = 30           # tip quaternion (path task)
 
 
-def env_step_flops(kinds, substeps):
+def env_step_flops(kinds, substeps, task=0):
     tot = 0
     for k in kinds:
-        chains = ["7R", "7R"] if k == "14B" else [k]
-        for c in chains:
+        for c in (["7R", "7R"] if k == "14B" else [k]):
             tot += substeps * FLOP_SUBSTEP[c] + FLOP_TIP[c] + FLOP_REWARD
+            if task == 1:
+                tot += FLOP_QUAT
     return tot
 
 
 def env_step_bytes(desc, obs_dim):
-    """Algorithmic HBM bytes of one env-step in the persistent rollout:
-    action row read, observation row, reward and done written."""
+    """Algorithmic HBM bytes of one env-step of the persistent rollout: the
+    action row read, observation row, reward and done written (waypoint
+    reads of the path task add 4 x 12 bytes)."""
     E = desc["num_envs"]
     dof = desc["chain_num_joints"].sum(1)
-    return int(4 * dof.sum() + E * (4 * obs_dim + 4 + 1))
+    extra = 48 * E if int(desc["task"]) == 1 else 0
+    return int(4 * dof.sum() + E * (4 * obs_dim + 4 + 1) + extra)
+
+
+def kernel_source_hash():
+    """Hash of the step-kernel sources; a profile summary names the hash it
+    was captured with, and its DRAM traffic is used only if they match."""
+    h = hashlib.sha256()
+    for f in ("sg_chain.cuh", "sg_device.cuh", "sg_kernels.cu", "sg_pair.cu"):
+        with open(os.path.join(ROOT, "paper_2310_04676_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` on the default workload, from the
+    committed ncu summary, if it was taken from the current sources."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_c3.md")
+    if not os.path.exists(p):
+        return None
+    text = open(p).read()
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    m = re.search(r"traffic_bytes_per_launch\[%s\]:\s*([0-9]+)" % re.escape(kernel), text)
+    return int(m.group(1)) if m else None
 
 
 def load_peaks():
@@ -69,21 +105,21 @@ class ClockSampler:
     def __init__(self, path, device):
         self.path, self.device, self.proc = path, device, None
 
-    def __enter__(self):
+    def start(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + q, "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
         time.sleep(0.3)
-        return self
 
-    def __exit__(self, *a):
+    def stop(self):
         if self.proc is not None:
             time.sleep(0.2)
             self.proc.terminate()
@@ -96,53 +132,302 @@ class ClockSampler:
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        rows = []
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        rows = [[x.strip() for x in line.split(",")] for line in open(self.path)]
+        rows = [r for r in rows if len(r) >= 9]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
-        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        num = lambda s: s.replace(".", "", 1).isdigit()
+        sm = sorted(float(r[1]) for r in rows if num(r[1]))
+        mx = max((float(r[2]) for r in rows if num(r[2])), default=None)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
-        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
-                "samples": len(rows)}
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows)}
 
 
+# ---- ranks (one process per GPU, independent replicas) ---------------------
 def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def cpu_baseline(wl, seconds=12.0):
-    """The FP64 oracle as it stands on this host's cores, on a bounded sample
-    of the workload (a fixed subset of envs, as many steps as fit)."""
+def reduce_max(x, world, device=None):
+    """Maximum of a float over all ranks (identity for one rank)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, seconds_per_rank, world, device=None):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    return world * units_per_rank / reduce_max(seconds_per_rank, world, device)
+
+
+def replica_desc(wl, rank):
+    """Rank 0 runs the workload as stated; rank r > 0 an independent replica
+    with its own seeded link parameters and goals."""
+    from paper_2310_04676_gb300 import workloads as W
+    if rank == 0:
+        return wl.desc
+    d = wl.desc
+    return W.make_desc(wl.kinds, seed_params=1 + 1000 * rank, seed_goals=3 + 1000 * rank,
+                       shared_params=False, k_limit=float(d["k_limit"].max()),
+                       episode_len=int(d["episode_len"]), task=int(d["task"]),
+                       path_len=int(d["path_len"] or 0))
+
+
+# ---- CPU baseline (the FP64 oracle as it stands) ----------------------------
+def cpu_baseline(wl, seconds=12.0, max_envs=2048):
+    """The oracle on this host's cores, on a bounded sample of the workload
+    (the first `max_envs` envs, as many steps as fit in `seconds`)."""
     import torch
     from oracle.env import OracleEnv
     from paper_2310_04676_gb300 import workloads as W
     E = wl.desc["num_envs"]
-    n_sample = min(E, 2048)
-    pick = np.arange(n_sample)
-    sub = {k: (v[pick] if isinstance(v, np.ndarray) and v.shape[:1] == (E,) else v)
+    n = min(E, max_envs)
+    sub = {k: (v[:n] if isinstance(v, np.ndarray) and v.shape[:1] == (E,) else v)
            for k, v in wl.desc.items()}
-    sub["num_envs"] = n_sample
+    sub["num_envs"] = n
     env = OracleEnv(sub)
     acts = W.joint_targets(sub, 64)
-    env.step(acts[0], wl.dt, wl.substeps)        # first step excluded, as the paper times
+    env.step(acts[0], wl.dt, wl.substeps)        # first step excluded (timing starts after it)
     t0 = time.perf_counter()
     steps = 0
     while time.perf_counter() - t0 < seconds and steps < 63:
         env.step(acts[1 + steps], wl.dt, wl.substeps)
         steps += 1
     el = time.perf_counter() - t0
-    return {"value": n_sample * steps / el, "unit": "env-steps/s", "cores": torch.get_num_threads(),
+    return {"value": n * steps / el, "unit": "env-steps/s", "cores": torch.get_num_threads(),
             "kind": "oracle",
             "sample": "%d of %d envs (same kind mix), %d steps, FP64 PyTorch CPU, %.1f s"
-                      % (n_sample, E, steps, el)}
+                      % (n, E, steps, el)}
+
+
+def grad_error(wl, acts_np, tg_np, da, dm, n_envs=16):
+    """Adjoint gradients of the first `n_envs` envs against the oracle's
+    reverse mode (FP64 autograd through its rollout): max per-env relative
+    error of dL/d(actions) and dL/d(mass)."""
+    import torch
+    from oracle.env import ee_rollout
+    desc = wl.desc
+    idx = np.arange(n_envs)
+    n = int(desc["chain_num_joints"][0, 0])
+    A = torch.tensor(acts_np[:, idx, :n], dtype=torch.float64, requires_grad=True)
+    m = torch.tensor(desc["link_mass"][idx, :n], dtype=torch.float64, requires_grad=True)
+    ee = ee_rollout(desc, A, wl.dt, wl.substeps, mass=m, env_idx=idx)
+    L = ((ee - torch.tensor(tg_np[:, idx, :1], dtype=torch.float64)) ** 2).sum()
+    ga, gm = torch.autograd.grad(L, [A, m])
+    rel = lambda x, y: np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-12)
+    ea = max(rel(da[:, e, :n], ga[:, e].numpy()) for e in range(n_envs))
+    em = max(rel(dm[e, :n], gm[e].numpy()) for e in range(n_envs))
+    return ea, em
+
+
+# ---- GPU measurements -------------------------------------------------------
+class Ctx:
+    def __init__(self, args, world, rank, local):
+        import torch
+        self.torch = torch
+        self.args, self.world, self.rank, self.local = args, world, rank, local
+        self.dev = torch.device("cuda", local)
+        self.stream = torch.cuda.current_stream()
+        self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=self.dev)
+
+    def barrier(self):
+        if self.world > 1:
+            self.torch.distributed.barrier()
+        self.torch.cuda.synchronize()
+
+    def timed(self, fn, steps, sampler=None):
+        """Per-step device times (ms) of fn, L2 flushed before each step."""
+        torch = self.torch
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        self.barrier()
+        if sampler:
+            sampler.start()
+        for k in range(steps):
+            self.flush.zero_()
+            evs[k][0].record(self.stream)
+            fn()
+            evs[k][1].record(self.stream)
+        self.barrier()
+        if sampler:
+            sampler.stop()
+        return [a.elapsed_time(b) for a, b in evs]
+
+
+def measure_rollout(cx, wl, desc, T, with_e2e=True):
+    """Autotuned persistent rollout vs the per-step forms on one workload."""
+    torch = cx.torch
+    from paper_2310_04676_gb300 import sg, workloads as W
+    args = cx.args
+    E, S, dt = desc["num_envs"], wl.substeps, wl.dt
+    acts = torch.as_tensor(W.joint_targets(desc, T, seed=2 + 1000 * cx.rank), device=cx.dev)
+    env = sg.Env(desc)
+    out = env.empty_outputs(T)
+    threads, mode, split, _ = env.autotune(acts, dt, S, out=out, repeats=3)
+    sgraph, plain = sg.Env(desc), sg.Env(desc)
+    sgraph.set_launch(threads, sg.ROLLOUT_STEP_GRAPH, split)
+    plain.set_launch(threads, sg.ROLLOUT_PERSISTENT, split)
+    out_g, out_p = sgraph.empty_outputs(T), plain.empty_outputs(T)
+
+    def plain_rollout():
+        o, r, d = out_p
+        for t in range(T):
+            plain.step(acts[t], dt, S, out=(o[t], r[t], d[t]))
+
+    forms = {"ours": lambda: env.rollout(acts, dt, S, out=out),
+             "step_graph": lambda: sgraph.rollout(acts, dt, S, out=out_g),
+             "plain": plain_rollout}
+    for _ in range(args.warmup):
+        for f in forms.values():
+            f()
+    cx.barrier()
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_r%d.csv" % cx.rank), cx.local)
+    ms = {"ours": cx.timed(forms["ours"], args.steps, clk)}
+    for k in ("step_graph", "plain"):
+        ms[k] = cx.timed(forms[k], args.steps)
+    same = True
+    qa, qda, _ = env.get_state()
+    for other, o2 in ((sgraph, out_g), (plain, out_p)):
+        qb, qdb, _ = other.get_state()
+        same = same and bool(torch.equal(qa, qb) and torch.equal(qda, qdb)
+                             and torch.equal(out[0], o2[0]))
+    res = {"T": T, "E": E, "ms": ms, "launch": (threads, mode, split), "same_bits": same,
+           "status": sg.STATUS_NAMES.get(env.sync_status()), "clocks": clk.summary(),
+           "obs_dim": env.obs_dim}
+    if with_e2e:
+        env_h = sg.Env(desc)
+        env_h.set_launch(threads, mode, split)
+        a_h = acts.cpu().pin_memory()
+        o_h = (torch.empty(T, E, env_h.obs_dim).pin_memory(), torch.empty(T, E).pin_memory(),
+               torch.empty(T, E, dtype=torch.uint8).pin_memory())
+        for _ in range(args.warmup):
+            env_h.rollout_host(a_h, dt, S, o_h)
+        res["ms_e2e"] = cx.timed(lambda: env_h.rollout_host(a_h, dt, S, o_h), args.steps)
+        res["h2d"] = T * E * env_h.max_joints * 4
+        res["d2h"] = T * E * (env_h.obs_dim * 4 + 4 + 1)
+    return res
+
+
+def measure_adjoint(cx, wl, desc, T, every=8):
+    """Differentiable rollout: checkpointed forward + adjoint, per rollout."""
+    torch = cx.torch
+    from paper_2310_04676_gb300 import sg, workloads as W
+    S, dt = wl.substeps, wl.dt
+    acts_np = W.joint_targets(desc, T, resample_every=8)
+    tg_np = W.loss_targets(desc, T)
+    acts = torch.as_tensor(acts_np, device=cx.dev)
+    tg = torch.as_tensor(tg_np, device=cx.dev)
+    env = sg.Env(desc)
+    nc = torch.as_tensor(desc["env_num_chains"], device=cx.dev)
+    mask = (torch.arange(2, device=cx.dev)[None, :] < nc[:, None]).float()[None, :, :, None]
+    res = {}
+
+    def fwd_bwd():
+        ee = env.diff_forward(acts, dt, S, every)
+        g = (2.0 * (ee - tg) * mask).contiguous()
+        res["grads"] = env.diff_backward(acts, g)
+
+    for _ in range(cx.args.warmup):
+        fwd_bwd()
+    ms = cx.timed(fwd_bwd, cx.args.steps)
+    da, dm = (x.cpu().numpy() for x in res["grads"])
+    return {"ms": ms, "T": T, "E": desc["num_envs"], "da": da, "dm": dm, "acts": acts_np,
+            "tg": tg_np, "every": every}
+
+
+def roofline(kernel_name, flops_launch, bytes_launch, ms_per_launch, props, peaks, peak_src):
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    s = ms_per_launch / 1e3
+    achieved = flops_launch / s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": profiled_traffic(kernel_name),
+            "kernel": kernel_name,
+            "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s max SM clock)"
+                           % (props.multi_processor_count, sm_max, peak_src),
+            "flops_per_launch": flops_launch, "algorithmic_bytes_per_launch": bytes_launch,
+            "hbm_gbs": bytes_launch / s / 1e9,
+            "hbm_frac": bytes_launch / s / 1e9 / float(peaks.get("hbm_gbs", 6800.0))}
+
+
+def base_line(args, world, value, ms_step, config):
+    return {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config}
+
+
+def run_rollout_config(cx, name, E=None):
+    from paper_2310_04676_gb300 import workloads as W
+    torch = cx.torch
+    wl = W.config(name, num_envs=E)
+    desc = replica_desc(wl, cx.rank)
+    T = ROLLOUT_T[name]
+    r = measure_rollout(cx, wl, desc, T, with_e2e=(name == "C3"))
+    args, world = cx.args, cx.world
+    units = r["E"] * T * args.steps
+    t = {k: sum(v) / 1e3 for k, v in r["ms"].items()}
+    value = aggregate_rate(units, t["ours"], world, cx.dev)
+    peaks, src = load_peaks()
+    props = torch.cuda.get_device_properties(cx.dev)
+    threads, mode, split = r["launch"]
+    kname = "step_kernel_pair" if split == 2 else "step_kernel"
+    flops = env_step_flops(wl.kinds, wl.substeps, int(desc["task"])) * T
+    nbytes = env_step_bytes(desc, r["obs_dim"]) * T
+    ms_launch = sum(r["ms"]["ours"]) / len(r["ms"]["ours"])
+    cfg = {"workload": wl.name, "envs_per_gpu": r["E"], "rollout_steps": T,
+           "substeps": wl.substeps, "dt": wl.dt, "form": "persistent kernel in a CUDA graph",
+           "launch": {"threads_per_block": threads, "mode": ["persistent", "step_graph"][mode],
+                      "chain_split": split},
+           "l2": "flushed (256 MiB write) before every timed step"}
+    line = base_line(args, world, value, 1e3 * t["ours"] / args.steps, cfg)
+    line["us_per_control_step"] = 1e6 * t["ours"] / args.steps / T
+    for k, label in (("step_graph", "%d single-step kernels replayed from a CUDA graph" % T),
+                     ("plain", "one sg_step call (one kernel launch) per control step")):
+        line[k] = {"value": aggregate_rate(units, t[k], world, cx.dev), "unit": "env-steps/s",
+                   "ms_per_step": 1e3 * t[k] / args.steps, "form": label,
+                   "gpu_launches": T * args.steps}
+    line["batched_over_plain"] = t["plain"] / t["ours"]
+    line["batched_over_step_graph"] = t["step_graph"] / t["ours"]
+    line["bitwise_equal_forms"] = r["same_bits"]
+    line["status"] = r["status"]
+    line["roofline"] = roofline(kname, flops, nbytes, ms_launch, props, peaks, src)
+    if "ms_e2e" in r:
+        te = sum(r["ms_e2e"]) / 1e3
+        line["e2e"] = {"value": aggregate_rate(units, te, world, cx.dev), "unit": "env-steps/s",
+                       "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]}
+    line["gpu_launches"] = args.steps
+    line["clocks"] = r["clocks"]
+    return line, wl
+
+
+def run_adjoint_config(cx, with_error):
+    from paper_2310_04676_gb300 import workloads as W
+    wl = W.config("C4")
+    desc = replica_desc(wl, cx.rank)
+    a = measure_adjoint(cx, wl, desc, wl.steps, every=8)
+    t = sum(a["ms"]) / 1e3
+    units = a["E"] * a["T"] * cx.args.steps
+    out = {"workload": "%s, T=%d, S=%d, checkpoints every %d steps"
+                       % (wl.name, a["T"], wl.substeps, a["every"]),
+           "value": aggregate_rate(units, t, cx.world, cx.dev),
+           "unit": "env-steps/s (forward with checkpoints + adjoint)",
+           "ms_per_rollout": 1e3 * t / cx.args.steps,
+           "gpu_launches": 2 * cx.args.steps}
+    if with_error:
+        ea, em = grad_error(wl, a["acts"], a["tg"], a["da"], a["dm"])
+        out["rel_err_actions"] = ea
+        out["rel_err_mass"] = em
+        out["error_vs"] = "FP64 oracle reverse mode, 16 envs, max per-env relative L2 error"
+    return out
 
 
 def run_reference(args):
@@ -151,23 +436,18 @@ def run_reference(args):
         return
     from paper_2310_04676_gb300 import workloads as W
     wl = W.config("C3")
-    vals = []
-    samples = []
     per = max(2.0, 150.0 / max(1, args.steps + args.warmup))
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(wl, seconds=per)
-        if i >= args.warmup:
-            vals.append(cb["value"])
-            samples.append(cb)
-    v = float(np.median(vals))
-    cb = dict(samples[-1])
+    runs = [cpu_baseline(wl, seconds=per) for _ in range(args.warmup + args.steps)]
+    v = float(np.median([r["value"] for r in runs[args.warmup:]]))
+    cb = dict(runs[-1])
     cb["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "env-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * T_ROLLOUT * wl.desc["num_envs"] / v,
+            "ms_per_step": 1e3 * ROLLOUT_T["C3"] * wl.desc["num_envs"] / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": wl.name, "rollout_steps": T_ROLLOUT,
-                                            "substeps": wl.substeps, "dt": wl.dt},
+            "data": "synthetic",
+            "config": {"workload": wl.name, "rollout_steps": ROLLOUT_T["C3"],
+                       "substeps": wl.substeps, "dt": wl.dt},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -180,196 +460,46 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="C3", choices=["C1", "C2", "C3", "C4", "C5"])
+    ap.add_argument("--envs", type=int, nargs="*", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
+    args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
 
     import torch
-    from paper_2310_04676_gb300 import sg, workloads as W
-
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    dev = torch.device("cuda", local)
+    cx = Ctx(args, world, rank, local)
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
 
-    wl = W.config("C3")
-    desc = wl.desc
-    if rank:
-        # independent replica per rank: its own link parameters and goals
-        desc = W.make_desc(wl.kinds, seed_params=1 + 1000 * rank, seed_goals=3 + 1000 * rank,
-                           episode_len=1000)
-    E = desc["num_envs"]
-    T, S, dt = T_ROLLOUT, wl.substeps, wl.dt
-    acts = torch.as_tensor(W.joint_targets(desc, T, seed=2 + 1000 * rank), device=dev)
-    stream = torch.cuda.current_stream()
-
-    env = sg.Env(desc)                 # persistent kernel in a CUDA graph (autotuned)
-    sgraph = sg.Env(desc)              # T single-step kernels replayed from a CUDA graph
-    plain = sg.Env(desc)               # T sg_step calls from the host
-    out = env.empty_outputs(T)
-    out_g = sgraph.empty_outputs(T)
-    out_p = plain.empty_outputs(T)
-    threads, mode, split, tune_ms = env.autotune(acts, dt, S, out=out, repeats=3)
-    sgraph.set_launch(threads, sg.ROLLOUT_STEP_GRAPH, split)
-    plain.set_launch(threads, sg.ROLLOUT_PERSISTENT, split)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-
-    def plain_rollout():
-        o, r, d = out_p
-        for t in range(T):
-            plain.step(acts[t], dt, S, out=(o[t], r[t], d[t]))
-
-    forms = {
-        "ours": lambda: env.rollout(acts, dt, S, out=out),
-        "step_graph": lambda: sgraph.rollout(acts, dt, S, out=out_g),
-        "plain": plain_rollout,
-    }
-    for _ in range(args.warmup):
-        for f in forms.values():
-            f()
-    barrier()
-
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_r%d.csv" % rank), local)
-
-    def timed(fn, sampler=None):
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        barrier()
-        if sampler:
-            sampler.__enter__()
-        for k in range(args.steps):
-            flush.zero_()                       # L2 flush, outside the timed events
-            evs[k][0].record(stream)
-            fn()
-            evs[k][1].record(stream)
-        barrier()
-        if sampler:
-            sampler.__exit__(None, None, None)
-        return [a.elapsed_time(b) for a, b in evs]
-
-    ms = timed(forms["ours"], clk)
-    ms_g = timed(forms["step_graph"])
-    ms_p = timed(forms["plain"])
-    t_ours, t_graph, t_plain = sum(ms) / 1e3, sum(ms_g) / 1e3, sum(ms_p) / 1e3
-
-    # identical arithmetic: all forms ran the same rollouts from the same state
-    qa, qda, _ = env.get_state()
-    same_bits = True
-    for other, o2 in ((sgraph, out_g), (plain, out_p)):
-        qb, qdb, _ = other.get_state()
-        same_bits = same_bits and bool(torch.equal(qa, qb) and torch.equal(qda, qdb)
-                                       and torch.equal(out[0], o2[0]))
-    status = env.sync_status()
-
-    # ---- end to end through the C ABI with host buffers
-    env_h = sg.Env(desc)
-    env_h.set_launch(threads, mode, split)
-    a_h = acts.cpu().pin_memory()
-    o_h = (torch.empty(T, E, env_h.obs_dim).pin_memory(), torch.empty(T, E).pin_memory(),
-           torch.empty(T, E, dtype=torch.uint8).pin_memory())
-    for _ in range(args.warmup):
-        env_h.rollout_host(a_h, dt, S, o_h)
-    barrier()
-    eve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    for k in range(args.steps):
-        eve[k][0].record(stream)
-        env_h.rollout_host(a_h, dt, S, o_h)
-        eve[k][1].record(stream)
-    barrier()
-    t_e2e = sum(a.elapsed_time(b) for a, b in eve) / 1e3
-    h2d = T * E * env_h.max_joints * 4
-    d2h = T * E * (env_h.obs_dim * 4 + 4 + 1)
-
-    # ---- aggregate over ranks (max time)
-    def rmax(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
-    t_ours, t_graph, t_plain, t_e2e = rmax(t_ours), rmax(t_graph), rmax(t_plain), rmax(t_e2e)
-    units = world * E * T * args.steps
-    value = units / t_ours
-
-    peaks, peak_src = load_peaks()
-    props = torch.cuda.get_device_properties(dev)
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-    flops_launch = env_step_flops(wl.kinds if rank == 0 else wl.kinds, S) * T
-    kernel_s = (sum(ms) / len(ms)) / 1e3
-    achieved = flops_launch / kernel_s / 1e12
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-    if os.path.exists(tfile):
-        with open(tfile) as f:
-            tj = json.load(f)
-        if tj.get("kernel_source_hash") == _source_hash():
-            traffic = tj.get("bytes_per_launch")
-
-    if rank == 0:
-        cb = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(wl)
-        line = {
-            "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t_ours / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl.name, "envs_per_gpu": E, "rollout_steps": T,
-                       "substeps": S, "dt": dt, "form": "persistent kernel in a CUDA graph",
-                       "launch": {"threads_per_block": threads,
-                                  "mode": ["persistent", "step_graph"][mode],
-                                  "chain_split": split},
-                       "l2": "flushed (256 MiB write) before every timed step"},
-            "plain": {"value": world * E * T * args.steps / t_plain, "unit": "env-steps/s",
-                      "ms_per_step": 1e3 * t_plain / args.steps,
-                      "form": "one sg_step call (one kernel launch) per control step",
-                      "gpu_launches": T * args.steps},
-            "step_graph": {"value": world * E * T * args.steps / t_graph, "unit": "env-steps/s",
-                           "ms_per_step": 1e3 * t_graph / args.steps,
-                           "form": "32 single-step kernels replayed from a CUDA graph",
-                           "gpu_launches": T * args.steps},
-            "batched_over_plain": t_plain / t_ours,
-            "batched_over_step_graph": t_graph / t_ours,
-            "bitwise_equal_forms": same_bits,
-            "status": sg.STATUS_NAMES.get(status, status),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                         "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-                         "kernel": "%s (persistent, T=32)" % (
-                             "step_kernel_pair" if split == 2 else "step_kernel"),
-                         "peak_source": "SMs x 128 FP32 lanes x 2 x %.0f MHz (%s max clock)"
-                                        % (sm_max, peak_src),
-                         "flops_per_launch": flops_launch,
-                         "hbm_gbs": env_step_bytes(desc, env.obs_dim) * T / kernel_s / 1e9},
-            "e2e": {"value": units / t_e2e, "unit": "env-steps/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps,
-            "clocks": clk.summary(),
-            "cpu_baseline": cb,
-        }
-        print(json.dumps(line))
+    if args.config == "C4":
+        g = run_adjoint_config(cx, with_error=want_cpu)
+        if rank == 0:
+            line = base_line(args, world, g["value"], g["ms_per_rollout"],
+                             {"workload": g["workload"]})
+            line["unit"] = g["unit"]
+            line["grad"] = g
+            line["gpu_launches"] = g["gpu_launches"]
+            print(json.dumps(line))
+    elif args.config == "C5" or args.envs:
+        for E in (args.envs or [1024, 4096, 16384, 65536, 262144]):
+            line, _ = run_rollout_config(cx, args.config, E)
+            if rank == 0:
+                print(json.dumps(line))
+    else:
+        line, wl = run_rollout_config(cx, args.config)
+        if args.config == "C3":
+            line["grad"] = run_adjoint_config(cx, with_error=want_cpu)
+        if rank == 0:
+            line["cpu_baseline"] = cpu_baseline(wl) if want_cpu else None
+            print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
-
-
-def _source_hash():
-    import hashlib
-    h = hashlib.sha256()
-    for f in ("sg_chain.cuh", "sg_kernels.cu"):
-        with open(os.path.join(ROOT, "paper_2310_04676_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
 
 
 if __name__ == "__main__":
