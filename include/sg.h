@@ -62,6 +62,12 @@ enum {
 };
 
 enum {
+  SG_DRIVE_POSITION = 0,    /* command = PD position target q* */
+  SG_DRIVE_VELOCITY = 1,    /* command = velocity target qd* */
+  SG_DRIVE_TORQUE = 2       /* command = joint torque / force */
+};
+
+enum {
   SG_DONE_TERMINATED = 1,   /* reserved: termination (never set by the tasks here) */
   SG_DONE_TIMEOUT = 2,      /* step count since reset reached episode_len */
   SG_DONE_NONFINITE = 4     /* q or qd became non-finite in this step */
@@ -88,9 +94,14 @@ enum {
  * about the centre of mass.  The tool tip of a chain is (0, 0, link_len)
  * of its last link.  Gravity is 9.81 m/s^2 along -z.
  *
- * Drive of joint i with target q*: tau = kp (q* - q) - (kd + damping) qd
- * + tau_lim, where tau_lim = -k_limit (q - q_hi) above q_hi,
- * -k_limit (q - q_lo) below q_lo, 0 inside.
+ * Drive of joint i with command a (Methods, "Simulation Setup": PD position
+ * or velocity targets, or torques), by joint_drive:
+ *   SG_DRIVE_POSITION: tau = kp (a - q) - (kd + damping) qd + tau_lim
+ *   SG_DRIVE_VELOCITY: tau = kd (a - qd) - damping qd + tau_lim
+ *   SG_DRIVE_TORQUE:   tau = a - damping qd + tau_lim
+ * where tau_lim = -k_limit (q - q_hi) above q_hi, -k_limit (q - q_lo) below
+ * q_lo, 0 inside.  Stiffness and damping act implicitly (at the end of each
+ * substep).  joint_drive may be NULL: all position targets.
  */
 typedef struct sg_desc {
   int32_t num_envs;                 /* E >= 1 */
@@ -114,6 +125,7 @@ typedef struct sg_desc {
   const float *path;                /* [E][path_len][3] waypoints (SG_TASK_PATH), else NULL */
   int32_t path_len;                 /* W >= 4 for SG_TASK_PATH */
   float alpha;                      /* path reward scale */
+  const int32_t *joint_drive;       /* [E][J] SG_DRIVE_*, or NULL (all position) */
 } sg_desc;
 
 /*
@@ -161,7 +173,8 @@ int32_t sg_max_joints(const sg_ctx *ctx);
 sg_status sg_reset(sg_ctx *ctx, const uint8_t *env_mask_dev);
 
 /* One control step of every env.
- *   actions_dev [E][J] float: PD position targets q* (padding ignored)
+ *   actions_dev [E][J] float: joint commands (position / velocity targets or
+ *               torques, per joint_drive; padding ignored)
  *   dt > 0 seconds, substeps 1..64 (substep length dt / substeps)
  *   obs_dev [E][D] float, reward_dev [E] float, done_dev [E] uint8 (outputs)
  * Does not reset envs: the caller passes done-derived masks to sg_reset. */

@@ -182,19 +182,34 @@ def limit_state(P, q):
     return tau_lim, (hi | lo)
 
 
+def drive_law(P, q, qd, a):
+    """Joint torque of the drive and its implicit coefficients, per joint
+    command type (Methods, "Simulation Setup": position or velocity PD
+    targets, or torques):
+        position: tau = kp (a - q) - (kd + b) qd + tau_lim,  k_s = kp + k_lim[act], d = kd + b
+        velocity: tau = kd (a - qd) - b qd + tau_lim,        k_s = k_lim[act],      d = kd + b
+        torque:   tau = a - b qd + tau_lim,                  k_s = k_lim[act],      d = b
+    Returns (tau, k_s, d)."""
+    tau_lim, active = limit_state(P, q)
+    klim = P.klim * active.to(DT)
+    pos, vel = P.drive == 0, P.drive == 1
+    tau = torch.where(pos, P.kp * (a - q) - (P.kd + P.b) * qd,
+                      torch.where(vel, P.kd * (a - qd) - P.b * qd, a - P.b * qd)) + tau_lim
+    ks = torch.where(pos, P.kp + klim, klim)
+    d = torch.where(pos | vel, P.kd + P.b, P.b)
+    return tau, ks, d
+
+
 def substep(tree, P, q, qd, qstar, h, gravity=GRAVITY):
     """One implicit-drive semi-implicit Euler substep of length h.
 
-    With k_s = kp + k_limit * [limit active at the substep start] and
-    d = kd + damping, the velocity change solves
+    With the drive torque tau_d, stiffness k_s and damping d of
+    ``drive_law`` (all taken at the substep start), the velocity change solves
         (M(q) + h d I + h^2 k_s I) dqd = h (tau_d - h k_s qd - c(q, qd)),
-        tau_d = kp (q* - q) - d qd + tau_lim(q),
-    then qd' = qd + dqd and q' = q + h qd'.  Returns (q', qd', dqd/h).
+    i.e. stiffness and damping act at the end-of-substep state; then
+    qd' = qd + dqd and q' = q + h qd'.  Returns (q', qd', dqd/h).
     """
-    tau_lim, active = limit_state(P, q)
-    ks = P.kp + P.klim * active.to(DT)
-    d = P.kd + P.b
-    tau_d = P.kp * (qstar - q) - d * qd + tau_lim
+    tau_d, ks, d = drive_law(P, q, qd, qstar)
     c = rnea(tree, P, q, qd, torch.zeros_like(q), gravity)
     M = crba(tree, P, q)
     A = M + torch.diag_embed(h * d + h * h * ks)

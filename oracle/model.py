@@ -49,6 +49,7 @@ class Params:
     kd: torch.Tensor
     b: torch.Tensor
     klim: torch.Tensor
+    drive: torch.Tensor    # [E, n] 0 position, 1 velocity, 2 torque command
     XT: list               # n x [E, 6, 6] fixed parent->joint transforms
     I: list                # n x [E, 6, 6] spatial inertias about link origins
 
@@ -102,8 +103,11 @@ def make_params(tree, desc, env_idx, mass=None):
         XT.append(plucker(eye, r))
         com = torch.stack([torch.zeros(E, dtype=DT), torch.zeros(E, dtype=DT), c[:, i]], -1)
         I.append(mcI(m[:, i], com, torch.diag_embed(Ic[:, i])))
+    jd = desc.get("joint_drive")
+    drive = (torch.zeros(E, n, dtype=torch.long) if jd is None
+             else torch.as_tensor(np.asarray(jd, dtype=np.int64)[env_idx][:, :n]))
     return Params(L, c, m, Ic, base, t(desc["q_lo"]), t(desc["q_hi"]), t(desc["kp"]),
-                  t(desc["kd"]), t(desc["damping"]), t(desc["k_limit"]), XT, I)
+                  t(desc["kd"]), t(desc["damping"]), t(desc["k_limit"]), drive, XT, I)
 
 
 def groups(desc):

@@ -7,7 +7,7 @@
 // theorem gives, for a cotangent lambda on dqd and mu = A^{-1} lambda:
 //   lambda_q  += -h k_s mu - h (dID/dq)^T mu
 //   lambda_qd += -h d mu - h^2 k_s mu - h (dID/dqd)^T mu
-//   lambda_q* +=  h kp mu
+//   lambda_q* +=  h (kp + g) mu            (g: command gain of the joint)
 //   lambda_m  += -h (dID/dm)^T mu            (a held fixed)
 // The vector-Jacobian product of ID is the reverse of the body-frame RNEA
 // below (forward sweep with qdd = a, backward sweep storing the link
@@ -306,10 +306,10 @@ __device__ __forceinline__ void substep_adjoint(const Pat& pat, const Rec& rec, 
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     if (!pat.active(i)) continue;
-    const float kp = rec.lf(i, LF_KP), d = rec.lf(i, LF_D);
+    const float kp = rec.lf(i, LF_KP), d = rec.lf(i, LF_D), ga = rec.lf(i, LF_GA);
     lq[i] += -h * ks[i] * mu[i] - h * gq[i];
     lqd[i] += -h * d * mu[i] - h * h * ks[i] * mu[i] - h * gqd[i];
-    lqs[i] += h * kp * mu[i];
+    lqs[i] += h * (kp + ga) * mu[i];
     lm[i] += -h * gm[i];
   }
 }

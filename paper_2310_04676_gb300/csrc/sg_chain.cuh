@@ -291,7 +291,10 @@ __device__ __forceinline__ void backward_sweep(const Pat& pat, const Rec& rec, c
 }
 
 // Implicit drive terms: arm = h d + h^2 k_s (added to the diagonal of M) and
-// rhs = h (tau_d - h k_s qd - c).
+// rhs = h (tau_d - h k_s qd - c), with the drive torque
+// tau_d = kp (q* - q) + g q* - d qd + tau_lim: the command q* is a position
+// target (g = 0), a velocity target (kp = 0, g = kd) or a torque (kp = 0,
+// g = 1, d = joint damping only), as packed per joint.
 template <class Pat>
 __device__ __forceinline__ void drive_terms(const Pat& pat, const Rec& rec, const float (&q)[7],
                                             const float (&qd)[7], const float (&qs)[7], float h,
@@ -303,6 +306,7 @@ __device__ __forceinline__ void drive_terms(const Pat& pat, const Rec& rec, cons
   for (int i = 0; i < N; ++i) {
     if (!pat.active(i)) continue;
     const float kp = rec.lf(i, LF_KP), d = rec.lf(i, LF_D), kl = rec.lf(i, LF_KLIM);
+    const float ga = rec.lf(i, LF_GA);
     const float lo = rec.lf(i, LF_QLO), hi = rec.lf(i, LF_QHI);
     float ks = kp, tl = 0.f;
     if (q[i] > hi) {
@@ -312,7 +316,7 @@ __device__ __forceinline__ void drive_terms(const Pat& pat, const Rec& rec, cons
       ks += kl;
       tl = -kl * (q[i] - lo);
     }
-    const float tau = kp * (qs[i] - q[i]) - d * qd[i] + tl;
+    const float tau = kp * (qs[i] - q[i]) + ga * qs[i] - d * qd[i] + tl;
     rhs[i] = h * (tau - h * ks * qd[i] - bias[i]);
     arm[i] = h * d + hh * ks;
   }

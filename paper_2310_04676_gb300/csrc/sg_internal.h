@@ -29,10 +29,10 @@ enum LinkField {
   LF_M,         // mass
   LF_IX, LF_IY, LF_IZ,   // rotational inertia about the COM
   LF_QLO, LF_QHI,
-  LF_KP,
-  LF_D,         // kd + damping
+  LF_KP,        // position stiffness kp (0 for velocity / torque commands)
+  LF_D,         // implicit damping: kd + damping (position, velocity) or damping (torque)
   LF_KLIM,
-  LF_PAD
+  LF_GA         // command gain: 0 (position), kd (velocity), 1 (torque)
 };
 
 // Chain classes: a warp holds 32 chain slots of one class, all single-chain

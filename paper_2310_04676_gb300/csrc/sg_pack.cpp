@@ -106,6 +106,8 @@ sg_status build_plan(const sg_desc* d, Plan* P, std::string* err) {
           return fail(SG_ERR_INVALID_ARG, "link_inertia entries must be > 0");
         if (d->kp[k] < 0.f || d->kd[k] < 0.f || d->damping[k] < 0.f || d->k_limit[k] < 0.f)
           return fail(SG_ERR_INVALID_ARG, "gains and damping must be >= 0");
+        if (d->joint_drive && (d->joint_drive[k] < SG_DRIVE_POSITION || d->joint_drive[k] > SG_DRIVE_TORQUE))
+          return fail(SG_ERR_INVALID_ARG, "joint_drive must be 0 (position), 1 (velocity) or 2 (torque)");
       }
       cls[c] = classify(n, ty, ax);
       ntot += n;
@@ -201,9 +203,11 @@ sg_status build_plan(const sg_desc* d, Plan* P, std::string* err) {
       LF(i, LF_IZ) = d->link_inertia[3 * k + 2];
       LF(i, LF_QLO) = d->q_lo[k];
       LF(i, LF_QHI) = d->q_hi[k];
-      LF(i, LF_KP) = d->kp[k];
-      LF(i, LF_D) = d->kd[k] + d->damping[k];
+      const int mode = d->joint_drive ? d->joint_drive[k] : SG_DRIVE_POSITION;
+      LF(i, LF_KP) = mode == SG_DRIVE_POSITION ? d->kp[k] : 0.f;
+      LF(i, LF_D) = mode == SG_DRIVE_TORQUE ? d->damping[k] : d->kd[k] + d->damping[k];
       LF(i, LF_KLIM) = d->k_limit[k];
+      LF(i, LF_GA) = mode == SG_DRIVE_POSITION ? 0.f : (mode == SG_DRIVE_VELOCITY ? d->kd[k] : 1.f);
       P->q0[(size_t)i * NS + s] = d->q0[k];
       P->mass0[(size_t)i * NS + s] = d->link_mass[k];
       for (int a = 0; a < 3; ++a)

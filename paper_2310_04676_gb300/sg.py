@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_CUDA", 3: "SG_ER
                 4: "SG_ERR_NONFINITE", 5: "SG_ERR_TIMEOUT", 6: "SG_ERR_UNSUPPORTED"}
 DONE_TERMINATED, DONE_TIMEOUT, DONE_NONFINITE = 1, 2, 4
 ROLLOUT_PERSISTENT, ROLLOUT_STEP_GRAPH = 0, 1
+DRIVE_POSITION, DRIVE_VELOCITY, DRIVE_TORQUE = 0, 1, 2
 
 
 class SgError(RuntimeError):
@@ -42,6 +43,7 @@ class SgDesc(ctypes.Structure):
         ("episode_len", ctypes.c_int32), ("task", ctypes.c_int32),
         ("goal", _c_f32p), ("path", _c_f32p), ("path_len", ctypes.c_int32),
         ("alpha", ctypes.c_float),
+        ("joint_drive", _c_i32p),
     ]
 
 
@@ -134,6 +136,7 @@ def make_c_desc(desc):
     d.episode_len = int(desc["episode_len"])
     d.task = int(desc["task"])
     d.alpha = float(desc.get("alpha", 1.0))
+    d.joint_drive = p("joint_drive", i32, (E, J), _c_i32p)
     return d, keep
 
 

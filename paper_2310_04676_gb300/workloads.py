@@ -60,8 +60,11 @@ def _box_inertia(m, L, w=BOX_WIDTH):
 
 def make_desc(kinds, *, seed_params=1, seed_goals=3, shared_params=False,
               k_limit=0.0, kp=50.0, kd=5.0, damping=0.1, episode_len=1000,
-              task=0, path_len=0, alpha=1.0, max_joints=None):
+              task=0, path_len=0, alpha=1.0, max_joints=None, drive=None):
     """Build an ``sg_desc`` dictionary for a list of arm kinds (one per env).
+
+    ``drive`` selects the joint command type (0 position target, 1 velocity
+    target, 2 torque): None (all position), an int, or an [E][J] array.
 
     Link lengths ~ U[0.05, 0.4] m and masses ~ U[0.1, 1.0] kg per link,
     solid-box inertias of width BOX_WIDTH, COM at mid-length, revolute
@@ -126,6 +129,9 @@ def make_desc(kinds, *, seed_params=1, seed_goals=3, shared_params=False,
             centre = np.array([0.3 * reach, 0.0, 0.5 * reach]) + d["base_offset"][e, c]
             d["goal"][e, c] = centre + rg.uniform(-0.15, 0.15, size=3)
             j0 += n
+    if drive is not None:
+        # joint command type: one code for all joints, or an [E][J] array
+        d["joint_drive"] = np.broadcast_to(np.asarray(drive, np.int32), (E, J)).copy()
     if task == 1:
         if any(len(KINDS[k]["chains"]) != 1 for k in kinds):
             raise ValueError("path following is defined for single-chain arms")

@@ -4,7 +4,7 @@ import numpy as np
 
 def chain_desc(chains, E=1, *, kp=0.0, kd=0.0, damping=0.0, k_limit=0.0,
                q_lo=-1.5707963, q_hi=1.5707963, base=None, episode_len=100, seed=0,
-               width=0.05, L=None, m=None):
+               width=0.05, L=None, m=None, drive=None):
     """``chains`` = list of (types, axes) per chain.  Link lengths/masses are
     drawn U[0.05, 0.4] / U[0.1, 1.0] unless given; inertias are solid boxes of
     side ``width`` (given to the oracle as plain inputs)."""
@@ -43,4 +43,6 @@ def chain_desc(chains, E=1, *, kp=0.0, kd=0.0, damping=0.0, k_limit=0.0,
                 d["kp"][e, j], d["kd"][e, j], d["damping"][e, j] = kp, kd, damping
                 d["k_limit"][e, j] = k_limit
                 j += 1
+    if drive is not None:
+        d["joint_drive"] = np.broadcast_to(np.asarray(drive, np.int32), (E, J)).copy()
     return d

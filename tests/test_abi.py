@@ -72,6 +72,7 @@ def test_plan_generic_class_and_path_obs(lib):
      sg.SG_ERR_UNSUPPORTED),
     (lambda d: d.__setitem__("episode_len", 0), sg.SG_ERR_INVALID_ARG),
     (lambda d: d.__setitem__("task", 7), sg.SG_ERR_INVALID_ARG),
+    (lambda d: d.__setitem__("joint_drive", np.full((2, 7), 3, np.int32)), sg.SG_ERR_INVALID_ARG),
 ])
 def test_plan_rejects_bad_descriptions(lib, mutate, code):
     d = W.make_desc(["7R", "4R"])

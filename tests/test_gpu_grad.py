@@ -188,3 +188,15 @@ def test_autograd_function_and_set_link_mass():
                                 np.arange(64))
     assert rel_env(acts.grad.cpu().numpy(), ga) <= 1e-3
     assert rel_env(mass.grad.cpu().numpy(), gm) <= 1e-3
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_adjoint_velocity_and_torque_commands(mode):
+    E, T, S = 32, 10, 2
+    desc = W.make_desc(["7R"] * E, drive=mode)
+    acts = W.joint_targets(desc, T, resample_every=4)
+    tg = W.loss_targets(desc, T)
+    _, da, dm = gpu_grads(desc, acts, tg, S, 4)
+    _, ga, gm, n = oracle_grads(desc, acts, tg, S, np.arange(E))
+    assert max(rel_env(da[:, e, :n], ga[:, e]) for e in range(E)) <= 1e-3
+    assert max(rel_env(dm[e, :n], gm[e]) for e in range(E)) <= 1e-3

@@ -272,3 +272,84 @@ def test_full_size_mixed_batch_sampled_parity():
     acc_gpu = (qd1.cpu().numpy()[pick].astype(np.float64) - qd[pick]) / wl.dt
     acc_ref = (ref.qd - qd[pick]) / wl.dt
     assert rel_rows(acc_gpu, acc_ref).max() <= 1e-4
+
+
+def _sub_desc(desc, pick):
+    E = desc["num_envs"]
+    sub = {k: (v[pick] if isinstance(v, np.ndarray) and v.shape[:1] == (E,) else v)
+           for k, v in desc.items()}
+    sub["num_envs"] = len(pick)
+    return sub
+
+
+def test_c1_latency_workload_trajectory():
+    """64 envs of one shared 7-DOF arm: 100 steps as two 50-step rollouts in
+    the autotuned plan; positions within 1e-3 and rewards within 1e-3 of the
+    oracle, time-out bit at the episode length."""
+    wl = W.config("C1")
+    desc = dict(wl.desc)
+    desc["episode_len"] = 100
+    env, ref = sg.Env(desc), OracleEnv(desc)
+    acts = W.joint_targets(desc, 100)
+    a = cuda(acts)
+    env.autotune(a[:50], wl.dt, wl.substeps)
+    for half in range(2):
+        obs, rew, done = env.rollout(a[50 * half:50 * (half + 1)], wl.dt, wl.substeps)
+    for t in range(100):
+        _, r_ref, d_ref = ref.step(acts[t], wl.dt, wl.substeps)
+    q, qd, sc = env.get_state()
+    assert rel_rows(q.cpu().numpy().astype(np.float64), ref.q).max() <= 1e-3
+    assert np.abs(rew[-1].cpu().numpy() - r_ref).max() <= 1e-3
+    assert (done[-1].cpu().numpy() == d_ref).all() and (d_ref == 2).all()
+
+
+def test_c2_path_following_full_size_sampled():
+    """8192 envs path following, one 50-step rollout in the autotuned plan;
+    64 sampled envs against the oracle (positions 1e-3, rewards 1e-3)."""
+    wl = W.config("C2")
+    desc = wl.desc
+    env = sg.Env(desc)
+    acts = W.joint_targets(desc, 50)
+    a = cuda(acts)
+    env.autotune(a, wl.dt, wl.substeps)
+    obs, rew, done = env.rollout(a, wl.dt, wl.substeps)
+    pick = np.random.default_rng(1).choice(desc["num_envs"], 64, replace=False)
+    ref = OracleEnv(_sub_desc(desc, pick))
+    for t in range(50):
+        _, r_ref, _ = ref.step(acts[t][pick], wl.dt, wl.substeps)
+    q, _, _ = env.get_state()
+    assert rel_rows(q.cpu().numpy()[pick].astype(np.float64), ref.q).max() <= 1e-3
+    assert np.abs(rew[-1].cpu().numpy()[pick] - r_ref).max() <= 1e-3
+
+
+def test_c5_largest_sweep_point_sampled():
+    """262144 envs with limit springs and 8 substeps (the largest sweep
+    point) in the autotuned plan: one step from a random state, 128 sampled
+    envs' accelerations within 1e-4 of the oracle."""
+    wl = W.config("C5", num_envs=262144)
+    desc = wl.desc
+    env = sg.Env(desc)
+    acts = W.joint_targets(desc, 2)
+    env.autotune(cuda(acts[:1]), wl.dt, wl.substeps, repeats=1)
+    q, qd = random_state(desc, 21)
+    env.set_state(cuda(q), cuda(qd))
+    env.rollout(cuda(acts[1:2]), wl.dt, wl.substeps)
+    q1, qd1, _ = env.get_state()
+    pick = np.random.default_rng(2).choice(desc["num_envs"], 128, replace=False)
+    ref = OracleEnv(_sub_desc(desc, pick))
+    ref.set_state(q[pick], qd[pick])
+    ref.step(acts[1][pick], wl.dt, wl.substeps)
+    acc_gpu = (qd1.cpu().numpy()[pick].astype(np.float64) - qd[pick]) / wl.dt
+    acc_ref = (ref.qd - qd[pick]) / wl.dt
+    assert rel_rows(acc_gpu, acc_ref).max() <= 1e-4
+
+
+@pytest.mark.parametrize("split", [1, 2])
+def test_velocity_and_torque_commands_match_oracle(split):
+    """Per-joint mix of position targets, velocity targets and torques."""
+    kinds = (["7R", "4R", "7P", "14B"] * 50)[:190]
+    E = len(kinds)
+    modes = np.random.default_rng(8).integers(0, 3, size=(E, 14)).astype(np.int32)
+    desc = W.make_desc(kinds, drive=modes, k_limit=1e3)
+    rel, env, *_ = one_step_accel(desc, 2, seed=3, split=split)
+    assert rel.max() <= 1e-4, rel.max()

@@ -50,3 +50,23 @@ def test_reverse_mode_matches_central_differences():
     rel = lambda x, y: ((x - y).abs().max() / y.abs().max()).item()
     assert rel(ga, fd_a) < 1e-6
     assert rel(gm, fd_m) < 1e-6
+
+
+def test_reverse_mode_matches_central_differences_velocity_and_torque_commands():
+    E, T, S, n = 2, 3, 2, 7
+    for mode in (1, 2):
+        d = W.make_desc(["7R"] * E, drive=mode)
+        acts = torch.as_tensor(W.joint_targets(d, T)[:, :, :n], dtype=D)
+        tg = torch.as_tensor(W.loss_targets(d, T)[:, :, :1], dtype=D)
+        a = acts.clone().requires_grad_(True)
+        L = _loss(d, a, None, tg, np.arange(E), T, S)
+        ga, = torch.autograd.grad(L.sum(), [a])
+        h = 1e-6
+        for (t, j) in [(0, 0), (1, 3), (2, 6), (0, 5)]:
+            ap, am = acts.clone(), acts.clone()
+            ap[t, :, j] += h
+            am[t, :, j] -= h
+            with torch.no_grad():
+                fd = (_loss(d, ap, None, tg, np.arange(E), T, S)
+                      - _loss(d, am, None, tg, np.arange(E), T, S)) / (2 * h)
+            assert torch.allclose(ga[t, :, j], fd, rtol=1e-6, atol=1e-9)

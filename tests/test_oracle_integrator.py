@@ -139,3 +139,48 @@ def test_limit_spring_pushes_back():
     assert active.all()
     assert tau[0, 0] < 0 and tau[1, 0] > 0
     assert np.isclose(tau[0, 0].item(), -1e3 * (2.0 - P.q_hi[0, 0].item()))
+
+
+def test_torque_command_pendulum_closed_form():
+    """Torque commands (no damping): qd' = qd + h (a + m g c sin q) / I_p."""
+    d = chain_desc([([0], [1])], E=3, seed=21, drive=2, kp=50.0, kd=5.0)
+    tree, P = single(d)
+    q, qd, a = rand((3, 1), 22, 1.5), rand((3, 1), 23, 1.0), rand((3, 1), 24, 2.0)
+    h = 1.0 / 240
+    q1, qd1, _ = dyn.substep(tree, P, q, qd, a, h)
+    m, c, Iyy = P.m[:, 0], P.c[:, 0], P.Ic[:, 0, 1]
+    acc = (a[:, 0] + m * G * c * torch.sin(q[:, 0])) / (Iyy + m * c * c)
+    assert torch.allclose(qd1[:, 0], qd[:, 0] + h * acc, rtol=1e-13)
+
+
+def test_velocity_command_converges_to_damped_target_speed():
+    """A free joint about the vertical axis under a velocity target v*:
+    I qdd = kd (v* - qd) - b qd, so qd -> kd v* / (kd + b)."""
+    d = chain_desc([([0], [2])], E=2, seed=25, drive=1, kp=50.0, kd=5.0, damping=0.4)
+    tree, P = single(d)
+    q, qd = torch.zeros(2, 1, dtype=D), torch.zeros(2, 1, dtype=D)
+    v = torch.tensor([[1.5], [-0.7]], dtype=D)
+    for _ in range(2000):
+        q, qd, _ = dyn.substep(tree, P, q, qd, v, 1.0 / 120)
+    assert torch.allclose(qd, v * 5.0 / 5.4, rtol=1e-9)
+
+
+def test_command_types_residual():
+    """Every command type satisfies its implicit-drive equation
+    M (qd' - qd)/h + c = tau(q, qd', a) with stiffness at q + h qd'."""
+    for mode in (1, 2):
+        d = chain_desc([([0, 0, 1, 0], [2, 1, 2, 1])], E=6, seed=26 + mode, kp=50.0, kd=5.0,
+                       damping=0.1, k_limit=1e3, drive=mode)
+        tree, P = single(d)
+        q = rand((6, 4), 27, 2.2)
+        q[:, 2] = rand((6,), 28, 0.3) + 0.1
+        qd, a = rand((6, 4), 29, 2.0), rand((6, 4), 30, 1.5)
+        h = 1.0 / 120
+        q1, qd1, _ = dyn.substep(tree, P, q, qd, a, h)
+        M = dyn.crba(tree, P, q)
+        c = dyn.rnea(tree, P, q, qd, torch.zeros_like(q))
+        tau_lim, active = dyn.limit_state(P, q)
+        drive = (P.kd * (a - qd1) - P.b * qd1) if mode == 1 else (a - P.b * qd1)
+        rhs = drive + tau_lim - h * P.klim * active.to(D) * qd1
+        lhs = (M @ ((qd1 - qd) / h)[..., None])[..., 0] + c
+        assert ((lhs - rhs).abs().max() / rhs.abs().max()) < 1e-11
