@@ -308,14 +308,12 @@ __device__ __forceinline__ void drive_terms(const Pat& pat, const Rec& rec, cons
     const float kp = rec.lf(i, LF_KP), d = rec.lf(i, LF_D), kl = rec.lf(i, LF_KLIM);
     const float ga = rec.lf(i, LF_GA);
     const float lo = rec.lf(i, LF_QLO), hi = rec.lf(i, LF_QHI);
-    float ks = kp, tl = 0.f;
-    if (q[i] > hi) {
-      ks += kl;
-      tl = -kl * (q[i] - hi);
-    } else if (q[i] < lo) {
-      ks += kl;
-      tl = -kl * (q[i] - lo);
-    }
+    // limit spring, active beyond either bound (selects, no branches)
+    const bool over = q[i] > hi, under = q[i] < lo;
+    const float bound = over ? hi : lo;
+    const bool act = over || under;
+    const float ks = kp + (act ? kl : 0.f);
+    const float tl = act ? -kl * (q[i] - bound) : 0.f;
     const float tau = kp * (qs[i] - q[i]) + ga * qs[i] - d * qd[i] + tl;
     rhs[i] = h * (tau - h * ks * qd[i] - bias[i]);
     arm[i] = h * d + hh * ks;
@@ -396,19 +394,33 @@ __device__ __forceinline__ void integrate(const Pat& pat, float (&q)[7], float (
 }
 
 // One implicit-drive semi-implicit Euler substep of one chain (one thread).
+// cq, sq hold cos / sin of the joint angles q on entry and are updated to
+// those of the new q on exit (the next substep and the tip kinematics reuse
+// them).
 template <class Pat>
-__device__ __forceinline__ void chain_substep(const Pat& pat, const Rec& rec, float (&q)[7],
-                                              float (&qd)[7], const float (&qs)[7], float h,
-                                              float grav) {
+__device__ __forceinline__ void chain_substep_trig(const Pat& pat, const Rec& rec, float (&q)[7],
+                                                   float (&qd)[7], const float (&qs)[7],
+                                                   float (&cq)[Pat::N], float (&sq)[Pat::N],
+                                                   float h, float grav) {
   constexpr int N = Pat::N;
-  float cq[N], sq[N], bias[N], M[N][N], rhs[N], arm[N];
+  float bias[N], M[N][N], rhs[N], arm[N];
   V3 F[N], Nm[N];
-  joint_sincos(pat, q, cq, sq);
   rnea_forward(pat, rec, q, qd, cq, sq, grav, F, Nm);
   backward_sweep<Pat, true, true>(pat, rec, q, cq, sq, F, Nm, bias, M);
   drive_terms(pat, rec, q, qd, qs, h, bias, rhs, arm);
   chol_solve(pat, M, arm, rhs);
   integrate(pat, q, qd, rhs, h);
+  joint_sincos(pat, q, cq, sq);
+}
+
+// One substep computing the joint trigonometry itself.
+template <class Pat>
+__device__ __forceinline__ void chain_substep(const Pat& pat, const Rec& rec, float (&q)[7],
+                                              float (&qd)[7], const float (&qs)[7], float h,
+                                              float grav) {
+  float cq[Pat::N], sq[Pat::N];
+  joint_sincos(pat, q, cq, sq);
+  chain_substep_trig(pat, rec, q, qd, qs, cq, sq, h, grav);
 }
 
 // col_u' = c col_u + s col_v, col_v' = -s col_u + c col_v
@@ -418,10 +430,13 @@ __device__ __forceinline__ void rot_cols(V3& u, V3& v, float c, float s) {
   v = V3{-s * a.x + c * b.x, -s * a.y + c * b.y, -s * a.z + c * b.z};
 }
 
-// World pose of the tool tip (and tip rotation columns) from q.
+// World pose of the tool tip (and tip rotation columns) from q, given the
+// cos / sin of the joint angles.
 template <class Pat>
-__device__ __forceinline__ void chain_tip(const Pat& pat, const Rec& rec, const float (&q)[7],
-                                          V3& tip, V3& r0, V3& r1, V3& r2) {
+__device__ __forceinline__ void chain_tip_trig(const Pat& pat, const Rec& rec, const float (&q)[7],
+                                               const float (&cq)[Pat::N],
+                                               const float (&sq)[Pat::N], V3& tip, V3& r0,
+                                               V3& r1, V3& r2) {
   constexpr int N = Pat::N;
   V3 p{rec.cf(CF_BX), rec.cf(CF_BY), rec.cf(CF_BZ)};
   V3 c0{1.f, 0.f, 0.f}, c1{0.f, 1.f, 0.f}, c2{0.f, 0.f, 1.f};
@@ -433,8 +448,7 @@ __device__ __forceinline__ void chain_tip(const Pat& pat, const Rec& rec, const 
       p.y += q[i] * c2.y;
       p.z += q[i] * c2.z;
     } else {
-      float s, c;
-      __sincosf(q[i], &s, &c);
+      const float s = sq[i], c = cq[i];
       const int a = pat.axis(i);
       // R <- R Rot_a with the in-plane pair (u, v) = ((a+1)%3, (a+2)%3)
       if (a == 2) rot_cols(c0, c1, c, s);
@@ -450,6 +464,14 @@ __device__ __forceinline__ void chain_tip(const Pat& pat, const Rec& rec, const 
   r0 = c0;
   r1 = c1;
   r2 = c2;
+}
+
+template <class Pat>
+__device__ __forceinline__ void chain_tip(const Pat& pat, const Rec& rec, const float (&q)[7],
+                                          V3& tip, V3& r0, V3& r1, V3& r2) {
+  float cq[Pat::N], sq[Pat::N];
+  joint_sincos(pat, q, cq, sq);
+  chain_tip_trig(pat, rec, q, cq, sq, tip, r0, r1, r2);
 }
 
 // Unit quaternion (x, y, z, w), w >= 0, of the rotation with columns r0, r1, r2

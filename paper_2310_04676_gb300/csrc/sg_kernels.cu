@@ -74,16 +74,22 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
   const float goal_x = rec.cf(CF_GX), goal_y = rec.cf(CF_GY), goal_z = rec.cf(CF_GZ);
   const size_t E = (size_t)a.num_envs;
   if (valid) load_targets(pat, a, 0, env, jo, qn);
+  // padding of this env's observation row (constant zero, written once)
+  if (c == 0)
+    for (int k = obs_len; k < D; ++k) srow[k] = 0.f;
+  float cq[N], sq[N];
+  joint_sincos(pat, q, cq, sq);
 
   for (int t = 0; t < a.T; ++t) {
 #pragma unroll
     for (int i = 0; i < 7; ++i) qs[i] = qn[i];
     if (valid && t + 1 < a.T) load_targets(pat, a, t + 1, env, jo, qn);   // prefetch
-    for (int k = 0; k < a.substeps; ++k) chain_substep(pat, rec, q, qd, qs, a.h, kGravity);
+    for (int k = 0; k < a.substeps; ++k)
+      chain_substep_trig(pat, rec, q, qd, qs, cq, sq, a.h, kGravity);
 
     // ---- epilogue: tip pose, reward, observation, done
     V3 tip, r0, r1, r2;
-    chain_tip(pat, rec, q, tip, r0, r1, r2);
+    chain_tip_trig(pat, rec, q, cq, sq, tip, r0, r1, r2);
     bool bad = false;
 #pragma unroll
     for (int i = 0; i < N; ++i)
@@ -141,7 +147,6 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
       srow[3 * ntot + 3 * nc + 3 * c + 2] = goal_z;
     }
     if (c == 0) {
-      for (int k = obs_len; k < D; ++k) srow[k] = 0.f;
       if (valid) {
         a.reward[(size_t)t * E + env] = reward;
         a.done[(size_t)t * E + env] =

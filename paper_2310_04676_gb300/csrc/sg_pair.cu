@@ -94,6 +94,10 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
   int sc = (valid && c == 0) ? a.step_count[env] : 0;
   const size_t E = (size_t)a.num_envs;
   if (valid && role == 0) load_targets(pat, a, 0, env, jo, qn);
+  if (role == 0 && c == 0)
+    for (int k = obs_len; k < D; ++k) srow[k] = 0.f;   // padding, written once
+  float cq[N], sq[N];
+  joint_sincos(pat, q, cq, sq);
 
   for (int t = 0; t < a.T; ++t) {
     if (role == 0) {
@@ -102,9 +106,7 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
       if (valid && t + 1 < a.T) load_targets(pat, a, t + 1, env, jo, qn);
     }
     for (int k = 0; k < a.substeps; ++k, ++xphase) {
-      float cq[N], sq[N];
       float* xb = xbuf + (xphase & 1) * kXHalf;   // double-buffered exchange
-      joint_sincos(pat, q, cq, sq);
       if (role == 0) {
         float bias[N], rhs[N], arm[N], Mdummy[N][N];
         V3 F[N], Nm[N];
@@ -143,6 +145,7 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
       }
       chol_apply(pat, L, inv, dqd);
       integrate(pat, q, qd, dqd, a.h);
+      joint_sincos(pat, q, cq, sq);
     }
 
     // ---- epilogue: role 0 stages q, qd, q* and writes done; role 1 the tip
@@ -165,14 +168,13 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
         if (a.task != SG_TASK_PATH) srow[2 * n + 3 * nc + jo + i] = qs[i];
       }
       if (c == 0) {
-        for (int k = obs_len; k < D; ++k) srow[k] = 0.f;
         if (valid)
           a.done[(size_t)t * E + env] = (uint8_t)((sc >= a.episode_len ? SG_DONE_TIMEOUT : 0) |
                                                   (bad ? SG_DONE_NONFINITE : 0));
       }
     } else {
       V3 tip, r0, r1, r2;
-      chain_tip(pat, rec, q, tip, r0, r1, r2);
+      chain_tip_trig(pat, rec, q, cq, sq, tip, r0, r1, r2);
       float reward;
       if (a.task == SG_TASK_PATH) {
         const int W = a.path_len, n = ntot;
