@@ -327,7 +327,7 @@ def measure_adjoint(cx, wl, desc, T, every=8):
     tg = torch.as_tensor(tg_np, device=cx.dev)
     env = sg.Env(desc)
     nc = torch.as_tensor(desc["env_num_chains"], device=cx.dev)
-    mask = (torch.arange(2, device=cx.dev)[None, :] < nc[:, None]).float()[None, :, :, None]
+    mask = (torch.arange(4, device=cx.dev)[None, :] < nc[:, None]).float()[None, :, :, None]
     res = {}
 
     def fwd_bwd():

@@ -2,11 +2,11 @@
  * sg.h -- C ABI of the batched articulated-arm simulation step (libsg.so).
  *
  * The library steps thousands of independent robot environments on one
- * GPU: each environment is one or two serial chains of revolute/prismatic
+ * GPU: each environment is one to four serial chains of revolute/prismatic
  * joints on a fixed base under PD joint drives (Surgical Gym, Methods,
  * "Simulation Setup": actors of rigid bodies joined by revolute/prismatic
  * joints, PD position targets as actions; Results, "Multi-Tool Target
- * Reaching": two arms per environment).  One step integrates the
+ * Reaching": two or three arms per environment).  One step integrates the
  * reduced-coordinate rigid-body dynamics with `substeps` implicit-drive
  * semi-implicit Euler substeps (Methods, "Simulation Setup": the engine
  * sub-steps every control step) and writes the per-environment
@@ -53,7 +53,8 @@ typedef enum sg_status {
 
 enum {
   SG_TASK_REACH = 0,        /* Target Reaching / Multi-Tool Target Reaching */
-  SG_TASK_PATH = 1          /* Path Following (single-chain envs only) */
+  SG_TASK_PATH = 1,         /* Path Following (single-chain envs only) */
+  SG_TASK_TRACK = 2         /* Active Tracking: reaching with moving goals */
 };
 
 enum {
@@ -74,7 +75,7 @@ enum {
 };
 
 enum {
-  SG_MAX_CHAINS = 2,        /* chains (arms) per environment */
+  SG_MAX_CHAINS = 4,        /* chains (arms) per environment */
   SG_MAX_CHAIN_JOINTS = 7   /* joints per chain */
 };
 
@@ -105,9 +106,9 @@ enum {
  */
 typedef struct sg_desc {
   int32_t num_envs;                 /* E >= 1 */
-  int32_t max_joints;               /* J, 1..14 */
-  const int32_t *env_num_chains;    /* [E]     1 or 2 */
-  const int32_t *chain_num_joints;  /* [E][2]  1..7 (second entry unused for 1 chain) */
+  int32_t max_joints;               /* J, 1..28 */
+  const int32_t *env_num_chains;    /* [E]     1..4 */
+  const int32_t *chain_num_joints;  /* [E][4]  1..7 (entries beyond env_num_chains unused) */
   const int32_t *joint_type;        /* [E][J]  SG_JOINT_* */
   const int32_t *joint_axis;        /* [E][J]  0=x 1=y 2=z */
   const float *link_len;            /* [E][J]  m */
@@ -117,25 +118,36 @@ typedef struct sg_desc {
   const float *q_lo, *q_hi;         /* [E][J]  joint limits (rad or m) */
   const float *kp, *kd, *damping;   /* [E][J]  drive stiffness, drive damping, joint damping */
   const float *k_limit;             /* [E][J]  limit-spring stiffness (0 = no spring) */
-  const float *base_offset;         /* [E][2][3] chain base positions (world) */
+  const float *base_offset;         /* [E][4][3] chain base positions (world) */
   const float *q0;                  /* [E][J]  state after reset (qd = 0) */
   int32_t episode_len;              /* steps until the time-out bit, >= 1 */
   int32_t task;                     /* SG_TASK_* */
-  const float *goal;                /* [E][2][3] per-chain goal (SG_TASK_REACH) */
+  const float *goal;                /* [E][4][3] per-chain goal (SG_TASK_REACH) */
   const float *path;                /* [E][path_len][3] waypoints (SG_TASK_PATH), else NULL */
   int32_t path_len;                 /* W >= 4 for SG_TASK_PATH */
   float alpha;                      /* path reward scale */
   const int32_t *joint_drive;       /* [E][J] SG_DRIVE_*, or NULL (all position) */
+  /* SG_TASK_TRACK (Results, "Active Tracking"): every step each chain's goal
+   * offset d (from its initial goal) and goal velocity v move as
+   *   d <- clamp(d + v, -track_limit, +track_limit) (per component),
+   *   v <- v + track_sigma * N(0, 1)^3,
+   * with the normal deviates drawn from a counter-based generator keyed by
+   * (seed, env, chain, step count after the step); reset sets d = v = 0. */
+  uint32_t seed;
+  float track_sigma;                /* > 0 for SG_TASK_TRACK */
+  float track_limit;                /* > 0 for SG_TASK_TRACK */
 } sg_desc;
 
 /*
  * Observation layout of env e (n = its total DOF, nc = its chains), padded
  * with zeros to D = sg_obs_dim():
- *   SG_TASK_REACH: [q(n), qd(n), tip_c(3) per chain, q*(n), goal_c(3) per chain]
+ *   SG_TASK_REACH, SG_TASK_TRACK:
+ *                  [q(n), qd(n), tip_c(3) per chain, q*(n), goal_c(3) per chain]
  *   SG_TASK_PATH:  [q(n), qd(n), tip(3), quat(4) = (x, y, z, w) with w >= 0,
  *                   waypoint[t+1](3), waypoint[t+2](3), waypoint[t+3](3)]
  * where t = steps since reset after this step and waypoint indices clamp at
- * path_len - 1.  Reward: REACH  -sum_c ||tip_c - goal_c||;
+ * path_len - 1.  Reward: REACH, TRACK  -sum_c ||tip_c - goal_c|| (the
+ *                                       current, moved goal for TRACK);
  *                        PATH   -alpha ||tip - waypoint[t]||.
  */
 
@@ -244,13 +256,13 @@ sg_status sg_autotune(sg_ctx *ctx, const float *actions_dev, int32_t T, float dt
  *
  * sg_diff_forward: T control steps from the current state with
  * actions_dev [T][E][J], writing the tool-tip position of every chain after
- * every step to ee_dev [T][E][2][3] (chain 1 entries are 0 for one-chain
- * envs).  The state (q, qd) is checkpointed every ckpt_every steps
+ * every step to ee_dev [T][E][4][3] (entries of chains an env does not have
+ * are 0).  The state (q, qd) is checkpointed every ckpt_every steps
  * (1..32) in context scratch memory (cudaMalloc on first use or growth);
  * the context's own state and step counts are NOT changed.  substeps 1..16.
  *
  * sg_diff_backward: the reverse pass of the last sg_diff_forward on this
- * context.  Given dl_dee_dev [T][E][2][3] = dL/d(ee) it writes
+ * context.  Given dl_dee_dev [T][E][4][3] = dL/d(ee) it writes
  * dactions_dev [T][E][J] = dL/d(actions) and dmass_dev [E][J] = dL/d(link
  * mass) (link inertias scale with the mass, centre of mass fixed); dq0_dev
  * and dqd0_dev [E][J] (either may be NULL) receive dL/d(initial q, qd).
@@ -277,9 +289,9 @@ sg_status sg_set_link_mass(sg_ctx *ctx, const float *mass_dev);
  *     L_e = sum_t sum_c ||ee[t][e][c] - target[t][e][c]||^2 .
  * It runs sg_diff_forward's forward kernel, the loss cotangent and
  * sg_diff_backward's adjoint kernel in one call and writes ee_dev
- * [T][E][2][3], loss_dev [E], dactions_dev [T][E][J] = dL/d(actions) and
- * dmass_dev [E][J] = dL/d(link mass); target_dev is [T][E][2][3] (chain-1
- * targets of one-chain envs are ignored).
+ * [T][E][4][3], loss_dev [E], dactions_dev [T][E][J] = dL/d(actions) and
+ * dmass_dev [E][J] = dL/d(link mass); target_dev is [T][E][4][3] (targets of
+ * chains an env does not have are ignored).
  *
  * Who needs it: callers that cannot allocate device memory when they need
  * gradients -- a training or control loop inside a host program that owns
@@ -293,7 +305,7 @@ sg_status sg_set_link_mass(sg_ctx *ctx, const float *mass_dev);
  * beforehand (sg_create allocates).
  *
  * Limits: substeps 1..16, ckpt_every 1..32, T 1..4096, and
- * (ceil(T / ckpt_every) + 1) * 14 * sg_plan_info.num_slots + 6 * T * E
+ * (ceil(T / ckpt_every) + 1) * 14 * sg_plan_info.num_slots + 12 * T * E
  * floats must fit in the 32 MiB (8388608 floats); larger requests return
  * SG_ERR_INVALID_ARG with a message and enqueue nothing.
  * All calls on a device share the one array and it keeps the last call's
@@ -309,6 +321,13 @@ sg_status sg_diff_track_noalloc(sg_ctx *ctx, const float *actions_dev, int32_t T
                                 int32_t substeps, int32_t ckpt_every, const float *target_dev,
                                 float *ee_dev, float *loss_dev, float *dactions_dev,
                                 float *dmass_dev);
+
+/* Goal state of SG_TASK_TRACK in caller layout: offset_dev (goal minus the
+ * initial goal) and velocity_dev, both [E][4][3] float (entries of chains an
+ * env does not have are written as 0 / ignored).  Either pointer may be
+ * NULL.  SG_ERR_INVALID_ARG for other tasks. */
+sg_status sg_get_goal_state(sg_ctx *ctx, float *offset_dev, float *velocity_dev);
+sg_status sg_set_goal_state(sg_ctx *ctx, const float *offset_dev, const float *velocity_dev);
 
 /* Synchronise the context's stream, then read and clear the device error
  * flags: SG_ERR_NONFINITE if any env produced a non-finite state since the

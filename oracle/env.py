@@ -10,11 +10,15 @@ Follows the paper's task definitions (Results, "Environments"):
 * Multi-Tool Target Reaching reward r = rho * sum_i ||eta_i - g_i||;
 * Path Following reward r = -alpha * ||eta_t - P(t)||, observation
   [q, qd, tip position, tip quaternion, next three waypoints];
+* Active Tracking: reaching with goals that move every step,
+  g = g0 + d, d <- clamp(d + v, +-limit), v <- v + sigma N(0, 1) (the
+  paper's random walk of the goal position and velocity with a maximum
+  offset; its noise variance "1^{-4}" is read as 1e-4, i.e. sigma = 0.01);
 * time-outs are reported apart from terminations (Methods, "Policy
   learning and control").
 
 Observation layouts (n = total DOF, nc = number of chains):
-  reach: [q(n), qd(n), tip_c(3) for each chain, q*(n), goal_c(3) for each chain]
+  reach, tracking: [q(n), qd(n), tip_c(3) for each chain, q*(n), goal_c(3) for each chain]
   path:  [q(n), qd(n), tip(3), quat(4) as (x, y, z, w) with w >= 0,
           waypoint[t+1], waypoint[t+2], waypoint[t+3]]
 padded with zeros to the widest env of the batch.  Done bits: bit0 =
@@ -26,6 +30,7 @@ import torch
 
 from . import dynamics as dyn
 from .model import PRISMATIC, groups, make_params
+from .rng import goal_noise
 from .spatial import DT
 
 
@@ -85,6 +90,8 @@ class OracleEnv:
         self.q = np.zeros((self.E, self.J))
         self.qd = np.zeros((self.E, self.J))
         self.step_count = np.zeros(self.E, np.int64)
+        self.goal_off = np.zeros((self.E, 4, 3))     # tracking task: goal offset, velocity
+        self.goal_vel = np.zeros((self.E, 4, 3))
         self.reset()
 
     # -- state -------------------------------------------------------------
@@ -93,6 +100,8 @@ class OracleEnv:
         self.q[m] = np.asarray(self.desc["q0"], np.float64)[m]
         self.qd[m] = 0.0
         self.step_count[m] = 0
+        self.goal_off[m] = 0.0
+        self.goal_vel[m] = 0.0
 
     def set_state(self, q, qd, step_count=None):
         self.q = np.array(q, np.float64, copy=True)
@@ -110,6 +119,8 @@ class OracleEnv:
         reward = np.zeros(self.E)
         done = np.zeros(self.E, np.uint8)
         self.step_count += 1
+        if self.task == 2:
+            self._move_goals()
         for idx, tree, P in self.groups:
             n = tree.n
             q = torch.as_tensor(self.q[idx, :n])
@@ -127,6 +138,24 @@ class OracleEnv:
         done[bad] |= 4
         return obs, reward, done
 
+    def _move_goals(self):
+        """One random-walk step of every chain's goal (tracking task)."""
+        nc = np.asarray(self.desc["env_num_chains"])
+        lim = float(self.desc["track_limit"])
+        sig = float(self.desc["track_sigma"])
+        env = np.arange(self.E)[:, None]
+        chain = np.arange(4)[None, :]
+        z = goal_noise(int(self.desc["seed"]), env, chain, self.step_count[:, None])
+        has = (chain < nc[:, None])[..., None]
+        self.goal_off = np.where(has, np.clip(self.goal_off + self.goal_vel, -lim, lim), 0.0)
+        self.goal_vel = np.where(has, self.goal_vel + sig * z, 0.0)
+
+    def goals(self, idx, nc):
+        g = np.asarray(self.desc["goal"], np.float64)[idx][:, :nc]
+        if self.task == 2:
+            g = g + self.goal_off[idx][:, :nc]
+        return g
+
     def _obs_reward(self, idx, tree, P, q, qd, qs):
         ee, _ = dyn.end_effectors(tree, P, q)                    # [E, nc, 3]
         nc = tree.n_chains
@@ -139,7 +168,7 @@ class OracleEnv:
             o = torch.cat([q, qd, ee[:, 0], quat, wp(1), wp(2), wp(3)], -1)
             r = -float(self.desc["alpha"]) * torch.linalg.norm(ee[:, 0] - wp(0), dim=-1)
         else:
-            goal = torch.as_tensor(np.asarray(self.desc["goal"], np.float64)[idx][:, :nc])
+            goal = torch.as_tensor(self.goals(idx, nc))
             o = torch.cat([q, qd, ee.reshape(len(idx), -1), qs, goal.reshape(len(idx), -1)], -1)
             r = -torch.linalg.norm(ee - goal, dim=-1).sum(-1)
         return o.numpy(), r.numpy()

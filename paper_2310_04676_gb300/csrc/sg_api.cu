@@ -29,6 +29,7 @@ struct sg_ctx {
   int32_t* d_warp_class = nullptr;
   int32_t* d_step_count = nullptr;
   int32_t* d_err = nullptr;
+  float* d_track = nullptr;        // [6][NS] goal offset / velocity (tracking task)
   int threads = 128;
   int rollout_mode = SG_ROLLOUT_PERSISTENT;
   int split = 1;
@@ -97,7 +98,7 @@ void free_ctx(sg_ctx* c) {
   if (!c) return;
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
-  void* ptrs[] = {c->d_params, c->d_q, c->d_qd, c->d_q0, c->d_path, c->d_slot_env,
+  void* ptrs[] = {c->d_params, c->d_q, c->d_qd, c->d_q0, c->d_path, c->d_slot_env, c->d_track,
                   c->d_slot_info, c->d_warp_class, c->d_step_count, c->d_err,
                   c->d_stage_act, c->d_stage_obs, c->d_stage_rew, c->d_stage_done,
                   c->d_snap_q, c->d_snap_qd, c->d_snap_sc, c->d_mass0, c->d_inertia0,
@@ -115,6 +116,7 @@ sg::StateArgs state_args(sg_ctx* c) {
   s.qd = c->d_qd;
   s.q0 = c->d_q0;
   s.step_count = c->d_step_count;
+  s.track = c->d_track;
   s.num_slots = c->plan.num_slots;
   s.max_joints = c->plan.max_joints;
   return s;
@@ -141,6 +143,10 @@ sg::StepArgs step_args(sg_ctx* c, float dt, int substeps, int T) {
   a.path_len = c->plan.path_len;
   a.episode_len = c->plan.episode_len;
   a.alpha = c->plan.alpha;
+  a.track = c->d_track;
+  a.seed = c->plan.seed;
+  a.track_sigma = c->plan.track_sigma;
+  a.track_limit = c->plan.track_limit;
   a.substeps = substeps;
   a.T = T;
   a.h = dt / (float)substeps;
@@ -320,6 +326,10 @@ sg_status sg_create(const sg_desc* desc, void* stream, sg_ctx** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_q, 0, sizeof(float) * sg::kMaxLinks * NS, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_qd, 0, sizeof(float) * sg::kMaxLinks * NS, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream);
+  if (e == cudaSuccess && P.task == SG_TASK_TRACK) {
+    e = cudaMalloc(&c->d_track, sizeof(float) * 6 * NS);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_track, 0, sizeof(float) * 6 * NS, c->stream);
+  }
   if (e == cudaSuccess) e = sg::prepare_step_kernel();
   if (e == cudaSuccess) e = sg::prepare_step_pair_kernel();
   if (e == cudaSuccess) e = sg::prepare_diff_kernels();
@@ -632,6 +642,22 @@ sg_status sg_set_link_mass(sg_ctx* ctx, const float* mass_dev) {
   m.num_slots = ctx->plan.num_slots;
   m.max_joints = ctx->plan.max_joints;
   return cuda_err(ctx, sg::launch_set_mass(m, ctx->stream), "sg_set_link_mass");
+}
+
+sg_status sg_get_goal_state(sg_ctx* ctx, float* offset_dev, float* velocity_dev) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  if (!ctx->d_track) return set_err(ctx, SG_ERR_INVALID_ARG, "goal state exists only for SG_TASK_TRACK");
+  return cuda_err(ctx, sg::launch_goal_state(state_args(ctx), offset_dev, velocity_dev, nullptr,
+                                             nullptr, ctx->stream),
+                  "sg_get_goal_state");
+}
+
+sg_status sg_set_goal_state(sg_ctx* ctx, const float* offset_dev, const float* velocity_dev) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  if (!ctx->d_track) return set_err(ctx, SG_ERR_INVALID_ARG, "goal state exists only for SG_TASK_TRACK");
+  return cuda_err(ctx, sg::launch_goal_state(state_args(ctx), nullptr, nullptr, offset_dev,
+                                             velocity_dev, ctx->stream),
+                  "sg_set_goal_state");
 }
 
 sg_status sg_sync_status(sg_ctx* ctx) {

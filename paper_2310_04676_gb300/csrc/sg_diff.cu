@@ -50,11 +50,11 @@ __device__ __forceinline__ SlotInfo slot_info(const DiffArgs& a, int slot) {
   SlotInfo s;
   s.env = a.slot_env[slot];
   s.valid = s.env >= 0;
-  const int info = a.slot_info[slot];
-  s.c = (info >> SI_C_SHIFT) & 1;
-  s.nc = (info >> SI_NC_SHIFT) & 3;
-  s.jo = (info >> SI_JO_SHIFT) & 15;
-  s.ntot = (info >> SI_NTOT_SHIFT) & 31;
+  const SlotFields f = decode_slot(a.slot_info[slot]);
+  s.c = f.c;
+  s.nc = f.nc;
+  s.jo = f.jo;
+  s.ntot = f.ntot;
   return s;
 }
 
@@ -123,11 +123,12 @@ __device__ __forceinline__ void diff_forward_chain(const DiffArgs& a, const Pat&
     V3 tip, r0, r1, r2;
     chain_tip(pat, rec, q, tip, r0, r1, r2);
     if (s.valid) {
-      float* e = a.ee + (((size_t)t * E + s.env) * 2 + s.c) * 3;
+      float* e = a.ee + (((size_t)t * E + s.env) * kMaxChains + s.c) * 3;
       e[0] = tip.x;
       e[1] = tip.y;
       e[2] = tip.z;
-      if (s.nc == 1) e[3] = e[4] = e[5] = 0.f;      // no second chain
+      if (s.c == 0)                                  // chains the env does not have
+        for (int k = 3 * s.nc; k < 3 * kMaxChains; ++k) e[k] = 0.f;
     }
   }
   put_ckpt(pat, a, a.nseg, slot, q, qd);
@@ -171,7 +172,7 @@ __device__ __forceinline__ void diff_backward_chain(const DiffArgs& a, const Pat
     for (int t = t1 - 1; t >= t0; --t) {
       // tool-tip cotangent of the state after step t
       if (s.valid) {
-        const float* g = a.dl_dee + (((size_t)t * E + s.env) * 2 + s.c) * 3;
+        const float* g = a.dl_dee + (((size_t)t * E + s.env) * kMaxChains + s.c) * 3;
         float gq[N];
 #pragma unroll
         for (int i = 0; i < N; ++i) gq[i] = 0.f;
@@ -267,7 +268,7 @@ __device__ __forceinline__ void diff_dispatch(const DiffArgs& a) {
       int code;
       const float cf = r.cf(CF_CODE);
       memcpy(&code, &cf, 4);
-      run(PatGen{code, (a.slot_info[slot] >> SI_NCHAIN_SHIFT) & 7});
+      run(PatGen{code, decode_slot(a.slot_info[slot]).nchain});
     }
   }
 }
@@ -286,9 +287,8 @@ __global__ void set_mass_kernel(MassArgs m) {
   if (slot >= m.num_slots) return;
   const int env = m.slot_env[slot];
   if (env < 0) return;
-  const int info = m.slot_info[slot];
-  const int n = (info >> SI_NCHAIN_SHIFT) & 7;
-  const int jo = (info >> SI_JO_SHIFT) & 15;
+  const SlotFields f = decode_slot(m.slot_info[slot]);
+  const int n = f.nchain, jo = f.jo;
   float* rec = m.params + (size_t)(slot / kWarp) * kRecordFloats + (slot % kWarp);
   for (int i = 0; i < n; ++i) {
     const float mnew = m.mass[(size_t)env * m.max_joints + jo + i];

@@ -20,8 +20,8 @@ struct DiffArgs {
   const float* qd;
   float* ckpt;             // [nseg + 1][2 * kMaxLinks][NS]
   const float* actions;    // [T][E][J]
-  float* ee;               // [T][E][2][3]      (forward output)
-  const float* dl_dee;     // [T][E][2][3]      (backward input)
+  float* ee;               // [T][E][kMaxChains][3]   (forward output)
+  const float* dl_dee;     // [T][E][kMaxChains][3]   (backward input)
   float* dactions;         // [T][E][J]         (backward output)
   float* dmass;            // [E][J]            (backward output)
   float* dq0;              // [E][J] or null    (backward output)

@@ -17,7 +17,8 @@ namespace sg {
 
 constexpr int kWarp = 32;
 constexpr int kMaxLinks = 7;          // joints per chain (SG_MAX_CHAIN_JOINTS)
-constexpr int kMaxDof = 14;           // joints per env
+constexpr int kMaxChains = 4;         // chains per env (SG_MAX_CHAINS)
+constexpr int kMaxDof = kMaxLinks * kMaxChains;   // joints per env
 constexpr int kChainFields = 8;       // per chain slot: base xyz, goal xyz, joint code, pad
 constexpr int kLinkFields = 12;       // per link: see LinkField
 constexpr int kRecordFloats = (kChainFields + kMaxLinks * kLinkFields) * kWarp;
@@ -35,18 +36,30 @@ enum LinkField {
   LF_GA         // command gain: 0 (position), kd (velocity), 1 (torque)
 };
 
-// Chain classes: a warp holds 32 chain slots of one class, all single-chain
-// envs or all two-chain envs (lanes 2k, 2k+1 = chains 0, 1 of one env).
+// Chain classes: a warp holds 32 chain slots of one class.  The chains of
+// one env occupy a lane group of 1, 2 or 4 adjacent lanes (an env with 3
+// chains leaves the fourth lane of its group idle); every env of a warp has
+// the same group size.
 enum ChainClass { CLS_7R = 0, CLS_7P = 1, CLS_GEN = 2, CLS_4R = 3, CLS_COUNT = 4 };
-constexpr int kPairedBit = 4;         // warp_class = cls | (paired ? kPairedBit : 0)
+constexpr int kGroupShift = 2;        // warp_class = cls | (log2(group size) << kGroupShift)
+SG_HD inline int group_log2(int warp_class) { return (warp_class >> kGroupShift) & 3; }
+SG_HD inline int group_log2_of(int num_chains) { return num_chains == 1 ? 0 : (num_chains == 2 ? 1 : 2); }
 
 // slot_info bit fields
 constexpr int SI_NCHAIN_SHIFT = 0;    // joints of this chain (3 bits)
-constexpr int SI_C_SHIFT = 3;         // chain index within the env (1 bit)
-constexpr int SI_NC_SHIFT = 4;        // chains of the env (2 bits)
-constexpr int SI_JO_SHIFT = 6;        // first joint of this chain in env joint order (4 bits)
-constexpr int SI_NTOT_SHIFT = 10;     // total DOF of the env (5 bits)
-constexpr int SI_OBSLEN_SHIFT = 15;   // observation length of the env (7 bits)
+constexpr int SI_C_SHIFT = 3;         // chain index within the env / lane in its group (2 bits)
+constexpr int SI_NC_SHIFT = 5;        // chains of the env (3 bits)
+constexpr int SI_JO_SHIFT = 8;        // first joint of this chain in env joint order (5 bits)
+constexpr int SI_NTOT_SHIFT = 13;     // total DOF of the env (5 bits)
+constexpr int SI_OBSLEN_SHIFT = 18;   // observation length of the env (7 bits)
+struct SlotFields {
+  int nchain, c, nc, jo, ntot, obs_len;
+};
+SG_HD inline SlotFields decode_slot(int info) {
+  return SlotFields{(info >> SI_NCHAIN_SHIFT) & 7, (info >> SI_C_SHIFT) & 3,
+                    (info >> SI_NC_SHIFT) & 7,     (info >> SI_JO_SHIFT) & 31,
+                    (info >> SI_NTOT_SHIFT) & 31,  (info >> SI_OBSLEN_SHIFT) & 127};
+}
 
 // Joint code of a generic chain: per joint 3 bits = axis (2 bits) | type << 2.
 SG_HD inline int joint_code_bits(int type, int axis) { return (axis & 3) | ((type & 1) << 2); }
@@ -58,6 +71,8 @@ constexpr int DEVERR_TIMEOUT = 2;
 struct Plan {
   int num_envs = 0, max_joints = 0, obs_dim = 0, task = 0, path_len = 0, episode_len = 0;
   float alpha = 1.f;
+  uint32_t seed = 0;
+  float track_sigma = 0.f, track_limit = 0.f;
   int num_slots = 0, num_warps = 0, num_chains = 0;
   int class_slots[CLS_COUNT] = {0, 0, 0, 0};
   std::vector<int32_t> slot_env;    // [NS] caller env index, -1 for padding
@@ -92,6 +107,7 @@ struct StepArgs {
   int32_t* step_count;      // [E]
   const float* path;        // [E][W][3]
   int32_t* err;             // device error word
+  float* track;             // [6][NS] goal offset xyz, goal velocity xyz (tracking task)
   const float* actions;     // [T][E][J]
   float* obs;               // [T][E][D]
   float* reward;            // [T][E]
@@ -99,6 +115,8 @@ struct StepArgs {
   int num_warps, num_slots, num_envs, max_joints, obs_dim, task, path_len, episode_len;
   int substeps, T;
   float alpha, h;
+  uint32_t seed;
+  float track_sigma, track_limit;
 };
 
 }  // namespace sg

@@ -12,6 +12,7 @@
 #include "sg_device.cuh"
 #include "sg_internal.h"
 #include "sg_kernels.h"
+#include "sg_rng.cuh"
 
 namespace sg {
 
@@ -39,22 +40,19 @@ __device__ __forceinline__ bool stage_record(const StepArgs& a, int gw, int cls,
 // warp writes each row to HBM with consecutive lanes on consecutive floats.
 template <class Pat>
 __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, const Rec& rec,
-                                          float* stage, int slot, int lane, bool paired) {
+                                          float* stage, int slot, int lane, int glog) {
   constexpr int N = Pat::N;
   const int env = a.slot_env[slot];
   const bool valid = env >= 0;
-  const int info = a.slot_info[slot];
-  const int c = (info >> SI_C_SHIFT) & 1;
-  const int nc = (info >> SI_NC_SHIFT) & 3;
-  const int jo = (info >> SI_JO_SHIFT) & 15;
-  const int ntot = (info >> SI_NTOT_SHIFT) & 31;
-  const int obs_len = (info >> SI_OBSLEN_SHIFT) & 127;
+  const SlotFields f = decode_slot(a.slot_info[slot]);
+  const int c = f.c, nc = f.nc, jo = f.jo, ntot = f.ntot, obs_len = f.obs_len;
   const int NS = a.num_slots;
   const int D = a.obs_dim, DP = stage_pitch(a.obs_dim);
-  const int nrows = paired ? 16 : 32;
-  float* srow = stage + (paired ? (lane >> 1) : lane) * DP;
+  const int g = 1 << glog;                        // lanes per env
+  const int nrows = kWarp >> glog;
+  float* srow = stage + (lane >> glog) * DP;
   // env owning stage row `lane` (rows >= nrows unused)
-  const int row_env = __shfl_sync(0xffffffffu, env, paired ? ((2 * lane) & 31) : lane);
+  const int row_env = __shfl_sync(0xffffffffu, env, (lane << glog) & 31);
 
   float q[7], qd[7], qs[7], qn[7];
 #pragma unroll
@@ -70,12 +68,22 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
     q[i] = a.q[(size_t)i * NS + slot];
     qd[i] = a.qd[(size_t)i * NS + slot];
   }
-  int sc = (valid && c == 0) ? a.step_count[env] : 0;
+  int sc = valid ? a.step_count[env] : 0;
   const float goal_x = rec.cf(CF_GX), goal_y = rec.cf(CF_GY), goal_z = rec.cf(CF_GZ);
+  // moving goal of the tracking task: offset and velocity
+  const bool track = a.task == SG_TASK_TRACK;
+  float gd[3] = {0.f, 0.f, 0.f}, gv[3] = {0.f, 0.f, 0.f};
+  if (track && valid) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      gd[k] = a.track[(size_t)k * NS + slot];
+      gv[k] = a.track[(size_t)(3 + k) * NS + slot];
+    }
+  }
   const size_t E = (size_t)a.num_envs;
   if (valid) load_targets(pat, a, 0, env, jo, qn);
   // padding of this env's observation row (constant zero, written once)
-  if (c == 0)
+  if (valid && c == 0)
     for (int k = obs_len; k < D; ++k) srow[k] = 0.f;
   float cq[N], sq[N];
   joint_sincos(pat, q, cq, sq);
@@ -95,7 +103,7 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
     for (int i = 0; i < N; ++i)
       if (pat.active(i)) bad = bad || !isfinite(q[i]) || !isfinite(qd[i]);
     bad = bad && valid;
-    if (paired) bad = bad || __shfl_xor_sync(0xffffffffu, bad ? 1 : 0, 1) != 0;
+    for (int off = 1; off < g; off <<= 1) bad = bad || __shfl_xor_sync(0xffffffffu, bad ? 1 : 0, off) != 0;
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, DEVERR_NONFINITE);
     ++sc;
 
@@ -108,6 +116,7 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
       const float dx = tip.x - p0[0], dy = tip.y - p0[1], dz = tip.z - p0[2];
       reward = -a.alpha * sqrtf(dx * dx + dy * dy + dz * dz);
       const int n = ntot;
+      if (valid) {
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         if (!pat.active(i)) continue;
@@ -128,23 +137,39 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
         srow[2 * n + 5 + 3 * k] = pk[1];
         srow[2 * n + 6 + 3 * k] = pk[2];
       }
-    } else {
-      const float dx = tip.x - goal_x, dy = tip.y - goal_y, dz = tip.z - goal_z;
-      reward = -sqrtf(dx * dx + dy * dy + dz * dz);
-      if (paired) reward += __shfl_xor_sync(0xffffffffu, reward, 1);
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        if (!pat.active(i)) continue;
-        srow[jo + i] = q[i];
-        srow[ntot + jo + i] = qd[i];
-        srow[2 * ntot + 3 * nc + jo + i] = qs[i];
       }
-      srow[2 * ntot + 3 * c + 0] = tip.x;
-      srow[2 * ntot + 3 * c + 1] = tip.y;
-      srow[2 * ntot + 3 * c + 2] = tip.z;
-      srow[3 * ntot + 3 * nc + 3 * c + 0] = goal_x;
-      srow[3 * ntot + 3 * nc + 3 * c + 1] = goal_y;
-      srow[3 * ntot + 3 * nc + 3 * c + 2] = goal_z;
+    } else {
+      float gx = goal_x, gy = goal_y, gz = goal_z;
+      if (track) {
+        float z[3];
+        goal_noise(a.seed, valid ? env : 0, c, sc, z[0], z[1], z[2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          gd[k] = fminf(fmaxf(gd[k] + gv[k], -a.track_limit), a.track_limit);
+          gv[k] += a.track_sigma * z[k];
+        }
+        gx += gd[0];
+        gy += gd[1];
+        gz += gd[2];
+      }
+      const float dx = tip.x - gx, dy = tip.y - gy, dz = tip.z - gz;
+      reward = valid ? -sqrtf(dx * dx + dy * dy + dz * dz) : 0.f;
+      for (int off = 1; off < g; off <<= 1) reward += __shfl_xor_sync(0xffffffffu, reward, off);
+      if (valid) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          if (!pat.active(i)) continue;
+          srow[jo + i] = q[i];
+          srow[ntot + jo + i] = qd[i];
+          srow[2 * ntot + 3 * nc + jo + i] = qs[i];
+        }
+        srow[2 * ntot + 3 * c + 0] = tip.x;
+        srow[2 * ntot + 3 * c + 1] = tip.y;
+        srow[2 * ntot + 3 * c + 2] = tip.z;
+        srow[3 * ntot + 3 * nc + 3 * c + 0] = gx;
+        srow[3 * ntot + 3 * nc + 3 * c + 1] = gy;
+        srow[3 * ntot + 3 * nc + 3 * c + 2] = gz;
+      }
     }
     if (c == 0) {
       if (valid) {
@@ -166,6 +191,13 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
       a.qd[(size_t)i * NS + slot] = qd[i];
     }
     if (c == 0) a.step_count[env] = sc;
+    if (track) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        a.track[(size_t)k * NS + slot] = gd[k];
+        a.track[(size_t)(3 + k) * NS + slot] = gv[k];
+      }
+    }
   }
 }
 
@@ -185,17 +217,17 @@ __global__ void __launch_bounds__(kMaxThreads) step_kernel(StepArgs a) {
   if (!stage_record(a, gw, wc, rec, bar, lane)) return;
   const Rec r{rec + lane};
   const int slot = gw * kWarp + lane;
-  const bool paired = (wc & kPairedBit) != 0;
+  const int glog = group_log2(wc);
   switch (wc & 3) {
-    case CLS_7R: run_chain(a, Pat7R{}, r, stage, slot, lane, paired); break;
-    case CLS_7P: run_chain(a, Pat7P{}, r, stage, slot, lane, paired); break;
-    case CLS_4R: run_chain(a, Pat4R{}, r, stage, slot, lane, paired); break;
+    case CLS_7R: run_chain(a, Pat7R{}, r, stage, slot, lane, glog); break;
+    case CLS_7P: run_chain(a, Pat7P{}, r, stage, slot, lane, glog); break;
+    case CLS_4R: run_chain(a, Pat4R{}, r, stage, slot, lane, glog); break;
     default: {
       int code;
       const float cf = r.cf(CF_CODE);
       memcpy(&code, &cf, 4);
-      const int n = (a.slot_info[slot] >> SI_NCHAIN_SHIFT) & 7;
-      run_chain(a, PatGen{code, n}, r, stage, slot, lane, paired);
+      const int n = decode_slot(a.slot_info[slot]).nchain;
+      run_chain(a, PatGen{code, n}, r, stage, slot, lane, glog);
     }
   }
 }
@@ -207,13 +239,39 @@ __global__ void reset_kernel(StateArgs s, const uint8_t* mask) {
   const int env = s.slot_env[slot];
   if (env < 0) return;
   if (mask && !mask[env]) return;
-  const int info = s.slot_info[slot];
-  const int n = (info >> SI_NCHAIN_SHIFT) & 7;
-  for (int i = 0; i < n; ++i) {
+  const SlotFields f = decode_slot(s.slot_info[slot]);
+  for (int i = 0; i < f.nchain; ++i) {
     s.q[(size_t)i * s.num_slots + slot] = s.q0[(size_t)i * s.num_slots + slot];
     s.qd[(size_t)i * s.num_slots + slot] = 0.f;
   }
-  if (((info >> SI_C_SHIFT) & 1) == 0) s.step_count[env] = 0;
+  if (f.c == 0) s.step_count[env] = 0;
+  if (s.track)
+    for (int k = 0; k < 6; ++k) s.track[(size_t)k * s.num_slots + slot] = 0.f;
+}
+
+// goal offset / velocity of the tracking task <-> caller layout [E][4][3]
+__global__ void goal_state_kernel(StateArgs s, float* off, float* vel, const float* off_in,
+                                  const float* vel_in) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= s.num_slots) return;
+  const int env = s.slot_env[slot];
+  if (env < 0) return;
+  const SlotFields f = decode_slot(s.slot_info[slot]);
+  const size_t base = ((size_t)env * kMaxChains + f.c) * 3;
+  for (int k = 0; k < 3; ++k) {
+    float* d = s.track + (size_t)k * s.num_slots + slot;
+    float* v = s.track + (size_t)(3 + k) * s.num_slots + slot;
+    if (off) off[base + k] = *d;
+    if (vel) vel[base + k] = *v;
+    if (off_in) *d = off_in[base + k];
+    if (vel_in) *v = vel_in[base + k];
+  }
+  if (f.c == 0) {               // chains the env does not have
+    for (int k = 3 * f.nc; k < 3 * kMaxChains; ++k) {
+      if (off) off[(size_t)env * kMaxChains * 3 + k] = 0.f;
+      if (vel) vel[(size_t)env * kMaxChains * 3 + k] = 0.f;
+    }
+  }
 }
 
 __global__ void get_state_kernel(StateArgs s, float* q_out, float* qd_out, int32_t* sc_out) {
@@ -221,11 +279,8 @@ __global__ void get_state_kernel(StateArgs s, float* q_out, float* qd_out, int32
   if (slot >= s.num_slots) return;
   const int env = s.slot_env[slot];
   if (env < 0) return;
-  const int info = s.slot_info[slot];
-  const int n = (info >> SI_NCHAIN_SHIFT) & 7;
-  const int c = (info >> SI_C_SHIFT) & 1;
-  const int jo = (info >> SI_JO_SHIFT) & 15;
-  const int ntot = (info >> SI_NTOT_SHIFT) & 31;
+  const SlotFields f = decode_slot(s.slot_info[slot]);
+  const int n = f.nchain, c = f.c, jo = f.jo, ntot = f.ntot;
   const size_t row = (size_t)env * s.max_joints;
   for (int i = 0; i < n; ++i) {
     if (q_out) q_out[row + jo + i] = s.q[(size_t)i * s.num_slots + slot];
@@ -246,10 +301,8 @@ __global__ void set_state_kernel(StateArgs s, const float* q_in, const float* qd
   if (slot >= s.num_slots) return;
   const int env = s.slot_env[slot];
   if (env < 0) return;
-  const int info = s.slot_info[slot];
-  const int n = (info >> SI_NCHAIN_SHIFT) & 7;
-  const int c = (info >> SI_C_SHIFT) & 1;
-  const int jo = (info >> SI_JO_SHIFT) & 15;
+  const SlotFields f = decode_slot(s.slot_info[slot]);
+  const int n = f.nchain, c = f.c, jo = f.jo;
   const size_t row = (size_t)env * s.max_joints;
   for (int i = 0; i < n; ++i) {
     if (q_in) s.q[(size_t)i * s.num_slots + slot] = q_in[row + jo + i];
@@ -280,6 +333,13 @@ cudaError_t launch_step(const StepArgs& a, int threads, cudaStream_t stream) {
 cudaError_t launch_reset(const StateArgs& s, const uint8_t* mask, cudaStream_t stream) {
   const int threads = 256, blocks = (s.num_slots + threads - 1) / threads;
   reset_kernel<<<blocks, threads, 0, stream>>>(s, mask);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_goal_state(const StateArgs& s, float* off, float* vel, const float* off_in,
+                              const float* vel_in, cudaStream_t stream) {
+  const int threads = 256, blocks = (s.num_slots + threads - 1) / threads;
+  goal_state_kernel<<<blocks, threads, 0, stream>>>(s, off, vel, off_in, vel_in);
   return cudaGetLastError();
 }
 

@@ -14,12 +14,13 @@ struct StateArgs {
   float* qd;
   const float* q0;
   int32_t* step_count;
+  float* track;             // [6][NS] goal offset / velocity (tracking task), or null
   int num_slots, max_joints;
 };
 
 constexpr int kMaxThreads = 256;   // largest step-kernel block
 
-constexpr int kMaxObsDim = 63;     // widest observation row the step kernel stages
+constexpr int kMaxObsDim = 127;    // widest observation row the step kernels stage
 
 // Row pitch (floats) of the per-warp observation stage: rows keep 8-byte
 // alignment when D is even; otherwise an odd pitch avoids bank conflicts.
@@ -39,5 +40,8 @@ cudaError_t launch_get_state(const StateArgs& s, float* q, float* qd, int32_t* s
                              cudaStream_t stream);
 cudaError_t launch_set_state(const StateArgs& s, const float* q, const float* qd,
                              const int32_t* sc, cudaStream_t stream);
+// copies the tracking-task goal state out (off, vel) and/or in (off_in, vel_in)
+cudaError_t launch_goal_state(const StateArgs& s, float* off, float* vel, const float* off_in,
+                              const float* vel_in, cudaStream_t stream);
 
 }  // namespace sg

@@ -60,21 +60,21 @@ cudaError_t noalloc_scratch(float** out) {
 
 // One thread per chain slot (warps aligned with the packing): dL/d(ee) =
 // 2 (ee - target) for the slot's chain, and the per-env loss
-// sum_t sum_c ||ee_c - target_c||^2 (the two chains of a two-arm env sit in
-// adjacent lanes and are summed with a shuffle).
+// sum_t sum_c ||ee_c - target_c||^2 (the chains of a multi-arm env sit in
+// one lane group and are summed with shuffles).
 __global__ void track_seed_kernel(DiffArgs a, const float* ee, const float* target,
                                   float* dl_dee, float* loss) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   const int gw = slot / kWarp;
   if (gw >= a.num_warps) return;                 // whole warps only (slots are warp-padded)
-  const bool paired = (a.warp_class[gw] & kPairedBit) != 0;
+  const int glog = group_log2(a.warp_class[gw]);
   const int env = a.slot_env[slot];
-  const int c = (a.slot_info[slot] >> SI_C_SHIFT) & 1;
+  const int c = decode_slot(a.slot_info[slot]).c;
   const size_t E = (size_t)a.num_envs;
   float acc = 0.f;
   if (env >= 0) {
     for (int t = 0; t < a.T; ++t) {
-      const size_t base = (((size_t)t * E + env) * 2 + c) * 3;
+      const size_t base = (((size_t)t * E + env) * kMaxChains + c) * 3;
       for (int k = 0; k < 3; ++k) {
         const float d = ee[base + k] - target[base + k];
         dl_dee[base + k] = 2.f * d;
@@ -82,7 +82,7 @@ __global__ void track_seed_kernel(DiffArgs a, const float* ee, const float* targ
       }
     }
   }
-  if (paired) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  for (int off = 1; off < (1 << glog); off <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
   if (env >= 0 && c == 0) loss[env] = acc;
 }
 
@@ -112,7 +112,7 @@ extern "C" sg_status sg_diff_track_noalloc(sg_ctx* ctx, const float* actions_dev
   DiffArgs a = context_diff_args(ctx);
   const int nseg = (T + ckpt_every - 1) / ckpt_every;
   const size_t ckpt_floats = (size_t)(nseg + 1) * 2 * kMaxLinks * a.num_slots;
-  const size_t seed_floats = (size_t)T * a.num_envs * 6;
+  const size_t seed_floats = (size_t)T * a.num_envs * 3 * kMaxChains;
   if (ckpt_floats + seed_floats > kNoAllocScratchFloats)
     return fail(SG_ERR_INVALID_ARG,
                 "sg_diff_track_noalloc: checkpoints + loss cotangent exceed the 32 MiB static "

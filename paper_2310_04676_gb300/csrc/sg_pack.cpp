@@ -2,8 +2,9 @@
 // environments out as warp-sized blocks of chain slots for the step kernel.
 //
 // Layout decisions (GB300-first):
-//  * one CUDA thread integrates one serial chain; a two-arm env occupies an
-//    adjacent lane pair (lanes 2k, 2k+1) of a warp;
+//  * one CUDA thread integrates one serial chain; the chains of a
+//    multi-arm env occupy a lane group of 2 or 4 adjacent lanes (a 3-arm env
+//    leaves the fourth lane of its group idle);
 //  * every warp holds chains of a single class (7R, 7P, generic, 4R) so the
 //    kernel dispatches once per warp with no divergence;
 //  * chains are grouped by class, longest chains first (their warps are
@@ -52,15 +53,19 @@ sg_status build_plan(const sg_desc* d, Plan* P, std::string* err) {
   if (!d) return fail(SG_ERR_INVALID_ARG, "desc is NULL");
   const int E = d->num_envs, J = d->max_joints;
   if (E < 1 || E > (1 << 26)) return fail(SG_ERR_INVALID_ARG, "num_envs out of range");
-  if (J < 1 || J > kMaxDof) return fail(SG_ERR_INVALID_ARG, "max_joints must be 1..14");
+  if (J < 1 || J > kMaxDof) return fail(SG_ERR_INVALID_ARG, "max_joints must be 1..28");
   if (!d->env_num_chains || !d->chain_num_joints || !d->joint_type || !d->joint_axis ||
       !d->link_len || !d->link_mass || !d->link_inertia || !d->link_com || !d->q_lo ||
       !d->q_hi || !d->kp || !d->kd || !d->damping || !d->k_limit || !d->base_offset || !d->q0)
     return fail(SG_ERR_INVALID_ARG, "a required desc array is NULL");
   if (d->episode_len < 1) return fail(SG_ERR_INVALID_ARG, "episode_len must be >= 1");
-  if (d->task != SG_TASK_REACH && d->task != SG_TASK_PATH)
+  if (d->task != SG_TASK_REACH && d->task != SG_TASK_PATH && d->task != SG_TASK_TRACK)
     return fail(SG_ERR_INVALID_ARG, "unknown task");
-  if (d->task == SG_TASK_REACH && !d->goal) return fail(SG_ERR_INVALID_ARG, "goal is NULL");
+  if (d->task != SG_TASK_PATH && !d->goal) return fail(SG_ERR_INVALID_ARG, "goal is NULL");
+  if (d->task == SG_TASK_TRACK &&
+      (!(d->track_sigma > 0.f) || !(d->track_limit > 0.f) || !finite(d->track_sigma) ||
+       !finite(d->track_limit)))
+    return fail(SG_ERR_INVALID_ARG, "tracking needs track_sigma > 0 and track_limit > 0");
   if (d->task == SG_TASK_PATH) {
     if (!d->path || d->path_len < 4) return fail(SG_ERR_INVALID_ARG, "path task needs path, path_len >= 4");
     if (!finite(d->alpha)) return fail(SG_ERR_INVALID_ARG, "alpha not finite");
@@ -72,14 +77,14 @@ sg_status build_plan(const sg_desc* d, Plan* P, std::string* err) {
     const int nc = d->env_num_chains[e];
     if (nc < 1 || nc > SG_MAX_CHAINS) {
       std::ostringstream o;
-      o << "env " << e << ": env_num_chains must be 1 or 2";
+      o << "env " << e << ": env_num_chains must be 1..4";
       return fail(SG_ERR_INVALID_ARG, o.str());
     }
     if (d->task == SG_TASK_PATH && nc != 1)
       return fail(SG_ERR_UNSUPPORTED, "path following is defined for single-chain envs");
-    int ntot = 0, cls[2] = {0, 0};
+    int ntot = 0, cls[kMaxChains] = {0, 0, 0, 0};
     for (int c = 0; c < nc; ++c) {
-      const int n = d->chain_num_joints[2 * e + c];
+      const int n = d->chain_num_joints[kMaxChains * e + c];
       if (n < 1 || n > kMaxLinks) {
         std::ostringstream o;
         o << "env " << e << ": chain_num_joints must be 1..7";
@@ -113,7 +118,8 @@ sg_status build_plan(const sg_desc* d, Plan* P, std::string* err) {
       ntot += n;
     }
     int k = cls[0];
-    if (nc == 2 && cls[1] != cls[0]) k = CLS_GEN;
+    for (int c = 1; c < nc; ++c)
+      if (cls[c] != cls[0]) k = CLS_GEN;
     env_cls[e] = k;
     env_ntot[e] = ntot;
     env_nc[e] = nc;
@@ -126,39 +132,44 @@ sg_status build_plan(const sg_desc* d, Plan* P, std::string* err) {
   P->path_len = d->task == SG_TASK_PATH ? d->path_len : 0;
   P->episode_len = d->episode_len;
   P->alpha = d->alpha;
+  P->seed = d->seed;
+  P->track_sigma = d->task == SG_TASK_TRACK ? d->track_sigma : 0.f;
+  P->track_limit = d->task == SG_TASK_TRACK ? d->track_limit : 0.f;
   P->obs_dim = 0;
   auto obs_len = [&](int e) {
     return d->task == SG_TASK_PATH ? 2 * env_ntot[e] + 16 : 3 * env_ntot[e] + 6 * env_nc[e];
   };
   for (int e = 0; e < E; ++e) P->obs_dim = std::max(P->obs_dim, obs_len(e));
+  if (P->obs_dim > 127) return fail(SG_ERR_UNSUPPORTED, "observation rows wider than 127 floats");
 
   static const int kOrder[CLS_COUNT] = {CLS_7R, CLS_7P, CLS_GEN, CLS_4R};
   P->slot_env.clear();
   P->slot_info.clear();
   P->warp_class.clear();
-  std::vector<int> slot_chain;   // chain index of each slot
+  std::vector<int> slot_chain;   // chain index (lane in its group) of each slot
   P->num_chains = 0;
   for (int k : kOrder) {
-    for (int paired = 1; paired >= 0; --paired) {
+    for (int glog = 2; glog >= 0; --glog) {
+      const int g = 1 << glog;
       const int first = (int)P->slot_env.size();
       for (int e = 0; e < E; ++e) {
-        if (env_cls[e] != k || (env_nc[e] == 2) != (paired == 1)) continue;
-        for (int c = 0; c < env_nc[e]; ++c) {
-          P->slot_env.push_back(e);
+        if (env_cls[e] != k || group_log2_of(env_nc[e]) != glog) continue;
+        for (int c = 0; c < g; ++c) {
+          P->slot_env.push_back(c < env_nc[e] ? e : -1 - e);   // idle lane of a 3-arm group
           slot_chain.push_back(c);
         }
+        P->class_slots[k] += env_nc[e];
+        P->num_chains += env_nc[e];
       }
       const int cnt = (int)P->slot_env.size() - first;
       if (cnt == 0) continue;
-      P->class_slots[k] += cnt;
-      P->num_chains += cnt;
       const int padded = (cnt + kWarp - 1) / kWarp * kWarp;
       const int ref_env = P->slot_env[first];
       for (int s = cnt; s < padded; ++s) {
         P->slot_env.push_back(-1 - ref_env);       // padding: copy of a real chain
-        slot_chain.push_back(paired ? (s & 1) : 0);
+        slot_chain.push_back(s % g);
       }
-      for (int w = 0; w < padded / kWarp; ++w) P->warp_class.push_back(k | (paired ? kPairedBit : 0));
+      for (int w = 0; w < padded / kWarp; ++w) P->warp_class.push_back(k | (glog << kGroupShift));
     }
   }
   const int NS = (int)P->slot_env.size();
@@ -175,8 +186,10 @@ sg_status build_plan(const sg_desc* d, Plan* P, std::string* err) {
     const bool pad = P->slot_env[s] < 0;
     const int e = pad ? -1 - P->slot_env[s] : P->slot_env[s];
     const int c = slot_chain[s];
-    const int n = d->chain_num_joints[2 * e + c];
-    const int jo = c == 0 ? 0 : d->chain_num_joints[2 * e];
+    const int cc = c < env_nc[e] ? c : 0;          // chain whose parameters the slot holds
+    const int n = d->chain_num_joints[kMaxChains * e + cc];
+    int jo = 0;
+    for (int j = 0; j < cc; ++j) jo += d->chain_num_joints[kMaxChains * e + j];
     P->slot_info[s] = (n << SI_NCHAIN_SHIFT) | (c << SI_C_SHIFT) | (env_nc[e] << SI_NC_SHIFT) |
                       (jo << SI_JO_SHIFT) | (env_ntot[e] << SI_NTOT_SHIFT) |
                       (obs_len(e) << SI_OBSLEN_SHIFT);
@@ -188,8 +201,8 @@ sg_status build_plan(const sg_desc* d, Plan* P, std::string* err) {
       return rec[(kChainFields + i * kLinkFields + f) * kWarp + lane];
     };
     for (int a = 0; a < 3; ++a) {
-      CF(CF_BX + a) = d->base_offset[(size_t)(2 * e + c) * 3 + a];
-      CF(CF_GX + a) = d->goal ? d->goal[(size_t)(2 * e + c) * 3 + a] : 0.f;
+      CF(CF_BX + a) = d->base_offset[(size_t)(kMaxChains * e + cc) * 3 + a];
+      CF(CF_GX + a) = d->goal ? d->goal[(size_t)(kMaxChains * e + cc) * 3 + a] : 0.f;
     }
     int code = 0;
     for (int i = 0; i < n; ++i) {

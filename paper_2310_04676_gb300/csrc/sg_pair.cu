@@ -25,6 +25,7 @@
 #include "sg_device.cuh"
 #include "sg_internal.h"
 #include "sg_kernels.h"
+#include "sg_rng.cuh"
 
 namespace sg {
 
@@ -56,22 +57,19 @@ __device__ __forceinline__ bool pair_wait(uint64_t* bar, unsigned& parity, int* 
 template <class Pat>
 __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, const Rec& rec,
                                          float* stage, float* xbuf, uint64_t* bars, int group,
-                                         int lane, int role, bool paired) {
+                                         int lane, int role, int glog) {
   constexpr int N = Pat::N;
   const int slot = group * kWarp + lane;
   const int env = a.slot_env[slot];
   const bool valid = env >= 0;
-  const int info = a.slot_info[slot];
-  const int c = (info >> SI_C_SHIFT) & 1;
-  const int nc = (info >> SI_NC_SHIFT) & 3;
-  const int jo = (info >> SI_JO_SHIFT) & 15;
-  const int ntot = (info >> SI_NTOT_SHIFT) & 31;
-  const int obs_len = (info >> SI_OBSLEN_SHIFT) & 127;
+  const SlotFields f = decode_slot(a.slot_info[slot]);
+  const int c = f.c, nc = f.nc, jo = f.jo, ntot = f.ntot, obs_len = f.obs_len;
   const int NS = a.num_slots;
   const int D = a.obs_dim, DP = stage_pitch(a.obs_dim);
-  const int nrows = paired ? 16 : 32;
-  float* srow = stage + (paired ? (lane >> 1) : lane) * DP;
-  const int row_env = __shfl_sync(0xffffffffu, env, paired ? ((2 * lane) & 31) : lane);
+  const int g = 1 << glog;                        // lanes per env
+  const int nrows = kWarp >> glog;
+  float* srow = stage + (lane >> glog) * DP;
+  const int row_env = __shfl_sync(0xffffffffu, env, (lane << glog) & 31);
   uint64_t* bar_x = bars + 1;
   uint64_t* bar_stage = bars + 2;
   unsigned ph_x = 0, ph_stage = 0;
@@ -91,10 +89,19 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
     q[i] = a.q[(size_t)i * NS + slot];
     qd[i] = a.qd[(size_t)i * NS + slot];
   }
-  int sc = (valid && c == 0) ? a.step_count[env] : 0;
+  int sc = valid ? a.step_count[env] : 0;
   const size_t E = (size_t)a.num_envs;
+  const bool track = a.task == SG_TASK_TRACK;
+  float gd[3] = {0.f, 0.f, 0.f}, gv[3] = {0.f, 0.f, 0.f};
+  if (track && valid && role == 1) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      gd[k] = a.track[(size_t)k * NS + slot];
+      gv[k] = a.track[(size_t)(3 + k) * NS + slot];
+    }
+  }
   if (valid && role == 0) load_targets(pat, a, 0, env, jo, qn);
-  if (role == 0 && c == 0)
+  if (valid && role == 0 && c == 0)
     for (int k = obs_len; k < D; ++k) srow[k] = 0.f;   // padding, written once
   float cq[N], sq[N];
   joint_sincos(pat, q, cq, sq);
@@ -157,15 +164,18 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
       for (int i = 0; i < N; ++i)
         if (pat.active(i)) bad = bad || !isfinite(q[i]) || !isfinite(qd[i]);
       bad = bad && valid;
-      if (paired) bad = bad || __shfl_xor_sync(0xffffffffu, bad ? 1 : 0, 1) != 0;
+      for (int off = 1; off < g; off <<= 1)
+        bad = bad || __shfl_xor_sync(0xffffffffu, bad ? 1 : 0, off) != 0;
       if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, DEVERR_NONFINITE);
       const int n = ntot;
+      if (valid) {
 #pragma unroll
-      for (int i = 0; i < N; ++i) {
-        if (!pat.active(i)) continue;
-        srow[jo + i] = q[i];
-        srow[n + jo + i] = qd[i];
-        if (a.task != SG_TASK_PATH) srow[2 * n + 3 * nc + jo + i] = qs[i];
+        for (int i = 0; i < N; ++i) {
+          if (!pat.active(i)) continue;
+          srow[jo + i] = q[i];
+          srow[n + jo + i] = qd[i];
+          if (a.task != SG_TASK_PATH) srow[2 * n + 3 * nc + jo + i] = qs[i];
+        }
       }
       if (c == 0) {
         if (valid)
@@ -183,6 +193,7 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
         const float* p0 = P + (size_t)min(t0, W - 1) * 3;
         const float dx = tip.x - p0[0], dy = tip.y - p0[1], dz = tip.z - p0[2];
         reward = -a.alpha * sqrtf(dx * dx + dy * dy + dz * dz);
+        if (valid) {
         srow[2 * n + 0] = tip.x;
         srow[2 * n + 1] = tip.y;
         srow[2 * n + 2] = tip.z;
@@ -197,17 +208,32 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
           srow[2 * n + 5 + 3 * k] = pk[1];
           srow[2 * n + 6 + 3 * k] = pk[2];
         }
+        }
       } else {
-        const float gx = rec.cf(CF_GX), gy = rec.cf(CF_GY), gz = rec.cf(CF_GZ);
+        float gx = rec.cf(CF_GX), gy = rec.cf(CF_GY), gz = rec.cf(CF_GZ);
+        if (track) {
+          float z[3];
+          goal_noise(a.seed, valid ? env : 0, c, sc, z[0], z[1], z[2]);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            gd[k] = fminf(fmaxf(gd[k] + gv[k], -a.track_limit), a.track_limit);
+            gv[k] += a.track_sigma * z[k];
+          }
+          gx += gd[0];
+          gy += gd[1];
+          gz += gd[2];
+        }
         const float dx = tip.x - gx, dy = tip.y - gy, dz = tip.z - gz;
-        reward = -sqrtf(dx * dx + dy * dy + dz * dz);
-        if (paired) reward += __shfl_xor_sync(0xffffffffu, reward, 1);
-        srow[2 * ntot + 3 * c + 0] = tip.x;
-        srow[2 * ntot + 3 * c + 1] = tip.y;
-        srow[2 * ntot + 3 * c + 2] = tip.z;
-        srow[3 * ntot + 3 * nc + 3 * c + 0] = gx;
-        srow[3 * ntot + 3 * nc + 3 * c + 1] = gy;
-        srow[3 * ntot + 3 * nc + 3 * c + 2] = gz;
+        reward = valid ? -sqrtf(dx * dx + dy * dy + dz * dz) : 0.f;
+        for (int off = 1; off < g; off <<= 1) reward += __shfl_xor_sync(0xffffffffu, reward, off);
+        if (valid) {
+          srow[2 * ntot + 3 * c + 0] = tip.x;
+          srow[2 * ntot + 3 * c + 1] = tip.y;
+          srow[2 * ntot + 3 * c + 2] = tip.z;
+          srow[3 * ntot + 3 * nc + 3 * c + 0] = gx;
+          srow[3 * ntot + 3 * nc + 3 * c + 1] = gy;
+          srow[3 * ntot + 3 * nc + 3 * c + 2] = gz;
+        }
       }
       if (valid && c == 0) a.reward[(size_t)t * E + env] = reward;
     }
@@ -228,6 +254,13 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
       a.qd[(size_t)i * NS + slot] = qd[i];
     }
     if (c == 0) a.step_count[env] = sc;
+  }
+  if (valid && role == 1 && track) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      a.track[(size_t)k * NS + slot] = gd[k];
+      a.track[(size_t)(3 + k) * NS + slot] = gv[k];
+    }
   }
 }
 
@@ -268,17 +301,17 @@ __global__ void __launch_bounds__(kMaxThreads) step_kernel_pair(StepArgs a) {
     return;
   }
   const Rec r{rec + lane};
-  const bool paired = (wc & kPairedBit) != 0;
+  const int glog = group_log2(wc);
   switch (wc & 3) {
-    case CLS_7R: run_pair(a, Pat7R{}, r, stage, xbuf, bars, group, lane, role, paired); break;
-    case CLS_7P: run_pair(a, Pat7P{}, r, stage, xbuf, bars, group, lane, role, paired); break;
-    case CLS_4R: run_pair(a, Pat4R{}, r, stage, xbuf, bars, group, lane, role, paired); break;
+    case CLS_7R: run_pair(a, Pat7R{}, r, stage, xbuf, bars, group, lane, role, glog); break;
+    case CLS_7P: run_pair(a, Pat7P{}, r, stage, xbuf, bars, group, lane, role, glog); break;
+    case CLS_4R: run_pair(a, Pat4R{}, r, stage, xbuf, bars, group, lane, role, glog); break;
     default: {
       int code;
       const float cf = r.cf(CF_CODE);
       memcpy(&code, &cf, 4);
-      const int n = (a.slot_info[group * kWarp + lane] >> SI_NCHAIN_SHIFT) & 7;
-      run_pair(a, PatGen{code, n}, r, stage, xbuf, bars, group, lane, role, paired);
+      const int n = decode_slot(a.slot_info[group * kWarp + lane]).nchain;
+      run_pair(a, PatGen{code, n}, r, stage, xbuf, bars, group, lane, role, glog);
     }
   }
 }

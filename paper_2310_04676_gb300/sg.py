@@ -12,6 +12,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libsg.so")
 
+TASK_REACH, TASK_PATH, TASK_TRACK = 0, 1, 2
 SG_OK, SG_ERR_INVALID_ARG, SG_ERR_CUDA, SG_ERR_OOM, SG_ERR_NONFINITE, SG_ERR_TIMEOUT, \
     SG_ERR_UNSUPPORTED = range(7)
 STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_CUDA", 3: "SG_ERR_OOM",
@@ -19,6 +20,7 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_CUDA", 3: "SG_ER
 DONE_TERMINATED, DONE_TIMEOUT, DONE_NONFINITE = 1, 2, 4
 ROLLOUT_PERSISTENT, ROLLOUT_STEP_GRAPH = 0, 1
 DRIVE_POSITION, DRIVE_VELOCITY, DRIVE_TORQUE = 0, 1, 2
+MAX_CHAINS = 4                     # chains per env (SG_MAX_CHAINS)
 
 
 class SgError(RuntimeError):
@@ -44,6 +46,7 @@ class SgDesc(ctypes.Structure):
         ("goal", _c_f32p), ("path", _c_f32p), ("path_len", ctypes.c_int32),
         ("alpha", ctypes.c_float),
         ("joint_drive", _c_i32p),
+        ("seed", ctypes.c_uint32), ("track_sigma", ctypes.c_float), ("track_limit", ctypes.c_float),
     ]
 
 
@@ -85,6 +88,8 @@ def load_library(path=LIB_PATH):
         "sg_diff_forward": (i32, [vp, vp, i32, f32, i32, i32, vp]),
         "sg_diff_backward": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "sg_set_link_mass": (i32, [vp, vp]),
+        "sg_get_goal_state": (i32, [vp, vp, vp]),
+        "sg_set_goal_state": (i32, [vp, vp, vp]),
         "sg_diff_track_noalloc": (i32, [vp, vp, i32, f32, i32, i32, vp, vp, vp, vp, vp]),
         "sg_last_error": (ctypes.c_char_p, [vp]),
     }
@@ -121,15 +126,15 @@ def make_c_desc(desc):
     d = SgDesc()
     d.num_envs, d.max_joints = E, J
     d.env_num_chains = p("env_num_chains", i32, (E,), _c_i32p)
-    d.chain_num_joints = p("chain_num_joints", i32, (E, 2), _c_i32p)
+    d.chain_num_joints = p("chain_num_joints", i32, (E, MAX_CHAINS), _c_i32p)
     d.joint_type = p("joint_type", i32, (E, J), _c_i32p)
     d.joint_axis = p("joint_axis", i32, (E, J), _c_i32p)
     for k in ("link_len", "link_mass", "link_com", "q_lo", "q_hi", "kp", "kd", "damping",
               "k_limit", "q0"):
         setattr(d, k, p(k, f32, (E, J), _c_f32p))
     d.link_inertia = p("link_inertia", f32, (E, J, 3), _c_f32p)
-    d.base_offset = p("base_offset", f32, (E, 2, 3), _c_f32p)
-    d.goal = p("goal", f32, (E, 2, 3), _c_f32p)
+    d.base_offset = p("base_offset", f32, (E, MAX_CHAINS, 3), _c_f32p)
+    d.goal = p("goal", f32, (E, MAX_CHAINS, 3), _c_f32p)
     W = int(desc.get("path_len") or 0)
     d.path = p("path", f32, (E, W, 3), _c_f32p) if W else ctypes.cast(None, _c_f32p)
     d.path_len = W
@@ -137,6 +142,9 @@ def make_c_desc(desc):
     d.task = int(desc["task"])
     d.alpha = float(desc.get("alpha", 1.0))
     d.joint_drive = p("joint_drive", i32, (E, J), _c_i32p)
+    d.seed = int(desc.get("seed", 0)) & 0xFFFFFFFF
+    d.track_sigma = float(desc.get("track_sigma", 0.0))
+    d.track_limit = float(desc.get("track_limit", 0.0))
     return d, keep
 
 
@@ -297,13 +305,13 @@ class Env:
         self._check(self.lib.sg_set_link_mass(self.ctx, _ptr(mass)))
 
     def diff_forward(self, actions, dt, substeps, ckpt_every=8):
-        """Tool-tip trajectory [T, E, 2, 3] from the current state (state
+        """Tool-tip trajectory [T, E, 4, 3] from the current state (state
         unchanged); checkpoints kept for diff_backward."""
         self._sync_stream()
         torch = self._torch
         T = int(actions.shape[0])
         self._want(actions, torch.float32, (T, self.num_envs, self.max_joints), "actions")
-        ee = torch.empty(T, self.num_envs, 2, 3, dtype=torch.float32, device=self.device)
+        ee = torch.empty(T, self.num_envs, MAX_CHAINS, 3, dtype=torch.float32, device=self.device)
         self._check(self.lib.sg_diff_forward(self.ctx, _ptr(actions), T, float(dt), int(substeps),
                                              int(ckpt_every), _ptr(ee)))
         return ee
@@ -315,7 +323,7 @@ class Env:
         torch = self._torch
         T = int(actions.shape[0])
         self._want(actions, torch.float32, (T, self.num_envs, self.max_joints), "actions")
-        self._want(dl_dee, torch.float32, (T, self.num_envs, 2, 3), "dl_dee")
+        self._want(dl_dee, torch.float32, (T, self.num_envs, MAX_CHAINS, 3), "dl_dee")
         da = torch.empty_like(actions)
         dm = torch.empty(self.num_envs, self.max_joints, dtype=torch.float32, device=self.device)
         dq0 = torch.empty_like(dm) if initial_state else None
@@ -323,6 +331,23 @@ class Env:
         self._check(self.lib.sg_diff_backward(self.ctx, _ptr(actions), _ptr(dl_dee), _ptr(da),
                                               _ptr(dm), _ptr(dq0), _ptr(dqd0)))
         return (da, dm, dq0, dqd0) if initial_state else (da, dm)
+
+    def get_goal_state(self):
+        """Tracking task: (goal offset, goal velocity) [E, 4, 3]."""
+        self._sync_stream()
+        torch = self._torch
+        off = torch.empty(self.num_envs, MAX_CHAINS, 3, dtype=torch.float32, device=self.device)
+        vel = torch.empty_like(off)
+        self._check(self.lib.sg_get_goal_state(self.ctx, _ptr(off), _ptr(vel)))
+        return off, vel
+
+    def set_goal_state(self, offset=None, velocity=None):
+        self._sync_stream()
+        shape = (self.num_envs, MAX_CHAINS, 3)
+        for t, name in ((offset, "offset"), (velocity, "velocity")):
+            if t is not None:
+                self._want(t, self._torch.float32, shape, name)
+        self._check(self.lib.sg_set_goal_state(self.ctx, _ptr(offset), _ptr(velocity)))
 
     def get_state(self):
         self._sync_stream()
@@ -357,7 +382,7 @@ def _autograd_function():
     class TipRollout(torch.autograd.Function):
         """Differentiable tool-tip rollout through the library's adjoint
         kernel: forward(env, actions [T,E,J], mass [E,J] or None, dt,
-        substeps, ckpt_every) -> ee [T,E,2,3]."""
+        substeps, ckpt_every) -> ee [T,E,4,3]."""
 
         @staticmethod
         def forward(ctx, env, actions, mass, dt, substeps, ckpt_every):
@@ -383,7 +408,7 @@ _TIP_ROLLOUT = None
 
 
 def tip_rollout(env, actions, dt, substeps, mass=None, ckpt_every=8):
-    """Tool-tip positions [T, E, 2, 3] as a differentiable function of the
+    """Tool-tip positions [T, E, 4, 3] as a differentiable function of the
     actions (and optionally the link masses) -- backward runs the adjoint
     kernel with checkpointing every ``ckpt_every`` steps.  One outstanding
     forward per Env: a second call before backward overwrites the

@@ -33,8 +33,13 @@ KINDS = {
     "7R": dict(chains=[(7, [0] * 7, _AXES7)]),
     "7P": dict(chains=[(7, [0, 0, 1, 0, 0, 0, 0], _AXES7)]),
     "14B": dict(chains=[(7, [0] * 7, _AXES7), (7, [0] * 7, _AXES7)]),
+    # three-arm (two instrument arms and a camera arm, all with the
+    # RRP... insertion structure of the paper's PSM / ECM)
+    "21T": dict(chains=[(7, [0, 0, 1, 0, 0, 0, 0], _AXES7)] * 3),
 }
+MAX_CHAINS = 4
 BIMANUAL_BASE_Y = 0.25
+TRIMANUAL_BASES = [(0.0, 0.3, 0.0), (0.0, -0.3, 0.0), (-0.2, 0.0, 0.0)]
 
 
 def kind_dof(kind: str) -> int:
@@ -60,7 +65,8 @@ def _box_inertia(m, L, w=BOX_WIDTH):
 
 def make_desc(kinds, *, seed_params=1, seed_goals=3, shared_params=False,
               k_limit=0.0, kp=50.0, kd=5.0, damping=0.1, episode_len=1000,
-              task=0, path_len=0, alpha=1.0, max_joints=None, drive=None):
+              task=0, path_len=0, alpha=1.0, max_joints=None, drive=None, seed=7,
+              track_sigma=0.01, track_limit=0.2):
     """Build an ``sg_desc`` dictionary for a list of arm kinds (one per env).
 
     ``drive`` selects the joint command type (0 position target, 1 velocity
@@ -78,33 +84,41 @@ def make_desc(kinds, *, seed_params=1, seed_goals=3, shared_params=False,
 
     f32 = np.float32
     d = dict(num_envs=E, max_joints=J, episode_len=int(episode_len), task=int(task),
-             alpha=float(alpha))
+             alpha=float(alpha), seed=int(seed), track_sigma=float(track_sigma),
+             track_limit=float(track_limit))
     d["env_num_chains"] = np.zeros(E, np.int32)
-    d["chain_num_joints"] = np.zeros((E, 2), np.int32)
+    d["chain_num_joints"] = np.zeros((E, MAX_CHAINS), np.int32)
     for name in ("joint_type", "joint_axis"):
         d[name] = np.zeros((E, J), np.int32)
     for name in ("link_len", "link_mass", "link_com", "q_lo", "q_hi", "kp", "kd",
                  "damping", "k_limit", "q0"):
         d[name] = np.zeros((E, J), f32)
     d["link_inertia"] = np.zeros((E, J, 3), f32)
-    d["base_offset"] = np.zeros((E, 2, 3), f32)
-    d["goal"] = np.zeros((E, 2, 3), f32)
+    d["base_offset"] = np.zeros((E, MAX_CHAINS, 3), f32)
+    d["goal"] = np.zeros((E, MAX_CHAINS, 3), f32)
 
-    shared_L = rp.uniform(0.05, 0.4, size=14)
-    shared_m = rp.uniform(0.1, 1.0, size=14)
+    shared_L = rp.uniform(0.05, 0.4, size=7 * MAX_CHAINS)
+    shared_m = rp.uniform(0.1, 1.0, size=7 * MAX_CHAINS)
     for e, kind in enumerate(kinds):
         chains = KINDS[kind]["chains"]
         d["env_num_chains"][e] = len(chains)
         if shared_params:
             Ls, ms = shared_L, shared_m
-        else:
+        elif len(chains) <= 2:
+            # (draw size kept for one- and two-arm envs: their seeded inputs
+            # are unchanged by the wider arrays)
             Ls = rp.uniform(0.05, 0.4, size=14)
             ms = rp.uniform(0.1, 1.0, size=14)
+        else:
+            Ls = rp.uniform(0.05, 0.4, size=7 * MAX_CHAINS)
+            ms = rp.uniform(0.1, 1.0, size=7 * MAX_CHAINS)
         j0 = 0
         for c, (n, types, axes) in enumerate(chains):
             d["chain_num_joints"][e, c] = n
             if len(chains) == 2:
                 d["base_offset"][e, c] = (0.0, BIMANUAL_BASE_Y if c == 0 else -BIMANUAL_BASE_Y, 0.0)
+            elif len(chains) == 3:
+                d["base_offset"][e, c] = TRIMANUAL_BASES[c]
             reach = 0.0
             for i in range(n):
                 j = j0 + i
@@ -262,9 +276,9 @@ def config(name, num_envs=None):
 
 
 def loss_targets(desc, T, seed=5):
-    """Per-env, per-chain EE targets [T][E][2][3], constant over the horizon
+    """Per-env, per-chain EE targets [T][E][4][3], constant over the horizon
     (seeded; a draw in the same cube as the reaching goals)."""
     E = desc["num_envs"]
     r = np.random.default_rng(seed)
-    g = desc["goal"].astype(np.float64) + r.uniform(-0.05, 0.05, size=(E, 2, 3))
-    return np.broadcast_to(g.astype(np.float32), (T, E, 2, 3)).copy()
+    g = desc["goal"].astype(np.float64) + r.uniform(-0.05, 0.05, size=(E, MAX_CHAINS, 3))
+    return np.broadcast_to(g.astype(np.float32), (T, E, MAX_CHAINS, 3)).copy()

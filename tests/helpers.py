@@ -14,15 +14,15 @@ def chain_desc(chains, E=1, *, kp=0.0, kd=0.0, damping=0.0, k_limit=0.0,
     d = dict(num_envs=E, max_joints=J, episode_len=episode_len, task=0, alpha=1.0,
              path=None, path_len=0)
     d["env_num_chains"] = np.full(E, len(chains), np.int32)
-    d["chain_num_joints"] = np.zeros((E, 2), np.int32)
+    d["chain_num_joints"] = np.zeros((E, 4), np.int32)
     d["joint_type"] = np.zeros((E, J), np.int32)
     d["joint_axis"] = np.zeros((E, J), np.int32)
     for k in ("link_len", "link_mass", "link_com", "q_lo", "q_hi", "kp", "kd", "damping",
               "k_limit", "q0"):
         d[k] = np.zeros((E, J), f32)
     d["link_inertia"] = np.zeros((E, J, 3), f32)
-    d["base_offset"] = np.zeros((E, 2, 3), f32)
-    d["goal"] = np.zeros((E, 2, 3), f32)
+    d["base_offset"] = np.zeros((E, 4, 3), f32)
+    d["goal"] = np.zeros((E, 4, 3), f32)
     for e in range(E):
         j = 0
         for c, (types, axes) in enumerate(chains):

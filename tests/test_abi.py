@@ -51,6 +51,14 @@ def test_plan_counts_and_obs_dim(lib):
     assert info["num_slots"] % 32 == 0
 
 
+def test_plan_three_arm_groups(lib):
+    d = W.make_desc(["21T"] * 5 + ["7R"] * 3)
+    info = sg.plan(d)
+    assert info["obs_dim"] == 3 * 21 + 18
+    assert info["class_slots"] == [3, 15, 0, 0]
+    assert info["num_chains"] == 18
+
+
 def test_plan_generic_class_and_path_obs(lib):
     from tests.helpers import chain_desc
     d = chain_desc([([0, 1, 0], [0, 2, 1])], E=5)
@@ -73,6 +81,7 @@ def test_plan_generic_class_and_path_obs(lib):
     (lambda d: d.__setitem__("episode_len", 0), sg.SG_ERR_INVALID_ARG),
     (lambda d: d.__setitem__("task", 7), sg.SG_ERR_INVALID_ARG),
     (lambda d: d.__setitem__("joint_drive", np.full((2, 7), 3, np.int32)), sg.SG_ERR_INVALID_ARG),
+    (lambda d: (d.__setitem__("task", 2), d.__setitem__("track_sigma", 0.0)), sg.SG_ERR_INVALID_ARG),
 ])
 def test_plan_rejects_bad_descriptions(lib, mutate, code):
     d = W.make_desc(["7R", "4R"])

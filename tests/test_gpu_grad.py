@@ -33,7 +33,7 @@ def gpu_grads(desc, acts, targets, S, every, env=None):
     ee = env.diff_forward(a, DT, S, every)
     tg = cuda(targets)
     nc = torch.as_tensor(desc["env_num_chains"], device="cuda")
-    chain_mask = (torch.arange(2, device="cuda")[None, :] < nc[:, None]).float()[None, :, :, None]
+    chain_mask = (torch.arange(4, device="cuda")[None, :] < nc[:, None]).float()[None, :, :, None]
     g = 2.0 * (ee - tg) * chain_mask
     da, dm = env.diff_backward(a, g.contiguous())
     return ee.cpu().numpy(), da.cpu().numpy(), dm.cpu().numpy()
@@ -58,7 +58,7 @@ def rel_env(x, y):
     return np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-12)
 
 
-@pytest.mark.parametrize("kind", ["7R", "7P", "4R", "14B"])
+@pytest.mark.parametrize("kind", ["7R", "7P", "4R", "14B", "21T"])
 def test_adjoint_matches_oracle_reverse_mode(kind):
     E, T, S = 48, 16, 2
     desc = W.make_desc([kind] * E)

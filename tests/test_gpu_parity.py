@@ -353,3 +353,79 @@ def test_velocity_and_torque_commands_match_oracle(split):
     desc = W.make_desc(kinds, drive=modes, k_limit=1e3)
     rel, env, *_ = one_step_accel(desc, 2, seed=3, split=split)
     assert rel.max() <= 1e-4, rel.max()
+
+
+@pytest.mark.parametrize("split", [1, 2])
+def test_three_arm_envs_match_oracle(split):
+    """Three-arm envs (lane groups of four with one idle lane) mixed with
+    one- and two-arm envs: accelerations, observation and reward."""
+    kinds = (["21T", "7R", "14B", "21T", "4R", "7P"] * 30)[:160]
+    desc = W.make_desc(kinds, k_limit=1e3)
+    assert sg.plan(desc)["obs_dim"] == 81
+    rel, env, obs, rew, done = one_step_accel(desc, 2, seed=4, split=split)
+    assert rel.max() <= 1e-4, rel.max()
+    # observation and reward formulas on the GPU state
+    q1, qd1, sc1 = env.get_state()
+    ref = OracleEnv(desc)
+    ref.set_state(q1.cpu().numpy(), qd1.cpu().numpy(), sc1.cpu().numpy())
+    acts = W.joint_targets(desc, 1, seed=11)[0]
+    o_ref = np.zeros((len(kinds), env.obs_dim))
+    r_ref = np.zeros(len(kinds))
+    for idx, tree, P in ref.groups:
+        n = tree.n
+        o, r = ref._obs_reward(idx, tree, P, torch.as_tensor(ref.q[idx, :n]),
+                               torch.as_tensor(ref.qd[idx, :n]),
+                               torch.as_tensor(acts[idx, :n].astype(np.float64)))
+        o_ref[idx, :o.shape[1]] = o
+        r_ref[idx] = r
+    assert np.abs(obs.cpu().numpy() - o_ref).max() <= 1e-5 * max(1.0, np.abs(o_ref).max())
+    assert np.abs(rew.cpu().numpy() - r_ref).max() <= 1e-5
+
+
+@pytest.mark.parametrize("split", [1, 2])
+def test_tracking_task_matches_oracle(split):
+    """Moving goals (counter-based noise drawn on both sides): goals in the
+    observation, rewards and the goal state follow the oracle over 40 steps;
+    masked reset clears the goal state."""
+    kinds = (["7R", "14B", "21T", "4R"] * 40)[:150]
+    desc = W.make_desc(kinds, task=2, track_sigma=0.02, track_limit=0.15, seed=99)
+    E = len(kinds)
+    env, ref = sg.Env(desc), OracleEnv(desc)
+    env.set_launch(128, sg.ROLLOUT_PERSISTENT, split)
+    acts = W.joint_targets(desc, 40)
+    obs, rew, done = env.rollout(cuda(acts), DT, 2)
+    for t in range(40):
+        o_ref, r_ref, _ = ref.step(acts[t], DT, 2)
+    off, vel = env.get_goal_state()
+    assert np.abs(off.cpu().numpy() - ref.goal_off).max() <= 1e-5
+    assert np.abs(vel.cpu().numpy() - ref.goal_vel).max() <= 1e-5
+    assert np.abs(rew[-1].cpu().numpy() - r_ref).max() <= 1e-3
+    dof = desc["chain_num_joints"].sum(1)
+    nc = desc["env_num_chains"]
+    for e in range(0, E, 7):
+        n, c = dof[e], nc[e]
+        g_obs = obs[-1, e].cpu().numpy()[3 * n + 3 * c:3 * n + 6 * c].reshape(c, 3)
+        assert np.abs(g_obs - ref.goals([e], c)[0]).max() <= 1e-5
+    mask = np.zeros(E, np.uint8)
+    mask[::2] = 1
+    env.reset(cuda(mask))
+    off, vel = env.get_goal_state()
+    assert (off.cpu().numpy()[::2] == 0).all() and (vel.cpu().numpy()[::2] == 0).all()
+    assert (off.cpu().numpy()[1::2] != 0).any()
+
+
+def test_tracking_rollout_equals_steps_and_state_roundtrip():
+    desc = W.make_desc(["7R", "14B"] * 50, task=2)
+    acts = cuda(W.joint_targets(desc, 16))
+    A, B = sg.Env(desc), sg.Env(desc)
+    o, r, d = A.rollout(acts, DT, 2)
+    for t in range(16):
+        ob, rb, db = B.step(acts[t], DT, 2)
+    assert torch.equal(o[-1], ob) and torch.equal(r[-1], rb)
+    off, vel = A.get_goal_state()
+    C = sg.Env(desc)
+    C.set_state(*A.get_state())
+    C.set_goal_state(off, vel)
+    oc, rc, _ = C.step(acts[0], DT, 2)
+    oa, ra, _ = A.step(acts[0], DT, 2)
+    assert torch.equal(oa, oc) and torch.equal(ra, rc)

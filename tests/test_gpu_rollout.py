@@ -23,7 +23,7 @@ def cuda(x):
 @pytest.mark.parametrize("mode", [sg.ROLLOUT_PERSISTENT, sg.ROLLOUT_STEP_GRAPH])
 @pytest.mark.parametrize("threads,split", [(32, 1), (128, 1), (256, 1), (64, 2), (256, 2)])
 def test_rollout_equals_steps_bitwise(mode, threads, split):
-    kinds = W.mixed_kinds(777, W.C3_FRACTIONS)
+    kinds = W.mixed_kinds(777, W.C3_FRACTIONS) + ["21T"] * 23
     desc = W.make_desc(kinds, episode_len=20)
     T = 32
     acts = cuda(W.joint_targets(desc, T))
@@ -49,7 +49,8 @@ def _close(x, y, tol):
     return (x - y).abs().max().item() <= tol * max(1.0, y.abs().max().item())
 
 
-@pytest.mark.parametrize("kinds", [["7R"], ["14B"], ["4R", "7P"], ["7R", "4R", "7P", "14B"]],
+@pytest.mark.parametrize("kinds", [["7R"], ["14B"], ["4R", "7P"], ["7R", "4R", "7P", "14B"],
+                                   ["21T", "7R"]],
                          ids=lambda k: "+".join(k))
 def test_warp_pair_kernel_matches_single_thread_kernel(kinds):
     """Chain split 2 (two cooperating warps per chain block) agrees with one

@@ -39,7 +39,7 @@ def _lib():
 def _reference(env, desc, acts, tgt, S, every):
     ee = env.diff_forward(acts, DT, S, every)
     nc = torch.as_tensor(desc["env_num_chains"], device="cuda")
-    mask = (torch.arange(2, device="cuda")[None, :] < nc[:, None]).float()[None, :, :, None]
+    mask = (torch.arange(4, device="cuda")[None, :] < nc[:, None]).float()[None, :, :, None]
     diff = (ee - tgt) * mask
     da, dm = env.diff_backward(acts, (2.0 * diff).contiguous())
     return ee, (diff ** 2).sum((0, 2, 3)), da, dm
@@ -54,7 +54,7 @@ def test_noalloc_matches_allocating_path_twice():
     for call, (T, S, every, seed) in enumerate([(24, 2, 8, 2), (17, 3, 5, 7)]):
         acts = torch.as_tensor(W.joint_targets(desc, T, seed=seed), device="cuda")
         tgt = torch.as_tensor(W.loss_targets(desc, T, seed=seed + 1), device="cuda")
-        ee = torch.empty(T, E, 2, 3, device="cuda")
+        ee = torch.empty(T, E, 4, 3, device="cuda")
         loss = torch.empty(E, device="cuda")
         da = torch.empty(T, E, J, device="cuda")
         dm = torch.empty(E, J, device="cuda")
@@ -65,7 +65,7 @@ def test_noalloc_matches_allocating_path_twice():
         ee_r, loss_r, da_r, dm_r = _reference(env, desc, acts, tgt, S, every)
         torch.cuda.synchronize()
         nc = torch.as_tensor(desc["env_num_chains"], device="cuda")
-        has = (torch.arange(2, device="cuda")[None, :] < nc[:, None])
+        has = (torch.arange(4, device="cuda")[None, :] < nc[:, None])
         assert _rel(ee[:, has], ee_r[:, has]) <= 1e-5, call
         assert _rel(loss, loss_r) <= 1e-5, call
         assert _rel(da, da_r) <= 1e-5, call
