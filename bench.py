@@ -316,6 +316,23 @@ def measure_rollout(cx, wl, desc, T, with_e2e=True):
     return res
 
 
+def measure_path_build(cx, desc, repeats=20):
+    """sg_set_paths over every env: device time per rebuild of all tables."""
+    torch = cx.torch
+    from paper_2310_04676_gb300 import sg
+    env = sg.Env(desc)
+    ctrl = torch.as_tensor(desc["path_ctrl"], device=cx.dev)
+    for _ in range(3):
+        env.set_paths(ctrl)
+    ms = cx.timed(lambda: env.set_paths(ctrl), repeats)
+    E, K, W_ = desc["num_envs"], int(desc["path_ctrl_len"]), int(desc["path_len"])
+    us = 1e3 * sum(ms) / len(ms)
+    nbytes = E * (K + W_) * 12                  # control points in, waypoint table out
+    return {"us_per_rebuild": us, "envs": E, "ctrl_points": K, "waypoints": W_,
+            "algorithmic_bytes": nbytes, "achieved_gbs": nbytes / (us * 1e-6) / 1e9,
+            "form": "sg_set_paths, all envs, one launch", "gpu_launches": 1}
+
+
 def measure_adjoint(cx, wl, desc, T, every=8):
     """Differentiable rollout: checkpointed forward + adjoint, per rollout."""
     torch = cx.torch
@@ -406,6 +423,8 @@ def run_rollout_config(cx, name, E=None):
                        "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]}
     line["gpu_launches"] = args.steps
     line["clocks"] = r["clocks"]
+    if int(desc["task"]) == 1 and desc.get("path_ctrl") is not None:
+        line["path_build"] = measure_path_build(cx, desc)
     return line, wl
 
 

@@ -123,7 +123,8 @@ typedef struct sg_desc {
   int32_t episode_len;              /* steps until the time-out bit, >= 1 */
   int32_t task;                     /* SG_TASK_* */
   const float *goal;                /* [E][4][3] per-chain goal (SG_TASK_REACH) */
-  const float *path;                /* [E][path_len][3] waypoints (SG_TASK_PATH), else NULL */
+  const float *path;                /* [E][path_len][3] waypoints (SG_TASK_PATH), or NULL
+                                       when path_ctrl is given, else NULL */
   int32_t path_len;                 /* W >= 4 for SG_TASK_PATH */
   float alpha;                      /* path reward scale */
   const int32_t *joint_drive;       /* [E][J] SG_DRIVE_*, or NULL (all position) */
@@ -136,6 +137,10 @@ typedef struct sg_desc {
   uint32_t seed;
   float track_sigma;                /* > 0 for SG_TASK_TRACK */
   float track_limit;                /* > 0 for SG_TASK_TRACK */
+  /* SG_TASK_PATH with path == NULL: the library builds each env's waypoint
+   * table on the device from these control points (see sg_set_paths). */
+  const float *path_ctrl;           /* [E][path_ctrl_len][3], else NULL */
+  int32_t path_ctrl_len;            /* K, 2..64 */
 } sg_desc;
 
 /*
@@ -233,7 +238,9 @@ sg_status sg_rollout_host(sg_ctx *ctx, const float *actions_host, int32_t T, flo
  * computes the bias forces and drive terms, the other the mass matrix and
  * the solve), which doubles the parallelism of batches too small to fill
  * the GPU; threads_per_block must then be 64, 128 or 256.  Results do not
- * depend on the plan (bit-identical). */
+ * depend on the threads per block or the rollout mode (bit-identical); the
+ * two chain splits round differently (they agree to FP32 rounding, not
+ * bit for bit). */
 sg_status sg_set_launch(sg_ctx *ctx, int32_t threads_per_block, int32_t rollout_mode,
                         int32_t chain_split);
 sg_status sg_get_launch(const sg_ctx *ctx, int32_t *threads_per_block, int32_t *rollout_mode,
@@ -328,6 +335,30 @@ sg_status sg_diff_track_noalloc(sg_ctx *ctx, const float *actions_dev, int32_t T
  * NULL.  SG_ERR_INVALID_ARG for other tasks. */
 sg_status sg_get_goal_state(sg_ctx *ctx, float *offset_dev, float *velocity_dev);
 sg_status sg_set_goal_state(sg_ctx *ctx, const float *offset_dev, const float *velocity_dev);
+
+/*
+ * Path-following waypoints built on the device (Results, "Path following":
+ * a cubic spline S(t) = a (t - t_i)^3 + b (t - t_i)^2 + c (t - t_i) + d
+ * through the path's points, sampled at regular intervals of distance along
+ * it).  For every env with env_mask_dev[e] != 0 (uint8 [E], device; NULL =
+ * all envs) the waypoint table is rebuilt from ctrl_dev [E][K][3] (device,
+ * float; rows of unmasked envs are not read):
+ *   - natural cubic spline through the K control points at t_i = i
+ *     (S'' = 0 at both ends);
+ *   - a polyline of 64 points per segment (t = t_i + j / 64) plus the end
+ *     point, and its cumulative chord length;
+ *   - waypoint w (0 <= w < path_len) at arc length w L / (path_len - 1)
+ *     along that polyline (L its length), by linear interpolation.
+ * K is 2..64 and need not equal path_ctrl_len.  Call it together with
+ * sg_reset for new per-episode paths: waypoint w is the target at w steps
+ * after reset.  Non-finite control points give non-finite waypoints.  The
+ * table is rebuilt asynchronously on the context's stream.
+ * SG_ERR_INVALID_ARG for other tasks, a NULL ctrl_dev or K out of range. */
+sg_status sg_set_paths(sg_ctx *ctx, const float *ctrl_dev, int32_t K, const uint8_t *env_mask_dev);
+
+/* Copy the waypoint tables [E][path_len][3] (float) into path_dev (device).
+ * SG_ERR_INVALID_ARG for other tasks. */
+sg_status sg_get_paths(sg_ctx *ctx, float *path_dev);
 
 /* Synchronise the context's stream, then read and clear the device error
  * flags: SG_ERR_NONFINITE if any env produced a non-finite state since the

@@ -15,6 +15,8 @@ environments of identical structure, loops over links in Python):
                   and an RK4 integrator for conservation tests.
 * ``env``         the per-environment observation, reward, done, reset and
                   step of the reaching / path-following / two-arm tasks.
+* ``path``        the path-following waypoints: natural cubic spline through
+                  control points, resampled at equal arc length.
 * ``rng``         the counter-based normal deviates of the tracking task's
                   moving goals (SplitMix64 finaliser, Box-Muller).
 * ``lagrangian``  an independent equation of motion from the Lagrangian
@@ -30,4 +32,4 @@ Parity pins: every function is checked in ``tests/test_oracle_*.py``
 against closed forms, invariants and finite differences; none is
 "parity unpinned".
 """
-from . import spatial, model, dynamics, env, lagrangian, rng  # noqa: F401
+from . import spatial, model, dynamics, env, lagrangian, path, rng  # noqa: F401

@@ -29,6 +29,7 @@ import numpy as np
 import torch
 
 from . import dynamics as dyn
+from . import path as path_mod
 from .model import PRISMATIC, groups, make_params
 from .rng import goal_noise
 from .spatial import DT
@@ -92,7 +93,20 @@ class OracleEnv:
         self.step_count = np.zeros(self.E, np.int64)
         self.goal_off = np.zeros((self.E, 4, 3))     # tracking task: goal offset, velocity
         self.goal_vel = np.zeros((self.E, 4, 3))
+        self.path = None                             # path task: waypoint tables [E, W, 3]
+        if self.task == 1:
+            W = int(desc["path_len"])
+            if desc.get("path") is not None:
+                self.path = np.asarray(desc["path"], np.float64).reshape(self.E, W, 3).copy()
+            else:
+                self.path = path_mod.waypoints(desc["path_ctrl"], W)
         self.reset()
+
+    def set_paths(self, ctrl, mask=None):
+        """New waypoint tables for the envs in ``mask`` from control points [E, K, 3]."""
+        m = np.ones(self.E, bool) if mask is None else np.asarray(mask).astype(bool)
+        if m.any():
+            self.path[m] = path_mod.waypoints(np.asarray(ctrl)[m], self.path.shape[1])
 
     # -- state -------------------------------------------------------------
     def reset(self, mask=None):
@@ -161,7 +175,7 @@ class OracleEnv:
         nc = tree.n_chains
         if self.task == 1:
             W = int(self.desc["path_len"])
-            path = np.asarray(self.desc["path"], np.float64)[idx]  # [E, W, 3]
+            path = self.path[idx]                                  # [E, W, 3]
             t = self.step_count[idx]
             wp = lambda k: torch.as_tensor(path[np.arange(len(idx)), np.minimum(t + k, W - 1)])
             quat = tip_quaternion(tree, q)[:, 0]

@@ -15,6 +15,7 @@
 #include "sg_internal.h"
 #include "sg_diff.h"
 #include "sg_kernels.h"
+#include "sg_path.h"
 
 struct sg_ctx {
   sg::Plan plan;
@@ -322,7 +323,16 @@ sg_status sg_create(const sg_desc* desc, void* stream, sg_ctx** out) {
   step(upload<float>(&c->d_qd, nullptr, (size_t)sg::kMaxLinks * NS, c->stream));
   step(upload<int32_t>(&c->d_step_count, nullptr, (size_t)P.num_envs, c->stream));
   step(upload<int32_t>(&c->d_err, nullptr, 1, c->stream));
-  step(upload(&c->d_path, P.path.empty() ? nullptr : P.path.data(), P.path.size(), c->stream));
+  const size_t path_floats = (size_t)P.num_envs * P.path_len * 3;
+  step(upload(&c->d_path, P.path.empty() ? nullptr : P.path.data(), path_floats, c->stream));
+  float* d_ctrl = nullptr;     // control points of device-built paths (freed below)
+  if (e == cudaSuccess && P.task == SG_TASK_PATH) e = sg::prepare_path_kernel();
+  if (!P.path_ctrl.empty()) {
+    step(upload(&d_ctrl, P.path_ctrl.data(), P.path_ctrl.size(), c->stream));
+    if (e == cudaSuccess)
+      e = sg::launch_build_paths(d_ctrl, P.path_ctrl_len, nullptr, P.num_envs, P.path_len,
+                                 c->d_path, c->stream);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_q, 0, sizeof(float) * sg::kMaxLinks * NS, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_qd, 0, sizeof(float) * sg::kMaxLinks * NS, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream);
@@ -335,6 +345,10 @@ sg_status sg_create(const sg_desc* desc, void* stream, sg_ctx** out) {
   if (e == cudaSuccess) e = sg::prepare_diff_kernels();
   if (e == cudaSuccess) e = sg::launch_reset(state_args(c), nullptr, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (d_ctrl) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(d_ctrl);
+  }
   if (e != cudaSuccess) {
     g_create_error = std::string("sg_create: ") + cudaGetErrorString(e);
     sg_status code = e == cudaErrorMemoryAllocation ? SG_ERR_OOM : SG_ERR_CUDA;
@@ -658,6 +672,31 @@ sg_status sg_set_goal_state(sg_ctx* ctx, const float* offset_dev, const float* v
   return cuda_err(ctx, sg::launch_goal_state(state_args(ctx), nullptr, nullptr, offset_dev,
                                              velocity_dev, ctx->stream),
                   "sg_set_goal_state");
+}
+
+sg_status sg_set_paths(sg_ctx* ctx, const float* ctrl_dev, int32_t K,
+                       const uint8_t* env_mask_dev) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  if (ctx->plan.task != SG_TASK_PATH)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "sg_set_paths: not a path-following context");
+  if (!ctrl_dev) return set_err(ctx, SG_ERR_INVALID_ARG, "sg_set_paths: ctrl_dev is NULL");
+  if (K < 2 || K > sg::kMaxPathCtrl)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "sg_set_paths: K must be 2..64");
+  return cuda_err(ctx,
+                  sg::launch_build_paths(ctrl_dev, K, env_mask_dev, ctx->plan.num_envs,
+                                         ctx->plan.path_len, ctx->d_path, ctx->stream),
+                  "sg_set_paths");
+}
+
+sg_status sg_get_paths(sg_ctx* ctx, float* path_dev) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  if (ctx->plan.task != SG_TASK_PATH)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "sg_get_paths: not a path-following context");
+  if (!path_dev) return set_err(ctx, SG_ERR_INVALID_ARG, "sg_get_paths: path_dev is NULL");
+  const size_t bytes = sizeof(float) * (size_t)ctx->plan.num_envs * ctx->plan.path_len * 3;
+  return cuda_err(ctx, cudaMemcpyAsync(path_dev, ctx->d_path, bytes, cudaMemcpyDeviceToDevice,
+                                       ctx->stream),
+                  "sg_get_paths");
 }
 
 sg_status sg_sync_status(sg_ctx* ctx) {

@@ -19,6 +19,7 @@ constexpr int kWarp = 32;
 constexpr int kMaxLinks = 7;          // joints per chain (SG_MAX_CHAIN_JOINTS)
 constexpr int kMaxChains = 4;         // chains per env (SG_MAX_CHAINS)
 constexpr int kMaxDof = kMaxLinks * kMaxChains;   // joints per env
+constexpr int kMaxPathCtrl = 64;      // control points of a device-built path
 constexpr int kChainFields = 8;       // per chain slot: base xyz, goal xyz, joint code, pad
 constexpr int kLinkFields = 12;       // per link: see LinkField
 constexpr int kRecordFloats = (kChainFields + kMaxLinks * kLinkFields) * kWarp;
@@ -82,7 +83,9 @@ struct Plan {
   std::vector<float> q0;            // [kMaxLinks][NS]
   std::vector<float> mass0;         // [kMaxLinks][NS] link masses of the description
   std::vector<float> inertia0;      // [3][kMaxLinks][NS] link inertias of the description
-  std::vector<float> path;          // [E][W][3] (path task)
+  std::vector<float> path;          // [E][W][3] (path task, table given)
+  std::vector<float> path_ctrl;     // [E][K][3] (path task, table built on the device)
+  int path_ctrl_len = 0;
 };
 
 // Validate `d` and build the packing plan; returns SG_OK or an error with *err set.

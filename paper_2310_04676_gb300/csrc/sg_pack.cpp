@@ -67,7 +67,16 @@ sg_status build_plan(const sg_desc* d, Plan* P, std::string* err) {
        !finite(d->track_limit)))
     return fail(SG_ERR_INVALID_ARG, "tracking needs track_sigma > 0 and track_limit > 0");
   if (d->task == SG_TASK_PATH) {
-    if (!d->path || d->path_len < 4) return fail(SG_ERR_INVALID_ARG, "path task needs path, path_len >= 4");
+    if (d->path_len < 4) return fail(SG_ERR_INVALID_ARG, "path task needs path_len >= 4");
+    if ((d->path != nullptr) == (d->path_ctrl != nullptr))
+      return fail(SG_ERR_INVALID_ARG, "path task needs exactly one of path and path_ctrl");
+    if (d->path_ctrl) {
+      if (d->path_ctrl_len < 2 || d->path_ctrl_len > kMaxPathCtrl)
+        return fail(SG_ERR_INVALID_ARG, "path_ctrl_len must be 2..64");
+      const size_t n = (size_t)E * d->path_ctrl_len * 3;
+      for (size_t i = 0; i < n; ++i)
+        if (!finite(d->path_ctrl[i])) return fail(SG_ERR_INVALID_ARG, "non-finite path_ctrl");
+    }
     if (!finite(d->alpha)) return fail(SG_ERR_INVALID_ARG, "alpha not finite");
   }
 
@@ -228,10 +237,15 @@ sg_status build_plan(const sg_desc* d, Plan* P, std::string* err) {
     }
     std::memcpy(&CF(CF_CODE), &code, 4);
   }
-  if (d->task == SG_TASK_PATH)
+  P->path.clear();
+  P->path_ctrl.clear();
+  P->path_ctrl_len = 0;
+  if (d->task == SG_TASK_PATH && d->path) {
     P->path.assign(d->path, d->path + (size_t)E * d->path_len * 3);
-  else
-    P->path.clear();
+  } else if (d->task == SG_TASK_PATH) {
+    P->path_ctrl.assign(d->path_ctrl, d->path_ctrl + (size_t)E * d->path_ctrl_len * 3);
+    P->path_ctrl_len = d->path_ctrl_len;
+  }
   return SG_OK;
 }
 

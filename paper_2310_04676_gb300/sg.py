@@ -47,6 +47,7 @@ class SgDesc(ctypes.Structure):
         ("alpha", ctypes.c_float),
         ("joint_drive", _c_i32p),
         ("seed", ctypes.c_uint32), ("track_sigma", ctypes.c_float), ("track_limit", ctypes.c_float),
+        ("path_ctrl", _c_f32p), ("path_ctrl_len", ctypes.c_int32),
     ]
 
 
@@ -91,6 +92,8 @@ def load_library(path=LIB_PATH):
         "sg_get_goal_state": (i32, [vp, vp, vp]),
         "sg_set_goal_state": (i32, [vp, vp, vp]),
         "sg_diff_track_noalloc": (i32, [vp, vp, i32, f32, i32, i32, vp, vp, vp, vp, vp]),
+        "sg_set_paths": (i32, [vp, vp, i32, u8p]),
+        "sg_get_paths": (i32, [vp, vp]),
         "sg_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -138,6 +141,9 @@ def make_c_desc(desc):
     W = int(desc.get("path_len") or 0)
     d.path = p("path", f32, (E, W, 3), _c_f32p) if W else ctypes.cast(None, _c_f32p)
     d.path_len = W
+    K = int(desc.get("path_ctrl_len") or 0)
+    d.path_ctrl = p("path_ctrl", f32, (E, K, 3), _c_f32p) if K else ctypes.cast(None, _c_f32p)
+    d.path_ctrl_len = K
     d.episode_len = int(desc["episode_len"])
     d.task = int(desc["task"])
     d.alpha = float(desc.get("alpha", 1.0))
@@ -348,6 +354,25 @@ class Env:
             if t is not None:
                 self._want(t, self._torch.float32, shape, name)
         self._check(self.lib.sg_set_goal_state(self.ctx, _ptr(offset), _ptr(velocity)))
+
+    def set_paths(self, ctrl, mask=None):
+        """Path task: rebuild the waypoint tables of the envs in ``mask``
+        (uint8 [E], None = all) from control points ctrl [E, K, 3]."""
+        self._sync_stream()
+        if ctrl.dim() != 3:
+            raise ValueError("ctrl must be [E, K, 3]")
+        self._want(ctrl, self._torch.float32, (self.num_envs, int(ctrl.shape[1]), 3), "ctrl")
+        if mask is not None:
+            self._want(mask, self._torch.uint8, (self.num_envs,), "mask")
+        self._check(self.lib.sg_set_paths(self.ctx, _ptr(ctrl), int(ctrl.shape[1]), _ptr(mask)))
+
+    def get_paths(self, path_len):
+        """Path task: the waypoint tables [E, path_len, 3]."""
+        self._sync_stream()
+        out = self._torch.empty(self.num_envs, int(path_len), 3, dtype=self._torch.float32,
+                                device=self.device)
+        self._check(self.lib.sg_get_paths(self.ctx, _ptr(out)))
+        return out
 
     def get_state(self):
         self._sync_stream()

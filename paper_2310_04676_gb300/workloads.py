@@ -7,7 +7,7 @@ revolute; Results, "Multi-Tool Target Reaching": two-arm variants).
 
 This module only builds *inputs*: per-environment robot descriptions
 (link lengths, masses, box inertias, joint axes and limits, drive gains),
-goals, path-following waypoint tables and joint-target action sequences.
+goals, path control points and joint-target action sequences.
 It holds none of the dynamics.  Both the CUDA path and the FP64 oracle
 consume exactly the arrays produced here.
 
@@ -149,59 +149,27 @@ def make_desc(kinds, *, seed_params=1, seed_goals=3, shared_params=False,
     if task == 1:
         if any(len(KINDS[k]["chains"]) != 1 for k in kinds):
             raise ValueError("path following is defined for single-chain arms")
-        W = int(path_len)
-        d["path_len"] = W
-        d["path"] = make_paths(d, W, rg)
+        d["path_len"] = int(path_len)          # waypoints the library builds per env
+        d["path_ctrl"] = make_path_ctrl(d, rg)
+        d["path_ctrl_len"] = d["path_ctrl"].shape[1]
+        d["path"] = None
     else:
         d["path_len"] = 0
         d["path"] = None
     return d
 
 
-def natural_cubic_spline(pts):
-    """Natural cubic spline through ``pts`` [K][3] at t_i = i.
-
-    Returns coefficients (a, b, c, d) per segment so that on [t_i, t_i+1]
-    S(t) = a (t-t_i)^3 + b (t-t_i)^2 + c (t-t_i) + d  (the form of the path
-    spline in Results, "Path following").  Natural end conditions
-    (S'' = 0 at both ends) are this build's reading; the paper names none.
-    """
-    from scipy.interpolate import CubicSpline
-    K = pts.shape[0]
-    cs = CubicSpline(np.arange(K, dtype=np.float64), pts, bc_type="natural")
-    # scipy stores c[k, i] for (t - t_i)^(3-k)
-    return cs.c[0], cs.c[1], cs.c[2], cs.c[3]
-
-
-def resample_equal_arclength(a, b, c, dd, W, dense=64):
-    """Waypoints at equal arc-length spacing along the spline (Results,
-    "Path following": waypoints sampled at regular distance intervals)."""
-    nseg = a.shape[0]
-    s = np.linspace(0.0, 1.0, dense, endpoint=False)
-    P = []
-    for i in range(nseg):
-        P.append(((a[i] * s[:, None] + b[i]) * s[:, None] + c[i]) * s[:, None] + dd[i])
-    last = a[-1] + b[-1] + c[-1] + dd[-1]
-    P = np.concatenate(P + [last[None]], 0)
-    seg = np.linalg.norm(np.diff(P, axis=0), axis=1)
-    cum = np.concatenate([[0.0], np.cumsum(seg)])
-    target = np.linspace(0.0, cum[-1], W)
-    out = np.empty((W, 3))
-    for k in range(3):
-        out[:, k] = np.interp(target, cum, P[:, k])
-    return out
-
-
-def make_paths(d, W, rng, npts=16):
+def make_path_ctrl(d, rng, npts=16):
+    """Control points [E][npts][3] of each env's path: uniform in a 0.3 m cube
+    centred at (0.3R, 0, 0.5R), R the arm's reach (the library builds the
+    spline and the waypoint table from them)."""
     E = d["num_envs"]
-    paths = np.zeros((E, W, 3), np.float32)
+    ctrl = np.zeros((E, npts, 3), np.float32)
     for e in range(E):
         reach = float(d["link_len"][e, : d["chain_num_joints"][e, 0]].sum())
         centre = np.array([0.3 * reach, 0.0, 0.5 * reach])
-        pts = centre + rng.uniform(-0.15, 0.15, size=(npts, 3))
-        a, b, c, dd = natural_cubic_spline(pts)
-        paths[e] = resample_equal_arclength(a, b, c, dd, W).astype(np.float32)
-    return paths
+        ctrl[e] = centre + rng.uniform(-0.15, 0.15, size=(npts, 3))
+    return ctrl
 
 
 def joint_targets(desc, T, *, seed=2, resample_every=50, t0=0):

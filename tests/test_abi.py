@@ -102,6 +102,23 @@ def test_path_task_rejects_two_arm_envs(lib):
     assert ei.value.status == sg.SG_ERR_UNSUPPORTED
 
 
+def test_path_task_inputs_are_validated(lib):
+    d = W.make_desc(["7R"] * 3, task=1, path_len=8)
+    sg.plan(d)                                             # control points only: fine
+    both = dict(d, path=np.zeros((3, 8, 3), np.float32))
+    short = dict(d, path_ctrl_len=1, path_ctrl=d["path_ctrl"][:, :1].copy())
+    bad = dict(d, path_ctrl=d["path_ctrl"].copy())
+    bad["path_ctrl"][1, 3, 2] = np.inf
+    few = dict(d, path_len=3)
+    for dd in (both, short, bad, few):
+        with pytest.raises(sg.SgError) as ei:
+            sg.plan(dd)
+        assert ei.value.status == sg.SG_ERR_INVALID_ARG
+    long_ = dict(d, path_ctrl_len=65, path_ctrl=np.zeros((3, 65, 3), np.float32))
+    with pytest.raises(sg.SgError):
+        sg.plan(long_)
+
+
 def test_null_context_calls_are_rejected(lib):
     assert lib.sg_step(None, None, ctypes.c_float(0.01), 1, None, None, None) == sg.SG_ERR_INVALID_ARG
     assert lib.sg_reset(None, None) == sg.SG_ERR_INVALID_ARG

@@ -156,6 +156,8 @@ def test_path_following_matches_oracle():
     env, ref = sg.Env(desc), OracleEnv(desc)
     assert env.obs_dim == 30
     acts = W.joint_targets(desc, T)
+    table = env.get_paths(T + 3).cpu().numpy()            # built on the device at create
+    assert np.abs(table - ref.path).max() <= 2e-6
     for t in range(T):
         q0, qd0, sc0 = env.get_state()
         obs, rew, done = env.step(cuda(acts[t]), DT, 4)
@@ -169,7 +171,9 @@ def test_path_following_matches_oracle():
         sgn = np.where((qg * qr).sum(1, keepdims=True) < 0, -1.0, 1.0)
         assert np.abs(qg * sgn - qr).max() <= 1e-5
         assert np.abs(o_g[:, :17] - o[:, :17]).max() <= 1e-5
-        assert np.abs(o_g[:, 21:] - o[:, 21:]).max() == 0          # waypoints copied
+        k = np.minimum(t + 1 + np.arange(1, 4), T + 2)
+        assert np.array_equal(o_g[:, 21:30], table[:, k].reshape(E, 9))   # waypoints copied
+        assert np.abs(o_g[:, 21:] - o[:, 21:]).max() <= 2e-6
         assert np.abs(rew.cpu().numpy() - r).max() <= 1e-5
     assert (done.cpu().numpy() == 2).all()
 

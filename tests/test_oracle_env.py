@@ -61,7 +61,7 @@ def test_path_following_obs_and_reward():
     for t in range(11):
         obs, rew, _ = env.step(acts[t], 1 / 60, 4)
         k = t + 1
-        path = d["path"]
+        path = env.path
         for e in range(3):
             o = obs[e]
             ee = o[14:17]

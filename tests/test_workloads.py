@@ -1,4 +1,4 @@
-"""Input generators: counts, ranges and the path spline (host-side inputs)."""
+"""Input generators: counts, ranges, path control points and action draws."""
 import numpy as np
 
 from paper_2310_04676_gb300 import workloads as W
@@ -23,26 +23,15 @@ def test_desc_ranges():
         assert np.allclose(d["q_hi"][e, :n][~pris], np.pi / 2)
 
 
-def test_natural_spline_interpolates_with_zero_end_curvature():
-    rng = np.random.default_rng(0)
-    pts = rng.uniform(-1, 1, size=(16, 3))
-    a, b, c, d = W.natural_cubic_spline(pts)
-    assert np.allclose(d, pts[:-1])
-    assert np.allclose(a[-1] + b[-1] + c[-1] + d[-1], pts[-1])
-    assert np.allclose(b[0], 0)                        # S''(t_0) = 2b = 0
-    assert np.allclose(6 * a[-1] + 2 * b[-1], 0)       # S''(t_end) = 0
-    # C2 continuity at interior knots
-    assert np.allclose(3 * a[:-1] + 2 * b[:-1] + c[:-1], c[1:])
-    assert np.allclose(6 * a[:-1] + 2 * b[:-1], 2 * b[1:])
-
-
-def test_waypoints_equally_spaced():
-    rng = np.random.default_rng(1)
-    pts = rng.uniform(-0.15, 0.15, size=(16, 3))
-    wp = W.resample_equal_arclength(*W.natural_cubic_spline(pts), 503)
-    seg = np.linalg.norm(np.diff(wp, axis=0), axis=1)
-    assert seg.std() / seg.mean() < 0.02
-    assert np.allclose(wp[0], pts[0]) and np.allclose(wp[-1], pts[-1])
+def test_path_control_points_in_goal_cube():
+    d = W.make_desc(["7R"] * 6, task=1, path_len=40)
+    assert d["path"] is None and d["path_len"] == 40
+    ctrl = d["path_ctrl"]
+    assert ctrl.shape == (6, d["path_ctrl_len"], 3) and ctrl.dtype == np.float32
+    for e in range(6):
+        R = d["link_len"][e, :7].sum()
+        centre = np.array([0.3 * R, 0.0, 0.5 * R])
+        assert (np.abs(ctrl[e] - centre) <= 0.15 + 1e-6).all()
 
 
 def test_joint_targets_resampled_every_50_steps():
