@@ -207,6 +207,18 @@ def cpu_baseline(wl, seconds=12.0, max_envs=2048):
                       % (n, E, steps, el)}
 
 
+def cpu_baseline_single_core(wl, seconds=6.0, max_envs=256):
+    """The same oracle restricted to one host thread, on a smaller sample."""
+    import torch
+    prev = torch.get_num_threads()
+    torch.set_num_threads(1)
+    try:
+        r = cpu_baseline(wl, seconds=seconds, max_envs=max_envs)
+    finally:
+        torch.set_num_threads(prev)
+    return r
+
+
 def grad_error(wl, acts_np, tg_np, da, dm, n_envs=16):
     """Adjoint gradients of the first `n_envs` envs against the oracle's
     reverse mode (FP64 autograd through its rollout): max per-env relative
@@ -270,7 +282,11 @@ def measure_rollout(cx, wl, desc, T, with_e2e=True):
     acts = torch.as_tensor(W.joint_targets(desc, T, seed=2 + 1000 * cx.rank), device=cx.dev)
     env = sg.Env(desc)
     out = env.empty_outputs(T)
-    threads, mode, split, _ = env.autotune(acts, dt, S, out=out, repeats=3)
+    if args.launch:
+        threads, mode, split = args.launch
+        env.set_launch(threads, mode, split)
+    else:
+        threads, mode, split, _ = env.autotune(acts, dt, S, out=out, repeats=3)
     sgraph, plain = sg.Env(desc), sg.Env(desc)
     sgraph.set_launch(threads, sg.ROLLOUT_STEP_GRAPH, split)
     plain.set_launch(threads, sg.ROLLOUT_PERSISTENT, split)
@@ -360,19 +376,38 @@ def measure_adjoint(cx, wl, desc, T, every=8):
             "tg": tg_np, "every": every}
 
 
+_FMA_RATE = {}
+
+
+def measured_fma_rate():
+    """FP32 FMA rate of this GPU from the library's probe (TFLOP/s), once."""
+    if "v" not in _FMA_RATE:
+        from paper_2310_04676_gb300 import sg
+        _FMA_RATE["v"] = sg.fp32_fma_rate()
+    return _FMA_RATE["v"]
+
+
 def roofline(kernel_name, flops_launch, bytes_launch, ms_per_launch, props, peaks, peak_src):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     s = ms_per_launch / 1e3
     achieved = flops_launch / s / 1e12
+    fma = measured_fma_rate()
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": profiled_traffic(kernel_name),
+            "fma_probe_tflops": fma, "frac_of_fma_probe": achieved / fma,
             "kernel": kernel_name,
             "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s max SM clock)"
                            % (props.multi_processor_count, sm_max, peak_src),
             "flops_per_launch": flops_launch, "algorithmic_bytes_per_launch": bytes_launch,
             "hbm_gbs": bytes_launch / s / 1e9,
             "hbm_frac": bytes_launch / s / 1e9 / float(peaks.get("hbm_gbs", 6800.0))}
+
+
+def stats(ms):
+    """Median and interquartile range of per-step device times (ms)."""
+    q1, med, q3 = np.percentile(np.asarray(ms, np.float64), [25, 50, 75])
+    return {"median_ms": float(med), "iqr_ms": float(q3 - q1), "n": len(ms)}
 
 
 def base_line(args, world, value, ms_step, config):
@@ -407,6 +442,7 @@ def run_rollout_config(cx, name, E=None):
            "l2": "flushed (256 MiB write) before every timed step"}
     line = base_line(args, world, value, 1e3 * t["ours"] / args.steps, cfg)
     line["us_per_control_step"] = 1e6 * t["ours"] / args.steps / T
+    line["step_time_stats"] = stats(r["ms"]["ours"])
     for k, label in (("step_graph", "%d single-step kernels replayed from a CUDA graph" % T),
                      ("plain", "one sg_step call (one kernel launch) per control step")):
         line[k] = {"value": aggregate_rate(units, t[k], world, cx.dev), "unit": "env-steps/s",
@@ -428,11 +464,11 @@ def run_rollout_config(cx, name, E=None):
     return line, wl
 
 
-def run_adjoint_config(cx, with_error):
+def run_adjoint_config(cx, with_error, name="C4", E=None, T=None, err_envs=16):
     from paper_2310_04676_gb300 import workloads as W
-    wl = W.config("C4")
+    wl = W.config(name, num_envs=E)
     desc = replica_desc(wl, cx.rank)
-    a = measure_adjoint(cx, wl, desc, wl.steps, every=8)
+    a = measure_adjoint(cx, wl, desc, T or wl.steps, every=8)
     t = sum(a["ms"]) / 1e3
     units = a["E"] * a["T"] * cx.args.steps
     out = {"workload": "%s, T=%d, S=%d, checkpoints every %d steps"
@@ -440,12 +476,14 @@ def run_adjoint_config(cx, with_error):
            "value": aggregate_rate(units, t, cx.world, cx.dev),
            "unit": "env-steps/s (forward with checkpoints + adjoint)",
            "ms_per_rollout": 1e3 * t / cx.args.steps,
+           "rollout_time_stats": stats(a["ms"]),
            "gpu_launches": 2 * cx.args.steps}
     if with_error:
-        ea, em = grad_error(wl, a["acts"], a["tg"], a["da"], a["dm"])
+        ea, em = grad_error(wl, a["acts"], a["tg"], a["da"], a["dm"], n_envs=err_envs)
         out["rel_err_actions"] = ea
         out["rel_err_mass"] = em
-        out["error_vs"] = "FP64 oracle reverse mode, 16 envs, max per-env relative L2 error"
+        out["error_vs"] = ("FP64 oracle reverse mode, %d envs, max per-env relative L2 error"
+                           % err_envs)
     return out
 
 
@@ -476,14 +514,19 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="C3", choices=["C1", "C2", "C3", "C4", "C5"])
     ap.add_argument("--envs", type=int, nargs="*", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch", default=None,
+                    help="threads,mode,split: fixed launch plan instead of the autotuner "
+                         "(used to profile one plan)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.launch:
+        args.launch = tuple(int(x) for x in args.launch.split(","))
     if args.impl == "reference":
         return run_reference(args)
 
@@ -510,12 +553,24 @@ def main():
             line, _ = run_rollout_config(cx, args.config, E)
             if rank == 0:
                 print(json.dumps(line))
+        if args.config == "C5" and not args.envs:
+            # the sweep's adjoint runs: 4096 envs, horizon 128, limit springs, 8 substeps
+            g = run_adjoint_config(cx, with_error=want_cpu, name="C5", E=4096, T=128, err_envs=4)
+            if rank == 0:
+                line = base_line(args, world, g["value"], g["ms_per_rollout"],
+                                 {"workload": g["workload"]})
+                line["unit"] = g["unit"]
+                line["grad"] = g
+                line["gpu_launches"] = g["gpu_launches"]
+                print(json.dumps(line))
     else:
         line, wl = run_rollout_config(cx, args.config)
         if args.config == "C3":
             line["grad"] = run_adjoint_config(cx, with_error=want_cpu)
         if rank == 0:
             line["cpu_baseline"] = cpu_baseline(wl) if want_cpu else None
+            if want_cpu:
+                line["cpu_baseline"]["single_core"] = cpu_baseline_single_core(wl)
             print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -366,6 +366,16 @@ sg_status sg_get_paths(sg_ctx *ctx, float *path_dev);
  * (or SG_ERR_CUDA if the stream reports an error). */
 sg_status sg_sync_status(sg_ctx *ctx);
 
+/* Measurement helper (not part of the method): the device's FP32 FMA rate in
+ * TFLOP/s (an FMA counts 2), the denominator of the step kernels' ALU
+ * roofline.  Runs `repeats` timed launches (after one warm-up) of a kernel
+ * with 8 independent FMA chains per thread, 8 blocks of 256 threads per SM
+ * and iters x 128 FMAs per thread, on `stream` (cudaStream_t, NULL = legacy
+ * default stream) of the current device, and writes the best rate to
+ * *tflops.  Synchronises the stream; allocates and frees a small buffer.
+ * SG_ERR_INVALID_ARG for iters < 1, repeats < 1 or a NULL tflops. */
+sg_status sg_measure_fp32_fma_rate(void *stream, int32_t iters, int32_t repeats, float *tflops);
+
 /* Message of the last failing call on ctx (never NULL; "" if none).
  * With ctx == NULL: the last sg_create failure of this thread. */
 const char *sg_last_error(const sg_ctx *ctx);

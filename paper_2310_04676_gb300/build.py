@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libsg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["sg_api.cu", "sg_kernels.cu", "sg_pair.cu", "sg_diff.cu", "sg_noalloc.cu", "sg_path.cu", "sg_pack.cpp"]
+SOURCES = ["sg_api.cu", "sg_kernels.cu", "sg_pair.cu", "sg_diff.cu", "sg_noalloc.cu", "sg_path.cu", "sg_peak.cu", "sg_pack.cpp"]
 
 
 def nvcc():

@@ -94,6 +94,7 @@ def load_library(path=LIB_PATH):
         "sg_diff_track_noalloc": (i32, [vp, vp, i32, f32, i32, i32, vp, vp, vp, vp, vp]),
         "sg_set_paths": (i32, [vp, vp, i32, u8p]),
         "sg_get_paths": (i32, [vp, vp]),
+        "sg_measure_fp32_fma_rate": (i32, [vp, i32, i32, ctypes.POINTER(f32)]),
         "sg_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -165,6 +166,19 @@ def plan(desc):
         raise SgError(st, buf.value.decode())
     return dict(obs_dim=info.obs_dim, num_slots=info.num_slots, num_chains=info.num_chains,
                 class_slots=list(info.class_slots))
+
+
+def fp32_fma_rate(iters=4096, repeats=5, stream=None):
+    """Measured FP32 FMA rate of the current device in TFLOP/s."""
+    import torch
+    lib = load_library()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = ctypes.c_float()
+    st = lib.sg_measure_fp32_fma_rate(ctypes.c_void_p(s.cuda_stream), int(iters), int(repeats),
+                                      ctypes.byref(out))
+    if st != SG_OK:
+        raise SgError(st, "sg_measure_fp32_fma_rate failed")
+    return float(out.value)
 
 
 def _ptr(t):
