@@ -41,10 +41,18 @@ ROLLOUT_T = {"C1": 50, "C2": 50, "C3": 32, "C5": 50}
 # Algorithmic FP32 operations of the step's formulation (an FMA counts 2),
 # counted by a counting-scalar run of the chain code: per substep of one
 # chain, and per step for the tool-tip kinematics of one chain.
-FLOP_SUBSTEP = {"4R": 774, "7R": 1697, "7P": 1580}
-FLOP_TIP = {"4R": 96, "7R": 168, "7P": 156}
+# Operations the compiler folds (a literal 0 operand, a factor of +-1, two
+# literals) are not counted; ncu's executed FFMA x 2 + FADD + FMUL of the
+# default workload agrees with this count to 2%.
+FLOP_SUBSTEP = {"4R": 581, "7R": 1424, "7P": 1296}
+FLOP_TIP = {"4R": 55, "7R": 127, "7P": 115}
 FLOP_REWARD = 9          # distance to the goal (per chain)
 FLOP_QUAT = 30           # tip quaternion (path task)
+# Adjoint pieces (same counting): one substep's adjoint (forward substep with
+# its factorisation recomputed, the solve with the factor, the reverse RNEA)
+# and the tool-tip Jacobian-transpose product.
+FLOP_SUBSTEP_ADJ = {"4R": 1460, "7R": 3278, "7P": 3069}
+FLOP_TIP_VJP = {"4R": 112, "7R": 238, "7P": 210}
 
 
 def env_step_flops(kinds, substeps, task=0):
@@ -55,6 +63,23 @@ def env_step_flops(kinds, substeps, task=0):
             if task == 1:
                 tot += FLOP_QUAT
     return tot
+
+
+def adjoint_flops(kinds, substeps, T, every):
+    """Algorithmic FLOPs of one differentiable rollout as the checkpointed
+    adjoint computes it: (forward kernel, backward kernel).  The backward
+    recomputes each segment from its checkpoint (all but its last step),
+    each step's substep start states, then runs S substep adjoints and one
+    tip product per step."""
+    fwd = bwd = 0
+    seg_steps = [min(every, T - t0) for t0 in range(0, T, every)]
+    for k in kinds:
+        for c in (["7R", "7R"] if k == "14B" else [k]):
+            sub = FLOP_SUBSTEP[c]
+            fwd += T * (substeps * sub + FLOP_TIP[c])
+            bwd += sum(L - 1 for L in seg_steps) * substeps * sub
+            bwd += T * ((substeps - 1) * sub + FLOP_TIP_VJP[c] + substeps * FLOP_SUBSTEP_ADJ[c])
+    return fwd, bwd
 
 
 def env_step_bytes(desc, obs_dim):
@@ -363,17 +388,29 @@ def measure_adjoint(cx, wl, desc, T, every=8):
     mask = (torch.arange(4, device=cx.dev)[None, :] < nc[:, None]).float()[None, :, :, None]
     res = {}
 
+    kev = []            # per timed rollout: events around the backward kernel
+
     def fwd_bwd():
         ee = env.diff_forward(acts, dt, S, every)
         g = (2.0 * (ee - tg) * mask).contiguous()
-        res["grads"] = env.diff_backward(acts, g)
+        if res.get("timing"):
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ev[0].record(cx.stream)
+            res["grads"] = env.diff_backward(acts, g)
+            ev[1].record(cx.stream)
+            kev.append(ev)
+        else:
+            res["grads"] = env.diff_backward(acts, g)
 
     for _ in range(cx.args.warmup):
         fwd_bwd()
+    res["timing"] = True
     ms = cx.timed(fwd_bwd, cx.args.steps)
+    res["timing"] = False
+    ms_bwd = [a.elapsed_time(b) for a, b in kev]
     da, dm = (x.cpu().numpy() for x in res["grads"])
-    return {"ms": ms, "T": T, "E": desc["num_envs"], "da": da, "dm": dm, "acts": acts_np,
-            "tg": tg_np, "every": every}
+    return {"ms": ms, "ms_bwd": ms_bwd, "T": T, "E": desc["num_envs"], "da": da, "dm": dm,
+            "acts": acts_np, "tg": tg_np, "every": every}
 
 
 _FMA_RATE = {}
@@ -383,7 +420,7 @@ def measured_fma_rate():
     """FP32 FMA rate of this GPU from the library's probe (TFLOP/s), once."""
     if "v" not in _FMA_RATE:
         from paper_2310_04676_gb300 import sg
-        _FMA_RATE["v"] = sg.fp32_fma_rate()
+        _FMA_RATE["v"] = sg.fp32_fma_rate(iters=1024, repeats=3)
     return _FMA_RATE["v"]
 
 
@@ -400,8 +437,9 @@ def roofline(kernel_name, flops_launch, bytes_launch, ms_per_launch, props, peak
             "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s max SM clock)"
                            % (props.multi_processor_count, sm_max, peak_src),
             "flops_per_launch": flops_launch, "algorithmic_bytes_per_launch": bytes_launch,
-            "hbm_gbs": bytes_launch / s / 1e9,
-            "hbm_frac": bytes_launch / s / 1e9 / float(peaks.get("hbm_gbs", 6800.0))}
+            "hbm_gbs": bytes_launch / s / 1e9 if bytes_launch else None,
+            "hbm_frac": (bytes_launch / s / 1e9 / float(peaks.get("hbm_gbs", 6800.0))
+                         if bytes_launch else None)}
 
 
 def stats(ms):
@@ -478,6 +516,17 @@ def run_adjoint_config(cx, with_error, name="C4", E=None, T=None, err_envs=16):
            "ms_per_rollout": 1e3 * t / cx.args.steps,
            "rollout_time_stats": stats(a["ms"]),
            "gpu_launches": 2 * cx.args.steps}
+    f_fwd, f_bwd = adjoint_flops(wl.kinds, wl.substeps, a["T"], a["every"])
+    peaks, src = load_peaks()
+    props = cx.torch.cuda.get_device_properties(cx.dev)
+    ms_b = sum(a["ms_bwd"]) / len(a["ms_bwd"])
+    rf = roofline("diff_backward_kernel", f_bwd, None, ms_b, props, peaks, src)
+    rf.pop("hbm_gbs", None), rf.pop("hbm_frac", None), rf.pop("algorithmic_bytes_per_launch", None)
+    rf["traffic"] = None
+    out["roofline"] = rf
+    out["flops_per_rollout"] = {"forward": f_fwd, "backward": f_bwd}
+    out["ms_backward_kernel"] = ms_b
+    out["rollout_tflops"] = (f_fwd + f_bwd) / (t / cx.args.steps) / 1e12
     if with_error:
         ea, em = grad_error(wl, a["acts"], a["tg"], a["da"], a["dm"], n_envs=err_envs)
         out["rel_err_actions"] = ea
@@ -546,6 +595,7 @@ def main():
                              {"workload": g["workload"]})
             line["unit"] = g["unit"]
             line["grad"] = g
+            line["roofline"] = g["roofline"]
             line["gpu_launches"] = g["gpu_launches"]
             print(json.dumps(line))
     elif args.config == "C5" or args.envs:
@@ -561,6 +611,7 @@ def main():
                                  {"workload": g["workload"]})
                 line["unit"] = g["unit"]
                 line["grad"] = g
+                line["roofline"] = g["roofline"]
                 line["gpu_launches"] = g["gpu_launches"]
                 print(json.dumps(line))
     else:
