@@ -249,14 +249,16 @@ __device__ __forceinline__ void tip_vjp(const Pat& pat, const Rec& rec, const fl
 }
 
 // Forward substep that also returns the Cholesky factor (L in the lower
-// triangle of M, inv = 1 / L_ii), the acceleration a = dqd / h and the
-// drive stiffness k_s of every joint (needed by the adjoint).
+// triangle of M, inv = 1 / L_ii), the velocity increment dqd, the
+// acceleration a = dqd / h and the drive stiffness k_s of every joint
+// (needed by the adjoint).
 template <class Pat>
 __device__ __forceinline__ void substep_record(const Pat& pat, const Rec& rec, const float (&q)[7],
                                                const float (&qd)[7], const float (&qs)[7], float h,
                                                float grav, float (&cq)[Pat::N], float (&sq)[Pat::N],
                                                float (&M)[Pat::N][Pat::N], float (&inv)[Pat::N],
-                                               float (&acc)[Pat::N], float (&ks)[Pat::N]) {
+                                               float (&acc)[Pat::N], float (&ks)[Pat::N],
+                                               float (&dqd)[Pat::N]) {
   constexpr int N = Pat::N;
   float bias[N], rhs[N], arm[N];
   V3 F[N], Nm[N];
@@ -269,6 +271,7 @@ __device__ __forceinline__ void substep_record(const Pat& pat, const Rec& rec, c
   const float hinv = 1.f / h;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
+    dqd[i] = rhs[i];
     if (!pat.active(i)) continue;
     acc[i] = rhs[i] * hinv;
     // k_s = (arm - h d) / h^2 recomputed directly from the limit test
@@ -278,18 +281,15 @@ __device__ __forceinline__ void substep_record(const Pat& pat, const Rec& rec, c
   }
 }
 
-// Adjoint of one substep.  On entry lq, lqd are the cotangents of the
-// substep's outputs (q', qd'); on exit those of its inputs (q, qd).  lqs and
-// lm accumulate the cotangents of the targets q* and the link masses.
+// Adjoint of one substep given its record (start state q, qd, joint
+// trigonometry, Cholesky factor, acceleration and drive stiffness).
 template <class Pat>
-__device__ __forceinline__ void substep_adjoint(const Pat& pat, const Rec& rec, const float (&q)[7],
-                                                const float (&qd)[7], const float (&qs)[7],
-                                                float h, float grav, float (&lq)[7],
-                                                float (&lqd)[7], float (&lqs)[7],
-                                                float (&lm)[7]) {
+__device__ __forceinline__ void substep_adjoint_rec(
+    const Pat& pat, const Rec& rec, const float (&q)[7], const float (&qd)[7],
+    const float (&cq)[Pat::N], const float (&sq)[Pat::N], const float (&M)[Pat::N][Pat::N],
+    const float (&inv)[Pat::N], const float (&acc)[Pat::N], const float (&ks)[Pat::N], float h,
+    float grav, float (&lq)[7], float (&lqd)[7], float (&lqs)[7], float (&lm)[7]) {
   constexpr int N = Pat::N;
-  float cq[N], sq[N], M[N][N], inv[N], acc[N], ks[N];
-  substep_record(pat, rec, q, qd, qs, h, grav, cq, sq, M, inv, acc, ks);
   float mu[N], gq[N], gqd[N], gm[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -312,6 +312,21 @@ __device__ __forceinline__ void substep_adjoint(const Pat& pat, const Rec& rec, 
     lqs[i] += h * (kp + ga) * mu[i];
     lm[i] += -h * gm[i];
   }
+}
+
+// Adjoint of one substep.  On entry lq, lqd are the cotangents of the
+// substep's outputs (q', qd'); on exit those of its inputs (q, qd).  lqs and
+// lm accumulate the cotangents of the targets q* and the link masses.
+template <class Pat>
+__device__ __forceinline__ void substep_adjoint(const Pat& pat, const Rec& rec, const float (&q)[7],
+                                                const float (&qd)[7], const float (&qs)[7],
+                                                float h, float grav, float (&lq)[7],
+                                                float (&lqd)[7], float (&lqs)[7],
+                                                float (&lm)[7]) {
+  constexpr int N = Pat::N;
+  float cq[N], sq[N], M[N][N], inv[N], acc[N], ks[N], dqd[N];
+  substep_record(pat, rec, q, qd, qs, h, grav, cq, sq, M, inv, acc, ks, dqd);
+  substep_adjoint_rec(pat, rec, q, qd, cq, sq, M, inv, acc, ks, h, grav, lq, lqd, lqs, lm);
 }
 
 }  // namespace sg

@@ -63,6 +63,9 @@ struct sg_ctx {
   // differentiable rollout: checkpoint scratch and the last forward's shape
   float* d_ckpt = nullptr;
   size_t ckpt_floats = 0;
+  float* d_replay = nullptr;       // warp-pair backward: two segments of substep records
+  size_t replay_floats = 0;
+  bool use_replay = false;
   bool diff_ready = false;
   int diff_T = 0, diff_substeps = 0, diff_every = 0;
   float diff_dt = 0.f;
@@ -103,7 +106,7 @@ void free_ctx(sg_ctx* c) {
                   c->d_slot_info, c->d_warp_class, c->d_step_count, c->d_err,
                   c->d_stage_act, c->d_stage_obs, c->d_stage_rew, c->d_stage_done,
                   c->d_snap_q, c->d_snap_qd, c->d_snap_sc, c->d_mass0, c->d_inertia0,
-                  c->d_ckpt};
+                  c->d_ckpt, c->d_replay};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -553,6 +556,7 @@ sg::DiffArgs diff_args(sg_ctx* c) {
   a.q = c->d_q;
   a.qd = c->d_qd;
   a.ckpt = c->d_ckpt;
+  a.replay = c->use_replay ? c->d_replay : nullptr;
   a.err = c->d_err;
   a.num_warps = c->plan.num_warps;
   a.num_slots = c->plan.num_slots;
@@ -613,6 +617,21 @@ sg_status sg_diff_forward(sg_ctx* ctx, const float* actions_dev, int32_t T, floa
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_ckpt, need * sizeof(float));
     if (e != cudaSuccess) return cuda_err(ctx, e, "sg_diff_forward: checkpoint buffer");
     ctx->ckpt_floats = need;
+  }
+  // replay buffers of the warp-pair backward (above the cap: the one-warp backward)
+  const size_t rneed = sg::replay_floats(ckpt_every, substeps, ctx->plan.num_slots);
+  ctx->use_replay = rneed <= sg::kMaxReplayFloats;
+  if (ctx->use_replay && rneed > ctx->replay_floats) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (ctx->d_replay) cudaFree(ctx->d_replay);
+    ctx->d_replay = nullptr;
+    ctx->replay_floats = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_replay, rneed * sizeof(float));
+    if (e != cudaSuccess) {
+      ctx->use_replay = false;
+      return cuda_err(ctx, e, "sg_diff_forward: replay buffer");
+    }
+    ctx->replay_floats = rneed;
   }
   ctx->diff_T = T;
   ctx->diff_dt = dt;

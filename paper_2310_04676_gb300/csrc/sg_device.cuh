@@ -51,6 +51,46 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return false;
 }
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait that may legitimately last milliseconds (a partner warp's whole
+// segment of work): bounded by wall time (limit_ns) and, should the timer
+// not advance, by an iteration count.
+__device__ __forceinline__ bool mbar_wait_timed(uint64_t* bar, unsigned parity,
+                                                unsigned long long limit_ns) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned it = 0; it < (1u << 30); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 63u && globaltimer_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait with a warp-uniform verdict; false (and the error flag set)
+// if the partner did not arrive in time.
+__device__ __forceinline__ bool pair_wait(uint64_t* bar, unsigned& parity, int* err, int lane) {
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity));
+  parity ^= 1u;
+  if (!ok && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+  return ok;
+}
+
+// pair_wait for hand-offs of whole segments (limit 2 s)
+__device__ __forceinline__ bool pair_wait_long(uint64_t* bar, unsigned& parity, int* err, int lane) {
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_timed(bar, parity, 2000000000ull));
+  parity ^= 1u;
+  if (!ok && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+  return ok;
+}
+
 template <class Pat>
 __device__ __forceinline__ void load_targets(const Pat& pat, const StepArgs& a, int t, int env,
                                              int jo, float (&dst)[7]) {

@@ -11,6 +11,15 @@
 // reversed substep by substep (the substep's input states are recomputed
 // from the step-start state), accumulating the cotangents of the targets and
 // of the link masses (see sg_adjoint.cuh for the substep adjoint).
+// Warp-pair backward: the same arithmetic split between two warps of one
+// block that share 32 chains.  The replay warp recomputes every substep of a
+// segment from its checkpoint -- state, joint trigonometry, Cholesky factor,
+// acceleration, drive stiffness -- into one of two global (L2-resident)
+// buffers, while the adjoint warp runs the reverse sweep of the previous
+// segment from the other buffer; mbarriers in shared memory hand the buffers
+// back and forth (bounded waits: a wait that runs out sets DEVERR_TIMEOUT and
+// both warps leave).  The adjoint warp's serial path per substep drops to
+// the triangular solve and the reverse RNEA.
 #include <cuda_runtime.h>
 
 #include "sg_adjoint.cuh"
@@ -281,6 +290,242 @@ __global__ void __launch_bounds__(kDiffThreads) diff_backward_kernel(DiffArgs a)
   diff_dispatch<true>(a);
 }
 
+// ---- warp-pair backward --------------------------------------------------
+enum ReplayField { RF_Q = 0, RF_QD = 7, RF_CQ = 14, RF_SQ = 21, RF_ACC = 28, RF_KS = 35,
+                   RF_INV = 42, RF_L = 49 };
+
+// strictly lower triangle of L, row by row: (i, j), i > j
+__device__ __forceinline__ constexpr int tri_lo(int i, int j) { return i * (i - 1) / 2 + j; }
+
+// buffer b, substep j of the segment, field f
+__device__ __forceinline__ float* replay_at(const DiffArgs& a, int b, int j, int f, int slot) {
+  return a.replay + (((size_t)b * a.ckpt_every * a.substeps + j) * kReplayFields + f) * a.num_slots +
+         slot;
+}
+
+template <class Pat>
+__device__ __forceinline__ void replay_put(const Pat& pat, const DiffArgs& a, int b, int j,
+                                           int slot, const float (&q)[7], const float (&qd)[7],
+                                           const float (&cq)[Pat::N], const float (&sq)[Pat::N],
+                                           const float (&M)[Pat::N][Pat::N],
+                                           const float (&inv)[Pat::N], const float (&acc)[Pat::N],
+                                           const float (&ks)[Pat::N]) {
+  const size_t NS = a.num_slots;
+  float* p = replay_at(a, b, j, 0, slot);
+#pragma unroll
+  for (int i = 0; i < Pat::N; ++i) {
+    if (!pat.active(i)) continue;
+    p[(RF_Q + i) * NS] = q[i];
+    p[(RF_QD + i) * NS] = qd[i];
+    p[(RF_CQ + i) * NS] = cq[i];
+    p[(RF_SQ + i) * NS] = sq[i];
+    p[(RF_ACC + i) * NS] = acc[i];
+    p[(RF_KS + i) * NS] = ks[i];
+    p[(RF_INV + i) * NS] = inv[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k)
+      if (pat.active(k)) p[(RF_L + tri_lo(i, k)) * NS] = M[i][k];
+  }
+}
+
+template <class Pat>
+__device__ __forceinline__ void replay_get(const Pat& pat, const DiffArgs& a, int b, int j,
+                                           int slot, float (&q)[7], float (&qd)[7],
+                                           float (&cq)[Pat::N], float (&sq)[Pat::N],
+                                           float (&M)[Pat::N][Pat::N], float (&inv)[Pat::N],
+                                           float (&acc)[Pat::N], float (&ks)[Pat::N]) {
+  const size_t NS = a.num_slots;
+  const float* p = replay_at(a, b, j, 0, slot);   // read from L2 (__ldcg): written by the partner warp
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    q[i] = 0.f;
+    qd[i] = 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < Pat::N; ++i) {
+    cq[i] = 1.f;
+    sq[i] = 0.f;
+    acc[i] = 0.f;
+    ks[i] = 0.f;
+    inv[i] = 0.f;
+#pragma unroll
+    for (int k = 0; k < Pat::N; ++k) M[i][k] = 0.f;
+    if (!pat.active(i)) continue;
+    q[i] = __ldcg(p + (RF_Q + i) * NS);
+    qd[i] = __ldcg(p + (RF_QD + i) * NS);
+    cq[i] = __ldcg(p + (RF_CQ + i) * NS);
+    sq[i] = __ldcg(p + (RF_SQ + i) * NS);
+    acc[i] = __ldcg(p + (RF_ACC + i) * NS);
+    ks[i] = __ldcg(p + (RF_KS + i) * NS);
+    inv[i] = __ldcg(p + (RF_INV + i) * NS);
+#pragma unroll
+    for (int k = 0; k < i; ++k)
+      if (pat.active(k)) M[i][k] = __ldcg(p + (RF_L + tri_lo(i, k)) * NS);
+  }
+}
+
+// Replay warp: segments last first, each into buffer (order & 1).
+template <class Pat>
+__device__ __forceinline__ void replay_role(const DiffArgs& a, const Pat& pat, const Rec& rec,
+                                            int slot, uint64_t* ready, uint64_t* freed, int lane) {
+  constexpr int N = Pat::N;
+  const SlotInfo s = slot_info(a, slot);
+  unsigned ph_free[2] = {0u, 0u};
+  for (int order = 0; order < a.nseg; ++order) {
+    const int seg = a.nseg - 1 - order, b = order & 1;
+    if (order >= 2 && !pair_wait_long(freed + b, ph_free[b], a.err, lane)) return;
+    __threadfence();
+    const int t0 = seg * a.ckpt_every;
+    const int t1 = min(a.T, t0 + a.ckpt_every);
+    float q[7], qd[7], qs[7];
+    get_ckpt(pat, a, seg, slot, q, qd);
+    for (int t = t0; t < t1; ++t) {
+      read_targets(pat, a, t, s, qs);
+      for (int k = 0; k < a.substeps; ++k) {
+        float cq[N], sq[N], M[N][N], inv[N], acc[N], ks[N], dqd[N];
+        substep_record(pat, rec, q, qd, qs, a.h, kGravity, cq, sq, M, inv, acc, ks, dqd);
+        replay_put(pat, a, b, (t - t0) * a.substeps + k, slot, q, qd, cq, sq, M, inv, acc, ks);
+        integrate(pat, q, qd, dqd, a.h);
+      }
+    }
+    __threadfence();   // the buffer is in L2 before the partner is told
+    mbar_arrive(ready + b);
+  }
+}
+
+// Adjoint warp: the reverse sweep, segment by segment from the replay buffers.
+template <class Pat>
+__device__ __forceinline__ void adjoint_role(const DiffArgs& a, const Pat& pat, const Rec& rec,
+                                             int slot, uint64_t* ready, uint64_t* freed,
+                                             int lane) {
+  constexpr int N = Pat::N;
+  const SlotInfo s = slot_info(a, slot);
+  const size_t E = (size_t)a.num_envs;
+  const int J = a.max_joints;
+  float lq[7], lqd[7], lm[7], qn[7], qdn[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    lq[i] = 0.f;
+    lqd[i] = 0.f;
+    lm[i] = 0.f;
+  }
+  get_ckpt(pat, a, a.nseg, slot, qn, qdn);     // state after the last step
+  unsigned ph_ready[2] = {0u, 0u};
+  for (int order = 0; order < a.nseg; ++order) {
+    const int seg = a.nseg - 1 - order, b = order & 1;
+    if (!pair_wait_long(ready + b, ph_ready[b], a.err, lane)) return;
+    __threadfence();
+    const int t0 = seg * a.ckpt_every;
+    const int t1 = min(a.T, t0 + a.ckpt_every);
+    for (int t = t1 - 1; t >= t0; --t) {
+      if (s.valid) {
+        const float* g = a.dl_dee + (((size_t)t * E + s.env) * kMaxChains + s.c) * 3;
+        float gq[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) gq[i] = 0.f;
+        tip_vjp(pat, rec, qn, V3{g[0], g[1], g[2]}, gq);
+#pragma unroll
+        for (int i = 0; i < N; ++i) lq[i] += gq[i];
+      }
+      float lqs[7];
+#pragma unroll
+      for (int i = 0; i < 7; ++i) lqs[i] = 0.f;
+      for (int k = a.substeps - 1; k >= 0; --k) {
+        float q[7], qd[7], cq[N], sq[N], M[N][N], inv[N], acc[N], ks[N];
+        replay_get(pat, a, b, (t - t0) * a.substeps + k, slot, q, qd, cq, sq, M, inv, acc, ks);
+        substep_adjoint_rec(pat, rec, q, qd, cq, sq, M, inv, acc, ks, a.h, kGravity, lq, lqd, lqs,
+                            lm);
+        if (k == 0) {
+#pragma unroll
+          for (int i = 0; i < 7; ++i) qn[i] = q[i];   // the state before step t
+        }
+      }
+      if (s.valid) {
+        float* row = a.dactions + ((size_t)t * E + s.env) * J;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+          if (pat.active(i)) row[s.jo + i] = lqs[i];
+        if (s.c == 0)
+          for (int j = s.ntot; j < J; ++j) row[j] = 0.f;
+      }
+    }
+    __threadfence();
+    mbar_arrive(freed + b);
+  }
+  if (s.valid) {
+    float* mrow = a.dmass + (size_t)s.env * J;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      if (!pat.active(i)) continue;
+      mrow[s.jo + i] = lm[i];
+      if (a.dq0) a.dq0[(size_t)s.env * J + s.jo + i] = lq[i];
+      if (a.dqd0) a.dqd0[(size_t)s.env * J + s.jo + i] = lqd[i];
+    }
+    if (s.c == 0) {
+      for (int j = s.ntot; j < J; ++j) {
+        mrow[j] = 0.f;
+        if (a.dq0) a.dq0[(size_t)s.env * J + j] = 0.f;
+        if (a.dqd0) a.dqd0[(size_t)s.env * J + j] = 0.f;
+      }
+    }
+  }
+}
+
+constexpr int kReplayBars = 5;   // tma, ready[2], free[2]
+
+__global__ void __launch_bounds__(kDiffPairThreads) diff_backward_pair_kernel(DiffArgs a) {
+  extern __shared__ __align__(128) float smem[];
+  const int w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int pairs = blockDim.x >> 6;
+  const int pair = w >> 1, role = w & 1;
+  float* rec = smem + (size_t)pair * kRecordFloats;
+  uint64_t* bar0 = reinterpret_cast<uint64_t*>(smem + (size_t)pairs * kRecordFloats);
+  uint64_t* bars = bar0 + (size_t)pair * kReplayBars;
+  // start-up: warp 0 initialises every pair's barriers before any warp leaves
+  if (w == 0 && lane < pairs) {
+    uint64_t* b = bar0 + (size_t)lane * kReplayBars;
+    mbar_init(b + 0, 1);
+    for (int k = 1; k < kReplayBars; ++k) mbar_init(b + k, kWarp);
+  }
+  __syncthreads();
+  const int gw = blockIdx.x * pairs + pair;
+  if (gw >= a.num_warps) return;
+  const int wc = a.warp_class[gw];
+  if (role == 0 && lane == 0) {
+    const unsigned bytes = (unsigned)record_bytes_dev(wc);
+    mbar_expect_tx(bars, bytes);
+    bulk_g2s(rec, a.params + (size_t)gw * kRecordFloats, bytes, bars);
+  }
+  unsigned ph_tma = 0;
+  if (!pair_wait(bars, ph_tma, a.err, lane)) {
+    mbar_wait_bounded(bars, 0);   // second bounded chance for an in-flight copy
+    return;
+  }
+  const Rec r{rec + lane};
+  const int slot = gw * kWarp + lane;
+  auto run = [&](const auto& pat) {
+    if (role == 0) replay_role(a, pat, r, slot, bars + 1, bars + 3, lane);
+    else adjoint_role(a, pat, r, slot, bars + 1, bars + 3, lane);
+  };
+  switch (wc & 3) {
+    case CLS_7R: run(Pat7R{}); break;
+    case CLS_7P: run(Pat7P{}); break;
+    case CLS_4R: run(Pat4R{}); break;
+    default: {
+      int code;
+      const float cf = r.cf(CF_CODE);
+      memcpy(&code, &cf, 4);
+      run(PatGen{code, decode_slot(a.slot_info[slot]).nchain});
+    }
+  }
+}
+
+size_t diff_pair_smem_bytes(int threads) {
+  const int pairs = threads / (2 * kWarp);
+  return (size_t)pairs * kRecordFloats * sizeof(float) + (size_t)pairs * kReplayBars * sizeof(uint64_t);
+}
+
 // link masses (and inertias, which scale with mass) from a caller array [E][J]
 __global__ void set_mass_kernel(MassArgs m) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
@@ -313,8 +558,12 @@ cudaError_t prepare_diff_kernels() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)diff_smem_bytes(kDiffThreads));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(diff_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)diff_smem_bytes(kDiffThreads));
+  e = cudaFuncSetAttribute(diff_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)diff_smem_bytes(kDiffThreads));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(diff_backward_pair_kernel,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)diff_pair_smem_bytes(kDiffPairThreads));
 }
 
 cudaError_t launch_diff_forward(const DiffArgs& a, cudaStream_t s) {
@@ -325,6 +574,12 @@ cudaError_t launch_diff_forward(const DiffArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_diff_backward(const DiffArgs& a, cudaStream_t s) {
+  if (a.replay) {
+    const int pairs = kDiffPairThreads / (2 * kWarp);
+    diff_backward_pair_kernel<<<(a.num_warps + pairs - 1) / pairs, kDiffPairThreads,
+                                diff_pair_smem_bytes(kDiffPairThreads), s>>>(a);
+    return cudaGetLastError();
+  }
   const int wpb = kDiffThreads / kWarp;
   diff_backward_kernel<<<(a.num_warps + wpb - 1) / wpb, kDiffThreads,
                          diff_smem_bytes(kDiffThreads), s>>>(a);

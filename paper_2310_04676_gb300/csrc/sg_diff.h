@@ -8,6 +8,8 @@
 namespace sg {
 
 constexpr int kDiffThreads = 128;
+constexpr int kDiffPairThreads = 128;  // two warp pairs per block (replay + adjoint warps)
+constexpr int kReplayFields = 70;      // per substep: q, qd, cos q, sin q, qdd, k_s, 1/L_ii (7 each), L (21)
 constexpr int kMaxCkptEvery = 32;      // checkpoint interval limit (thread-local segment buffer)
 constexpr int kMaxDiffSubsteps = 16;   // substeps limit of the differentiable rollout
 
@@ -26,10 +28,18 @@ struct DiffArgs {
   float* dmass;            // [E][J]            (backward output)
   float* dq0;              // [E][J] or null    (backward output)
   float* dqd0;             // [E][J] or null    (backward output)
+  float* replay;           // [2][ckpt_every * substeps][kReplayFields][NS] or null
   int32_t* err;
   int num_warps, num_slots, num_envs, max_joints, T, substeps, ckpt_every, nseg;
   float h;
 };
+
+constexpr size_t kMaxReplayFloats = (size_t)1 << 28;   // 1 GiB of replay buffers at most
+
+// Floats of the replay buffers of the warp-pair backward kernel.
+inline size_t replay_floats(int ckpt_every, int substeps, int num_slots) {
+  return (size_t)2 * ckpt_every * substeps * kReplayFields * num_slots;
+}
 
 struct MassArgs {
   float* params;
@@ -49,6 +59,9 @@ cudaStream_t context_stream(sg_ctx* ctx);
 
 cudaError_t prepare_diff_kernels();
 cudaError_t launch_diff_forward(const DiffArgs& a, cudaStream_t s);
+// Reverse pass: with a.replay set, the warp-pair kernel (one warp replays
+// the next segment's substeps while its partner runs the adjoint of the
+// current one); otherwise the one-warp kernel.
 cudaError_t launch_diff_backward(const DiffArgs& a, cudaStream_t s);
 cudaError_t launch_set_mass(const MassArgs& m, cudaStream_t s);
 

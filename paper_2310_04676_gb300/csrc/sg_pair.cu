@@ -41,19 +41,6 @@ constexpr int kPairBars = 3;                      // tma, exchange, stage
 
 __device__ __forceinline__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Bounded wait with a warp-uniform verdict; false (and the error flag set)
-// if the partner did not arrive in time.
-__device__ __forceinline__ bool pair_wait(uint64_t* bar, unsigned& parity, int* err, int lane) {
-  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity));
-  parity ^= 1u;
-  if (!ok && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
-  return ok;
-}
-
 template <class Pat>
 __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, const Rec& rec,
                                          float* stage, float* xbuf, uint64_t* bars, int group,
