@@ -198,6 +198,17 @@ sg_status sg_reset(sg_ctx *ctx, const uint8_t *env_mask_dev);
 sg_status sg_step(sg_ctx *ctx, const float *actions_dev, float dt, int32_t substeps,
                   float *obs_dev, float *reward_dev, uint8_t *done_dev);
 
+/* The observation of the current state, laid out as sg_step reports it,
+ * without advancing time: q, qd, tool tips (and orientation) of the current
+ * state, targets_dev [E][J] as the current commands q*, the current goals
+ * (tracking: including their present offsets) or the waypoints after the
+ * current step count (path).  Rows of envs with env_mask_dev[e] != 0 (uint8
+ * [E], device; NULL = all) are written to obs_dev [E][D]; other rows are not
+ * touched.  State, step counts, goals and the error flags are unchanged.  Use
+ * it after sg_reset to obtain the first observation of new episodes. */
+sg_status sg_observe(sg_ctx *ctx, const float *targets_dev, const uint8_t *env_mask_dev,
+                     float *obs_dev);
+
 /* Read / write the state in caller layout: q, qd [E][J] float (padding
  * joints are written as 0 by sg_get_state and ignored by sg_set_state),
  * step_count [E] int32.  Any of the three pointers may be NULL to skip it. */

@@ -17,8 +17,12 @@ environments of identical structure, loops over links in Python):
                   step of the reaching / path-following / two-arm tasks.
 * ``path``        the path-following waypoints: natural cubic spline through
                   control points, resampled at equal arc length.
+* ``ppo``         the GPU-resident PPO loop: actor/critic MLPs, rollout with
+                  time-out bootstrapping and resets, GAE, clipped PPO update
+                  with Adam.
 * ``rng``         the counter-based normal deviates of the tracking task's
-                  moving goals (SplitMix64 finaliser, Box-Muller).
+                  moving goals and of the policy's exploration noise
+                  (SplitMix64 finaliser, Box-Muller).
 * ``lagrangian``  an independent equation of motion from the Lagrangian
                   L = T - V of plain forward kinematics (complex-step
                   Jacobians, central finite differences).
@@ -32,4 +36,4 @@ Parity pins: every function is checked in ``tests/test_oracle_*.py``
 against closed forms, invariants and finite differences; none is
 "parity unpinned".
 """
-from . import spatial, model, dynamics, env, lagrangian, path, rng  # noqa: F401
+from . import spatial, model, dynamics, env, lagrangian, path, ppo, rng  # noqa: F401

@@ -152,6 +152,24 @@ class OracleEnv:
         done[bad] |= 4
         return obs, reward, done
 
+    def observe(self, targets, mask=None):
+        """Observation rows [E][D] of the current state with ``targets`` as the
+        current commands, without advancing time (rows outside ``mask`` are
+        returned as NaN)."""
+        targets = np.asarray(targets, np.float64)
+        m = np.ones(self.E, bool) if mask is None else np.asarray(mask).astype(bool)
+        obs = np.full((self.E, self.D), np.nan)
+        for idx, tree, P in self.groups:
+            n = tree.n
+            o, _ = self._obs_reward(idx, tree, P, torch.as_tensor(self.q[idx, :n]),
+                                    torch.as_tensor(self.qd[idx, :n]),
+                                    torch.as_tensor(targets[idx, :n]))
+            rows = np.zeros((len(idx), self.D))
+            rows[:, : o.shape[1]] = o
+            sel = m[idx]
+            obs[idx[sel]] = rows[sel]
+        return obs
+
     def _move_goals(self):
         """One random-walk step of every chain's goal (tracking task)."""
         nc = np.asarray(self.desc["env_num_chains"])

@@ -29,6 +29,34 @@ def splitmix64_next(state):
     return s, mix64(s)
 
 
+def _key_words(seed, env, lo, step, shift):
+    u64 = lambda x: np.asarray(x).astype(np.uint64)
+    with np.errstate(over="ignore"):
+        key = mix64(u64(seed) + GOLDEN)
+        key = mix64(key + GOLDEN + u64(env))
+        key = mix64(key + GOLDEN + ((u64(step) << np.uint64(shift)) | u64(lo)))
+        return mix64(key + GOLDEN), mix64(key + GOLDEN + GOLDEN)
+
+
+def _box_muller(w0, w1):
+    s = 2.0 ** -24
+    top = lambda w: ((w >> np.uint64(40)).astype(np.float64) + 0.5) * s
+    mid = lambda w: (((w >> np.uint64(16)) & np.uint64(0xFFFFFF)).astype(np.float64) + 0.5) * s
+    u0, u1, u2, u3 = top(w0), mid(w0), top(w1), mid(w1)
+    r0 = np.sqrt(-2.0 * np.log(u0))
+    r1 = np.sqrt(-2.0 * np.log(u2))
+    return np.stack([r0 * np.cos(2 * np.pi * u1), r0 * np.sin(2 * np.pi * u1),
+                     r1 * np.cos(2 * np.pi * u3), r1 * np.sin(2 * np.pi * u3)], -1)
+
+
+def action_noise(seed, env, block, step):
+    """Four standard normal deviates for (seed, env, joint block, step) of
+    the policy's exploration noise: joint j of an env uses block j // 4,
+    component j % 4 (key: step << 5 | block).  Returns [..., 4] float64."""
+    w0, w1 = _key_words(seed, env, block, step, 5)
+    return _box_muller(w0, w1)
+
+
 def goal_noise(seed, env, chain, step):
     """Three standard normal deviates for (seed, env, chain, step); array
     arguments broadcast.  Returns [..., 3] float64."""

@@ -395,6 +395,20 @@ sg_status sg_step(sg_ctx* ctx, const float* actions_dev, float dt, int32_t subst
   return cuda_err(ctx, launch_plan(ctx, a, ctx->stream), "sg_step");
 }
 
+sg_status sg_observe(sg_ctx* ctx, const float* targets_dev, const uint8_t* env_mask_dev,
+                     float* obs_dev) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  if (!targets_dev || !obs_dev)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "sg_observe: targets and obs must be non-NULL");
+  sg::StepArgs a = step_args(ctx, 1.f, 1, 1);
+  a.actions = targets_dev;
+  a.obs = obs_dev;
+  a.obs_mask = env_mask_dev;
+  a.observe = 1;
+  a.substeps = 0;
+  return cuda_err(ctx, sg::launch_step(a, ctx->threads, ctx->stream), "sg_observe");
+}
+
 sg_status sg_rollout(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt,
                      int32_t substeps, float* obs_dev, float* reward_dev, uint8_t* done_dev) {
   sg_status st = check_rollout_args(ctx, actions_dev, T, dt, substeps, obs_dev, reward_dev, done_dev);

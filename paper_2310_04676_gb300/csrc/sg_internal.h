@@ -115,8 +115,11 @@ struct StepArgs {
   float* obs;               // [T][E][D]
   float* reward;            // [T][E]
   uint8_t* done;            // [T][E]
+  const uint8_t* obs_mask;  // observe mode: envs whose rows are written (null: all)
   int num_warps, num_slots, num_envs, max_joints, obs_dim, task, path_len, episode_len;
   int substeps, T;
+  int observe;              // 1: write the observation of the current state only (T = 1,
+                            // no substeps, no reward/done, state and counters unchanged)
   float alpha, h;
   uint32_t seed;
   float track_sigma, track_limit;

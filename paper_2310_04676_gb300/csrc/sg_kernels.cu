@@ -51,8 +51,9 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
   const int g = 1 << glog;                        // lanes per env
   const int nrows = kWarp >> glog;
   float* srow = stage + (lane >> glog) * DP;
-  // env owning stage row `lane` (rows >= nrows unused)
-  const int row_env = __shfl_sync(0xffffffffu, env, (lane << glog) & 31);
+  // env owning stage row `lane` (rows >= nrows unused; -1: row not written)
+  const int sel_env = (valid && (!a.obs_mask || a.obs_mask[env])) ? env : -1;
+  const int row_env = __shfl_sync(0xffffffffu, sel_env, (lane << glog) & 31);
 
   float q[7], qd[7], qs[7], qn[7];
 #pragma unroll
@@ -104,8 +105,8 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
       if (pat.active(i)) bad = bad || !isfinite(q[i]) || !isfinite(qd[i]);
     bad = bad && valid;
     for (int off = 1; off < g; off <<= 1) bad = bad || __shfl_xor_sync(0xffffffffu, bad ? 1 : 0, off) != 0;
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, DEVERR_NONFINITE);
-    ++sc;
+    if (__any_sync(0xffffffffu, bad) && lane == 0 && !a.observe) atomicOr(a.err, DEVERR_NONFINITE);
+    if (!a.observe) ++sc;
 
     float reward;
     if (a.task == SG_TASK_PATH) {
@@ -140,7 +141,7 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
       }
     } else {
       float gx = goal_x, gy = goal_y, gz = goal_z;
-      if (track) {
+      if (track && !a.observe) {
         float z[3];
         goal_noise(a.seed, valid ? env : 0, c, sc, z[0], z[1], z[2]);
 #pragma unroll
@@ -148,6 +149,8 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
           gd[k] = fminf(fmaxf(gd[k] + gv[k], -a.track_limit), a.track_limit);
           gv[k] += a.track_sigma * z[k];
         }
+      }
+      if (track) {
         gx += gd[0];
         gy += gd[1];
         gz += gd[2];
@@ -171,7 +174,7 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
         srow[3 * ntot + 3 * nc + 3 * c + 2] = gz;
       }
     }
-    if (c == 0) {
+    if (c == 0 && !a.observe) {
       if (valid) {
         a.reward[(size_t)t * E + env] = reward;
         a.done[(size_t)t * E + env] =
@@ -183,7 +186,7 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
     __syncwarp();
   }
 
-  if (valid) {
+  if (valid && !a.observe) {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       if (!pat.active(i)) continue;

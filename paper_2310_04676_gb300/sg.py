@@ -78,6 +78,7 @@ def load_library(path=LIB_PATH):
         "sg_max_joints": (i32, [vp]),
         "sg_reset": (i32, [vp, u8p]),
         "sg_step": (i32, [vp, vp, f32, i32, vp, vp, u8p]),
+        "sg_observe": (i32, [vp, vp, u8p, vp]),
         "sg_get_state": (i32, [vp, vp, vp, vp]),
         "sg_set_state": (i32, [vp, vp, vp, vp]),
         "sg_sync_status": (i32, [vp]),
@@ -264,6 +265,19 @@ class Env:
         self._check(self.lib.sg_step(self.ctx, _ptr(actions), float(dt), int(substeps),
                                      _ptr(obs), _ptr(rew), _ptr(done)))
         return obs, rew, done
+
+    def observe(self, targets, mask=None, out=None):
+        """Observation of the current state (no time advance): rows of the
+        envs in ``mask`` (uint8 [E], None = all) are written to ``out``."""
+        self._sync_stream()
+        torch = self._torch
+        self._want(targets, torch.float32, (self.num_envs, self.max_joints), "targets")
+        if mask is not None:
+            self._want(mask, torch.uint8, (self.num_envs,), "mask")
+        if out is None:
+            out = torch.zeros(self.num_envs, self.obs_dim, dtype=torch.float32, device=self.device)
+        self._check(self.lib.sg_observe(self.ctx, _ptr(targets), _ptr(mask), _ptr(out)))
+        return out
 
     def rollout(self, actions, dt, substeps, out=None):
         """T steps in one call: actions [T, E, J] -> obs [T, E, D], reward

@@ -433,3 +433,31 @@ def test_tracking_rollout_equals_steps_and_state_roundtrip():
     oc, rc, _ = C.step(acts[0], DT, 2)
     oa, ra, _ = A.step(acts[0], DT, 2)
     assert torch.equal(oa, oc) and torch.equal(ra, rc)
+
+
+@pytest.mark.parametrize("task", [0, 1, 2])
+def test_observe_matches_step_rows_and_oracle(task):
+    """sg_observe: with the last step's commands it reproduces that step's
+    observation rows bit for bit; after a masked reset it writes exactly the
+    masked rows, equal to the oracle's observation of the reset state."""
+    kinds = ["7R"] * 40 if task == 1 else (["7R", "14B", "21T", "4R", "7P"] * 8)
+    desc = W.make_desc(kinds, task=task, path_len=20 if task == 1 else 0, episode_len=50)
+    E = len(kinds)
+    env, ref = sg.Env(desc), OracleEnv(desc)
+    acts = W.joint_targets(desc, 6)
+    for t in range(6):
+        obs, _, _ = env.step(cuda(acts[t]), DT, 2)
+        ref.step(acts[t], DT, 2)
+    again = env.observe(cuda(acts[5]))
+    assert torch.equal(again, obs)
+    mask = np.zeros(E, np.uint8)
+    mask[::3] = 1
+    env.reset(cuda(mask))
+    ref.reset(mask)
+    sentinel = torch.full_like(obs, 7.0)
+    out = env.observe(cuda(acts[5]), cuda(mask), out=sentinel.clone())
+    m = torch.as_tensor(mask.astype(bool), device="cuda")
+    assert torch.equal(out[~m], sentinel[~m])
+    o_ref = ref.observe(acts[5], mask)
+    got = out.cpu().numpy()[mask.astype(bool)]
+    assert np.abs(got - o_ref[mask.astype(bool)]).max() <= 1e-5
