@@ -606,6 +606,7 @@ DiffArgs context_diff_args(sg_ctx* c) {
 }
 void context_set_error(sg_ctx* c, const char* msg) { c->last_error = msg; }
 cudaStream_t context_stream(sg_ctx* c) { return c->stream; }
+const std::vector<int32_t>& context_env_dof(sg_ctx* c) { return c->plan.env_dof; }
 }  // namespace sg
 
 extern "C" {

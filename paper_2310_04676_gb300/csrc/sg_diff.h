@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "sg_internal.h"
 
 namespace sg {
@@ -56,6 +58,8 @@ struct MassArgs {
 DiffArgs context_diff_args(sg_ctx* ctx);
 void context_set_error(sg_ctx* ctx, const char* msg);
 cudaStream_t context_stream(sg_ctx* ctx);
+// total joints of every env [E] (host copy of the description)
+const std::vector<int32_t>& context_env_dof(sg_ctx* ctx);
 
 cudaError_t prepare_diff_kernels();
 cudaError_t launch_diff_forward(const DiffArgs& a, cudaStream_t s);

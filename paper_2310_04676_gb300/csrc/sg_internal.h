@@ -79,6 +79,7 @@ struct Plan {
   std::vector<int32_t> slot_env;    // [NS] caller env index, -1 for padding
   std::vector<int32_t> slot_info;   // [NS] SI_* fields
   std::vector<int32_t> warp_class;  // [NW]
+  std::vector<int32_t> env_dof;     // [E] total joints of each env
   std::vector<float> params;        // [NW][kRecordFloats]
   std::vector<float> q0;            // [kMaxLinks][NS]
   std::vector<float> mass0;         // [kMaxLinks][NS] link masses of the description

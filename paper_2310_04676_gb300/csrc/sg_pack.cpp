@@ -135,6 +135,7 @@ sg_status build_plan(const sg_desc* d, Plan* P, std::string* err) {
   }
 
   // ---- order the chain slots ---------------------------------------------
+  P->env_dof.assign(env_ntot.begin(), env_ntot.end());
   P->num_envs = E;
   P->max_joints = J;
   P->task = d->task;

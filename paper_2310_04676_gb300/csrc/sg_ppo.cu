@@ -1,0 +1,831 @@
+// GPU-resident PPO loop (include/sg_ppo.h): the policy and value networks,
+// action sampling, env stepping, time-out bootstrapping, resets, GAE and the
+// clipped PPO update, all on the env context's stream.
+//
+// Layout: activations are row-major [rows][width] (rows = envs while
+// collecting, minibatch rows while updating); weights row-major [out][in].
+// GEMMs are cuBLAS SGEMMs on the row-major data seen as column-major
+// transposes (FP32, or TF32 tensor cores); bias + ELU, the Gaussian head and
+// its gradient, GAE, the gathers, the reductions (fixed-order, so results do
+// not depend on scheduling) and Adam are the kernels below.
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sg.h"
+#include "sg_diff.h"
+#include "sg_internal.h"
+#include "sg_ppo.h"
+#include "sg_rng.cuh"
+
+namespace sg {
+namespace {
+
+constexpr int kH1 = 256, kH2 = 128, kH3 = 64;
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 512;            // partial sums of the two-stage reductions
+constexpr float kHalfLog2Pi = 0.91893853320467274f;
+
+// ---- parameter layout ------------------------------------------------------
+struct Layer {
+  size_t w, b;       // offsets of W [out][in] and b [out]
+  int in, out;
+};
+struct Net {
+  Layer l[4];
+};
+struct Layout {
+  Net actor, critic;
+  size_t log_std, total;
+};
+
+Layout make_layout(int D, int A) {
+  Layout L;
+  size_t k = 0;
+  const int dims[4] = {D, kH1, kH2, kH3};
+  auto net = [&](Net& n, int out_last) {
+    for (int i = 0; i < 4; ++i) {
+      n.l[i].in = dims[i];
+      n.l[i].out = i < 3 ? dims[i + 1] : out_last;
+      n.l[i].w = k;
+      k += (size_t)n.l[i].in * n.l[i].out;
+      n.l[i].b = k;
+      k += n.l[i].out;
+    }
+  };
+  net(L.actor, A);
+  L.log_std = k;
+  k += A;
+  net(L.critic, 1);
+  L.total = k;
+  return L;
+}
+
+// ---- kernels -----------------------------------------------------------------
+__device__ __forceinline__ float elu(float x) { return x > 0.f ? x : expm1f(x); }
+
+// Y[r][c] = act(Y[r][c] + b[c]) in place
+__global__ void bias_act_kernel(float* __restrict__ Y, const float* __restrict__ b, long long n,
+                                int width, int do_elu) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float z = Y[i] + b[i % width];
+    Y[i] = do_elu ? elu(z) : z;
+  }
+}
+
+// dY <- dY * ELU'(z), with ELU' from the stored output y: 1 for y > 0, y + 1 otherwise
+__global__ void elu_backward_kernel(float* __restrict__ dY, const float* __restrict__ Y,
+                                    long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float y = Y[i];
+    dY[i] *= y > 0.f ? 1.f : y + 1.f;
+  }
+}
+
+// Actions, log-probabilities and values of one collect step (thread per env).
+__global__ void sample_kernel(const float* __restrict__ mu, const float* __restrict__ log_std,
+                              const float* __restrict__ mask, const long long* __restrict__ step,
+                              int t, uint32_t seed, int E, int A, float* __restrict__ actions,
+                              float* __restrict__ logp) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const long long gstep = *step + t;
+  float lp = 0.f;
+  for (int blk = 0; blk * 4 < A; ++blk) {
+    float z[4];
+    action_noise(seed, e, blk, gstep, z);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = 4 * blk + c;
+      if (j >= A) break;
+      const float ls = log_std[j];
+      actions[(size_t)e * A + j] = mu[(size_t)e * A + j] + expf(ls) * z[c];
+      if (mask[(size_t)e * A + j] != 0.f) lp += -0.5f * z[c] * z[c] - ls - kHalfLog2Pi;
+    }
+  }
+  logp[e] = lp;
+}
+
+// Bootstrap time-outs into the reward and mark envs to reset.
+__global__ void bootstrap_kernel(float* __restrict__ reward, const uint8_t* __restrict__ done,
+                                 const float* __restrict__ value, float gamma, int E,
+                                 uint8_t* __restrict__ reset) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const uint8_t d = done[e];
+  if (d & SG_DONE_TIMEOUT) reward[e] += gamma * value[e];
+  reset[e] = d != 0 ? 1 : 0;
+}
+
+// GAE over the n steps of every env (thread per env).
+__global__ void gae_kernel(const float* __restrict__ reward, const float* __restrict__ value,
+                           const uint8_t* __restrict__ done, int n, int E, float gamma, float lam,
+                           float* __restrict__ adv, float* __restrict__ ret) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  float next = 0.f;
+  for (int t = n - 1; t >= 0; --t) {
+    const size_t i = (size_t)t * E + e;
+    const float keep = done[i] ? 0.f : 1.f;
+    const float delta = reward[i] + gamma * value[i + E] * keep - value[i];
+    next = delta + gamma * lam * keep * next;
+    adv[i] = next;
+    ret[i] = next + value[i];
+  }
+}
+
+__global__ void advance_kernel(long long* step, int n) { *step += n; }
+
+// Block reduction of a double (all threads get the result).
+__device__ double block_sum(double v, double* sh) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) r += __shfl_down_sync(0xffffffffu, r, off);
+    if (threadIdx.x == 0) sh[0] = r;
+  }
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Stage 1: per-block sums of x and x^2 (fixed grid, fixed order).
+__global__ void __launch_bounds__(kRedThreads)
+moments_partial_kernel(const float* __restrict__ x, long long n, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double s = 0.0, q = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    s += v;
+    q += v * v;
+  }
+  s = block_sum(s, sh);
+  q = block_sum(q, sh);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = s;
+    part[2 * blockIdx.x + 1] = q;
+  }
+}
+
+// Stage 2: mean and 1 / (unbiased std + 1e-8) of the advantages.
+__global__ void __launch_bounds__(kRedThreads)
+moments_final_kernel(const double* __restrict__ part, int nblk, long long n,
+                     float* __restrict__ norm) {
+  __shared__ double sh[32];
+  double s = 0.0, q = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+    s += part[2 * i];
+    q += part[2 * i + 1];
+  }
+  s = block_sum(s, sh);
+  q = block_sum(q, sh);
+  if (threadIdx.x == 0) {
+    const double mean = s / (double)n;
+    const double var = n > 1 ? (q - (double)n * mean * mean) / (double)(n - 1) : 0.0;
+    norm[0] = (float)mean;
+    norm[1] = (float)(1.0 / (sqrt(var > 0.0 ? var : 0.0) + 1e-8));
+  }
+}
+
+struct Batch {
+  const float *obs, *act, *logp, *value, *adv, *ret, *jmask, *norm;
+};
+struct MiniBatch {
+  float *obs, *act, *logp, *value, *adv, *ret, *mask;
+};
+
+// Gather minibatch rows (warp per row): row index b = t * E + e.
+__global__ void gather_kernel(Batch src, MiniBatch dst, const int32_t* __restrict__ idx, int M,
+                              int E, int D, int A) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= M) return;
+  const long long b = idx[row];
+  const int e = (int)(b % E);
+  for (int k = lane; k < D; k += 32) dst.obs[(size_t)row * D + k] = src.obs[(size_t)b * D + k];
+  for (int k = lane; k < A; k += 32) {
+    dst.act[(size_t)row * A + k] = src.act[(size_t)b * A + k];
+    dst.mask[(size_t)row * A + k] = src.jmask[(size_t)e * A + k];
+  }
+  if (lane == 0) {
+    dst.logp[row] = src.logp[b];
+    dst.value[row] = src.value[b];
+    dst.adv[row] = (src.adv[b] - src.norm[0]) * src.norm[1];
+    dst.ret[row] = src.ret[b];
+  }
+}
+
+struct HeadArgs {
+  const float *mu, *v, *log_std;
+  MiniBatch mb;
+  float *d_mu, *d_v;
+  float* part;          // [blocks][2 + 2A]: surrogate sum, value-loss sum, dlogstd_j, count_j
+  int M, A;
+  float clip, value_coef;
+};
+
+// Losses of the minibatch and their gradients with respect to the actor's
+// mean, the critic's value and log_std (thread per row; per-block partials).
+__global__ void __launch_bounds__(kRedThreads) head_kernel(HeadArgs h) {
+  __shared__ double sh[32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ok = i < h.M;
+  const int A = h.A;
+  const float inv_m = 1.f / (float)h.M;
+  float surr = 0.f, vl = 0.f;
+  float g_logp = 0.f;
+  float zz[kMaxDof];
+  if (ok) {
+    float lp = 0.f;
+    for (int j = 0; j < A; ++j) {
+      const float ls = h.log_std[j];
+      const float z = (h.mb.act[(size_t)i * A + j] - h.mu[(size_t)i * A + j]) * expf(-ls);
+      zz[j] = z;
+      if (h.mb.mask[(size_t)i * A + j] != 0.f) lp += -0.5f * z * z - ls - kHalfLog2Pi;
+    }
+    const float ratio = expf(lp - h.mb.logp[i]);
+    const float adv = h.mb.adv[i];
+    const float s1 = -adv * ratio;
+    const float s2 = -adv * fminf(fmaxf(ratio, 1.f - h.clip), 1.f + h.clip);
+    surr = fmaxf(s1, s2);
+    // d max(s1, s2) / d logp: the clipped branch is flat where it is the larger
+    g_logp = (s2 > s1) ? 0.f : -adv * ratio;
+    const float v = h.v[i], vo = h.mb.value[i], R = h.mb.ret[i];
+    const float dv = fminf(fmaxf(v - vo, -h.clip), h.clip);
+    const float vc = vo + dv;
+    const float l1 = (v - R) * (v - R), l2 = (vc - R) * (vc - R);
+    vl = fmaxf(l1, l2);
+    float gv;
+    if (l1 > l2) gv = 2.f * (v - R);
+    else if (l2 > l1) gv = (v - vo >= -h.clip && v - vo <= h.clip) ? 2.f * (vc - R) : 0.f;
+    else gv = 0.5f * (2.f * (v - R) + ((v - vo >= -h.clip && v - vo <= h.clip) ? 2.f * (vc - R) : 0.f));
+    h.d_v[i] = h.value_coef * gv * inv_m;
+    const float g = g_logp * inv_m;
+    for (int j = 0; j < A; ++j) {
+      const float m = h.mb.mask[(size_t)i * A + j];
+      h.d_mu[(size_t)i * A + j] = m != 0.f ? g * zz[j] * expf(-h.log_std[j]) : 0.f;
+    }
+  }
+  const int stride = 2 + 2 * A;
+  double s = block_sum(ok ? (double)surr : 0.0, sh);
+  if (threadIdx.x == 0) h.part[(size_t)blockIdx.x * stride + 0] = (float)s;
+  s = block_sum(ok ? (double)vl : 0.0, sh);
+  if (threadIdx.x == 0) h.part[(size_t)blockIdx.x * stride + 1] = (float)s;
+  for (int j = 0; j < A; ++j) {
+    const float m = ok ? h.mb.mask[(size_t)i * A + j] : 0.f;
+    const double gls = (ok && m != 0.f) ? (double)(g_logp * inv_m) * (zz[j] * zz[j] - 1.0) : 0.0;
+    s = block_sum(gls, sh);
+    if (threadIdx.x == 0) h.part[(size_t)blockIdx.x * stride + 2 + j] = (float)s;
+    s = block_sum(m, sh);
+    if (threadIdx.x == 0) h.part[(size_t)blockIdx.x * stride + 2 + A + j] = (float)s;
+  }
+}
+
+// Final reduction of the head partials: log_std gradient (surrogate +
+// entropy terms) and the minibatch's loss statistics.
+__global__ void head_final_kernel(const float* __restrict__ part, int nblk, int A, int M,
+                                  const float* __restrict__ log_std, float entropy_coef,
+                                  float* __restrict__ grad_log_std, float* __restrict__ stats) {
+  const int j = threadIdx.x;          // one thread per column of the partials
+  const int stride = 2 + 2 * A;
+  if (j >= stride) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(size_t)b * stride + j];
+  __shared__ double col[2 + 2 * kMaxDof];
+  col[j] = s;
+  __syncthreads();
+  if (j < A) {
+    const double cnt = col[2 + A + j] / (double)M;          // mean over rows of the mask
+    grad_log_std[j] = (float)(col[2 + j] - (double)entropy_coef * cnt);
+  }
+  if (j == 0 && stats) {
+    double ent = 0.0;
+    for (int k = 0; k < A; ++k) ent += (0.5 + kHalfLog2Pi + (double)log_std[k]) * col[2 + A + k] / M;
+    stats[0] = (float)(col[0] / M);
+    stats[1] = (float)(col[1] / M);
+    stats[2] = (float)ent;
+  }
+}
+
+// Sum of squares of the gradient: stage 1 per block, stage 2 the clip factor.
+__global__ void __launch_bounds__(kRedThreads)
+sumsq_partial_kernel(const float* __restrict__ g, long long n, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    s += (double)g[i] * g[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+clip_final_kernel(const double* __restrict__ part, int nblk, float max_norm,
+                  float* __restrict__ clip_coef, float* __restrict__ stats) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    const double norm = sqrt(s);
+    const double c = (double)max_norm / (norm + 1e-6);
+    *clip_coef = (float)(c < 1.0 ? c : 1.0);
+    if (stats) stats[3] = (float)norm;
+  }
+}
+
+// Adam with bias correction on the clipped gradient.
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ clip_coef, long long n, float lr, float bc1,
+                            float bc2) {
+  const float c = *clip_coef;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i] * c;
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+  }
+}
+
+int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+}
+
+}  // namespace
+}  // namespace sg
+
+using sg::Layer;
+using sg::Layout;
+using sg::Net;
+
+struct sg_ppo {
+  sg_ctx* env = nullptr;
+  sg_ppo_config cfg{};
+  int E = 0, D = 0, A = 0, n = 0, M = 0;
+  long long B = 0;
+  Layout L{};
+  cudaStream_t stream = nullptr;       // the stream the collect graph was captured for
+  cublasHandle_t blas = nullptr;
+  void* blas_ws = nullptr;
+  float* ones = nullptr;               // [rows] for bias gradients
+  float *params = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+  long long adam_t = 0;
+  long long* d_step = nullptr;         // global step of the exploration noise
+  float *obs = nullptr, *actions = nullptr, *logp = nullptr, *values = nullptr, *rewards = nullptr;
+  uint8_t* dones = nullptr;
+  float *adv = nullptr, *ret = nullptr;
+  float* jmask = nullptr;              // [E][A]
+  uint8_t* reset_mask = nullptr;       // [E]
+  float* zero_targets = nullptr;       // [E][A]
+  // activations and their gradients, [rows_max][width]
+  float *ha[3] = {nullptr, nullptr, nullptr}, *hc[3] = {nullptr, nullptr, nullptr};
+  float *mu = nullptr, *vout = nullptr, *dbuf0 = nullptr, *dbuf1 = nullptr;
+  float *dmu = nullptr, *dv = nullptr;  // loss gradients w.r.t. the actor mean and the value
+  sg::MiniBatch mb{};
+  float* head_part = nullptr;
+  double* red_part = nullptr;
+  float* norm = nullptr;               // advantage mean, 1 / std
+  float* clip_coef = nullptr;
+  cudaGraphExec_t collect_exec = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+sg_status fail(sg_ppo* p, sg_status code, const std::string& msg) {
+  if (p && p->env) sg::context_set_error(p->env, msg.c_str());
+  return code;
+}
+
+sg_status cuda_fail(sg_ppo* p, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return SG_OK;
+  return fail(p, e == cudaErrorMemoryAllocation ? SG_ERR_OOM : SG_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+cudaError_t dalloc(sg_ppo* p, T** ptr, size_t count) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), sizeof(T) * (count ? count : 1));
+  if (e == cudaSuccess) p->allocs.push_back(*ptr);
+  return e;
+}
+
+bool blas_ok(cublasStatus_t s) { return s == CUBLAS_STATUS_SUCCESS; }
+
+// Y[rows][out] = X[rows][in] W^T
+bool gemm_fwd(sg_ppo* p, const float* X, int rows, const Layer& l, float* Y) {
+  const float one = 1.f, zero = 0.f;
+  return blas_ok(cublasSgemm(p->blas, CUBLAS_OP_T, CUBLAS_OP_N, l.out, rows, l.in, &one,
+                             p->params + l.w, l.in, X, l.in, &zero, Y, l.out));
+}
+// dX[rows][in] = dY[rows][out] W
+bool gemm_bwd_data(sg_ppo* p, const float* dY, int rows, const Layer& l, float* dX) {
+  const float one = 1.f, zero = 0.f;
+  return blas_ok(cublasSgemm(p->blas, CUBLAS_OP_N, CUBLAS_OP_N, l.in, rows, l.out, &one,
+                             p->params + l.w, l.in, dY, l.out, &zero, dX, l.in));
+}
+// dW[out][in] = dY^T X ; db[out] = dY^T 1
+bool gemm_bwd_weight(sg_ppo* p, const float* dY, const float* X, int rows, const Layer& l) {
+  const float one = 1.f, zero = 0.f;
+  if (!blas_ok(cublasSgemm(p->blas, CUBLAS_OP_N, CUBLAS_OP_T, l.in, l.out, rows, &one, X, l.in,
+                           dY, l.out, &zero, p->grad + l.w, l.in)))
+    return false;
+  return blas_ok(cublasSgemv(p->blas, CUBLAS_OP_N, l.out, rows, &one, dY, l.out, p->ones, 1, &zero,
+                             p->grad + l.b, 1));
+}
+
+cudaError_t bias_act(sg_ppo* p, float* Y, int rows, const Layer& l, bool elu) {
+  const long long n = (long long)rows * l.out;
+  sg::bias_act_kernel<<<sg::grid_for(n, 256), 256, 0, p->stream>>>(Y, p->params + l.b, n, l.out,
+                                                                    elu ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// Forward of one network over `rows` inputs; hidden outputs kept in h[0..2].
+bool net_forward(sg_ppo* p, const Net& net, const float* X, int rows, float* const (&h)[3],
+                 float* out) {
+  const float* in = X;
+  for (int i = 0; i < 4; ++i) {
+    float* y = i < 3 ? h[i] : out;
+    if (!gemm_fwd(p, in, rows, net.l[i], y)) return false;
+    if (bias_act(p, y, rows, net.l[i], i < 3) != cudaSuccess) return false;
+    in = y;
+  }
+  return true;
+}
+
+// Backward of one network from dOut [rows][out]; weight gradients into p->grad.
+bool net_backward(sg_ppo* p, const Net& net, const float* X, int rows, float* const (&h)[3],
+                  const float* dOut) {
+  const float* dY = dOut;
+  float* bufs[2] = {p->dbuf0, p->dbuf1};
+  for (int i = 3; i >= 0; --i) {
+    const float* in = i > 0 ? h[i - 1] : X;
+    if (!gemm_bwd_weight(p, dY, in, rows, net.l[i])) return false;
+    if (i == 0) break;
+    float* dX = bufs[i & 1];
+    if (!gemm_bwd_data(p, dY, rows, net.l[i], dX)) return false;
+    const long long n = (long long)rows * net.l[i].in;
+    sg::elu_backward_kernel<<<sg::grid_for(n, 256), 256, 0, p->stream>>>(dX, h[i - 1], n);
+    if (cudaGetLastError() != cudaSuccess) return false;
+    dY = dX;
+  }
+  return true;
+}
+
+sg_status bind_stream(sg_ppo* p, cudaStream_t s) {
+  p->stream = s;
+  if (!blas_ok(cublasSetStream(p->blas, s))) return fail(p, SG_ERR_CUDA, "cublasSetStream failed");
+  return SG_OK;
+}
+
+// The collect loop as a sequence of launches on p->stream (captured once).
+sg_status enqueue_collect(sg_ppo* p) {
+  const int E = p->E, A = p->A, D = p->D, n = p->n;
+  const sg_ppo_config& c = p->cfg;
+  const int tb = 128, eb = (E + tb - 1) / tb;
+  // the observations after the previous collect (or sg_ppo_reset) start this one
+  cudaError_t ce = cudaMemcpyAsync(p->obs, p->obs + (size_t)n * E * D, (size_t)E * D * 4,
+                                   cudaMemcpyDeviceToDevice, p->stream);
+  if (ce != cudaSuccess) return cuda_fail(p, ce, "sg_ppo_collect");
+  for (int t = 0; t < n; ++t) {
+    float* o_t = p->obs + (size_t)t * E * D;
+    float* o_next = p->obs + (size_t)(t + 1) * E * D;
+    float* a_t = p->actions + (size_t)t * E * A;
+    float* v_t = p->values + (size_t)t * E;
+    if (!net_forward(p, p->L.actor, o_t, E, p->ha, p->mu) ||
+        !net_forward(p, p->L.critic, o_t, E, p->hc, v_t))
+      return fail(p, SG_ERR_CUDA, "sg_ppo_collect: network forward failed");
+    sg::sample_kernel<<<eb, tb, 0, p->stream>>>(p->mu, p->params + p->L.log_std, p->jmask,
+                                               p->d_step, t, c.seed, E, A, a_t,
+                                               p->logp + (size_t)t * E);
+    sg_status st = sg_step(p->env, a_t, c.dt, c.substeps, o_next, p->rewards + (size_t)t * E,
+                           p->dones + (size_t)t * E);
+    if (st != SG_OK) return st;
+    sg::bootstrap_kernel<<<eb, tb, 0, p->stream>>>(p->rewards + (size_t)t * E,
+                                                  p->dones + (size_t)t * E, v_t, c.gamma, E,
+                                                  p->reset_mask);
+    if ((st = sg_reset(p->env, p->reset_mask)) != SG_OK) return st;
+    if ((st = sg_observe(p->env, a_t, p->reset_mask, o_next)) != SG_OK) return st;
+  }
+  if (!net_forward(p, p->L.critic, p->obs + (size_t)n * E * D, E, p->hc,
+                   p->values + (size_t)n * E))
+    return fail(p, SG_ERR_CUDA, "sg_ppo_collect: critic forward failed");
+  sg::gae_kernel<<<eb, tb, 0, p->stream>>>(p->rewards, p->values, p->dones, n, E, c.gamma, c.lam,
+                                          p->adv, p->ret);
+  sg::moments_partial_kernel<<<sg::kRedBlocks, sg::kRedThreads, 0, p->stream>>>(p->adv, p->B,
+                                                                                p->red_part);
+  sg::moments_final_kernel<<<1, sg::kRedThreads, 0, p->stream>>>(p->red_part, sg::kRedBlocks,
+                                                                 p->B, p->norm);
+  sg::advance_kernel<<<1, 1, 0, p->stream>>>(p->d_step, n);
+  return cuda_fail(p, cudaGetLastError(), "sg_ppo_collect");
+}
+
+}  // namespace
+
+extern "C" {
+
+sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
+  if (!out) return SG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!env || !cfg) return SG_ERR_INVALID_ARG;
+  sg_ppo* p = new (std::nothrow) sg_ppo();
+  if (!p) return SG_ERR_OOM;
+  p->env = env;
+  p->cfg = *cfg;
+  const sg_ppo_config& c = *cfg;
+  p->E = sg_num_envs(env);
+  p->D = sg_obs_dim(env);
+  p->A = sg_max_joints(env);
+  p->n = c.n_steps;
+  p->B = (long long)p->E * c.n_steps;
+  auto bad = [&](const char* m) {
+    fail(p, SG_ERR_INVALID_ARG, std::string("sg_ppo_create: ") + m);
+    delete p;
+    return SG_ERR_INVALID_ARG;
+  };
+  if (c.n_steps < 1 || c.n_steps > 4096) return bad("n_steps must be 1..4096");
+  if (c.epochs < 1 || c.minibatches < 1) return bad("epochs and minibatches must be >= 1");
+  if (p->B % c.minibatches != 0) return bad("minibatches must divide num_envs * n_steps");
+  if (p->B / c.minibatches > (1 << 30)) return bad("minibatch too large");
+  if (!(c.gamma >= 0.f && c.gamma <= 1.f) || !(c.lam >= 0.f && c.lam <= 1.f))
+    return bad("gamma and lam must be in [0, 1]");
+  if (!(c.clip > 0.f) || !(c.lr > 0.f) || !(c.max_grad_norm > 0.f) || !(c.dt > 0.f))
+    return bad("clip, lr, max_grad_norm and dt must be > 0");
+  if (!std::isfinite(c.value_coef) || !std::isfinite(c.entropy_coef)) return bad("coefficients must be finite");
+  if (c.substeps < 1 || c.substeps > 64) return bad("substeps must be 1..64");
+  p->M = (int)(p->B / c.minibatches);
+  p->L = sg::make_layout(p->D, p->A);
+  const int rows = p->M > p->E ? p->M : p->E;
+  const int E = p->E, A = p->A, D = p->D, n = p->n;
+  cudaError_t e = cudaSuccess;
+  auto step = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  const size_t P = p->L.total;
+  step(dalloc(p, &p->params, P));
+  step(dalloc(p, &p->grad, P));
+  step(dalloc(p, &p->adam_m, P));
+  step(dalloc(p, &p->adam_v, P));
+  step(dalloc(p, &p->d_step, 1));
+  step(dalloc(p, &p->obs, (size_t)(n + 1) * E * D));
+  step(dalloc(p, &p->actions, (size_t)n * E * A));
+  step(dalloc(p, &p->logp, (size_t)n * E));
+  step(dalloc(p, &p->values, (size_t)(n + 1) * E));
+  step(dalloc(p, &p->rewards, (size_t)n * E));
+  step(dalloc(p, &p->dones, (size_t)n * E));
+  step(dalloc(p, &p->adv, (size_t)n * E));
+  step(dalloc(p, &p->ret, (size_t)n * E));
+  step(dalloc(p, &p->jmask, (size_t)E * A));
+  step(dalloc(p, &p->reset_mask, (size_t)E));
+  step(dalloc(p, &p->zero_targets, (size_t)E * A));
+  const int widths[3] = {sg::kH1, sg::kH2, sg::kH3};
+  for (int i = 0; i < 3; ++i) {
+    step(dalloc(p, &p->ha[i], (size_t)rows * widths[i]));
+    step(dalloc(p, &p->hc[i], (size_t)rows * widths[i]));
+  }
+  step(dalloc(p, &p->mu, (size_t)rows * A));
+  step(dalloc(p, &p->vout, (size_t)rows));
+  step(dalloc(p, &p->dbuf0, (size_t)rows * sg::kH1));
+  step(dalloc(p, &p->dbuf1, (size_t)rows * sg::kH1));
+  step(dalloc(p, &p->dmu, (size_t)p->M * A));
+  step(dalloc(p, &p->dv, (size_t)p->M));
+  step(dalloc(p, &p->ones, (size_t)rows));
+  step(dalloc(p, &p->mb.obs, (size_t)p->M * D));
+  step(dalloc(p, &p->mb.act, (size_t)p->M * A));
+  step(dalloc(p, &p->mb.mask, (size_t)p->M * A));
+  step(dalloc(p, &p->mb.logp, (size_t)p->M));
+  step(dalloc(p, &p->mb.value, (size_t)p->M));
+  step(dalloc(p, &p->mb.adv, (size_t)p->M));
+  step(dalloc(p, &p->mb.ret, (size_t)p->M));
+  const int head_blocks = (p->M + sg::kRedThreads - 1) / sg::kRedThreads;
+  step(dalloc(p, &p->head_part, (size_t)head_blocks * (2 + 2 * A)));
+  step(dalloc(p, &p->red_part, (size_t)2 * sg::kRedBlocks));
+  step(dalloc(p, &p->norm, 2));
+  step(dalloc(p, &p->clip_coef, 1));
+  const size_t ws_bytes = (size_t)32 << 20;
+  step(cudaMalloc(&p->blas_ws, ws_bytes));
+  if (e != cudaSuccess) {
+    sg_status st = cuda_fail(p, e, "sg_ppo_create");
+    sg_ppo_destroy(p);
+    return st;
+  }
+  // host-built constants: joint mask, ones, zero targets
+  std::vector<float> jm((size_t)E * A, 0.f), ones((size_t)rows, 1.f);
+  const std::vector<int32_t>& dof = sg::context_env_dof(env);
+  for (int k = 0; k < E; ++k)
+    for (int j = 0; j < A && j < dof[k]; ++j) jm[(size_t)k * A + j] = 1.f;
+  cudaStream_t s = sg::context_stream(env);
+  step(cudaMemcpyAsync(p->jmask, jm.data(), jm.size() * 4, cudaMemcpyHostToDevice, s));
+  step(cudaMemcpyAsync(p->ones, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice, s));
+  step(cudaMemsetAsync(p->zero_targets, 0, (size_t)E * A * 4, s));
+  step(cudaMemsetAsync(p->params, 0, P * 4, s));
+  step(cudaMemsetAsync(p->adam_m, 0, P * 4, s));
+  step(cudaMemsetAsync(p->adam_v, 0, P * 4, s));
+  step(cudaMemsetAsync(p->d_step, 0, sizeof(long long), s));
+  step(cudaStreamSynchronize(s));     // the host vectors above go out of scope
+  if (e != cudaSuccess) {
+    sg_status st = cuda_fail(p, e, "sg_ppo_create");
+    sg_ppo_destroy(p);
+    return st;
+  }
+  if (!blas_ok(cublasCreate(&p->blas)) ||
+      !blas_ok(cublasSetWorkspace(p->blas, p->blas_ws, ws_bytes)) ||
+      !blas_ok(cublasSetMathMode(p->blas, c.tf32 ? CUBLAS_TF32_TENSOR_OP_MATH
+                                                 : CUBLAS_PEDANTIC_MATH)) ||
+      !blas_ok(cublasSetPointerMode(p->blas, CUBLAS_POINTER_MODE_HOST))) {
+    fail(p, SG_ERR_CUDA, "sg_ppo_create: cuBLAS initialisation failed");
+    sg_ppo_destroy(p);
+    return SG_ERR_CUDA;
+  }
+  bind_stream(p, s);
+  *out = p;
+  return SG_OK;
+}
+
+void sg_ppo_destroy(sg_ppo* p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->collect_exec) cudaGraphExecDestroy(p->collect_exec);
+  if (p->blas) cublasDestroy(p->blas);
+  if (p->blas_ws) cudaFree(p->blas_ws);
+  for (void* a : p->allocs) cudaFree(a);
+  delete p;
+}
+
+int64_t sg_ppo_num_params(const sg_ppo* p) { return p ? (int64_t)p->L.total : 0; }
+
+sg_status sg_ppo_set_params(sg_ppo* p, const float* src) {
+  if (!p || !src) return SG_ERR_INVALID_ARG;
+  bind_stream(p, sg::context_stream(p->env));
+  return cuda_fail(p, cudaMemcpyAsync(p->params, src, p->L.total * 4, cudaMemcpyDeviceToDevice,
+                                      p->stream),
+                   "sg_ppo_set_params");
+}
+
+sg_status sg_ppo_get_params(sg_ppo* p, float* dst) {
+  if (!p || !dst) return SG_ERR_INVALID_ARG;
+  bind_stream(p, sg::context_stream(p->env));
+  return cuda_fail(p, cudaMemcpyAsync(dst, p->params, p->L.total * 4, cudaMemcpyDeviceToDevice,
+                                      p->stream),
+                   "sg_ppo_get_params");
+}
+
+sg_status sg_ppo_reset(sg_ppo* p, int64_t step0) {
+  if (!p) return SG_ERR_INVALID_ARG;
+  bind_stream(p, sg::context_stream(p->env));
+  sg_status st = sg_reset(p->env, nullptr);
+  // the first observations go where a collect leaves its last ones
+  if (st == SG_OK)
+    st = sg_observe(p->env, p->zero_targets, nullptr, p->obs + (size_t)p->n * p->E * p->D);
+  if (st != SG_OK) return st;
+  cudaError_t e = cudaMemsetAsync(p->adam_m, 0, p->L.total * 4, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->adam_v, 0, p->L.total * 4, p->stream);
+  const long long s0 = step0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_step, &s0, sizeof(long long), cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);   // s0 is a host local
+  p->adam_t = 0;
+  return cuda_fail(p, e, "sg_ppo_reset");
+}
+
+sg_status sg_ppo_collect(sg_ppo* p) {
+  if (!p) return SG_ERR_INVALID_ARG;
+  cudaStream_t s = sg::context_stream(p->env);
+  if (!p->collect_exec) {
+    // capture on a private stream, then replay on the env's stream
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(p, e, "sg_ppo_collect: stream");
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    sg_status st = SG_OK;
+    if (e == cudaSuccess) {
+      sg_set_stream(p->env, cap);
+      bind_stream(p, cap);
+      st = enqueue_collect(p);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(cap, &g);
+      if (e == cudaSuccess) e = ee;
+      if (e == cudaSuccess && st == SG_OK) e = cudaGraphInstantiate(&p->collect_exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+    }
+    sg_set_stream(p->env, s);
+    bind_stream(p, s);
+    cudaStreamDestroy(cap);
+    if (st != SG_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(p, e, "sg_ppo_collect: capture");
+  }
+  bind_stream(p, s);
+  return cuda_fail(p, cudaGraphLaunch(p->collect_exec, s), "sg_ppo_collect");
+}
+
+sg_status sg_ppo_update(sg_ppo* p, const int32_t* perm, float* stats) {
+  if (!p || !perm) return SG_ERR_INVALID_ARG;
+  bind_stream(p, sg::context_stream(p->env));
+  const sg_ppo_config& c = p->cfg;
+  const int M = p->M, A = p->A, D = p->D, E = p->E;
+  const long long P = (long long)p->L.total;
+  sg::Batch src{p->obs, p->actions, p->logp, p->values, p->adv, p->ret, p->jmask, p->norm};
+  const int head_blocks = (M + sg::kRedThreads - 1) / sg::kRedThreads;
+  for (int ep = 0; ep < c.epochs; ++ep) {
+    for (int k = 0; k < c.minibatches; ++k) {
+      const int32_t* idx = perm + (size_t)ep * p->B + (size_t)k * M;
+      float* st = stats ? stats + 4 * ((size_t)ep * c.minibatches + k) : nullptr;
+      sg::gather_kernel<<<(int)(((long long)M * 32 + 255) / 256), 256, 0, p->stream>>>(
+          src, p->mb, idx, M, E, D, A);
+      if (!net_forward(p, p->L.actor, p->mb.obs, M, p->ha, p->mu) ||
+          !net_forward(p, p->L.critic, p->mb.obs, M, p->hc, p->vout))
+        return fail(p, SG_ERR_CUDA, "sg_ppo_update: forward failed");
+      sg::HeadArgs h{p->mu, p->vout, p->params + p->L.log_std, p->mb, p->dmu, p->dv,
+                     p->head_part, M, A, c.clip, c.value_coef};
+      sg::head_kernel<<<head_blocks, sg::kRedThreads, 0, p->stream>>>(h);
+      sg::head_final_kernel<<<1, 64, 0, p->stream>>>(p->head_part, head_blocks, A, M,
+                                                     p->params + p->L.log_std, c.entropy_coef,
+                                                     p->grad + p->L.log_std, st);
+      if (!net_backward(p, p->L.actor, p->mb.obs, M, p->ha, p->dmu) ||
+          !net_backward(p, p->L.critic, p->mb.obs, M, p->hc, p->dv))
+        return fail(p, SG_ERR_CUDA, "sg_ppo_update: backward failed");
+      sg::sumsq_partial_kernel<<<sg::kRedBlocks, sg::kRedThreads, 0, p->stream>>>(p->grad, P,
+                                                                                  p->red_part);
+      sg::clip_final_kernel<<<1, sg::kRedThreads, 0, p->stream>>>(p->red_part, sg::kRedBlocks,
+                                                                  c.max_grad_norm, p->clip_coef,
+                                                                  st);
+      ++p->adam_t;
+      const float bc1 = (float)(1.0 - std::pow(0.9, (double)p->adam_t));
+      const float bc2 = (float)(1.0 - std::pow(0.999, (double)p->adam_t));
+      sg::adam_kernel<<<sg::grid_for(P, 256), 256, 0, p->stream>>>(
+          p->params, p->grad, p->adam_m, p->adam_v, p->clip_coef, P, c.lr, bc1, bc2);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(p, e, "sg_ppo_update");
+    }
+  }
+  return SG_OK;
+}
+
+namespace {
+// (device pointer, bytes) of a rollout buffer
+bool buffer_of(sg_ppo* p, int which, void** ptr, size_t* bytes) {
+  const size_t nE = (size_t)p->n * p->E;
+  switch (which) {
+    case SG_PPO_OBS: *ptr = p->obs; *bytes = (nE + p->E) * p->D * 4; return true;
+    case SG_PPO_ACTIONS: *ptr = p->actions; *bytes = nE * p->A * 4; return true;
+    case SG_PPO_LOGP: *ptr = p->logp; *bytes = nE * 4; return true;
+    case SG_PPO_VALUES: *ptr = p->values; *bytes = (nE + p->E) * 4; return true;
+    case SG_PPO_REWARDS: *ptr = p->rewards; *bytes = nE * 4; return true;
+    case SG_PPO_DONES: *ptr = p->dones; *bytes = nE; return true;
+    case SG_PPO_ADVANTAGES: *ptr = p->adv; *bytes = nE * 4; return true;
+    case SG_PPO_RETURNS: *ptr = p->ret; *bytes = nE * 4; return true;
+    case SG_PPO_GRAD: *ptr = p->grad; *bytes = p->L.total * 4; return true;
+    default: return false;
+  }
+}
+}  // namespace
+
+sg_status sg_ppo_get_buffer(sg_ppo* p, int32_t which, void* dst) {
+  if (!p || !dst) return SG_ERR_INVALID_ARG;
+  void* ptr;
+  size_t bytes;
+  if (!buffer_of(p, which, &ptr, &bytes)) return fail(p, SG_ERR_INVALID_ARG, "unknown buffer");
+  bind_stream(p, sg::context_stream(p->env));
+  return cuda_fail(p, cudaMemcpyAsync(dst, ptr, bytes, cudaMemcpyDeviceToDevice, p->stream),
+                   "sg_ppo_get_buffer");
+}
+
+sg_status sg_ppo_set_buffer(sg_ppo* p, int32_t which, const void* src) {
+  if (!p || !src) return SG_ERR_INVALID_ARG;
+  void* ptr;
+  size_t bytes;
+  if (!buffer_of(p, which, &ptr, &bytes)) return fail(p, SG_ERR_INVALID_ARG, "unknown buffer");
+  bind_stream(p, sg::context_stream(p->env));
+  cudaError_t e = cudaMemcpyAsync(ptr, src, bytes, cudaMemcpyDeviceToDevice, p->stream);
+  if (e == cudaSuccess && which == SG_PPO_ADVANTAGES) {
+    // the update normalises with the batch moments: recompute them
+    sg::moments_partial_kernel<<<sg::kRedBlocks, sg::kRedThreads, 0, p->stream>>>(p->adv, p->B,
+                                                                                  p->red_part);
+    sg::moments_final_kernel<<<1, sg::kRedThreads, 0, p->stream>>>(p->red_part, sg::kRedBlocks,
+                                                                   p->B, p->norm);
+    e = cudaGetLastError();
+  }
+  return cuda_fail(p, e, "sg_ppo_set_buffer");
+}
+
+}  // extern "C"

@@ -51,6 +51,23 @@ class SgDesc(ctypes.Structure):
     ]
 
 
+class SgPpoConfig(ctypes.Structure):
+    _fields_ = [("n_steps", ctypes.c_int32), ("epochs", ctypes.c_int32),
+                ("minibatches", ctypes.c_int32), ("gamma", ctypes.c_float), ("lam", ctypes.c_float),
+                ("clip", ctypes.c_float), ("value_coef", ctypes.c_float),
+                ("entropy_coef", ctypes.c_float), ("lr", ctypes.c_float),
+                ("max_grad_norm", ctypes.c_float), ("dt", ctypes.c_float),
+                ("substeps", ctypes.c_int32), ("seed", ctypes.c_uint32), ("tf32", ctypes.c_int32)]
+
+
+PPO_OBS, PPO_ACTIONS, PPO_LOGP, PPO_VALUES, PPO_REWARDS, PPO_DONES, PPO_ADVANTAGES, PPO_RETURNS, \
+    PPO_GRAD = range(9)
+
+PPO_DEFAULTS = dict(n_steps=24, epochs=5, minibatches=4, gamma=0.99, lam=0.95, clip=0.2,
+                    value_coef=1.0, entropy_coef=0.01, lr=1e-3, max_grad_norm=1.0, dt=1.0 / 60.0,
+                    substeps=2, seed=1, tf32=0)
+
+
 class SgPlanInfo(ctypes.Structure):
     _fields_ = [("obs_dim", ctypes.c_int32), ("num_slots", ctypes.c_int32),
                 ("num_chains", ctypes.c_int32), ("class_slots", ctypes.c_int32 * 4)]
@@ -96,6 +113,16 @@ def load_library(path=LIB_PATH):
         "sg_set_paths": (i32, [vp, vp, i32, u8p]),
         "sg_get_paths": (i32, [vp, vp]),
         "sg_measure_fp32_fma_rate": (i32, [vp, i32, i32, ctypes.POINTER(f32)]),
+        "sg_ppo_create": (i32, [vp, ctypes.POINTER(SgPpoConfig), ctypes.POINTER(vp)]),
+        "sg_ppo_destroy": (None, [vp]),
+        "sg_ppo_num_params": (ctypes.c_int64, [vp]),
+        "sg_ppo_set_params": (i32, [vp, vp]),
+        "sg_ppo_get_params": (i32, [vp, vp]),
+        "sg_ppo_reset": (i32, [vp, ctypes.c_int64]),
+        "sg_ppo_collect": (i32, [vp]),
+        "sg_ppo_update": (i32, [vp, vp, vp]),
+        "sg_ppo_get_buffer": (i32, [vp, i32, vp]),
+        "sg_ppo_set_buffer": (i32, [vp, i32, vp]),
         "sg_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -427,6 +454,99 @@ class Env:
     def sync_status(self):
         """Synchronise and return the device status code (raises nothing)."""
         return self.lib.sg_sync_status(self.ctx)
+
+
+class PPO:
+    """GPU-resident PPO loop over the envs of ``env`` (see include/sg_ppo.h).
+
+    Keyword arguments override ``PPO_DEFAULTS``."""
+
+    def __init__(self, env, **cfg):
+        import torch
+        self._torch = torch
+        self.env = env
+        self.lib = env.lib
+        c = dict(PPO_DEFAULTS, **cfg)
+        self.cfg = c
+        conf = SgPpoConfig(**{k: c[k] for k, _ in SgPpoConfig._fields_})
+        h = ctypes.c_void_p()
+        env._sync_stream()
+        st = self.lib.sg_ppo_create(env.ctx, ctypes.byref(conf), ctypes.byref(h))
+        if st != SG_OK:
+            raise SgError(st, self.lib.sg_last_error(env.ctx).decode())
+        self.h = h
+        self.num_params = int(self.lib.sg_ppo_num_params(h))
+        self.E, self.D, self.A = env.num_envs, env.obs_dim, env.max_joints
+        self.n = c["n_steps"]
+        self.B = self.E * self.n
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sg_ppo_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        self.env._check(st)
+
+    def set_params(self, flat):
+        self.env._sync_stream()
+        self.env._want(flat, self._torch.float32, (self.num_params,), "params")
+        self._check(self.lib.sg_ppo_set_params(self.h, _ptr(flat)))
+
+    def get_params(self):
+        self.env._sync_stream()
+        out = self._torch.empty(self.num_params, dtype=self._torch.float32, device=self.env.device)
+        self._check(self.lib.sg_ppo_get_params(self.h, _ptr(out)))
+        return out
+
+    def reset(self, step0=0):
+        self.env._sync_stream()
+        self._check(self.lib.sg_ppo_reset(self.h, int(step0)))
+
+    def collect(self):
+        self.env._sync_stream()
+        self._check(self.lib.sg_ppo_collect(self.h))
+
+    def update(self, perms, stats=True):
+        """perms: int32 [epochs][B] device tensor; returns per-minibatch
+        (surrogate, value loss, entropy, grad norm) as a [epochs*mb][4] tensor."""
+        torch = self._torch
+        self.env._sync_stream()
+        self.env._want(perms, torch.int32, (self.cfg["epochs"], self.B), "perms")
+        out = None
+        if stats:
+            out = torch.empty(self.cfg["epochs"] * self.cfg["minibatches"], 4,
+                              dtype=torch.float32, device=self.env.device)
+        self._check(self.lib.sg_ppo_update(self.h, _ptr(perms), _ptr(out)))
+        return out
+
+    def _shape(self, which):
+        n, E, D, A = self.n, self.E, self.D, self.A
+        torch = self._torch
+        return {PPO_OBS: ((n + 1, E, D), torch.float32), PPO_ACTIONS: ((n, E, A), torch.float32),
+                PPO_LOGP: ((n, E), torch.float32), PPO_VALUES: ((n + 1, E), torch.float32),
+                PPO_REWARDS: ((n, E), torch.float32), PPO_DONES: ((n, E), torch.uint8),
+                PPO_ADVANTAGES: ((n, E), torch.float32), PPO_RETURNS: ((n, E), torch.float32),
+                PPO_GRAD: ((self.num_params,), torch.float32)}[which]
+
+    def get_buffer(self, which):
+        self.env._sync_stream()
+        shape, dt = self._shape(which)
+        out = self._torch.empty(shape, dtype=dt, device=self.env.device)
+        self._check(self.lib.sg_ppo_get_buffer(self.h, int(which), _ptr(out)))
+        return out
+
+    def set_buffer(self, which, src):
+        self.env._sync_stream()
+        shape, dt = self._shape(which)
+        self.env._want(src, dt, shape, "buffer")
+        self._check(self.lib.sg_ppo_set_buffer(self.h, int(which), _ptr(src)))
 
 
 def _autograd_function():

@@ -250,3 +250,52 @@ def loss_targets(desc, T, seed=5):
     r = np.random.default_rng(seed)
     g = desc["goal"].astype(np.float64) + r.uniform(-0.05, 0.05, size=(E, MAX_CHAINS, 3))
     return np.broadcast_to(g.astype(np.float32), (T, E, MAX_CHAINS, 3)).copy()
+
+
+# ---- PPO inputs: initial network parameters and minibatch permutations ------
+PPO_HIDDEN = (256, 128, 64)
+
+
+def ppo_param_sizes(D, A):
+    """Sizes of the flat parameter vector's pieces in order (actor W, b per
+    layer, log_std, critic W, b per layer) with their fan-in (0: log_std)."""
+    dims = (D,) + PPO_HIDDEN
+    out = []
+    for net_out in (A, 1):
+        for i in range(4):
+            fan_in, fan_out = dims[i], (dims[i + 1] if i < 3 else net_out)
+            out += [(fan_out * fan_in, fan_in), (fan_out, fan_in)]
+        if net_out == A:
+            out.append((A, 0))
+    return out
+
+
+def ppo_init_params(D, A, seed=11):
+    """Seeded initial parameters: weights and biases U(-1/sqrt(fan_in),
+    1/sqrt(fan_in)) (the common default for linear layers), log_std = 0."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for n, fan_in in ppo_param_sizes(D, A):
+        if fan_in == 0:
+            parts.append(np.zeros(n))
+        else:
+            k = 1.0 / math.sqrt(fan_in)
+            parts.append(rng.uniform(-k, k, size=n))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def ppo_perms(B, epochs, seed=13, iteration=0):
+    """Minibatch permutations [epochs][B] (int32) of one update."""
+    rng = np.random.default_rng([seed, iteration])
+    return np.stack([rng.permutation(B) for _ in range(epochs)]).astype(np.int32)
+
+
+def ppo_config(name="P1", num_envs=None):
+    """The with-learning workload: PPO on a reaching batch of 7-DOF
+    insertion-joint arms (the PSM stand-in), 24 steps per env per update,
+    5 epochs of 4 minibatches."""
+    if name != "P1":
+        raise KeyError(name)
+    E = num_envs or 16384
+    d = make_desc(["7P"] * E, episode_len=250)
+    return Workload(d, ["7P"] * E, 1.0 / 60.0, 2, 24, "P1 PPO reach 7P x%d" % E)
