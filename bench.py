@@ -48,6 +48,7 @@ FLOP_SUBSTEP = {"4R": 581, "7R": 1424, "7P": 1296}
 FLOP_TIP = {"4R": 55, "7R": 127, "7P": 115}
 FLOP_REWARD = 9          # distance to the goal (per chain)
 FLOP_QUAT = 30           # tip quaternion (path task)
+W_HIDDEN = (256, 128, 64)   # hidden widths of the PPO networks
 # Adjoint pieces (same counting): one substep's adjoint (forward substep with
 # its factorisation recomputed, the solve with the factor, the reverse RNEA)
 # and the tool-tip Jacobian-transpose product.
@@ -536,6 +537,105 @@ def run_adjoint_config(cx, with_error, name="C4", E=None, T=None, err_envs=16):
     return out
 
 
+def ppo_flops(D, A, E, n, epochs):
+    """Algorithmic FLOPs of one PPO iteration's dense layers (an FMA counts
+    2): the forward of both networks per env and step plus the last values,
+    and per update row the forward, the weight gradients and the input
+    gradients of every layer but the first."""
+    dims = (D,) + W_HIDDEN
+    fw = lambda out: 2 * sum(a * b for a, b in zip(dims, dims[1:] + (out,)))
+    fwd = fw(A) + fw(1)
+    bwd = 2 * fwd - 2 * D * W_HIDDEN[0] * 2          # dW of all layers + dX of layers 2..4
+    collect = (n * E + E) * fwd - E * fw(A)
+    update = epochs * n * E * (fwd + bwd)
+    return collect, update
+
+
+def run_ppo_config(cx, name="P1", E=None):
+    """The with-learning workload: collect + update per iteration."""
+    torch = cx.torch
+    from paper_2310_04676_gb300 import sg, workloads as W
+    args = cx.args
+    wl = W.ppo_config(name, num_envs=E)
+    desc = replica_desc(wl, cx.rank)
+    env = sg.Env(desc)
+    tf32 = 0 if args.ppo_fp32 else 1
+    ppo = sg.PPO(env, n_steps=wl.steps, epochs=5, minibatches=4, dt=wl.dt, substeps=wl.substeps,
+                 seed=1 + cx.rank, tf32=tf32)
+    D, A, En = env.obs_dim, env.max_joints, env.num_envs
+    ppo.set_params(torch.as_tensor(W.ppo_init_params(D, A), device=cx.dev))
+    ppo.reset(0)
+    perms_h = torch.as_tensor(W.ppo_perms(ppo.B, 5)).pin_memory()
+    perms = perms_h.to(cx.dev)
+    stats_h = torch.empty(20, 4).pin_memory()
+    ev = []
+
+    def iteration(e2e=False):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        if e2e:
+            perms.copy_(perms_h, non_blocking=True)
+        a.record(cx.stream)
+        ppo.collect()
+        b.record(cx.stream)
+        st = ppo.update(perms)
+        if e2e:
+            stats_h.copy_(st, non_blocking=True)
+        ev.append((a, b))
+
+    for _ in range(args.warmup):
+        iteration()
+    ev.clear()
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_ppo_r%d.csv" % cx.rank), cx.local)
+    ms = cx.timed(iteration, args.steps, clk)
+    ms_collect = [a.elapsed_time(b) for a, b in ev]
+    ev.clear()
+    ms_e2e = cx.timed(lambda: iteration(True), args.steps)
+    frames = En * wl.steps * args.steps
+    t = sum(ms) / 1e3
+    value = aggregate_rate(frames, t, world=cx.world, device=cx.dev)
+    f_col, f_upd = ppo_flops(D, A, En, wl.steps, 5)
+    it_s = t / args.steps
+    peaks, src = load_peaks()
+    # TF32 dense peak: the measured bf16 burst peak x the nominal TF32 / BF16 ratio (1.1 / 2.25)
+    peak = float(peaks.get("bf16_tflops", 1900.0)) * (1.1 / 2.25) if tf32 else \
+        torch.cuda.get_device_properties(cx.dev).multi_processor_count * 128 * 2 * \
+        float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    achieved = (f_col + f_upd) / it_s / 1e12
+    cfg = {"workload": wl.name, "envs_per_gpu": En, "n_steps": wl.steps, "epochs": 5,
+           "minibatches": 4, "minibatch_rows": ppo.B // 4, "substeps": wl.substeps, "dt": wl.dt,
+           "networks": "actor and critic MLP %d-256-128-64-{%d,1}, ELU" % (D, A),
+           "gemm": "cuBLAS TF32 tensor cores" if tf32 else "cuBLAS FP32",
+           "l2": "flushed (256 MiB write) before every timed iteration"}
+    line = base_line(args, cx.world, value, 1e3 * it_s, cfg)
+    line["metric"] = "with-learning frames/s (collect + PPO update), context for the step metric"
+    line["unit"] = "frames/s"
+    line["dtype"] = "tf32" if tf32 else "f32"
+    line["iteration_time_stats"] = stats(ms)
+    line["ms_collect"] = float(np.mean(ms_collect))
+    line["ms_update"] = 1e3 * it_s - float(np.mean(ms_collect))
+    line["roofline"] = {"bound": "tensor" if tf32 else "alu", "achieved": achieved, "peak": peak,
+                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                        "kernel": "whole iteration (dense layers' FLOPs / iteration time)",
+                        "peak_source": ("measured bf16 burst x 1.1/2.25 (%s)" % src) if tf32
+                        else "SMs x 128 x 2 x max SM clock",
+                        "flops_per_iteration": {"collect": f_col, "update": f_upd}}
+    line["e2e"] = {"value": aggregate_rate(frames, sum(ms_e2e) / 1e3, world=cx.world, device=cx.dev),
+                   "unit": "frames/s", "h2d_bytes_per_step": int(perms_h.numel() * 4),
+                   "d2h_bytes_per_step": int(stats_h.numel() * 4)}
+    # kernels of this library per iteration: per collect step 8 bias/ELU, sampling, the env
+    # step, bootstrap, reset, observe; then 4 bias (last values), GAE, 2 moments, step
+    # counter; per minibatch gather, 8 bias/ELU, 2 loss-head, 6 ELU-backward, 2 norm, Adam
+    n_mb = 5 * 4
+    line["gpu_launches"] = (wl.steps * 13 + 8 + n_mb * 20) * args.steps
+    line["library_launches"] = (wl.steps * 8 + 4 + n_mb * 30) * args.steps   # cuBLAS GEMM/GEMV
+    line["clocks"] = clk.summary()
+    line["status"] = sg.STATUS_NAMES.get(env.sync_status())
+    line["paper_context"] = ("Table II: 6.8 s per 1M timesteps with learning (147,059 frames/s), "
+                             "20,000 envs on one 8 GB Quadro RTX 4000 (different engine and task)")
+    return line
+
+
 def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
@@ -566,7 +666,8 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="C3", choices=["C1", "C2", "C3", "C4", "C5"])
+    ap.add_argument("--config", default="C3", choices=["C1", "C2", "C3", "C4", "C5", "P1"])
+    ap.add_argument("--ppo-fp32", action="store_true", help="P1: FP32 GEMMs instead of TF32")
     ap.add_argument("--envs", type=int, nargs="*", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--launch", default=None,
@@ -588,7 +689,11 @@ def main():
     cx = Ctx(args, world, rank, local)
     want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
 
-    if args.config == "C4":
+    if args.config == "P1":
+        line = run_ppo_config(cx)
+        if rank == 0:
+            print(json.dumps(line))
+    elif args.config == "C4":
         g = run_adjoint_config(cx, with_error=want_cpu)
         if rank == 0:
             line = base_line(args, world, g["value"], g["ms_per_rollout"],

@@ -69,31 +69,77 @@ Layout make_layout(int D, int A) {
 // ---- kernels -----------------------------------------------------------------
 __device__ __forceinline__ float elu(float x) { return x > 0.f ? x : expm1f(x); }
 
-// Y[r][c] = act(Y[r][c] + b[c]) in place
-__global__ void bias_act_kernel(float* __restrict__ Y, const float* __restrict__ b, long long n,
+// Y[r][c] = act(Y[r][c] + b[c]) in place (width a multiple of 4: float4 path)
+__global__ void bias_act4_kernel(float4* __restrict__ Y, const float4* __restrict__ b, int n4,
+                                 int width4, int do_elu) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
+    float4 z = Y[i];
+    const float4 c = b[i % width4];
+    z.x += c.x;
+    z.y += c.y;
+    z.z += c.z;
+    z.w += c.w;
+    if (do_elu) {
+      z.x = elu(z.x);
+      z.y = elu(z.y);
+      z.z = elu(z.z);
+      z.w = elu(z.w);
+    }
+    Y[i] = z;
+  }
+}
+
+__global__ void bias_act_kernel(float* __restrict__ Y, const float* __restrict__ b, int n,
                                 int width, int do_elu) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float z = Y[i] + b[i % width];
     Y[i] = do_elu ? elu(z) : z;
   }
 }
 
 // dY <- dY * ELU'(z), with ELU' from the stored output y: 1 for y > 0, y + 1 otherwise
-__global__ void elu_backward_kernel(float* __restrict__ dY, const float* __restrict__ Y,
-                                    long long n) {
+__device__ __forceinline__ float delu(float y) { return y > 0.f ? 1.f : y + 1.f; }
+
+__global__ void elu_backward4_kernel(float4* __restrict__ dY, const float4* __restrict__ Y, int n4) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
+    const float4 y = Y[i];
+    float4 d = dY[i];
+    d.x *= delu(y.x);
+    d.y *= delu(y.y);
+    d.z *= delu(y.z);
+    d.w *= delu(y.w);
+    dY[i] = d;
+  }
+}
+
+// Zero-padded copy of rows [rows][w] -> [rows][wp]
+__global__ void pad_rows_kernel(const float* __restrict__ src, int rows, int w, int wp,
+                                float* __restrict__ dst) {
+  const long long n = (long long)rows * wp;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const float y = Y[i];
-    dY[i] *= y > 0.f ? 1.f : y + 1.f;
+    const int r = (int)(i / wp), c = (int)(i - (long long)r * wp);
+    dst[i] = c < w ? src[(size_t)r * w + c] : 0.f;
   }
+}
+
+// Public <-> internal (padded) parameter layouts: internal[map[i]] = public[i]
+__global__ void scatter_kernel(const float* __restrict__ pub, const int32_t* __restrict__ map,
+                               int n, float* __restrict__ in) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    in[map[i]] = pub[i];
+}
+__global__ void gather_params_kernel(const float* __restrict__ in, const int32_t* __restrict__ map,
+                                     int n, float* __restrict__ pub) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    pub[i] = in[map[i]];
 }
 
 // Actions, log-probabilities and values of one collect step (thread per env).
 __global__ void sample_kernel(const float* __restrict__ mu, const float* __restrict__ log_std,
                               const float* __restrict__ mask, const long long* __restrict__ step,
-                              int t, uint32_t seed, int E, int A, float* __restrict__ actions,
-                              float* __restrict__ logp) {
+                              int t, uint32_t seed, int E, int A, int Ap,
+                              float* __restrict__ actions, float* __restrict__ logp) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   const long long gstep = *step + t;
@@ -106,7 +152,7 @@ __global__ void sample_kernel(const float* __restrict__ mu, const float* __restr
       const int j = 4 * blk + c;
       if (j >= A) break;
       const float ls = log_std[j];
-      actions[(size_t)e * A + j] = mu[(size_t)e * A + j] + expf(ls) * z[c];
+      actions[(size_t)e * A + j] = mu[(size_t)e * Ap + j] + expf(ls) * z[c];
       if (mask[(size_t)e * A + j] != 0.f) lp += -0.5f * z[c] * z[c] - ls - kHalfLog2Pi;
     }
   }
@@ -209,13 +255,14 @@ struct MiniBatch {
 
 // Gather minibatch rows (warp per row): row index b = t * E + e.
 __global__ void gather_kernel(Batch src, MiniBatch dst, const int32_t* __restrict__ idx, int M,
-                              int E, int D, int A) {
+                              int E, int D, int Dp, int A) {
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= M) return;
   const long long b = idx[row];
   const int e = (int)(b % E);
-  for (int k = lane; k < D; k += 32) dst.obs[(size_t)row * D + k] = src.obs[(size_t)b * D + k];
+  for (int k = lane; k < Dp; k += 32)
+    dst.obs[(size_t)row * Dp + k] = k < D ? src.obs[(size_t)b * D + k] : 0.f;
   for (int k = lane; k < A; k += 32) {
     dst.act[(size_t)row * A + k] = src.act[(size_t)b * A + k];
     dst.mask[(size_t)row * A + k] = src.jmask[(size_t)e * A + k];
@@ -233,7 +280,7 @@ struct HeadArgs {
   MiniBatch mb;
   float *d_mu, *d_v;
   float* part;          // [blocks][2 + 2A]: surrogate sum, value-loss sum, dlogstd_j, count_j
-  int M, A;
+  int M, A, Ap;
   float clip, value_coef;
 };
 
@@ -252,7 +299,7 @@ __global__ void __launch_bounds__(kRedThreads) head_kernel(HeadArgs h) {
     float lp = 0.f;
     for (int j = 0; j < A; ++j) {
       const float ls = h.log_std[j];
-      const float z = (h.mb.act[(size_t)i * A + j] - h.mu[(size_t)i * A + j]) * expf(-ls);
+      const float z = (h.mb.act[(size_t)i * A + j] - h.mu[(size_t)i * h.Ap + j]) * expf(-ls);
       zz[j] = z;
       if (h.mb.mask[(size_t)i * A + j] != 0.f) lp += -0.5f * z * z - ls - kHalfLog2Pi;
     }
@@ -274,9 +321,9 @@ __global__ void __launch_bounds__(kRedThreads) head_kernel(HeadArgs h) {
     else gv = 0.5f * (2.f * (v - R) + ((v - vo >= -h.clip && v - vo <= h.clip) ? 2.f * (vc - R) : 0.f));
     h.d_v[i] = h.value_coef * gv * inv_m;
     const float g = g_logp * inv_m;
-    for (int j = 0; j < A; ++j) {
-      const float m = h.mb.mask[(size_t)i * A + j];
-      h.d_mu[(size_t)i * A + j] = m != 0.f ? g * zz[j] * expf(-h.log_std[j]) : 0.f;
+    for (int j = 0; j < h.Ap; ++j) {
+      const float m = j < A ? h.mb.mask[(size_t)i * A + j] : 0.f;
+      h.d_mu[(size_t)i * h.Ap + j] = m != 0.f ? g * zz[j] * expf(-h.log_std[j]) : 0.f;
     }
   }
   const int stride = 2 + 2 * A;
@@ -380,8 +427,12 @@ struct sg_ppo {
   sg_ctx* env = nullptr;
   sg_ppo_config cfg{};
   int E = 0, D = 0, A = 0, n = 0, M = 0;
+  int Dp = 0, Ap = 0;                  // obs and action widths padded to multiples of 4
   long long B = 0;
-  Layout L{};
+  Layout L{};                          // internal (padded) parameter layout
+  size_t public_params = 0;            // length of the caller's flat vector
+  int32_t* pub2int = nullptr;          // [public_params] internal index of each public entry
+  float* xin = nullptr;                // [E][Dp] padded observations of the collect step
   cudaStream_t stream = nullptr;       // the stream the collect graph was captured for
   cublasHandle_t blas = nullptr;
   void* blas_ws = nullptr;
@@ -454,8 +505,14 @@ bool gemm_bwd_weight(sg_ppo* p, const float* dY, const float* X, int rows, const
 
 cudaError_t bias_act(sg_ppo* p, float* Y, int rows, const Layer& l, bool elu) {
   const long long n = (long long)rows * l.out;
-  sg::bias_act_kernel<<<sg::grid_for(n, 256), 256, 0, p->stream>>>(Y, p->params + l.b, n, l.out,
-                                                                    elu ? 1 : 0);
+  if (l.out % 4 == 0) {
+    sg::bias_act4_kernel<<<sg::grid_for(n / 4, 256), 256, 0, p->stream>>>(
+        reinterpret_cast<float4*>(Y), reinterpret_cast<const float4*>(p->params + l.b),
+        (int)(n / 4), l.out / 4, elu ? 1 : 0);
+  } else {
+    sg::bias_act_kernel<<<sg::grid_for(n, 256), 256, 0, p->stream>>>(Y, p->params + l.b, (int)n,
+                                                                      l.out, elu ? 1 : 0);
+  }
   return cudaGetLastError();
 }
 
@@ -483,8 +540,9 @@ bool net_backward(sg_ppo* p, const Net& net, const float* X, int rows, float* co
     if (i == 0) break;
     float* dX = bufs[i & 1];
     if (!gemm_bwd_data(p, dY, rows, net.l[i], dX)) return false;
-    const long long n = (long long)rows * net.l[i].in;
-    sg::elu_backward_kernel<<<sg::grid_for(n, 256), 256, 0, p->stream>>>(dX, h[i - 1], n);
+    const long long n = (long long)rows * net.l[i].in;      // hidden widths: multiples of 4
+    sg::elu_backward4_kernel<<<sg::grid_for(n / 4, 256), 256, 0, p->stream>>>(
+        reinterpret_cast<float4*>(dX), reinterpret_cast<const float4*>(h[i - 1]), (int)(n / 4));
     if (cudaGetLastError() != cudaSuccess) return false;
     dY = dX;
   }
@@ -511,11 +569,13 @@ sg_status enqueue_collect(sg_ppo* p) {
     float* o_next = p->obs + (size_t)(t + 1) * E * D;
     float* a_t = p->actions + (size_t)t * E * A;
     float* v_t = p->values + (size_t)t * E;
-    if (!net_forward(p, p->L.actor, o_t, E, p->ha, p->mu) ||
-        !net_forward(p, p->L.critic, o_t, E, p->hc, v_t))
+    sg::pad_rows_kernel<<<sg::grid_for((long long)E * p->Dp, 256), 256, 0, p->stream>>>(
+        o_t, E, D, p->Dp, p->xin);
+    if (!net_forward(p, p->L.actor, p->xin, E, p->ha, p->mu) ||
+        !net_forward(p, p->L.critic, p->xin, E, p->hc, v_t))
       return fail(p, SG_ERR_CUDA, "sg_ppo_collect: network forward failed");
     sg::sample_kernel<<<eb, tb, 0, p->stream>>>(p->mu, p->params + p->L.log_std, p->jmask,
-                                               p->d_step, t, c.seed, E, A, a_t,
+                                               p->d_step, t, c.seed, E, A, p->Ap, a_t,
                                                p->logp + (size_t)t * E);
     sg_status st = sg_step(p->env, a_t, c.dt, c.substeps, o_next, p->rewards + (size_t)t * E,
                            p->dones + (size_t)t * E);
@@ -526,8 +586,9 @@ sg_status enqueue_collect(sg_ppo* p) {
     if ((st = sg_reset(p->env, p->reset_mask)) != SG_OK) return st;
     if ((st = sg_observe(p->env, a_t, p->reset_mask, o_next)) != SG_OK) return st;
   }
-  if (!net_forward(p, p->L.critic, p->obs + (size_t)n * E * D, E, p->hc,
-                   p->values + (size_t)n * E))
+  sg::pad_rows_kernel<<<sg::grid_for((long long)E * p->Dp, 256), 256, 0, p->stream>>>(
+      p->obs + (size_t)n * E * D, E, D, p->Dp, p->xin);
+  if (!net_forward(p, p->L.critic, p->xin, E, p->hc, p->values + (size_t)n * E))
     return fail(p, SG_ERR_CUDA, "sg_ppo_collect: critic forward failed");
   sg::gae_kernel<<<eb, tb, 0, p->stream>>>(p->rewards, p->values, p->dones, n, E, c.gamma, c.lam,
                                           p->adv, p->ret);
@@ -573,7 +634,11 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
   if (!std::isfinite(c.value_coef) || !std::isfinite(c.entropy_coef)) return bad("coefficients must be finite");
   if (c.substeps < 1 || c.substeps > 64) return bad("substeps must be 1..64");
   p->M = (int)(p->B / c.minibatches);
-  p->L = sg::make_layout(p->D, p->A);
+  p->Dp = (p->D + 3) & ~3;
+  p->Ap = (p->A + 3) & ~3;
+  p->L = sg::make_layout(p->Dp, p->Ap);
+  const Layout Lpub = sg::make_layout(p->D, p->A);
+  p->public_params = Lpub.total;
   const int rows = p->M > p->E ? p->M : p->E;
   const int E = p->E, A = p->A, D = p->D, n = p->n;
   cudaError_t e = cudaSuccess;
@@ -602,14 +667,16 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
     step(dalloc(p, &p->ha[i], (size_t)rows * widths[i]));
     step(dalloc(p, &p->hc[i], (size_t)rows * widths[i]));
   }
-  step(dalloc(p, &p->mu, (size_t)rows * A));
+  step(dalloc(p, &p->mu, (size_t)rows * p->Ap));
+  step(dalloc(p, &p->xin, (size_t)E * p->Dp));
+  step(dalloc(p, &p->pub2int, p->public_params));
   step(dalloc(p, &p->vout, (size_t)rows));
   step(dalloc(p, &p->dbuf0, (size_t)rows * sg::kH1));
   step(dalloc(p, &p->dbuf1, (size_t)rows * sg::kH1));
-  step(dalloc(p, &p->dmu, (size_t)p->M * A));
+  step(dalloc(p, &p->dmu, (size_t)p->M * p->Ap));
   step(dalloc(p, &p->dv, (size_t)p->M));
   step(dalloc(p, &p->ones, (size_t)rows));
-  step(dalloc(p, &p->mb.obs, (size_t)p->M * D));
+  step(dalloc(p, &p->mb.obs, (size_t)p->M * p->Dp));
   step(dalloc(p, &p->mb.act, (size_t)p->M * A));
   step(dalloc(p, &p->mb.mask, (size_t)p->M * A));
   step(dalloc(p, &p->mb.logp, (size_t)p->M));
@@ -628,8 +695,24 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
     sg_ppo_destroy(p);
     return st;
   }
-  // host-built constants: joint mask, ones, zero targets
+  // host-built constants: joint mask, ones, zero targets, public -> internal parameter map
   std::vector<float> jm((size_t)E * A, 0.f), ones((size_t)rows, 1.f);
+  std::vector<int32_t> map(p->public_params);
+  {
+    const Net* pn[2] = {&Lpub.actor, &Lpub.critic};
+    const Net* in[2] = {&p->L.actor, &p->L.critic};
+    for (int k = 0; k < 2; ++k)
+      for (int i = 0; i < 4; ++i) {
+        const Layer &a = pn[k]->l[i], &b = in[k]->l[i];
+        for (int r = 0; r < a.out; ++r) {
+          for (int q = 0; q < a.in; ++q) map[a.w + (size_t)r * a.in + q] = (int32_t)(b.w + (size_t)r * b.in + q);
+          map[a.b + r] = (int32_t)(b.b + r);
+        }
+      }
+    for (int j = 0; j < A; ++j) map[Lpub.log_std + j] = (int32_t)(p->L.log_std + j);
+  }
+  step(cudaMemcpyAsync(p->pub2int, map.data(), map.size() * 4, cudaMemcpyHostToDevice,
+                       sg::context_stream(env)));
   const std::vector<int32_t>& dof = sg::context_env_dof(env);
   for (int k = 0; k < E; ++k)
     for (int j = 0; j < A && j < dof[k]; ++j) jm[(size_t)k * A + j] = 1.f;
@@ -638,6 +721,7 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
   step(cudaMemcpyAsync(p->ones, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice, s));
   step(cudaMemsetAsync(p->zero_targets, 0, (size_t)E * A * 4, s));
   step(cudaMemsetAsync(p->params, 0, P * 4, s));
+  step(cudaMemsetAsync(p->grad, 0, P * 4, s));
   step(cudaMemsetAsync(p->adam_m, 0, P * 4, s));
   step(cudaMemsetAsync(p->adam_v, 0, P * 4, s));
   step(cudaMemsetAsync(p->d_step, 0, sizeof(long long), s));
@@ -671,22 +755,27 @@ void sg_ppo_destroy(sg_ppo* p) {
   delete p;
 }
 
-int64_t sg_ppo_num_params(const sg_ppo* p) { return p ? (int64_t)p->L.total : 0; }
+int64_t sg_ppo_num_params(const sg_ppo* p) { return p ? (int64_t)p->public_params : 0; }
 
 sg_status sg_ppo_set_params(sg_ppo* p, const float* src) {
   if (!p || !src) return SG_ERR_INVALID_ARG;
   bind_stream(p, sg::context_stream(p->env));
-  return cuda_fail(p, cudaMemcpyAsync(p->params, src, p->L.total * 4, cudaMemcpyDeviceToDevice,
-                                      p->stream),
-                   "sg_ppo_set_params");
+  cudaError_t e = cudaMemsetAsync(p->params, 0, p->L.total * 4, p->stream);   // padding stays 0
+  const int n = (int)p->public_params;
+  if (e == cudaSuccess) {
+    sg::scatter_kernel<<<sg::grid_for(n, 256), 256, 0, p->stream>>>(src, p->pub2int, n, p->params);
+    e = cudaGetLastError();
+  }
+  return cuda_fail(p, e, "sg_ppo_set_params");
 }
 
 sg_status sg_ppo_get_params(sg_ppo* p, float* dst) {
   if (!p || !dst) return SG_ERR_INVALID_ARG;
   bind_stream(p, sg::context_stream(p->env));
-  return cuda_fail(p, cudaMemcpyAsync(dst, p->params, p->L.total * 4, cudaMemcpyDeviceToDevice,
-                                      p->stream),
-                   "sg_ppo_get_params");
+  const int n = (int)p->public_params;
+  sg::gather_params_kernel<<<sg::grid_for(n, 256), 256, 0, p->stream>>>(p->params, p->pub2int, n,
+                                                                         dst);
+  return cuda_fail(p, cudaGetLastError(), "sg_ppo_get_params");
 }
 
 sg_status sg_ppo_reset(sg_ppo* p, int64_t step0) {
@@ -751,12 +840,12 @@ sg_status sg_ppo_update(sg_ppo* p, const int32_t* perm, float* stats) {
       const int32_t* idx = perm + (size_t)ep * p->B + (size_t)k * M;
       float* st = stats ? stats + 4 * ((size_t)ep * c.minibatches + k) : nullptr;
       sg::gather_kernel<<<(int)(((long long)M * 32 + 255) / 256), 256, 0, p->stream>>>(
-          src, p->mb, idx, M, E, D, A);
+          src, p->mb, idx, M, E, D, p->Dp, A);
       if (!net_forward(p, p->L.actor, p->mb.obs, M, p->ha, p->mu) ||
           !net_forward(p, p->L.critic, p->mb.obs, M, p->hc, p->vout))
         return fail(p, SG_ERR_CUDA, "sg_ppo_update: forward failed");
       sg::HeadArgs h{p->mu, p->vout, p->params + p->L.log_std, p->mb, p->dmu, p->dv,
-                     p->head_part, M, A, c.clip, c.value_coef};
+                     p->head_part, M, A, p->Ap, c.clip, c.value_coef};
       sg::head_kernel<<<head_blocks, sg::kRedThreads, 0, p->stream>>>(h);
       sg::head_final_kernel<<<1, 64, 0, p->stream>>>(p->head_part, head_blocks, A, M,
                                                      p->params + p->L.log_std, c.entropy_coef,
@@ -794,7 +883,7 @@ bool buffer_of(sg_ppo* p, int which, void** ptr, size_t* bytes) {
     case SG_PPO_DONES: *ptr = p->dones; *bytes = nE; return true;
     case SG_PPO_ADVANTAGES: *ptr = p->adv; *bytes = nE * 4; return true;
     case SG_PPO_RETURNS: *ptr = p->ret; *bytes = nE * 4; return true;
-    case SG_PPO_GRAD: *ptr = p->grad; *bytes = p->L.total * 4; return true;
+    case SG_PPO_GRAD: *ptr = p->grad; *bytes = p->public_params * 4; return true;
     default: return false;
   }
 }
@@ -806,6 +895,12 @@ sg_status sg_ppo_get_buffer(sg_ppo* p, int32_t which, void* dst) {
   size_t bytes;
   if (!buffer_of(p, which, &ptr, &bytes)) return fail(p, SG_ERR_INVALID_ARG, "unknown buffer");
   bind_stream(p, sg::context_stream(p->env));
+  if (which == SG_PPO_GRAD) {
+    const int n = (int)p->public_params;
+    sg::gather_params_kernel<<<sg::grid_for(n, 256), 256, 0, p->stream>>>(
+        p->grad, p->pub2int, n, static_cast<float*>(dst));
+    return cuda_fail(p, cudaGetLastError(), "sg_ppo_get_buffer");
+  }
   return cuda_fail(p, cudaMemcpyAsync(dst, ptr, bytes, cudaMemcpyDeviceToDevice, p->stream),
                    "sg_ppo_get_buffer");
 }
@@ -814,7 +909,8 @@ sg_status sg_ppo_set_buffer(sg_ppo* p, int32_t which, const void* src) {
   if (!p || !src) return SG_ERR_INVALID_ARG;
   void* ptr;
   size_t bytes;
-  if (!buffer_of(p, which, &ptr, &bytes)) return fail(p, SG_ERR_INVALID_ARG, "unknown buffer");
+  if (!buffer_of(p, which, &ptr, &bytes) || which == SG_PPO_GRAD)
+    return fail(p, SG_ERR_INVALID_ARG, "unknown or read-only buffer");
   bind_stream(p, sg::context_stream(p->env));
   cudaError_t e = cudaMemcpyAsync(ptr, src, bytes, cudaMemcpyDeviceToDevice, p->stream);
   if (e == cudaSuccess && which == SG_PPO_ADVANTAGES) {
