@@ -234,14 +234,25 @@ enum { SG_ROLLOUT_PERSISTENT = 0, SG_ROLLOUT_STEP_GRAPH = 1 };
 sg_status sg_rollout(sg_ctx *ctx, const float *actions_dev, int32_t T, float dt,
                      int32_t substeps, float *obs_dev, float *reward_dev, uint8_t *done_dev);
 
-/* sg_rollout with HOST buffers (same shapes): copies actions to the device,
- * runs the rollout and copies obs, reward and done back, all enqueued on
- * the context's stream (the first call allocates device staging buffers with
- * cudaMalloc).  Page-locked host memory gives asynchronous copies; the
- * outputs are valid after sg_sync_status() or a stream synchronisation. */
+/* sg_rollout with HOST buffers (same shapes), enqueued on the context's
+ * stream; the outputs are valid after sg_sync_status() or a stream
+ * synchronisation.  Two ways to move the data, chosen by sg_set_host_io:
+ *   - direct (default when all four buffers are page-locked host memory the
+ *     device can address, e.g. cudaHostAlloc / cudaHostRegister): the
+ *     rollout kernel reads the actions from and writes obs, reward and done
+ *     to host memory itself (NVLink-C2C on Grace-Blackwell), so transfers
+ *     overlap the computation;
+ *   - staged (otherwise, or when forced): copies the actions to device
+ *     staging buffers (cudaMalloc on first use or growth), runs the rollout
+ *     and copies the outputs back. */
 sg_status sg_rollout_host(sg_ctx *ctx, const float *actions_host, int32_t T, float dt,
                           int32_t substeps, float *obs_host, float *reward_host,
                           uint8_t *done_host);
+
+/* How sg_rollout_host moves its data: SG_HOST_IO_AUTO (direct access where
+ * possible, the default) or SG_HOST_IO_STAGED (always staged copies). */
+enum { SG_HOST_IO_AUTO = 0, SG_HOST_IO_STAGED = 1 };
+sg_status sg_set_host_io(sg_ctx *ctx, int32_t mode);
 
 /* Launch plan: threads per block (32, 64, 128 or 256), the rollout mode
  * and the chain split: 1 = one thread integrates one chain (a warp holds 32

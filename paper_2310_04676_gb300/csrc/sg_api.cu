@@ -34,6 +34,7 @@ struct sg_ctx {
   int threads = 128;
   int rollout_mode = SG_ROLLOUT_PERSISTENT;
   int split = 1;
+  int host_io = SG_HOST_IO_AUTO;
   std::string last_error;
   // captured rollout (CUDA graph) and the arguments it was captured for
   cudaStream_t capture_stream = nullptr;
@@ -96,6 +97,23 @@ cudaError_t upload(T** dst, const T* src, size_t n, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   if (n && src) return cudaMemcpyAsync(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice, s);
   return cudaSuccess;
+}
+
+// Device address of page-locked host memory the current device can access,
+// or null (pageable or unknown memory: use staged copies).
+void* device_view(const void* host) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, host) != cudaSuccess) {
+    cudaGetLastError();   // clear the sticky-free error of an unknown pointer
+    return nullptr;
+  }
+  if (attr.type != cudaMemoryTypeHost || !attr.devicePointer) return nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  int mapped = 0;
+  if (cudaDeviceGetAttribute(&mapped, cudaDevAttrCanMapHostMemory, dev) != cudaSuccess || !mapped)
+    return nullptr;
+  return attr.devicePointer;
 }
 
 void free_ctx(sg_ctx* c) {
@@ -416,12 +434,29 @@ sg_status sg_rollout(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt,
   return run_rollout(ctx, actions_dev, T, dt, substeps, obs_dev, reward_dev, done_dev);
 }
 
+sg_status sg_set_host_io(sg_ctx* ctx, int32_t mode) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  if (mode != SG_HOST_IO_AUTO && mode != SG_HOST_IO_STAGED)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "sg_set_host_io: mode must be 0 (auto) or 1 (staged)");
+  ctx->host_io = mode;
+  return SG_OK;
+}
+
 sg_status sg_rollout_host(sg_ctx* ctx, const float* actions_host, int32_t T, float dt,
                           int32_t substeps, float* obs_host, float* reward_host,
                           uint8_t* done_host) {
   sg_status st =
       check_rollout_args(ctx, actions_host, T, dt, substeps, obs_host, reward_host, done_host);
   if (st != SG_OK) return st;
+  if (ctx->host_io == SG_HOST_IO_AUTO) {
+    // page-locked host memory the device can address: the kernel moves the data itself
+    void *a_d = device_view(actions_host), *o_d = device_view(obs_host);
+    void *r_d = device_view(reward_host), *d_d = device_view(done_host);
+    if (a_d && o_d && r_d && d_d)
+      return run_rollout(ctx, static_cast<const float*>(a_d), T, dt, substeps,
+                         static_cast<float*>(o_d), static_cast<float*>(r_d),
+                         static_cast<uint8_t*>(d_d));
+  }
   const size_t E = ctx->plan.num_envs, J = ctx->plan.max_joints, D = ctx->plan.obs_dim;
   cudaError_t e = cudaSuccess;
   if (T > ctx->stage_T) {

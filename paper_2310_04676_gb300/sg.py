@@ -18,6 +18,7 @@ SG_OK, SG_ERR_INVALID_ARG, SG_ERR_CUDA, SG_ERR_OOM, SG_ERR_NONFINITE, SG_ERR_TIM
 STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_CUDA", 3: "SG_ERR_OOM",
                 4: "SG_ERR_NONFINITE", 5: "SG_ERR_TIMEOUT", 6: "SG_ERR_UNSUPPORTED"}
 DONE_TERMINATED, DONE_TIMEOUT, DONE_NONFINITE = 1, 2, 4
+HOST_IO_AUTO, HOST_IO_STAGED = 0, 1
 ROLLOUT_PERSISTENT, ROLLOUT_STEP_GRAPH = 0, 1
 DRIVE_POSITION, DRIVE_VELOCITY, DRIVE_TORQUE = 0, 1, 2
 MAX_CHAINS = 4                     # chains per env (SG_MAX_CHAINS)
@@ -99,6 +100,7 @@ def load_library(path=LIB_PATH):
         "sg_get_state": (i32, [vp, vp, vp, vp]),
         "sg_set_state": (i32, [vp, vp, vp, vp]),
         "sg_sync_status": (i32, [vp]),
+        "sg_set_host_io": (i32, [vp, i32]),
         "sg_rollout": (i32, [vp, vp, i32, f32, i32, vp, vp, u8p]),
         "sg_rollout_host": (i32, [vp, vp, i32, f32, i32, vp, vp, u8p]),
         "sg_set_launch": (i32, [vp, i32, i32, i32]),
@@ -330,6 +332,10 @@ class Env:
         T = int(actions.shape[0])
         self._check(self.lib.sg_rollout_host(self.ctx, _ptr(actions), T, float(dt), int(substeps),
                                              _ptr(obs), _ptr(rew), _ptr(done)))
+
+    def set_host_io(self, mode):
+        """HOST_IO_AUTO (direct access to page-locked host buffers) or HOST_IO_STAGED."""
+        self._check(self.lib.sg_set_host_io(self.ctx, int(mode)))
 
     def set_launch(self, threads_per_block, mode, chain_split=1):
         self._check(self.lib.sg_set_launch(self.ctx, int(threads_per_block), int(mode),

@@ -90,10 +90,24 @@ def test_host_rollout_matches_device_rollout():
     out = (torch.empty(T, B.num_envs, B.obs_dim).pin_memory(),
            torch.empty(T, B.num_envs).pin_memory(),
            torch.empty(T, B.num_envs, dtype=torch.uint8).pin_memory())
-    B.rollout_host(a_h, DT, 2, out)
+    B.rollout_host(a_h, DT, 2, out)              # page-locked: direct host access
     assert B.sync_status() == sg.SG_OK
     assert torch.equal(out[0], obs.cpu()) and torch.equal(out[1], rew.cpu())
     assert torch.equal(out[2], done.cpu())
+    # staged copies (forced, and automatically for pageable memory) give the same bits
+    for mode, pin in ((sg.HOST_IO_STAGED, True), (sg.HOST_IO_AUTO, False)):
+        C = sg.Env(desc)
+        C.set_host_io(mode)
+        mk = (lambda t: t.pin_memory()) if pin else (lambda t: t)
+        a2 = mk(torch.from_numpy(acts_np.copy()))
+        o2 = (mk(torch.empty(T, C.num_envs, C.obs_dim)), mk(torch.empty(T, C.num_envs)),
+              mk(torch.empty(T, C.num_envs, dtype=torch.uint8)))
+        C.rollout_host(a2, DT, 2, o2)
+        assert C.sync_status() == sg.SG_OK
+        assert torch.equal(o2[0], out[0]) and torch.equal(o2[1], out[1])
+        assert torch.equal(o2[2], out[2])
+    with pytest.raises(sg.SgError):
+        B.set_host_io(5)
 
 
 def test_autotune_keeps_state_and_picks_a_plan():
