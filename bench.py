@@ -66,20 +66,23 @@ def env_step_flops(kinds, substeps, task=0):
     return tot
 
 
-def adjoint_flops(kinds, substeps, T, every):
-    """Algorithmic FLOPs of one differentiable rollout as the checkpointed
-    adjoint computes it: (forward kernel, backward kernel).  The backward
-    recomputes each segment from its checkpoint (all but its last step),
-    each step's substep start states, then runs S substep adjoints and one
-    tip product per step."""
+def adjoint_flops(kinds, substeps, T, every, replay=True):
+    """Algorithmic FLOPs of one differentiable rollout: (forward kernel,
+    backward kernel).  The warp-pair backward (replay buffers) recomputes
+    every substep once, inside its substep adjoint (FLOP_SUBSTEP_ADJ counts
+    the recomputed forward substep with its factorisation), plus one tip
+    product per step; the one-warp backward also recomputes each segment
+    from its checkpoint and each step's substep start states."""
     fwd = bwd = 0
     seg_steps = [min(every, T - t0) for t0 in range(0, T, every)]
     for k in kinds:
         for c in (["7R", "7R"] if k == "14B" else [k]):
             sub = FLOP_SUBSTEP[c]
             fwd += T * (substeps * sub + FLOP_TIP[c])
-            bwd += sum(L - 1 for L in seg_steps) * substeps * sub
-            bwd += T * ((substeps - 1) * sub + FLOP_TIP_VJP[c] + substeps * FLOP_SUBSTEP_ADJ[c])
+            bwd += T * (FLOP_TIP_VJP[c] + substeps * FLOP_SUBSTEP_ADJ[c])
+            if not replay:
+                bwd += sum(L - 1 for L in seg_steps) * substeps * sub
+                bwd += T * (substeps - 1) * sub
     return fwd, bwd
 
 
@@ -410,12 +413,13 @@ def measure_adjoint(cx, wl, desc, T, every=8):
     for _ in range(cx.args.warmup):
         fwd_bwd()
     res["timing"] = True
-    ms = cx.timed(fwd_bwd, cx.args.steps)
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_adj_r%d.csv" % cx.rank), cx.local)
+    ms = cx.timed(fwd_bwd, cx.args.steps, clk)
     res["timing"] = False
     ms_bwd = [a.elapsed_time(b) for a, b in kev]
     da, dm = (x.cpu().numpy() for x in res["grads"])
     return {"ms": ms, "ms_bwd": ms_bwd, "T": T, "E": desc["num_envs"], "da": da, "dm": dm,
-            "acts": acts_np, "tg": tg_np, "every": every}
+            "acts": acts_np, "tg": tg_np, "every": every, "clocks": clk.summary()}
 
 
 _FMA_RATE = {}
@@ -538,6 +542,7 @@ def run_adjoint_config(cx, with_error, name="C4", E=None, T=None, err_envs=16):
     out["flops_per_rollout"] = {"forward": f_fwd, "backward": f_bwd}
     out["ms_backward_kernel"] = ms_b
     out["rollout_tflops"] = (f_fwd + f_bwd) / (t / cx.args.steps) / 1e12
+    out["clocks"] = a["clocks"]
     if with_error:
         ea, em = grad_error(wl, a["acts"], a["tg"], a["da"], a["dm"], n_envs=err_envs)
         out["rel_err_actions"] = ea
@@ -712,6 +717,7 @@ def main():
             line["grad"] = g
             line["roofline"] = g["roofline"]
             line["gpu_launches"] = g["gpu_launches"]
+            line["clocks"] = g["clocks"]
             print(json.dumps(line))
     elif args.config == "C5" or args.envs:
         for E in (args.envs or [1024, 4096, 16384, 65536, 262144]):
@@ -728,6 +734,7 @@ def main():
                 line["grad"] = g
                 line["roofline"] = g["roofline"]
                 line["gpu_launches"] = g["gpu_launches"]
+                line["clocks"] = g["clocks"]
                 print(json.dumps(line))
     else:
         line, wl = run_rollout_config(cx, args.config)
