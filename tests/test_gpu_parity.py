@@ -96,6 +96,24 @@ def test_generic_chains_match_oracle(chains, split):
 
 
 @pytest.mark.parametrize("split", [1, 2])
+def test_largest_and_smallest_envs_match_oracle(split):
+    """The widest env the description allows (four 7-joint chains, 28 DOF,
+    108-wide observation rows) and envs of single-joint chains."""
+    seven_r = ([0] * 7, [2, 1, 2, 1, 2, 1, 2])
+    seven_p = ([0, 0, 1, 0, 0, 0, 0], [2, 1, 2, 1, 2, 1, 2])
+    mixed = ([0, 1, 0, 0, 0, 0, 0], [0, 2, 1, 2, 0, 1, 2])
+    desc = chain_desc([seven_r, seven_p, mixed, seven_r], E=37, seed=9, kp=50.0, kd=5.0,
+                      damping=0.1, base=[(0, 0.3, 0), (0, -0.3, 0), (-0.2, 0, 0), (0.2, 0, 0)])
+    rel, env, obs, *_ = one_step_accel(desc, 2, split=split)
+    assert env.max_joints == 28 and env.obs_dim == 3 * 28 + 6 * 4
+    assert rel.max() <= 1e-4, rel.max()
+    desc = chain_desc([([0], [2]), ([1], [2])], E=45, seed=3, kp=50.0, kd=5.0, damping=0.1,
+                      base=[(0, 0.2, 0), (0, -0.2, 0)])
+    rel, env, *_ = one_step_accel(desc, 2, split=split)
+    assert rel.max() <= 1e-4, rel.max()
+
+
+@pytest.mark.parametrize("split", [1, 2])
 def test_limit_springs_match_oracle(split):
     desc = W.make_desc(["7R"] * 150 + ["7P"] * 40, k_limit=1e3)
     rel, *_ = one_step_accel(desc, 8, split=split)
