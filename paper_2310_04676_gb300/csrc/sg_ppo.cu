@@ -100,18 +100,6 @@ __global__ void bias_act_kernel(float* __restrict__ Y, const float* __restrict__
 // dY <- dY * ELU'(z), with ELU' from the stored output y: 1 for y > 0, y + 1 otherwise
 __device__ __forceinline__ float delu(float y) { return y > 0.f ? 1.f : y + 1.f; }
 
-__global__ void elu_backward4_kernel(float4* __restrict__ dY, const float4* __restrict__ Y, int n4) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
-    const float4 y = Y[i];
-    float4 d = dY[i];
-    d.x *= delu(y.x);
-    d.y *= delu(y.y);
-    d.z *= delu(y.z);
-    d.w *= delu(y.w);
-    dY[i] = d;
-  }
-}
-
 // Zero-padded copy of rows [rows][w] -> [rows][wp]
 __global__ void pad_rows_kernel(const float* __restrict__ src, int rows, int w, int wp,
                                 float* __restrict__ dst) {
@@ -207,6 +195,81 @@ __device__ double block_sum(double v, double* sh) {
   return r;
 }
 
+// dZ = dY * ELU'(y) in place and per-block column sums of dZ (the bias
+// gradient of the layer that produced y).  Block b takes rows [b*chunk,
+// (b+1)*chunk); a thread owns 4 adjacent columns (float4) of every
+// `groups`-th row, four rows in flight per iteration.
+constexpr int kBGradBlocks = 608;
+__device__ __forceinline__ float4 delu4(float4 d, float4 y) {
+  return make_float4(d.x * delu(y.x), d.y * delu(y.y), d.z * delu(y.z), d.w * delu(y.w));
+}
+__global__ void __launch_bounds__(256)
+elu_backward_bgrad_kernel(float* __restrict__ dY, const float* __restrict__ Y, int rows, int w,
+                          float* __restrict__ part) {
+  const int w4 = w >> 2;
+  const int groups = blockDim.x / w4;               // rows processed side by side (w | 1024)
+  const int c4 = threadIdx.x % w4, g = threadIdx.x / w4;
+  const int chunk = (rows + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
+  float4* d4 = reinterpret_cast<float4*>(dY);
+  const float4* y4 = reinterpret_cast<const float4*>(Y);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto add = [&](float4 v) {
+    acc.x += v.x;
+    acc.y += v.y;
+    acc.z += v.z;
+    acc.w += v.w;
+  };
+  int r = r0 + g;
+  for (; r + 3 * groups < r1; r += 4 * groups) {
+    size_t k[4];
+    float4 d[4], y[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      k[u] = (size_t)(r + u * groups) * w4 + c4;
+      d[u] = d4[k[u]];
+      y[u] = y4[k[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4 z = delu4(d[u], y[u]);
+      d4[k[u]] = z;
+      add(z);
+    }
+  }
+  for (; r < r1; r += groups) {
+    const size_t k = (size_t)r * w4 + c4;
+    const float4 z = delu4(d4[k], y4[k]);
+    d4[k] = z;
+    add(z);
+  }
+  __shared__ float4 sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if (g == 0) {
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < groups; ++k) {
+      const float4 v = sh[k * w4 + c4];
+      t.x += v.x;
+      t.y += v.y;
+      t.z += v.z;
+      t.w += v.w;
+    }
+    reinterpret_cast<float4*>(part + (size_t)blockIdx.x * w)[c4] = t;
+  }
+}
+
+// Bias gradient from the partials: grad[c] = sum_b part[b][c] (block per column).
+__global__ void __launch_bounds__(128)
+bgrad_final_kernel(const float* __restrict__ part, int nblk, int w, float* __restrict__ grad) {
+  __shared__ double sh[32];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(size_t)b * w + c];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) grad[c] = (float)s;
+}
+
 // Stage 1: per-block sums of x and x^2 (fixed grid, fixed order).
 __global__ void __launch_bounds__(kRedThreads)
 moments_partial_kernel(const float* __restrict__ x, long long n, double* __restrict__ part) {
@@ -287,7 +350,6 @@ struct HeadArgs {
 // Losses of the minibatch and their gradients with respect to the actor's
 // mean, the critic's value and log_std (thread per row; per-block partials).
 __global__ void __launch_bounds__(kRedThreads) head_kernel(HeadArgs h) {
-  __shared__ double sh[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool ok = i < h.M;
   const int A = h.A;
@@ -326,34 +388,49 @@ __global__ void __launch_bounds__(kRedThreads) head_kernel(HeadArgs h) {
       h.d_mu[(size_t)i * h.Ap + j] = m != 0.f ? g * zz[j] * expf(-h.log_std[j]) : 0.f;
     }
   }
+  // per-block sums of (surrogate, value loss, dlogstd_j, count_j): warp
+  // shuffles per column, then the warps' partials in a fixed order
   const int stride = 2 + 2 * A;
-  double s = block_sum(ok ? (double)surr : 0.0, sh);
-  if (threadIdx.x == 0) h.part[(size_t)blockIdx.x * stride + 0] = (float)s;
-  s = block_sum(ok ? (double)vl : 0.0, sh);
-  if (threadIdx.x == 0) h.part[(size_t)blockIdx.x * stride + 1] = (float)s;
-  for (int j = 0; j < A; ++j) {
-    const float m = ok ? h.mb.mask[(size_t)i * A + j] : 0.f;
-    const double gls = (ok && m != 0.f) ? (double)(g_logp * inv_m) * (zz[j] * zz[j] - 1.0) : 0.0;
-    s = block_sum(gls, sh);
-    if (threadIdx.x == 0) h.part[(size_t)blockIdx.x * stride + 2 + j] = (float)s;
-    s = block_sum(m, sh);
-    if (threadIdx.x == 0) h.part[(size_t)blockIdx.x * stride + 2 + A + j] = (float)s;
+  __shared__ float wpart[kRedThreads / 32][2 + 2 * kMaxDof];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int col = 0; col < stride; ++col) {
+    float x;
+    if (col == 0) x = ok ? surr : 0.f;
+    else if (col == 1) x = ok ? vl : 0.f;
+    else {
+      const int j = col < 2 + A ? col - 2 : col - 2 - A;
+      const float m = ok ? h.mb.mask[(size_t)i * A + j] : 0.f;
+      x = col < 2 + A ? ((ok && m != 0.f) ? g_logp * inv_m * (zz[j] * zz[j] - 1.f) : 0.f) : m;
+    }
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    if (lane == 0) wpart[w][col] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < stride) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += wpart[k][threadIdx.x];
+    h.part[(size_t)blockIdx.x * stride + threadIdx.x] = (float)t;
   }
 }
 
 // Final reduction of the head partials: log_std gradient (surrogate +
-// entropy terms) and the minibatch's loss statistics.
-__global__ void head_final_kernel(const float* __restrict__ part, int nblk, int A, int M,
-                                  const float* __restrict__ log_std, float entropy_coef,
-                                  float* __restrict__ grad_log_std, float* __restrict__ stats) {
-  const int j = threadIdx.x;          // one thread per column of the partials
+// entropy terms) and the minibatch's loss statistics (one block; each warp
+// sums whole columns with its lanes, fixed order).
+__global__ void __launch_bounds__(kRedThreads)
+head_final_kernel(const float* __restrict__ part, int nblk, int A, int M,
+                  const float* __restrict__ log_std, float entropy_coef,
+                  float* __restrict__ grad_log_std, float* __restrict__ stats) {
   const int stride = 2 + 2 * A;
-  if (j >= stride) return;
-  double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[(size_t)b * stride + j];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __shared__ double col[2 + 2 * kMaxDof];
-  col[j] = s;
+  for (int c = w; c < stride; c += nw) {
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * stride + c];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) col[c] = s;
+  }
   __syncthreads();
+  const int j = threadIdx.x;
   if (j < A) {
     const double cnt = col[2 + A + j] / (double)M;          // mean over rows of the mask
     grad_log_std[j] = (float)(col[2 + j] - (double)entropy_coef * cnt);
@@ -452,6 +529,7 @@ struct sg_ppo {
   float *dmu = nullptr, *dv = nullptr;  // loss gradients w.r.t. the actor mean and the value
   sg::MiniBatch mb{};
   float* head_part = nullptr;
+  float* bgrad_part = nullptr;         // [kBGradBlocks][256] bias-gradient partial sums
   double* red_part = nullptr;
   float* norm = nullptr;               // advantage mean, 1 / std
   float* clip_coef = nullptr;
@@ -493,12 +571,14 @@ bool gemm_bwd_data(sg_ppo* p, const float* dY, int rows, const Layer& l, float* 
   return blas_ok(cublasSgemm(p->blas, CUBLAS_OP_N, CUBLAS_OP_N, l.in, rows, l.out, &one,
                              p->params + l.w, l.in, dY, l.out, &zero, dX, l.in));
 }
-// dW[out][in] = dY^T X ; db[out] = dY^T 1
-bool gemm_bwd_weight(sg_ppo* p, const float* dY, const float* X, int rows, const Layer& l) {
+// dW[out][in] = dY^T X ; with_bias: db[out] = dY^T 1
+bool gemm_bwd_weight(sg_ppo* p, const float* dY, const float* X, int rows, const Layer& l,
+                     bool with_bias) {
   const float one = 1.f, zero = 0.f;
   if (!blas_ok(cublasSgemm(p->blas, CUBLAS_OP_N, CUBLAS_OP_T, l.in, l.out, rows, &one, X, l.in,
                            dY, l.out, &zero, p->grad + l.w, l.in)))
     return false;
+  if (!with_bias) return true;
   return blas_ok(cublasSgemv(p->blas, CUBLAS_OP_N, l.out, rows, &one, dY, l.out, p->ones, 1, &zero,
                              p->grad + l.b, 1));
 }
@@ -530,19 +610,22 @@ bool net_forward(sg_ppo* p, const Net& net, const float* X, int rows, float* con
 }
 
 // Backward of one network from dOut [rows][out]; weight gradients into p->grad.
+// Below the output layer the ELU backward also sums the bias gradient.
 bool net_backward(sg_ppo* p, const Net& net, const float* X, int rows, float* const (&h)[3],
                   const float* dOut) {
   const float* dY = dOut;
   float* bufs[2] = {p->dbuf0, p->dbuf1};
   for (int i = 3; i >= 0; --i) {
     const float* in = i > 0 ? h[i - 1] : X;
-    if (!gemm_bwd_weight(p, dY, in, rows, net.l[i])) return false;
+    if (!gemm_bwd_weight(p, dY, in, rows, net.l[i], i == 3)) return false;
     if (i == 0) break;
     float* dX = bufs[i & 1];
     if (!gemm_bwd_data(p, dY, rows, net.l[i], dX)) return false;
-    const long long n = (long long)rows * net.l[i].in;      // hidden widths: multiples of 4
-    sg::elu_backward4_kernel<<<sg::grid_for(n / 4, 256), 256, 0, p->stream>>>(
-        reinterpret_cast<float4*>(dX), reinterpret_cast<const float4*>(h[i - 1]), (int)(n / 4));
+    const int w = net.l[i].in;                    // hidden widths 64, 128, 256 divide 256
+    sg::elu_backward_bgrad_kernel<<<sg::kBGradBlocks, 256, 0, p->stream>>>(dX, h[i - 1], rows, w,
+                                                                           p->bgrad_part);
+    sg::bgrad_final_kernel<<<w, 128, 0, p->stream>>>(p->bgrad_part, sg::kBGradBlocks, w,
+                                                    p->grad + net.l[i - 1].b);
     if (cudaGetLastError() != cudaSuccess) return false;
     dY = dX;
   }
@@ -686,6 +769,7 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
   const int head_blocks = (p->M + sg::kRedThreads - 1) / sg::kRedThreads;
   step(dalloc(p, &p->head_part, (size_t)head_blocks * (2 + 2 * A)));
   step(dalloc(p, &p->red_part, (size_t)2 * sg::kRedBlocks));
+  step(dalloc(p, &p->bgrad_part, (size_t)sg::kBGradBlocks * sg::kH1));
   step(dalloc(p, &p->norm, 2));
   step(dalloc(p, &p->clip_coef, 1));
   const size_t ws_bytes = (size_t)32 << 20;
@@ -847,7 +931,7 @@ sg_status sg_ppo_update(sg_ppo* p, const int32_t* perm, float* stats) {
       sg::HeadArgs h{p->mu, p->vout, p->params + p->L.log_std, p->mb, p->dmu, p->dv,
                      p->head_part, M, A, p->Ap, c.clip, c.value_coef};
       sg::head_kernel<<<head_blocks, sg::kRedThreads, 0, p->stream>>>(h);
-      sg::head_final_kernel<<<1, 64, 0, p->stream>>>(p->head_part, head_blocks, A, M,
+      sg::head_final_kernel<<<1, sg::kRedThreads, 0, p->stream>>>(p->head_part, head_blocks, A, M,
                                                      p->params + p->L.log_std, c.entropy_coef,
                                                      p->grad + p->L.log_std, st);
       if (!net_backward(p, p->L.actor, p->mb.obs, M, p->ha, p->dmu) ||
