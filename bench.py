@@ -15,11 +15,15 @@ launching stream, W warm-up steps, K timed steps, L2 flushed (a 256 MiB
 write, outside the events) before every timed step, max over ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--config C1|C2|C3|C4|C5] [--envs E ...]
+                  [--config C1|C2|C3|C4|C5|P1] [--envs E ...] [--launch T,M,S]
 
 --config selects one of the other workloads (C1: 64 envs, latency; C2: 8192
-envs path following; C4: adjoint of a 64-step rollout of 2048 envs; C5: the
-limit-spring 7-DOF sweep over --envs sizes); each prints one line.
+envs path following, with the rebuild time of the path tables; C4: adjoint
+of a 64-step rollout of 2048 envs; C5: the limit-spring 7-DOF sweep over
+--envs sizes plus the 4096-env, 128-step adjoint; P1: the PPO loop with
+learning, 16384 envs); each prints one line per workload.  --launch fixes
+the launch plan (threads per block, rollout mode, chain split) instead of
+running the autotuner, to profile one plan.
 """
 import argparse
 import hashlib
@@ -39,8 +43,8 @@ METRIC = "env-steps/s at 16k mixed-DOF envs, batched vs plain; % FP32 roofline; 
 ROLLOUT_T = {"C1": 50, "C2": 50, "C3": 32, "C5": 50}
 
 # Algorithmic FP32 operations of the step's formulation (an FMA counts 2),
-# counted by a counting-scalar run of the chain code: per substep of one
-# chain, and per step for the tool-tip kinematics of one chain.
+# counted by running the chain code on a counting scalar type: per substep
+# of one chain, and per step for the tool-tip kinematics of one chain.
 # Operations the compiler folds (a literal 0 operand, a factor of +-1, two
 # literals) are not counted; ncu's executed FFMA x 2 + FADD + FMUL of the
 # default workload agrees with this count to 2%.
