@@ -43,8 +43,10 @@ METRIC = "env-steps/s at 16k mixed-DOF envs, batched vs plain; % FP32 roofline; 
 ROLLOUT_T = {"C1": 50, "C2": 50, "C3": 32, "C5": 50}
 
 # Algorithmic FP32 operations of the step's formulation (an FMA counts 2),
-# counted by running the chain code on a counting scalar type: per substep
-# of one chain, and per step for the tool-tip kinematics of one chain.
+# counted by running the chain code on a counting scalar type
+# (paper_2310_04676_gb300/flops; tests/test_flop_counts.py keeps these
+# constants equal to its output): per substep of one chain, and per step for
+# the tool-tip kinematics of one chain.
 # Operations the compiler folds (a literal 0 operand, a factor of +-1, two
 # literals) are not counted; ncu's executed FFMA x 2 + FADD + FMUL of the
 # default workload agrees with this count to 2%.
