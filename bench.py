@@ -362,10 +362,11 @@ def measure_rollout(cx, wl, desc, T, with_e2e=True):
         for _ in range(args.warmup):
             env_h.rollout_host(a_h, dt, S, o_h)
         res["ms_e2e"] = cx.timed(lambda: env_h.rollout_host(a_h, dt, S, o_h), args.steps)
-        env_h.set_host_io(sg.HOST_IO_STAGED)
-        for _ in range(args.warmup):
-            env_h.rollout_host(a_h, dt, S, o_h)
-        res["ms_e2e_staged"] = cx.timed(lambda: env_h.rollout_host(a_h, dt, S, o_h), args.steps)
+        for mode, key in ((sg.HOST_IO_STAGED, "ms_e2e_staged"), (sg.HOST_IO_DIRECT, "ms_e2e_direct")):
+            env_h.set_host_io(mode)
+            for _ in range(args.warmup):
+                env_h.rollout_host(a_h, dt, S, o_h)
+            res[key] = cx.timed(lambda: env_h.rollout_host(a_h, dt, S, o_h), args.steps)
         res["h2d"] = T * E * env_h.max_joints * 4
         res["d2h"] = T * E * (env_h.obs_dim * 4 + 4 + 1)
     return res
@@ -509,11 +510,15 @@ def run_rollout_config(cx, name, E=None):
     if "ms_e2e" in r:
         te = sum(r["ms_e2e"]) / 1e3
         ts = sum(r["ms_e2e_staged"]) / 1e3
+        td = sum(r["ms_e2e_direct"]) / 1e3
         line["e2e"] = {"value": aggregate_rate(units, te, world, cx.dev), "unit": "env-steps/s",
                        "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
-                       "path": "sg_rollout_host on pinned host buffers: the rollout kernel reads "
-                               "actions from and writes obs/reward/done to host memory directly "
-                               "(NVLink-C2C)",
+                       "path": "sg_rollout_host on pinned host buffers, pipelined: the 32 steps "
+                               "run as 8 chunks whose copy-in, rollout kernel and copy-out "
+                               "overlap on separate streams",
+                       "direct": {"value": aggregate_rate(units, td, world, cx.dev),
+                                  "path": "the rollout kernel reads and writes the pinned "
+                                          "host buffers itself (NVLink-C2C)"},
                        "staged": {"value": aggregate_rate(units, ts, world, cx.dev),
                                   "path": "copy in, device rollout, copy out"}}
     line["gpu_launches"] = args.steps

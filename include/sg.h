@@ -236,22 +236,24 @@ sg_status sg_rollout(sg_ctx *ctx, const float *actions_dev, int32_t T, float dt,
 
 /* sg_rollout with HOST buffers (same shapes), enqueued on the context's
  * stream; the outputs are valid after sg_sync_status() or a stream
- * synchronisation.  Two ways to move the data, chosen by sg_set_host_io:
- *   - direct (default when all four buffers are page-locked host memory the
- *     device can address, e.g. cudaHostAlloc / cudaHostRegister): the
- *     rollout kernel reads the actions from and writes obs, reward and done
- *     to host memory itself (NVLink-C2C on Grace-Blackwell), so transfers
- *     overlap the computation;
- *   - staged (otherwise, or when forced): copies the actions to device
- *     staging buffers (cudaMalloc on first use or growth), runs the rollout
- *     and copies the outputs back. */
+ * synchronisation.  The actions are copied to device staging buffers
+ * (cudaMalloc on first use or growth) and the outputs back; how, by
+ * sg_set_host_io:
+ *   SG_HOST_IO_AUTO (default): pipelined -- the T steps run as up to 8
+ *     chunks; copy-in of the next chunk, the rollout kernel of this one and
+ *     copy-out of the previous one proceed together on two internal copy
+ *     streams (page-locked host memory makes the copies asynchronous);
+ *   SG_HOST_IO_STAGED: copy in, rollout, copy out, one after another;
+ *   SG_HOST_IO_DIRECT: when all four buffers are page-locked host memory the
+ *     device can address (cudaHostAlloc / cudaHostRegister), the rollout
+ *     kernel reads the actions from and writes the outputs to host memory
+ *     itself (NVLink-C2C on Grace-Blackwell); otherwise as STAGED.
+ * All three compute the same bits as sg_rollout. */
 sg_status sg_rollout_host(sg_ctx *ctx, const float *actions_host, int32_t T, float dt,
                           int32_t substeps, float *obs_host, float *reward_host,
                           uint8_t *done_host);
 
-/* How sg_rollout_host moves its data: SG_HOST_IO_AUTO (direct access where
- * possible, the default) or SG_HOST_IO_STAGED (always staged copies). */
-enum { SG_HOST_IO_AUTO = 0, SG_HOST_IO_STAGED = 1 };
+enum { SG_HOST_IO_AUTO = 0, SG_HOST_IO_STAGED = 1, SG_HOST_IO_DIRECT = 2 };
 sg_status sg_set_host_io(sg_ctx *ctx, int32_t mode);
 
 /* Launch plan: threads per block (32, 64, 128 or 256), the rollout mode

@@ -35,6 +35,9 @@ struct sg_ctx {
   int rollout_mode = SG_ROLLOUT_PERSISTENT;
   int split = 1;
   int host_io = SG_HOST_IO_AUTO;
+  // pipelined host rollout: copy streams and events
+  cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
+  cudaEvent_t host_ev[2 + 2 * 8] = {};
   std::string last_error;
   // captured rollout (CUDA graph) and the arguments it was captured for
   cudaStream_t capture_stream = nullptr;
@@ -80,6 +83,9 @@ namespace {
 
 thread_local std::string g_create_error;
 
+constexpr int kHostChunks = 8;                    // pipelined host rollout: chunks of steps
+constexpr int kHostEvents = 2 + 2 * kHostChunks;
+
 sg_status set_err(sg_ctx* ctx, sg_status code, const std::string& msg) {
   if (ctx) ctx->last_error = msg;
   return code;
@@ -118,6 +124,10 @@ void* device_view(const void* host) {
 
 void free_ctx(sg_ctx* c) {
   if (!c) return;
+  for (cudaEvent_t ev : c->host_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (c->h2d_stream) cudaStreamDestroy(c->h2d_stream);
+  if (c->d2h_stream) cudaStreamDestroy(c->d2h_stream);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   void* ptrs[] = {c->d_params, c->d_q, c->d_qd, c->d_q0, c->d_path, c->d_slot_env, c->d_track,
@@ -191,6 +201,63 @@ bool valid_threads(int t) { return t == 32 || t == 64 || t == 128 || t == 256; }
 cudaError_t launch_plan(const sg_ctx* c, const sg::StepArgs& a, cudaStream_t s) {
   return c->split == 2 ? sg::launch_step_pair(a, c->threads, s)
                        : sg::launch_step(a, c->threads, s);
+}
+
+// Host rollout as a pipeline of chunks of steps: copy-in of chunk c + 1 (h2d
+// stream), the persistent kernel of chunk c (context stream) and copy-out of
+// chunk c - 1 (d2h stream) overlap; events order each chunk's three stages,
+// and the context stream waits for the last copy-out.  The chunked launches
+// compute the same bits as one launch (state is stored and reloaded exactly
+// between launches).
+sg_status pipelined_host_rollout(sg_ctx* c, const float* act_h, int T, float dt, int substeps,
+                                 float* obs_h, float* rew_h, uint8_t* done_h) {
+  const size_t E = c->plan.num_envs, J = c->plan.max_joints, D = c->plan.obs_dim;
+  const int nch = T < kHostChunks ? T : kHostChunks;
+  const int len = (T + nch - 1) / nch;
+  cudaError_t e = cudaSuccess;
+  if (!c->h2d_stream) e = cudaStreamCreateWithFlags(&c->h2d_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !c->d2h_stream)
+    e = cudaStreamCreateWithFlags(&c->d2h_stream, cudaStreamNonBlocking);
+  for (int k = 0; k < kHostEvents && e == cudaSuccess; ++k)
+    if (!c->host_ev[k]) e = cudaEventCreateWithFlags(&c->host_ev[k], cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_err(c, e, "sg_rollout_host: streams");
+  // both copy streams start after the work already queued on the context stream
+  cudaEvent_t start = c->host_ev[0], fin = c->host_ev[1];
+  e = cudaEventRecord(start, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->h2d_stream, start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->d2h_stream, start, 0);
+  for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+    const int t0 = k * len, t1 = t0 + len < T ? t0 + len : T;
+    if (t0 >= t1) break;
+    const size_t n = (size_t)(t1 - t0);
+    cudaEvent_t in = c->host_ev[2 + 2 * k], done_k = c->host_ev[3 + 2 * k];
+    e = cudaMemcpyAsync(c->d_stage_act + (size_t)t0 * E * J, act_h + (size_t)t0 * E * J,
+                        sizeof(float) * n * E * J, cudaMemcpyHostToDevice, c->h2d_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(in, c->h2d_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, in, 0);
+    if (e == cudaSuccess) {
+      sg::StepArgs a = step_args(c, dt, substeps, (int)n);
+      a.actions = c->d_stage_act + (size_t)t0 * E * J;
+      a.obs = c->d_stage_obs + (size_t)t0 * E * D;
+      a.reward = c->d_stage_rew + (size_t)t0 * E;
+      a.done = c->d_stage_done + (size_t)t0 * E;
+      e = launch_plan(c, a, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(done_k, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->d2h_stream, done_k, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(obs_h + (size_t)t0 * E * D, c->d_stage_obs + (size_t)t0 * E * D,
+                          sizeof(float) * n * E * D, cudaMemcpyDeviceToHost, c->d2h_stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rew_h + (size_t)t0 * E, c->d_stage_rew + (size_t)t0 * E,
+                          sizeof(float) * n * E, cudaMemcpyDeviceToHost, c->d2h_stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(done_h + (size_t)t0 * E, c->d_stage_done + (size_t)t0 * E, n * E,
+                          cudaMemcpyDeviceToHost, c->d2h_stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(fin, c->d2h_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, fin, 0);
+  return cuda_err(c, e, "sg_rollout_host");
 }
 
 // Enqueue (capturing first if needed) the rollout graph on the context's stream.
@@ -436,8 +503,9 @@ sg_status sg_rollout(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt,
 
 sg_status sg_set_host_io(sg_ctx* ctx, int32_t mode) {
   if (!ctx) return SG_ERR_INVALID_ARG;
-  if (mode != SG_HOST_IO_AUTO && mode != SG_HOST_IO_STAGED)
-    return set_err(ctx, SG_ERR_INVALID_ARG, "sg_set_host_io: mode must be 0 (auto) or 1 (staged)");
+  if (mode != SG_HOST_IO_AUTO && mode != SG_HOST_IO_STAGED && mode != SG_HOST_IO_DIRECT)
+    return set_err(ctx, SG_ERR_INVALID_ARG,
+                   "sg_set_host_io: mode must be 0 (pipelined), 1 (staged) or 2 (direct)");
   ctx->host_io = mode;
   return SG_OK;
 }
@@ -448,7 +516,7 @@ sg_status sg_rollout_host(sg_ctx* ctx, const float* actions_host, int32_t T, flo
   sg_status st =
       check_rollout_args(ctx, actions_host, T, dt, substeps, obs_host, reward_host, done_host);
   if (st != SG_OK) return st;
-  if (ctx->host_io == SG_HOST_IO_AUTO) {
+  if (ctx->host_io == SG_HOST_IO_DIRECT) {
     // page-locked host memory the device can address: the kernel moves the data itself
     void *a_d = device_view(actions_host), *o_d = device_view(obs_host);
     void *r_d = device_view(reward_host), *d_d = device_view(done_host);
@@ -474,21 +542,26 @@ sg_status sg_rollout_host(sg_ctx* ctx, const float* actions_host, int32_t T, flo
     if (e != cudaSuccess) return cuda_err(ctx, e, "sg_rollout_host: staging");
     ctx->stage_T = T;
   }
-  e = cudaMemcpyAsync(ctx->d_stage_act, actions_host, sizeof(float) * T * E * J,
-                      cudaMemcpyHostToDevice, ctx->stream);
-  if (e != cudaSuccess) return cuda_err(ctx, e, "sg_rollout_host: copy in");
-  st = run_rollout(ctx, ctx->d_stage_act, T, dt, substeps, ctx->d_stage_obs, ctx->d_stage_rew,
-                   ctx->d_stage_done);
-  if (st != SG_OK) return st;
-  e = cudaMemcpyAsync(obs_host, ctx->d_stage_obs, sizeof(float) * T * E * D,
-                      cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(reward_host, ctx->d_stage_rew, sizeof(float) * T * E,
+  if (ctx->host_io == SG_HOST_IO_STAGED || ctx->host_io == SG_HOST_IO_DIRECT) {
+    // serial: copy in, rollout, copy out, all on the context's stream
+    e = cudaMemcpyAsync(ctx->d_stage_act, actions_host, sizeof(float) * T * E * J,
+                        cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "sg_rollout_host: copy in");
+    st = run_rollout(ctx, ctx->d_stage_act, T, dt, substeps, ctx->d_stage_obs, ctx->d_stage_rew,
+                     ctx->d_stage_done);
+    if (st != SG_OK) return st;
+    e = cudaMemcpyAsync(obs_host, ctx->d_stage_obs, sizeof(float) * T * E * D,
                         cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(done_host, ctx->d_stage_done, (size_t)T * E, cudaMemcpyDeviceToHost,
-                        ctx->stream);
-  return cuda_err(ctx, e, "sg_rollout_host: copy out");
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(reward_host, ctx->d_stage_rew, sizeof(float) * T * E,
+                          cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(done_host, ctx->d_stage_done, (size_t)T * E, cudaMemcpyDeviceToHost,
+                          ctx->stream);
+    return cuda_err(ctx, e, "sg_rollout_host: copy out");
+  }
+  return pipelined_host_rollout(ctx, actions_host, T, dt, substeps, obs_host, reward_host,
+                                done_host);
 }
 
 sg_status sg_set_launch(sg_ctx* ctx, int32_t threads_per_block, int32_t rollout_mode,

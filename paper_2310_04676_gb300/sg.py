@@ -18,7 +18,7 @@ SG_OK, SG_ERR_INVALID_ARG, SG_ERR_CUDA, SG_ERR_OOM, SG_ERR_NONFINITE, SG_ERR_TIM
 STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_CUDA", 3: "SG_ERR_OOM",
                 4: "SG_ERR_NONFINITE", 5: "SG_ERR_TIMEOUT", 6: "SG_ERR_UNSUPPORTED"}
 DONE_TERMINATED, DONE_TIMEOUT, DONE_NONFINITE = 1, 2, 4
-HOST_IO_AUTO, HOST_IO_STAGED = 0, 1
+HOST_IO_AUTO, HOST_IO_STAGED, HOST_IO_DIRECT = 0, 1, 2
 ROLLOUT_PERSISTENT, ROLLOUT_STEP_GRAPH = 0, 1
 DRIVE_POSITION, DRIVE_VELOCITY, DRIVE_TORQUE = 0, 1, 2
 MAX_CHAINS = 4                     # chains per env (SG_MAX_CHAINS)
@@ -334,7 +334,8 @@ class Env:
                                              _ptr(obs), _ptr(rew), _ptr(done)))
 
     def set_host_io(self, mode):
-        """HOST_IO_AUTO (direct access to page-locked host buffers) or HOST_IO_STAGED."""
+        """HOST_IO_AUTO (pipelined copies), HOST_IO_STAGED (serial copies) or
+        HOST_IO_DIRECT (the kernel accesses page-locked host buffers)."""
         self._check(self.lib.sg_set_host_io(self.ctx, int(mode)))
 
     def set_launch(self, threads_per_block, mode, chain_split=1):

@@ -90,12 +90,13 @@ def test_host_rollout_matches_device_rollout():
     out = (torch.empty(T, B.num_envs, B.obs_dim).pin_memory(),
            torch.empty(T, B.num_envs).pin_memory(),
            torch.empty(T, B.num_envs, dtype=torch.uint8).pin_memory())
-    B.rollout_host(a_h, DT, 2, out)              # page-locked: direct host access
+    B.rollout_host(a_h, DT, 2, out)              # default: pipelined chunks
     assert B.sync_status() == sg.SG_OK
     assert torch.equal(out[0], obs.cpu()) and torch.equal(out[1], rew.cpu())
     assert torch.equal(out[2], done.cpu())
-    # staged copies (forced, and automatically for pageable memory) give the same bits
-    for mode, pin in ((sg.HOST_IO_STAGED, True), (sg.HOST_IO_AUTO, False)):
+    # serial copies, direct host access and pageable memory give the same bits
+    for mode, pin in ((sg.HOST_IO_STAGED, True), (sg.HOST_IO_DIRECT, True),
+                      (sg.HOST_IO_AUTO, False), (sg.HOST_IO_DIRECT, False)):
         C = sg.Env(desc)
         C.set_host_io(mode)
         mk = (lambda t: t.pin_memory()) if pin else (lambda t: t)
