@@ -369,6 +369,7 @@ def measure_rollout(cx, wl, desc, T, with_e2e=True):
             res[key] = cx.timed(lambda: env_h.rollout_host(a_h, dt, S, o_h), args.steps)
         res["h2d"] = T * E * env_h.max_joints * 4
         res["d2h"] = T * E * (env_h.obs_dim * 4 + 4 + 1)
+        res["link"] = host_link_floor(cx, res["h2d"], res["d2h"])
     return res
 
 
@@ -387,6 +388,48 @@ def measure_path_build(cx, desc, repeats=20):
     return {"us_per_rebuild": us, "envs": E, "ctrl_points": K, "waypoints": W_,
             "algorithmic_bytes": nbytes, "achieved_gbs": nbytes / (us * 1e-6) / 1e9,
             "form": "sg_set_paths, all envs, one launch", "gpu_launches": 1}
+
+
+def host_link_floor(cx, h2d_bytes, d2h_bytes, repeats=10):
+    """The host link's floor for one end-to-end step: plain pinned-memory
+    copies of the same byte counts, both directions in flight on two
+    streams (CUDA events, best of `repeats`)."""
+    torch = cx.torch
+    hi = torch.empty(h2d_bytes // 4).pin_memory()
+    di = torch.empty(h2d_bytes // 4, device=cx.dev)
+    ho = torch.empty(d2h_bytes // 4).pin_memory()
+    do = torch.empty(d2h_bytes // 4, device=cx.dev)
+    s1, s2 = torch.cuda.Stream(cx.dev), torch.cuda.Stream(cx.dev)
+
+    def copies(which):
+        cur = torch.cuda.current_stream(cx.dev)
+        s1.wait_stream(cur)
+        s2.wait_stream(cur)
+        if which in ("in", "both"):
+            with torch.cuda.stream(s1):
+                di.copy_(hi, non_blocking=True)
+        if which in ("out", "both"):
+            with torch.cuda.stream(s2):
+                ho.copy_(do, non_blocking=True)
+        cur.wait_stream(s1)
+        cur.wait_stream(s2)
+
+    out = {}
+    for which in ("in", "out", "both"):
+        best = None
+        for _ in range(repeats + 2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            copies(which)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        out[which] = best
+    return {"h2d_gbs": h2d_bytes / (out["in"] * 1e-3) / 1e9,
+            "d2h_gbs": d2h_bytes / (out["out"] * 1e-3) / 1e9,
+            "floor_ms_per_step": out["both"],
+            "how": "pinned-memory copies of the step's bytes, both directions on two streams"}
 
 
 def measure_adjoint(cx, wl, desc, T, every=8):
@@ -519,6 +562,8 @@ def run_rollout_config(cx, name, E=None):
                        "direct": {"value": aggregate_rate(units, td, world, cx.dev),
                                   "path": "the rollout kernel reads and writes the pinned "
                                           "host buffers itself (NVLink-C2C)"},
+                       "link": dict(r["link"], frac=r["link"]["floor_ms_per_step"] /
+                                    (1e3 * te / args.steps)),
                        "staged": {"value": aggregate_rate(units, ts, world, cx.dev),
                                   "path": "copy in, device rollout, copy out"}}
     line["gpu_launches"] = args.steps
