@@ -108,6 +108,45 @@ __device__ __forceinline__ void get_ckpt(const Pat& pat, const DiffArgs& a, int 
   }
 }
 
+// dL/d(actions) of step t (the env's padding joints as 0, written by chain 0)
+template <class Pat>
+__device__ __forceinline__ void write_action_grads(const Pat& pat, const DiffArgs& a,
+                                                   const SlotInfo& s, int t,
+                                                   const float (&lqs)[7]) {
+  if (!s.valid) return;
+  const int J = a.max_joints;
+  float* row = a.dactions + ((size_t)t * a.num_envs + s.env) * J;
+#pragma unroll
+  for (int i = 0; i < Pat::N; ++i)
+    if (pat.active(i)) row[s.jo + i] = lqs[i];
+  if (s.c == 0)
+    for (int j = s.ntot; j < J; ++j) row[j] = 0.f;
+}
+
+// dL/d(link mass) and, when requested, dL/d(initial q, qd)
+template <class Pat>
+__device__ __forceinline__ void write_final_grads(const Pat& pat, const DiffArgs& a,
+                                                  const SlotInfo& s, const float (&lq)[7],
+                                                  const float (&lqd)[7], const float (&lm)[7]) {
+  if (!s.valid) return;
+  const int J = a.max_joints;
+  const size_t r = (size_t)s.env * J;
+#pragma unroll
+  for (int i = 0; i < Pat::N; ++i) {
+    if (!pat.active(i)) continue;
+    a.dmass[r + s.jo + i] = lm[i];
+    if (a.dq0) a.dq0[r + s.jo + i] = lq[i];
+    if (a.dqd0) a.dqd0[r + s.jo + i] = lqd[i];
+  }
+  if (s.c == 0) {
+    for (int j = s.ntot; j < J; ++j) {
+      a.dmass[r + j] = 0.f;
+      if (a.dq0) a.dq0[r + j] = 0.f;
+      if (a.dqd0) a.dqd0[r + j] = 0.f;
+    }
+  }
+}
+
 template <class Pat>
 __device__ __forceinline__ void diff_forward_chain(const DiffArgs& a, const Pat& pat,
                                                    const Rec& rec, int slot) {
@@ -149,7 +188,6 @@ __device__ __forceinline__ void diff_backward_chain(const DiffArgs& a, const Pat
   constexpr int N = Pat::N;
   const SlotInfo s = slot_info(a, slot);
   const size_t E = (size_t)a.num_envs;
-  const int J = a.max_joints;
   float lq[7], lqd[7], lm[7];
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
@@ -222,33 +260,10 @@ __device__ __forceinline__ void diff_backward_chain(const DiffArgs& a, const Pat
         }
         substep_adjoint(pat, rec, q, qd, qs, a.h, kGravity, lq, lqd, lqs, lm);
       }
-      if (s.valid) {
-        float* row = a.dactions + ((size_t)t * E + s.env) * J;
-#pragma unroll
-        for (int i = 0; i < N; ++i)
-          if (pat.active(i)) row[s.jo + i] = lqs[i];
-        if (s.c == 0)
-          for (int j = s.ntot; j < J; ++j) row[j] = 0.f;
-      }
+      write_action_grads(pat, a, s, t, lqs);
     }
   }
-  if (s.valid) {
-    float* mrow = a.dmass + (size_t)s.env * J;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      if (!pat.active(i)) continue;
-      mrow[s.jo + i] = lm[i];
-      if (a.dq0) a.dq0[(size_t)s.env * J + s.jo + i] = lq[i];
-      if (a.dqd0) a.dqd0[(size_t)s.env * J + s.jo + i] = lqd[i];
-    }
-    if (s.c == 0) {
-      for (int j = s.ntot; j < J; ++j) {
-        mrow[j] = 0.f;
-        if (a.dq0) a.dq0[(size_t)s.env * J + j] = 0.f;
-        if (a.dqd0) a.dqd0[(size_t)s.env * J + j] = 0.f;
-      }
-    }
-  }
+  write_final_grads(pat, a, s, lq, lqd, lm);
 }
 
 template <bool kBackward>
@@ -401,7 +416,6 @@ __device__ __forceinline__ void adjoint_role(const DiffArgs& a, const Pat& pat, 
   constexpr int N = Pat::N;
   const SlotInfo s = slot_info(a, slot);
   const size_t E = (size_t)a.num_envs;
-  const int J = a.max_joints;
   float lq[7], lqd[7], lm[7], qn[7], qdn[7];
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
@@ -440,35 +454,12 @@ __device__ __forceinline__ void adjoint_role(const DiffArgs& a, const Pat& pat, 
           for (int i = 0; i < 7; ++i) qn[i] = q[i];   // the state before step t
         }
       }
-      if (s.valid) {
-        float* row = a.dactions + ((size_t)t * E + s.env) * J;
-#pragma unroll
-        for (int i = 0; i < N; ++i)
-          if (pat.active(i)) row[s.jo + i] = lqs[i];
-        if (s.c == 0)
-          for (int j = s.ntot; j < J; ++j) row[j] = 0.f;
-      }
+      write_action_grads(pat, a, s, t, lqs);
     }
     __threadfence();
     mbar_arrive(freed + b);
   }
-  if (s.valid) {
-    float* mrow = a.dmass + (size_t)s.env * J;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      if (!pat.active(i)) continue;
-      mrow[s.jo + i] = lm[i];
-      if (a.dq0) a.dq0[(size_t)s.env * J + s.jo + i] = lq[i];
-      if (a.dqd0) a.dqd0[(size_t)s.env * J + s.jo + i] = lqd[i];
-    }
-    if (s.c == 0) {
-      for (int j = s.ntot; j < J; ++j) {
-        mrow[j] = 0.f;
-        if (a.dq0) a.dq0[(size_t)s.env * J + j] = 0.f;
-        if (a.dqd0) a.dqd0[(size_t)s.env * J + j] = 0.f;
-      }
-    }
-  }
+  write_final_grads(pat, a, s, lq, lqd, lm);
 }
 
 constexpr int kReplayBars = 5;   // tma, ready[2], free[2]
