@@ -112,8 +112,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel):
-    """DRAM bytes per launch of `kernel` on the default workload, from the
+def profiled_counter(kernel, name):
+    """A per-launch counter (`traffic_bytes_per_launch`,
+    `executed_flops_per_launch`) of `kernel` on the default workload, from the
     committed ncu summary, if it was taken from the current sources."""
     p = os.path.join(ROOT, "profiles", "step_kernel_c3.md")
     if not os.path.exists(p):
@@ -122,8 +123,12 @@ def profiled_traffic(kernel):
     m = re.search(r"source_hash:\s*([0-9a-f]+)", text)
     if not m or m.group(1) != kernel_source_hash():
         return None
-    m = re.search(r"traffic_bytes_per_launch\[%s\]:\s*([0-9]+)" % re.escape(kernel), text)
+    m = re.search(r"%s\[%s\]:\s*([0-9]+)" % (re.escape(name), re.escape(kernel)), text)
     return int(m.group(1)) if m else None
+
+
+def profiled_traffic(kernel):
+    return profiled_counter(kernel, "traffic_bytes_per_launch")
 
 
 def load_peaks():
@@ -472,6 +477,14 @@ def measure_adjoint(cx, wl, desc, T, every=8):
             "acts": acts_np, "tg": tg_np, "every": every, "clocks": clk.summary()}
 
 
+def executed_rate(kernel, seconds):
+    """Executed FP32 TFLOP/s (ncu's FFMA x 2 + FADD + FMUL of the default
+    workload's launch over this launch time), when the committed profile
+    matches the sources and this is the default workload's launch."""
+    f = profiled_counter(kernel, "executed_flops_per_launch")
+    return f / seconds / 1e12 if f else None
+
+
 _FMA_RATE = {}
 
 
@@ -483,19 +496,24 @@ def measured_fma_rate():
     return _FMA_RATE["v"]
 
 
-def roofline(kernel_name, flops_launch, bytes_launch, ms_per_launch, props, peaks, peak_src):
+def roofline(kernel_name, flops_launch, bytes_launch, ms_per_launch, props, peaks, peak_src,
+             profiled=False):
+    """`profiled`: this is the launch the committed ncu summary was taken
+    from (the default workload), so its DRAM traffic and executed FLOPs apply."""
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     s = ms_per_launch / 1e3
     achieved = flops_launch / s / 1e12
     fma = measured_fma_rate()
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": profiled_traffic(kernel_name),
+            "frac": achieved / peak,
+            "traffic": profiled_traffic(kernel_name) if profiled else None,
             "fma_probe_tflops": fma, "frac_of_fma_probe": achieved / fma,
             "kernel": kernel_name,
             "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s max SM clock)"
                            % (props.multi_processor_count, sm_max, peak_src),
             "flops_per_launch": flops_launch, "algorithmic_bytes_per_launch": bytes_launch,
+            "executed_tflops": executed_rate(kernel_name, s) if profiled else None,
             "hbm_gbs": bytes_launch / s / 1e9 if bytes_launch else None,
             "hbm_frac": (bytes_launch / s / 1e9 / float(peaks.get("hbm_gbs", 6800.0))
                          if bytes_launch else None)}
@@ -549,7 +567,8 @@ def run_rollout_config(cx, name, E=None):
     line["batched_over_step_graph"] = t["step_graph"] / t["ours"]
     line["bitwise_equal_forms"] = r["same_bits"]
     line["status"] = r["status"]
-    line["roofline"] = roofline(kname, flops, nbytes, ms_launch, props, peaks, src)
+    line["roofline"] = roofline(kname, flops, nbytes, ms_launch, props, peaks, src,
+                                profiled=(name == "C3" and E is None and args.gpus == 1))
     if "ms_e2e" in r:
         te = sum(r["ms_e2e"]) / 1e3
         ts = sum(r["ms_e2e_staged"]) / 1e3
@@ -591,7 +610,7 @@ def run_adjoint_config(cx, with_error, name="C4", E=None, T=None, err_envs=16):
     peaks, src = load_peaks()
     props = cx.torch.cuda.get_device_properties(cx.dev)
     ms_b = sum(a["ms_bwd"]) / len(a["ms_bwd"])
-    rf = roofline("diff_backward_kernel", f_bwd, None, ms_b, props, peaks, src)
+    rf = roofline("diff_backward_pair_kernel", f_bwd, None, ms_b, props, peaks, src)
     rf.pop("hbm_gbs", None), rf.pop("hbm_frac", None), rf.pop("algorithmic_bytes_per_launch", None)
     rf["traffic"] = None
     out["roofline"] = rf
