@@ -127,4 +127,23 @@ __device__ __forceinline__ void write_rows(float* obs_t, const float* stage, int
   }
 }
 
+// write_rows with the row count known at compile time (loop fully unrolled)
+template <int kRows>
+__device__ __forceinline__ void write_rows_n(float* obs_t, const float* stage, int row_env, int D,
+                                             int DP, int lane) {
+  if ((D & 1) == 0 && D <= 2 * kWarp) {
+    const int half = D >> 1;
+#pragma unroll
+    for (int rr = 0; rr < kRows; ++rr) {
+      const int er = __shfl_sync(0xffffffffu, row_env, rr);
+      if (er >= 0 && lane < half) {
+        const float2 v = reinterpret_cast<const float2*>(stage + rr * DP)[lane];
+        reinterpret_cast<float2*>(obs_t + (size_t)er * D)[lane] = v;
+      }
+    }
+  } else {
+    write_rows(obs_t, stage, row_env, kRows, D, DP, lane);
+  }
+}
+
 }  // namespace sg

@@ -38,9 +38,13 @@ __device__ __forceinline__ bool stage_record(const StepArgs& a, int gw, int cls,
 // Observation rows are first assembled in a per-warp shared-memory stage
 // (one row per env of the warp, odd row pitch: no bank conflicts), then the
 // warp writes each row to HBM with consecutive lanes on consecutive floats.
-template <class Pat>
+// kGlog: log2 of the lanes per env (1, 2 or 4 chains in a lane group), a
+// compile-time constant so that the group reductions and the row write-out
+// unroll completely.
+template <int kGlog, class Pat>
 __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, const Rec& rec,
-                                          float* stage, int slot, int lane, int glog) {
+                                          float* stage, int slot, int lane) {
+  constexpr int glog = kGlog;
   constexpr int N = Pat::N;
   const int env = a.slot_env[slot];
   const bool valid = env >= 0;
@@ -48,8 +52,8 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
   const int c = f.c, nc = f.nc, jo = f.jo, ntot = f.ntot, obs_len = f.obs_len;
   const int NS = a.num_slots;
   const int D = a.obs_dim, DP = stage_pitch(a.obs_dim);
-  const int g = 1 << glog;                        // lanes per env
-  const int nrows = kWarp >> glog;
+  constexpr int g = 1 << glog;                    // lanes per env
+  constexpr int nrows = kWarp >> glog;
   float* srow = stage + (lane >> glog) * DP;
   // env owning stage row `lane` (rows >= nrows unused; -1: row not written)
   const int sel_env = (valid && (!a.obs_mask || a.obs_mask[env])) ? env : -1;
@@ -182,7 +186,7 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
       }
     }
     __syncwarp();
-    write_rows(a.obs + (size_t)t * E * D, stage, row_env, nrows, D, DP, lane);
+    write_rows_n<nrows>(a.obs + (size_t)t * E * D, stage, row_env, D, DP, lane);
     __syncwarp();
   }
 
@@ -221,16 +225,21 @@ __global__ void __launch_bounds__(kMaxThreads) step_kernel(StepArgs a) {
   const Rec r{rec + lane};
   const int slot = gw * kWarp + lane;
   const int glog = group_log2(wc);
+  auto run = [&](const auto& pat) {
+    if (glog == 0) run_chain<0>(a, pat, r, stage, slot, lane);
+    else if (glog == 1) run_chain<1>(a, pat, r, stage, slot, lane);
+    else run_chain<2>(a, pat, r, stage, slot, lane);
+  };
   switch (wc & 3) {
-    case CLS_7R: run_chain(a, Pat7R{}, r, stage, slot, lane, glog); break;
-    case CLS_7P: run_chain(a, Pat7P{}, r, stage, slot, lane, glog); break;
-    case CLS_4R: run_chain(a, Pat4R{}, r, stage, slot, lane, glog); break;
+    case CLS_7R: run(Pat7R{}); break;
+    case CLS_7P: run(Pat7P{}); break;
+    case CLS_4R: run(Pat4R{}); break;
     default: {
       int code;
       const float cf = r.cf(CF_CODE);
       memcpy(&code, &cf, 4);
       const int n = decode_slot(a.slot_info[slot]).nchain;
-      run_chain(a, PatGen{code, n}, r, stage, slot, lane, glog);
+      run(PatGen{code, n});
     }
   }
 }

@@ -41,10 +41,12 @@ constexpr int kPairBars = 3;                      // tma, exchange, stage
 
 __device__ __forceinline__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
-template <class Pat>
+// kGlog: log2 of the lanes per env, a compile-time constant (see run_chain)
+template <int kGlog, class Pat>
 __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, const Rec& rec,
                                          float* stage, float* xbuf, uint64_t* bars, int group,
-                                         int lane, int role, int glog) {
+                                         int lane, int role) {
+  constexpr int glog = kGlog;
   constexpr int N = Pat::N;
   const int slot = group * kWarp + lane;
   const int env = a.slot_env[slot];
@@ -53,8 +55,8 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
   const int c = f.c, nc = f.nc, jo = f.jo, ntot = f.ntot, obs_len = f.obs_len;
   const int NS = a.num_slots;
   const int D = a.obs_dim, DP = stage_pitch(a.obs_dim);
-  const int g = 1 << glog;                        // lanes per env
-  const int nrows = kWarp >> glog;
+  constexpr int g = 1 << glog;                    // lanes per env
+  constexpr int nrows = kWarp >> glog;
   float* srow = stage + (lane >> glog) * DP;
   const int row_env = __shfl_sync(0xffffffffu, env, (lane << glog) & 31);
   uint64_t* bar_x = bars + 1;
@@ -227,10 +229,10 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
     mbar_arrive(bar_stage);
     if (!pair_wait(bar_stage, ph_stage, a.err, lane)) return;
     // each role writes half of the staged rows
-    const int half = nrows >> 1;
+    constexpr int half = nrows >> 1;
     const int r0 = role * half;
     const int ev = __shfl_sync(0xffffffffu, row_env, (lane + r0) & 31);
-    write_rows(a.obs + (size_t)t * E * D, stage + r0 * DP, ev, half, D, DP, lane);
+    write_rows_n<half>(a.obs + (size_t)t * E * D, stage + r0 * DP, ev, D, DP, lane);
   }
 
   if (valid && role == 0) {
@@ -289,16 +291,21 @@ __global__ void __launch_bounds__(kMaxThreads) step_kernel_pair(StepArgs a) {
   }
   const Rec r{rec + lane};
   const int glog = group_log2(wc);
+  auto run = [&](const auto& pat) {
+    if (glog == 0) run_pair<0>(a, pat, r, stage, xbuf, bars, group, lane, role);
+    else if (glog == 1) run_pair<1>(a, pat, r, stage, xbuf, bars, group, lane, role);
+    else run_pair<2>(a, pat, r, stage, xbuf, bars, group, lane, role);
+  };
   switch (wc & 3) {
-    case CLS_7R: run_pair(a, Pat7R{}, r, stage, xbuf, bars, group, lane, role, glog); break;
-    case CLS_7P: run_pair(a, Pat7P{}, r, stage, xbuf, bars, group, lane, role, glog); break;
-    case CLS_4R: run_pair(a, Pat4R{}, r, stage, xbuf, bars, group, lane, role, glog); break;
+    case CLS_7R: run(Pat7R{}); break;
+    case CLS_7P: run(Pat7P{}); break;
+    case CLS_4R: run(Pat4R{}); break;
     default: {
       int code;
       const float cf = r.cf(CF_CODE);
       memcpy(&code, &cf, 4);
       const int n = decode_slot(a.slot_info[group * kWarp + lane]).nchain;
-      run_pair(a, PatGen{code, n}, r, stage, xbuf, bars, group, lane, role, glog);
+      run(PatGen{code, n});
     }
   }
 }
