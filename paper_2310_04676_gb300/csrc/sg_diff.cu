@@ -164,12 +164,15 @@ __device__ __forceinline__ void diff_forward_chain(const DiffArgs& a, const Pat&
     qd[i] = a.qd[(size_t)i * a.num_slots + slot];
   }
   const size_t E = (size_t)a.num_envs;
+  float cq[Pat::N], sq[Pat::N];            // trigonometry of q, carried across substeps
+  joint_sincos(pat, q, cq, sq);
   for (int t = 0; t < a.T; ++t) {
     if (t % a.ckpt_every == 0) put_ckpt(pat, a, t / a.ckpt_every, slot, q, qd);
     read_targets(pat, a, t, s, qs);
-    for (int k = 0; k < a.substeps; ++k) chain_substep(pat, rec, q, qd, qs, a.h, kGravity);
+    for (int k = 0; k < a.substeps; ++k)
+      chain_substep_trig(pat, rec, q, qd, qs, cq, sq, a.h, kGravity);
     V3 tip, r0, r1, r2;
-    chain_tip(pat, rec, q, tip, r0, r1, r2);
+    chain_tip_trig(pat, rec, q, cq, sq, tip, r0, r1, r2);
     if (s.valid) {
       float* e = a.ee + (((size_t)t * E + s.env) * kMaxChains + s.c) * 3;
       e[0] = tip.x;
