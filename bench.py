@@ -641,18 +641,15 @@ def ppo_flops(D, A, E, n, epochs):
     return collect, update
 
 
-def run_ppo_config(cx, name="P1", E=None):
-    """The with-learning workload: collect + update per iteration."""
+def measure_ppo(cx, wl, desc, tf32):
+    """Iteration times (collect + update) of the PPO loop in one GEMM mode."""
     torch = cx.torch
     from paper_2310_04676_gb300 import sg, workloads as W
     args = cx.args
-    wl = W.ppo_config(name, num_envs=E)
-    desc = replica_desc(wl, cx.rank)
     env = sg.Env(desc)
-    tf32 = 0 if args.ppo_fp32 else 1
     ppo = sg.PPO(env, n_steps=wl.steps, epochs=5, minibatches=4, dt=wl.dt, substeps=wl.substeps,
                  seed=1 + cx.rank, tf32=tf32)
-    D, A, En = env.obs_dim, env.max_joints, env.num_envs
+    D, A = env.obs_dim, env.max_joints
     ppo.set_params(torch.as_tensor(W.ppo_init_params(D, A), device=cx.dev))
     ppo.reset(0)
     perms_h = torch.as_tensor(W.ppo_perms(ppo.B, 5)).pin_memory()
@@ -681,46 +678,74 @@ def run_ppo_config(cx, name="P1", E=None):
     ms_collect = [a.elapsed_time(b) for a, b in ev]
     ev.clear()
     ms_e2e = cx.timed(lambda: iteration(True), args.steps)
-    frames = En * wl.steps * args.steps
-    t = sum(ms) / 1e3
-    value = aggregate_rate(frames, t, world=cx.world, device=cx.dev)
-    f_col, f_upd = ppo_flops(D, A, En, wl.steps, 5)
-    it_s = t / args.steps
+    return {"ms": ms, "ms_collect": ms_collect, "ms_e2e": ms_e2e, "clocks": clk.summary(),
+            "status": sg.STATUS_NAMES.get(env.sync_status()), "D": D, "A": A,
+            "E": env.num_envs, "B": ppo.B, "h2d": int(perms_h.numel() * 4),
+            "d2h": int(stats_h.numel() * 4)}
+
+
+def run_ppo_config(cx, name="P1", E=None):
+    """The with-learning workload: collect + update per iteration, with FP32
+    GEMMs (the line's value) and with TF32 tensor-core GEMMs (beside it)."""
+    torch = cx.torch
+    from paper_2310_04676_gb300 import workloads as W
+    args = cx.args
+    wl = W.ppo_config(name, num_envs=E)
+    desc = replica_desc(wl, cx.rank)
     peaks, src = load_peaks()
-    # TF32 dense peak: the measured bf16 burst peak x the nominal TF32 / BF16 ratio (1.1 / 2.25)
-    peak = float(peaks.get("bf16_tflops", 1900.0)) * (1.1 / 2.25) if tf32 else \
-        torch.cuda.get_device_properties(cx.dev).multi_processor_count * 128 * 2 * \
-        float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    achieved = (f_col + f_upd) / it_s / 1e12
+    props = torch.cuda.get_device_properties(cx.dev)
+    fp32_peak = props.multi_processor_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) \
+        * 1e6 / 1e12
+    tf32_peak = float(peaks.get("bf16_tflops", 1900.0)) * (1.1 / 2.25)
+    runs = {m: measure_ppo(cx, wl, desc, m) for m in (0, 1)}
+    r = runs[0]
+    D, A, En = r["D"], r["A"], r["E"]
+    frames = En * wl.steps * args.steps
+    f_col, f_upd = ppo_flops(D, A, En, wl.steps, 5)
+
+    def summary(rr, peak):
+        t = sum(rr["ms"]) / 1e3
+        it = t / args.steps
+        return {"value": aggregate_rate(frames, t, world=cx.world, device=cx.dev),
+                "ms_per_iteration": 1e3 * it, "ms_collect": float(np.mean(rr["ms_collect"])),
+                "ms_update": 1e3 * it - float(np.mean(rr["ms_collect"])),
+                "achieved_tflops": (f_col + f_upd) / it / 1e12,
+                "frac": (f_col + f_upd) / it / 1e12 / peak}
+
+    s32, stf = summary(r, fp32_peak), summary(runs[1], tf32_peak)
     cfg = {"workload": wl.name, "envs_per_gpu": En, "n_steps": wl.steps, "epochs": 5,
-           "minibatches": 4, "minibatch_rows": ppo.B // 4, "substeps": wl.substeps, "dt": wl.dt,
+           "minibatches": 4, "minibatch_rows": r["B"] // 4, "substeps": wl.substeps, "dt": wl.dt,
            "networks": "actor and critic MLP %d-256-128-64-{%d,1}, ELU" % (D, A),
-           "gemm": "cuBLAS TF32 tensor cores" if tf32 else "cuBLAS FP32",
+           "gemm": "cuBLAS FP32 SGEMM (tensor cores off)",
            "l2": "flushed (256 MiB write) before every timed iteration"}
-    line = base_line(args, cx.world, value, 1e3 * it_s, cfg)
+    line = base_line(args, cx.world, s32["value"], s32["ms_per_iteration"], cfg)
     line["metric"] = "with-learning frames/s (collect + PPO update), context for the step metric"
     line["unit"] = "frames/s"
-    line["dtype"] = "tf32" if tf32 else "f32"
-    line["iteration_time_stats"] = stats(ms)
-    line["ms_collect"] = float(np.mean(ms_collect))
-    line["ms_update"] = 1e3 * it_s - float(np.mean(ms_collect))
-    line["roofline"] = {"bound": "tensor" if tf32 else "alu", "achieved": achieved, "peak": peak,
-                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+    line["dtype"] = "f32"
+    line["iteration_time_stats"] = stats(r["ms"])
+    line["ms_collect"] = s32["ms_collect"]
+    line["ms_update"] = s32["ms_update"]
+    line["roofline"] = {"bound": "alu", "achieved": s32["achieved_tflops"], "peak": fp32_peak,
+                        "unit": "TFLOP/s", "frac": s32["frac"], "traffic": None,
                         "kernel": "whole iteration (dense layers' FLOPs / iteration time)",
-                        "peak_source": ("measured bf16 burst x 1.1/2.25 (%s)" % src) if tf32
-                        else "SMs x 128 x 2 x max SM clock",
+                        "peak_source": "SMs x 128 FP32 lanes x 2 x max SM clock",
                         "flops_per_iteration": {"collect": f_col, "update": f_upd}}
-    line["e2e"] = {"value": aggregate_rate(frames, sum(ms_e2e) / 1e3, world=cx.world, device=cx.dev),
-                   "unit": "frames/s", "h2d_bytes_per_step": int(perms_h.numel() * 4),
-                   "d2h_bytes_per_step": int(stats_h.numel() * 4)}
-    # kernels of this library per iteration: per collect step 8 bias/ELU, sampling, the env
-    # step, bootstrap, reset, observe; then 4 bias (last values), GAE, 2 moments, step
-    # counter; per minibatch gather, 8 bias/ELU, 2 loss-head, 6 ELU-backward, 2 norm, Adam
+    line["tf32"] = dict(stf, dtype="tf32", gemm="cuBLAS TF32 tensor cores",
+                        peak=tf32_peak, peak_source="measured bf16 burst x 1.1/2.25 (%s)" % src,
+                        note="reduced-precision GEMM inputs (10-bit mantissa): context only")
+    line["e2e"] = {"value": aggregate_rate(frames, sum(r["ms_e2e"]) / 1e3, world=cx.world,
+                                           device=cx.dev),
+                   "unit": "frames/s", "h2d_bytes_per_step": r["h2d"],
+                   "d2h_bytes_per_step": r["d2h"]}
+    # kernels of this library per iteration: per collect step 8 bias/ELU, pad, sampling,
+    # the env step, bootstrap, reset, observe; then pad, 4 bias (last values), GAE,
+    # 2 moments, step counter; per minibatch gather, 8 bias/ELU, 2 loss-head,
+    # 6 ELU-backward + 6 bias-gradient sums, 2 norm, Adam
     n_mb = 5 * 4
-    line["gpu_launches"] = (wl.steps * 13 + 8 + n_mb * 20) * args.steps
-    line["library_launches"] = (wl.steps * 8 + 4 + n_mb * 30) * args.steps   # cuBLAS GEMM/GEMV
-    line["clocks"] = clk.summary()
-    line["status"] = sg.STATUS_NAMES.get(env.sync_status())
+    line["gpu_launches"] = (wl.steps * 14 + 9 + n_mb * 26) * args.steps
+    line["library_launches"] = (wl.steps * 8 + 4 + n_mb * 24) * args.steps   # cuBLAS GEMM/GEMV
+    line["clocks"] = r["clocks"]
+    line["status"] = r["status"]
     line["paper_context"] = ("Table II: 6.8 s per 1M timesteps with learning (147,059 frames/s), "
                              "20,000 envs on one 8 GB Quadro RTX 4000 (different engine and task)")
     return line
@@ -757,7 +782,6 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="C3", choices=["C1", "C2", "C3", "C4", "C5", "P1"])
-    ap.add_argument("--ppo-fp32", action="store_true", help="P1: FP32 GEMMs instead of TF32")
     ap.add_argument("--envs", type=int, nargs="*", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--launch", default=None,
