@@ -817,8 +817,9 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
   }
   if (!blas_ok(cublasCreate(&p->blas)) ||
       !blas_ok(cublasSetWorkspace(p->blas, p->blas_ws, ws_bytes)) ||
+      // FP32 mode: the default math mode, which never lowers FP32 products to TF32
       !blas_ok(cublasSetMathMode(p->blas, c.tf32 ? CUBLAS_TF32_TENSOR_OP_MATH
-                                                 : CUBLAS_PEDANTIC_MATH)) ||
+                                                 : CUBLAS_DEFAULT_MATH)) ||
       !blas_ok(cublasSetPointerMode(p->blas, CUBLAS_POINTER_MODE_HOST))) {
     fail(p, SG_ERR_CUDA, "sg_ppo_create: cuBLAS initialisation failed");
     sg_ppo_destroy(p);
