@@ -32,6 +32,7 @@ import os
 import re
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -288,6 +289,8 @@ class Ctx:
         self.dev = torch.device("cuda", local)
         self.stream = torch.cuda.current_stream()
         self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=self.dev)
+        self.out_dir = args.out_dir or os.path.join(tempfile.gettempdir(), "sg_bench")
+        os.makedirs(self.out_dir, exist_ok=True)
 
     def barrier(self):
         if self.world > 1:
@@ -344,8 +347,7 @@ def measure_rollout(cx, wl, desc, T, with_e2e=True):
         for f in forms.values():
             f()
     cx.barrier()
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_r%d.csv" % cx.rank), cx.local)
+    clk = ClockSampler(os.path.join(cx.out_dir, "clocks_r%d.csv" % cx.rank), cx.local)
     ms = {"ours": cx.timed(forms["ours"], args.steps, clk)}
     for k in ("step_graph", "plain"):
         ms[k] = cx.timed(forms[k], args.steps)
@@ -468,7 +470,7 @@ def measure_adjoint(cx, wl, desc, T, every=8):
     for _ in range(cx.args.warmup):
         fwd_bwd()
     res["timing"] = True
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_adj_r%d.csv" % cx.rank), cx.local)
+    clk = ClockSampler(os.path.join(cx.out_dir, "clocks_adj_r%d.csv" % cx.rank), cx.local)
     ms = cx.timed(fwd_bwd, cx.args.steps, clk)
     res["timing"] = False
     ms_bwd = [a.elapsed_time(b) for a, b in kev]
@@ -673,7 +675,7 @@ def measure_ppo(cx, wl, desc, tf32):
     for _ in range(args.warmup):
         iteration()
     ev.clear()
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_ppo_r%d.csv" % cx.rank), cx.local)
+    clk = ClockSampler(os.path.join(cx.out_dir, "clocks_ppo_r%d.csv" % cx.rank), cx.local)
     ms = cx.timed(iteration, args.steps, clk)
     ms_collect = [a.elapsed_time(b) for a, b in ev]
     ev.clear()
@@ -784,6 +786,8 @@ def main():
     ap.add_argument("--config", default="C3", choices=["C1", "C2", "C3", "C4", "C5", "P1"])
     ap.add_argument("--envs", type=int, nargs="*", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--out-dir", default=None,
+                    help="where the nvidia-smi clock samples go (default: a temporary directory)")
     ap.add_argument("--launch", default=None,
                     help="threads,mode,split: fixed launch plan instead of the autotuner "
                          "(used to profile one plan)")

@@ -48,7 +48,7 @@ typedef enum sg_status {
   SG_ERR_OOM = 3,           /* device or host allocation failed */
   SG_ERR_NONFINITE = 4,     /* a kernel saw a non-finite state (sg_sync_status) */
   SG_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up (sg_sync_status) */
-  SG_ERR_UNSUPPORTED = 6    /* valid request outside what this build implements */
+  SG_ERR_UNSUPPORTED = 6    /* valid request outside what this library implements */
 } sg_status;
 
 enum {

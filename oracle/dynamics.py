@@ -14,8 +14,8 @@
                   else (gravity, Coriolis, centrifugal) explicitly.  The
                   paper's engine sub-steps each control step (Methods,
                   "Simulation Setup"); the drive formula is the PD joint
-                  drive named there; the implicit treatment is this build's
-                  reading (the paper gives no integrator formula).
+                  drive named there; the implicit treatment is a reading
+                  (the paper gives no integrator formula).
 * ``rk4_step``    classical Runge-Kutta 4 of the continuous dynamics, used
                   only for conservation tests.
 """

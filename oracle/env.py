@@ -6,7 +6,7 @@ Follows the paper's task definitions (Results, "Environments"):
   position, current PD targets) (Methods, "Observation Space"), plus the
   goal for the goal tasks;
 * Target Reaching reward  r = rho * ||eta_t - g|| with rho = -1 (the sign
-  is this build's reading: the paper leaves rho's sign open);
+  is a reading: the paper leaves rho's sign open);
 * Multi-Tool Target Reaching reward r = rho * sum_i ||eta_i - g_i||;
 * Path Following reward r = -alpha * ||eta_t - P(t)||, observation
   [q, qd, tip position, tip quaternion, next three waypoints];

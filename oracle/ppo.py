@@ -8,7 +8,7 @@ n_steps split into large minibatches, generalized advantage estimation
 (Schulman et al. 2016), time-outs told apart from terminations and handled
 by adding the critic's value prediction to the reward ("bootstrapping"), and
 a policy network with hidden layers 256, 128, 64 and ELU activations.
-Readings where it is silent (each also stated in the design doc):
+Readings where it is silent:
 
 * actor and critic are separate MLPs D -> 256 -> 128 -> 64 -> out with ELU
   after every hidden layer; the policy is a diagonal Gaussian with a
