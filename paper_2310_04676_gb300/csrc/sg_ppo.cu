@@ -11,6 +11,7 @@
 #include <cublas_v2.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -69,23 +70,42 @@ Layout make_layout(int D, int A) {
 // ---- kernels -----------------------------------------------------------------
 __device__ __forceinline__ float elu(float x) { return x > 0.f ? x : expm1f(x); }
 
-// Y[r][c] = act(Y[r][c] + b[c]) in place (width a multiple of 4: float4 path)
-__global__ void bias_act4_kernel(float4* __restrict__ Y, const float4* __restrict__ b, int n4,
-                                 int width4, int do_elu) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
-    float4 z = Y[i];
-    const float4 c = b[i % width4];
-    z.x += c.x;
-    z.y += c.y;
-    z.z += c.z;
-    z.w += c.w;
-    if (do_elu) {
-      z.x = elu(z.x);
-      z.y = elu(z.y);
-      z.z = elu(z.z);
-      z.w = elu(z.w);
-    }
-    Y[i] = z;
+// Y[r][c] = act(Y[r][c] + b[c]) in place (width a multiple of 4: float4 path).
+// A thread owns 4 adjacent columns (its bias in registers) of every
+// `groups`-th row, two rows in flight, so no per-element index arithmetic is
+// needed.
+__device__ __forceinline__ float4 bias_act4(float4 z, float4 c, int do_elu) {
+  z.x += c.x;
+  z.y += c.y;
+  z.z += c.z;
+  z.w += c.w;
+  if (do_elu) {
+    z.x = elu(z.x);
+    z.y = elu(z.y);
+    z.z = elu(z.z);
+    z.w = elu(z.w);
+  }
+  return z;
+}
+
+__global__ void __launch_bounds__(256)
+bias_act4_kernel(float4* __restrict__ Y, const float4* __restrict__ b, int rows, int width4,
+                 int do_elu) {
+  const int groups = blockDim.x / width4;           // rows side by side (width4 | 256)
+  const int c4 = threadIdx.x % width4, g = threadIdx.x / width4;
+  if (g >= groups) return;
+  const float4 c = b[c4];
+  const int stride = gridDim.x * groups;
+  int r = blockIdx.x * groups + g;
+  for (; r + stride < rows; r += 2 * stride) {
+    const size_t k0 = (size_t)r * width4 + c4, k1 = k0 + (size_t)stride * width4;
+    const float4 z0 = Y[k0], z1 = Y[k1];
+    Y[k0] = bias_act4(z0, c, do_elu);
+    Y[k1] = bias_act4(z1, c, do_elu);
+  }
+  if (r < rows) {
+    const size_t k = (size_t)r * width4 + c4;
+    Y[k] = bias_act4(Y[k], c, do_elu);
   }
 }
 
@@ -584,11 +604,14 @@ bool gemm_bwd_weight(sg_ppo* p, const float* dY, const float* X, int rows, const
 }
 
 cudaError_t bias_act(sg_ppo* p, float* Y, int rows, const Layer& l, bool elu) {
+  if (rows <= 0) return cudaSuccess;
   const long long n = (long long)rows * l.out;
-  if (l.out % 4 == 0) {
-    sg::bias_act4_kernel<<<sg::grid_for(n / 4, 256), 256, 0, p->stream>>>(
-        reinterpret_cast<float4*>(Y), reinterpret_cast<const float4*>(p->params + l.b),
-        (int)(n / 4), l.out / 4, elu ? 1 : 0);
+  if (l.out % 4 == 0 && 256 % (l.out / 4) == 0) {
+    const int groups = 256 / (l.out / 4);
+    const int blocks = (int)std::min<long long>((rows + groups - 1) / groups, 152 * 8);
+    sg::bias_act4_kernel<<<blocks, 256, 0, p->stream>>>(
+        reinterpret_cast<float4*>(Y), reinterpret_cast<const float4*>(p->params + l.b), rows,
+        l.out / 4, elu ? 1 : 0);
   } else {
     sg::bias_act_kernel<<<sg::grid_for(n, 256), 256, 0, p->stream>>>(Y, p->params + l.b, (int)n,
                                                                       l.out, elu ? 1 : 0);
