@@ -103,11 +103,19 @@ def env_step_bytes(desc, obs_dim):
     return int(4 * dof.sum() + E * (4 * obs_dim + 4 + 1) + extra)
 
 
-def kernel_source_hash():
-    """Hash of the step-kernel sources; a profile summary names the hash it
-    was captured with, and its DRAM traffic is used only if they match."""
+KERNEL_SOURCES = {
+    "step_kernel": ("sg_internal.h", "sg_kernels.h", "sg_rng.cuh", "sg_chain.cuh",
+                    "sg_device.cuh", "sg_kernels.cu"),
+    "step_kernel_pair": ("sg_internal.h", "sg_kernels.h", "sg_rng.cuh", "sg_chain.cuh",
+                         "sg_device.cuh", "sg_pair.cu"),
+}
+
+
+def kernel_source_hash(kernel):
+    """Hash of the sources a step kernel is compiled from; a profile summary
+    names the hash per kernel, and its counters are used only if it matches."""
     h = hashlib.sha256()
-    for f in ("sg_chain.cuh", "sg_device.cuh", "sg_kernels.cu", "sg_pair.cu"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2310_04676_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -118,11 +126,11 @@ def profiled_counter(kernel, name):
     `executed_flops_per_launch`) of `kernel` on the default workload, from the
     committed ncu summary, if it was taken from the current sources."""
     p = os.path.join(ROOT, "profiles", "step_kernel_c3.md")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or kernel not in KERNEL_SOURCES:
         return None
     text = open(p).read()
-    m = re.search(r"source_hash:\s*([0-9a-f]+)", text)
-    if not m or m.group(1) != kernel_source_hash():
+    m = re.search(r"source_hash\[%s\]:\s*([0-9a-f]+)" % re.escape(kernel), text)
+    if not m or m.group(1) != kernel_source_hash(kernel):
         return None
     m = re.search(r"%s\[%s\]:\s*([0-9]+)" % (re.escape(name), re.escape(kernel)), text)
     return int(m.group(1)) if m else None

@@ -260,7 +260,10 @@ __global__ void __launch_bounds__(kMaxThreads) step_kernel_pair(StepArgs a) {
   const int w = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int pairs = blockDim.x >> 6;
-  const int pair = w >> 1, role = w & 1;
+  // the first `pairs` warps take role 0, the rest role 1: with four pairs
+  // per block, warps w and w + 4 share one of the SM's four schedulers, so
+  // each scheduler holds one warp of each role instead of two of the same
+  const int pair = w % pairs, role = w / pairs;
   const int stage_floats = kWarp * stage_pitch(a.obs_dim);
   float* rec = smem + (size_t)pair * kRecordFloats;
   float* stage = smem + (size_t)pairs * kRecordFloats + (size_t)pair * stage_floats;

@@ -52,16 +52,18 @@ def _close(x, y, tol):
 @pytest.mark.parametrize("kinds", [["7R"], ["14B"], ["4R", "7P"], ["7R", "4R", "7P", "14B"],
                                    ["21T", "7R"]],
                          ids=lambda k: "+".join(k))
-def test_warp_pair_kernel_matches_single_thread_kernel(kinds):
+@pytest.mark.parametrize("pair_threads", [128, 256])
+def test_warp_pair_kernel_matches_single_thread_kernel(kinds, pair_threads):
     """Chain split 2 (two cooperating warps per chain block) agrees with one
     thread per chain to rounding (1e-5 of the largest entry over 6 steps),
-    with identical done flags, for every chain class."""
+    with identical done flags, for every chain class and with two or four
+    pairs per block."""
     desc = W.make_desc((kinds * 200)[:200])
     T = 6
     acts = cuda(W.joint_targets(desc, T))
     A, B = sg.Env(desc), sg.Env(desc)
     A.set_launch(128, sg.ROLLOUT_PERSISTENT, 1)
-    B.set_launch(128, sg.ROLLOUT_PERSISTENT, 2)
+    B.set_launch(pair_threads, sg.ROLLOUT_PERSISTENT, 2)
     oa, ra, da = A.rollout(acts, DT, 2)
     ob, rb, db = B.rollout(acts, DT, 2)
     assert _close(ob, oa, 1e-5) and _close(rb, ra, 1e-5) and torch.equal(da, db)
