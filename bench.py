@@ -256,6 +256,45 @@ def cpu_baseline(wl, seconds=12.0, max_envs=2048):
                       % (n, E, steps, el)}
 
 
+def equal_accuracy(wl, launch, n_envs=64, steps=100):
+    """Joint positions of the first `n_envs` envs after `steps` control steps,
+    in the measured launch plan, as one persistent rollout and as one sg_step
+    call per step, against the FP64 oracle from the same initial state:
+    max over envs of ||q_gpu - q_ref|| / max(||q_ref||, 1e-3) (tolerance
+    1e-3, as in the parity tests)."""
+    import torch
+    from oracle.env import OracleEnv
+    from paper_2310_04676_gb300 import sg, workloads as W
+    E = wl.desc["num_envs"]
+    n = min(E, n_envs)
+    sub = {k: (v[:n] if isinstance(v, np.ndarray) and v.shape[:1] == (E,) else v)
+           for k, v in wl.desc.items()}
+    sub["num_envs"] = n
+    sub["episode_len"] = max(int(sub["episode_len"]), steps + 1)
+    acts = W.joint_targets(sub, steps)
+    ref = OracleEnv(sub)
+    for t in range(steps):
+        ref.step(acts[t], wl.dt, wl.substeps)
+    threads, mode, split = launch
+    a = torch.as_tensor(acts, device="cuda")
+    out = {}
+    for form in ("rollout", "plain"):
+        env = sg.Env(sub)
+        env.set_launch(threads, mode, split)
+        if form == "rollout":
+            env.rollout(a, wl.dt, wl.substeps)
+        else:
+            for t in range(steps):
+                env.step(a[t], wl.dt, wl.substeps)
+        q = env.get_state()[0].cpu().numpy().astype(np.float64)
+        err = np.linalg.norm(q - ref.q, axis=1) / np.maximum(np.linalg.norm(ref.q, axis=1), 1e-3)
+        out[form] = float(err.max())
+        env.close()
+    return {"q_rel_err_max": out, "tolerance": 1e-3, "within": max(out.values()) <= 1e-3,
+            "sample": "first %d of %d envs, %d steps from the initial state, measured launch "
+                      "plan; FP64 oracle" % (n, E, steps)}
+
+
 def cpu_baseline_single_core(wl, seconds=6.0, max_envs=256):
     """The same oracle restricted to one host thread, on a smaller sample."""
     import torch
@@ -855,6 +894,11 @@ def main():
             line["cpu_baseline"] = cpu_baseline(wl) if want_cpu else None
             if want_cpu:
                 line["cpu_baseline"]["single_core"] = cpu_baseline_single_core(wl)
+                launch = line["config"]["launch"]
+                line["equal_accuracy"] = equal_accuracy(
+                    wl, (launch["threads_per_block"],
+                         {"persistent": 0, "step_graph": 1}[launch["mode"]],
+                         launch["chain_split"]))
             print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
