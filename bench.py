@@ -59,7 +59,7 @@ W_HIDDEN = (256, 128, 64)   # hidden widths of the PPO networks
 # Adjoint pieces (same counting): one substep's adjoint (forward substep with
 # its factorisation recomputed, the solve with the factor, the reverse RNEA)
 # and the tool-tip Jacobian-transpose product.
-FLOP_SUBSTEP_ADJ = {"4R": 1460, "7R": 3278, "7P": 3069}
+FLOP_SUBSTEP_ADJ = {"4R": 1460, "7R": 3278, "7P": 3070}
 FLOP_TIP_VJP = {"4R": 112, "7R": 238, "7P": 210}
 
 
@@ -75,11 +75,12 @@ def env_step_flops(kinds, substeps, task=0):
 
 def adjoint_flops(kinds, substeps, T, every, replay=True):
     """Algorithmic FLOPs of one differentiable rollout: (forward kernel,
-    backward kernel).  The warp-pair backward (replay buffers) recomputes
-    every substep once, inside its substep adjoint (FLOP_SUBSTEP_ADJ counts
-    the recomputed forward substep with its factorisation), plus one tip
-    product per step; the one-warp backward also recomputes each segment
-    from its checkpoint and each step's substep start states."""
+    backward kernel).  The pipelined backward (replay buffers) recomputes
+    every substep once, in a replay warp, with its inverse-dynamics sweeps
+    (FLOP_SUBSTEP_ADJ counts the recomputed forward substep with its
+    factorisation, the sweeps and their reverse), plus one tip product per
+    step; the one-warp backward also recomputes each segment from its
+    checkpoint and each step's substep start states."""
     fwd = bwd = 0
     seg_steps = [min(every, T - t0) for t0 in range(0, T, every)]
     for k in kinds:
@@ -659,7 +660,7 @@ def run_adjoint_config(cx, with_error, name="C4", E=None, T=None, err_envs=16):
     peaks, src = load_peaks()
     props = cx.torch.cuda.get_device_properties(cx.dev)
     ms_b = sum(a["ms_bwd"]) / len(a["ms_bwd"])
-    rf = roofline("diff_backward_pair_kernel", f_bwd, None, ms_b, props, peaks, src)
+    rf = roofline("diff_backward_pipe_kernel", f_bwd, None, ms_b, props, peaks, src)
     rf.pop("hbm_gbs", None), rf.pop("hbm_frac", None), rf.pop("algorithmic_bytes_per_launch", None)
     rf["traffic"] = None
     out["roofline"] = rf

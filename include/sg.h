@@ -290,9 +290,10 @@ sg_status sg_autotune(sg_ctx *ctx, const float *actions_dev, int32_t T, float dt
  * every step to ee_dev [T][E][4][3] (entries of chains an env does not have
  * are 0).  The state (q, qd) is checkpointed every ckpt_every steps
  * (1..32) in context scratch memory (cudaMalloc on first use or growth),
- * together with the backward pass's replay buffers (2 * ckpt_every *
- * substeps * 70 * num_slots floats while that stays within 1 GiB; beyond it
- * the backward pass runs without them, more slowly);
+ * together with the backward pass's replay buffers (3 * ckpt_every *
+ * substeps * 210 * num_slots floats while that stays within 1 GiB; beyond it
+ * the backward pass runs without them, more slowly; with them, the forward
+ * also leaves the last segment's substep records there);
  * the context's own state and step counts are NOT changed.  substeps 1..16.
  *
  * sg_diff_backward: the reverse pass of the last sg_diff_forward on this
@@ -300,10 +301,11 @@ sg_status sg_autotune(sg_ctx *ctx, const float *actions_dev, int32_t T, float dt
  * dactions_dev [T][E][J] = dL/d(actions) and dmass_dev [E][J] = dL/d(link
  * mass) (link inertias scale with the mass, centre of mass fixed); dq0_dev
  * and dqd0_dev [E][J] (either may be NULL) receive dL/d(initial q, qd).
- * actions_dev must hold the same values as in the forward call.  Each
- * segment between checkpoints is recomputed from its checkpoint (by a
- * second warp, one segment ahead of the reverse sweep, when the replay
- * buffers exist).  Joint
+ * actions_dev must hold the same values as in the forward call (it may be
+ * called more than once after one forward).  Each segment between
+ * checkpoints is recomputed from its checkpoint (when the replay buffers
+ * exist: by two further warps, ahead of the reverse sweep; the first call
+ * after a forward takes the last segment from the forward's records).  Joint
  * limit springs switch on and off at the limits; the gradient is that of
  * the active branch.
  */

@@ -10,8 +10,9 @@
 //   lambda_q* +=  h (kp + g) mu            (g: command gain of the joint)
 //   lambda_m  += -h (dID/dm)^T mu            (a held fixed)
 // The vector-Jacobian product of ID is the reverse of the body-frame RNEA
-// below (forward sweep with qdd = a, backward sweep storing the link
-// wrenches, then both sweeps reversed).  Link inertias scale with the link
+// below: id_sweeps (forward sweep with qdd = a, backward sweep giving the
+// link wrenches; independent of the cotangent), then rnea_vjp_rev (both
+// sweeps reversed).  Link inertias scale with the link
 // mass (fixed box size), so d(F, N)/dm = (F, N) / m.
 #pragma once
 
@@ -40,25 +41,23 @@ __device__ __forceinline__ void kz_adj(V3 w, V3 Kb, V3& wb, V3& wdb) {
 // e_a x v
 __device__ __forceinline__ V3 axis_x(int a, V3 v) { return axis_cross(a, v); }
 
-// Vector-Jacobian product of tau = ID(q, qd, qdd) (gravity by base
-// acceleration): given mu, accumulates gq += (dID/dq)^T mu, gqd += (dID/dqd)^T
-// mu and gm += (dID/dm)^T mu.
-template <class Pat>
-__device__ __forceinline__ void rnea_vjp(const Pat& pat, const Rec& rec, const float (&q)[7],
-                                         const float (&qd)[7], const float (&qdd)[Pat::N],
-                                         const float (&cq)[Pat::N], const float (&sq)[Pat::N],
-                                         float grav, const float (&mu)[Pat::N],
-                                         float (&gq)[Pat::N], float (&gqd)[Pat::N],
-                                         float (&gm)[Pat::N]) {
+// Inverse-dynamics sweeps of tau = ID(q, qd, qdd) (gravity by base
+// acceleration; no cotangent involved): base to tip, every link's angular
+// velocity w, angular acceleration wd, origin acceleration acc, inertial
+// force F and moment Nm about its COM (out.fwd); tip to base, the wrench
+// (f, n) it transmits about its origin (out.bwd).
+template <class Pat, class Out>
+__device__ __forceinline__ void id_sweeps(const Pat& pat, const Rec& rec, const float (&q)[7],
+                                          const float (&qd)[7], const float (&qdd)[Pat::N],
+                                          const float (&cq)[Pat::N], const float (&sq)[Pat::N],
+                                          float grav, Out& out) {
   constexpr int N = Pat::N;
-  V3 W[N], WD[N], ACC[N], F[N], Nm[N], FL[N], NL[N];
-  float ell[N], ellb[N];
-  // ---- forward sweep with qdd
+  V3 F[N], Nm[N];
+  float ell[N];
   {
     V3 w{0.f, 0.f, 0.f}, wd{0.f, 0.f, 0.f}, acc{0.f, 0.f, grav};
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      ellb[i] = 0.f;
       if (!pat.active(i)) continue;
       const int a = pat.axis(i);
       ell[i] = (i == 0 ? 0.f : rec.lf(i - 1, LF_L)) + (pat.type(i) == 1 ? q[i] : 0.f);
@@ -81,18 +80,15 @@ __device__ __forceinline__ void rnea_vjp(const Pat& pat, const Rec& rec, const f
         ap.z += qdd[i];
       }
       acc = ap;
-      W[i] = w;
-      WD[i] = wd;
-      ACC[i] = acc;
       const float c = rec.lf(i, LF_C), m = rec.lf(i, LF_M);
       const float Ix = rec.lf(i, LF_IX), Iy = rec.lf(i, LF_IY), Iz = rec.lf(i, LF_IZ);
       const V3 Kc = kz(w, wd);
       F[i] = V3{m * (acc.x + c * Kc.x), m * (acc.y + c * Kc.y), m * (acc.z + c * Kc.z)};
       Nm[i] = V3{Ix * wd.x + (Iz - Iy) * w.y * w.z, Iy * wd.y + (Ix - Iz) * w.z * w.x,
                  Iz * wd.z + (Iy - Ix) * w.x * w.y};
+      out.fwd(i, w, wd, acc, F[i], Nm[i]);
     }
   }
-  // ---- backward sweep, storing the wrench (f, n) of every link about its origin
   {
     V3 fc{0.f, 0.f, 0.f}, nc{0.f, 0.f, 0.f};
 #pragma unroll
@@ -101,8 +97,7 @@ __device__ __forceinline__ void rnea_vjp(const Pat& pat, const Rec& rec, const f
       const float c = rec.lf(i, LF_C);
       const V3 f = v3add(F[i], fc);
       const V3 n{Nm[i].x - c * F[i].y + nc.x, Nm[i].y + c * F[i].x + nc.y, Nm[i].z + nc.z};
-      FL[i] = f;
-      NL[i] = n;
+      out.bwd(i, f, n);
       if (i > 0) {
         V3 fp = f, np = n;
         if (pat.type(i) == 0) {
@@ -115,6 +110,49 @@ __device__ __forceinline__ void rnea_vjp(const Pat& pat, const Rec& rec, const f
         nc = np;
       }
     }
+  }
+}
+
+// id_sweeps output kept in thread-local arrays; also the accessor
+// rnea_vjp_rev reads them through.
+template <int N>
+struct SweepArrays {
+  V3 W[N], WD[N], ACC[N], F[N], Nm[N], FL[N], NL[N];
+  __device__ __forceinline__ void fwd(int i, V3 w, V3 wd, V3 acc, V3 f, V3 n) {
+    W[i] = w;
+    WD[i] = wd;
+    ACC[i] = acc;
+    F[i] = f;
+    Nm[i] = n;
+  }
+  __device__ __forceinline__ void bwd(int i, V3 f, V3 n) {
+    FL[i] = f;
+    NL[i] = n;
+  }
+  __device__ __forceinline__ V3 w(int i) const { return W[i]; }
+  __device__ __forceinline__ V3 wd(int i) const { return WD[i]; }
+  __device__ __forceinline__ V3 acc(int i) const { return ACC[i]; }
+  __device__ __forceinline__ V3 f(int i) const { return F[i]; }
+  __device__ __forceinline__ V3 nm(int i) const { return Nm[i]; }
+  __device__ __forceinline__ V3 fl(int i) const { return FL[i]; }
+  __device__ __forceinline__ V3 nl(int i) const { return NL[i]; }
+};
+
+// Reverse of id_sweeps: given mu and the sweeps' quantities (accessor sw),
+// accumulates gq += (dID/dq)^T mu, gqd += (dID/dqd)^T mu and
+// gm += (dID/dm)^T mu.
+template <class Pat, class Sw>
+__device__ __forceinline__ void rnea_vjp_rev(const Pat& pat, const Rec& rec, const float (&q)[7],
+                                             const float (&qd)[7], const float (&cq)[Pat::N],
+                                             const float (&sq)[Pat::N], const Sw& sw,
+                                             const float (&mu)[Pat::N], float (&gq)[Pat::N],
+                                             float (&gqd)[Pat::N], float (&gm)[Pat::N]) {
+  constexpr int N = Pat::N;
+  float ell[N], ellb[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    ellb[i] = 0.f;
+    ell[i] = (i == 0 ? 0.f : rec.lf(i - 1, LF_L)) + (pat.type(i) == 1 ? q[i] : 0.f);
   }
   // ---- reverse of the backward sweep (base to tip): link wrench adjoints
   V3 Fb[N], Nb[N];
@@ -132,16 +170,17 @@ __device__ __forceinline__ void rnea_vjp(const Pat& pat, const Rec& rec, const f
       if (i + 1 < N && pat.active(i + 1)) {
         const int j = i + 1;
         const float e = ell[j];
+        const V3 flj = sw.fl(j);
         V3 gb{fb.x + e * nb.y, fb.y - e * nb.x, fb.z};
-        V3 g = FL[j];
-        if (pat.type(j) == 0) g = to_parent(pat.axis(j), cq[j], sq[j], FL[j]);
+        V3 g = flj;
+        if (pat.type(j) == 0) g = to_parent(pat.axis(j), cq[j], sq[j], flj);
         ellb[j] += -nb.x * g.y + nb.y * g.x;
         V3 nbj = nb, fbj = gb;
         if (pat.type(j) == 0) {
           const int a = pat.axis(j);
           nbj = to_child(a, cq[j], sq[j], nb);
           fbj = to_child(a, cq[j], sq[j], gb);
-          gq[j] += dot3(nbj, axis_x(a, NL[j])) + dot3(fbj, axis_x(a, FL[j]));
+          gq[j] += dot3(nbj, axis_x(a, sw.nl(j))) + dot3(fbj, axis_x(a, flj));
         }
         fb = fbj;
         nb = nbj;
@@ -156,13 +195,13 @@ __device__ __forceinline__ void rnea_vjp(const Pat& pat, const Rec& rec, const f
       if (!pat.active(i)) continue;
       const float c = rec.lf(i, LF_C), m = rec.lf(i, LF_M);
       const float Ix = rec.lf(i, LF_IX), Iy = rec.lf(i, LF_IY), Iz = rec.lf(i, LF_IZ);
-      const V3 w = W[i], wd = WD[i];
+      const V3 w = sw.w(i), wd = sw.wd(i);
       // F = m (acc + c K(w, wd)), N = I wd + w x (I w)
       accb.x += m * Fb[i].x;
       accb.y += m * Fb[i].y;
       accb.z += m * Fb[i].z;
       kz_adj(w, V3{m * c * Fb[i].x, m * c * Fb[i].y, m * c * Fb[i].z}, wb, wdb);
-      gm[i] += (dot3(Fb[i], F[i]) + dot3(Nb[i], Nm[i])) / m;
+      gm[i] += (dot3(Fb[i], sw.f(i)) + dot3(Nb[i], sw.nm(i))) / m;
       const V3 nb = Nb[i];
       wdb.x += Ix * nb.x;
       wdb.y += Iy * nb.y;
@@ -171,14 +210,14 @@ __device__ __forceinline__ void rnea_vjp(const Pat& pat, const Rec& rec, const f
       wb.y += nb.x * (Iz - Iy) * w.z + nb.z * (Iy - Ix) * w.x;
       wb.z += nb.x * (Iz - Iy) * w.y + nb.y * (Ix - Iz) * w.x;
       // joint i: parent quantities (link i-1, or the fixed base)
-      const V3 wp = i > 0 ? W[i - 1] : V3{0.f, 0.f, 0.f};
-      const V3 wdp = i > 0 ? WD[i - 1] : V3{0.f, 0.f, 0.f};
+      const V3 wp = i > 0 ? sw.w(i - 1) : V3{0.f, 0.f, 0.f};
+      const V3 wdp = i > 0 ? sw.wd(i - 1) : V3{0.f, 0.f, 0.f};
       V3 wpb, wdpb, apb;
       if (pat.type(i) == 0) {
         const int a = pat.axis(i);
         const V3 wr = to_child(a, cq[i], sq[i], wp);
         const V3 wdr = to_child(a, cq[i], sq[i], wdp);
-        const V3 apr = ACC[i];
+        const V3 apr = sw.acc(i);
         const V3 wrxa = cross_axis(wr, a);
         gqd[i] += compc(wb, a) + dot3(wdb, wrxa);
         const V3 axwdb = axis_x(a, wdb);
@@ -281,14 +320,15 @@ __device__ __forceinline__ void substep_record(const Pat& pat, const Rec& rec, c
   }
 }
 
-// Adjoint of one substep given its record (start state q, qd, joint
-// trigonometry, Cholesky factor, acceleration and drive stiffness).
-template <class Pat>
-__device__ __forceinline__ void substep_adjoint_rec(
+// Adjoint of one substep given its start state (q, qd, joint trigonometry),
+// the Cholesky factor, the drive stiffness and the inverse-dynamics sweeps
+// (accessor sw).
+template <class Pat, class Sw>
+__device__ __forceinline__ void substep_adjoint_sw(
     const Pat& pat, const Rec& rec, const float (&q)[7], const float (&qd)[7],
     const float (&cq)[Pat::N], const float (&sq)[Pat::N], const float (&M)[Pat::N][Pat::N],
-    const float (&inv)[Pat::N], const float (&acc)[Pat::N], const float (&ks)[Pat::N], float h,
-    float grav, float (&lq)[7], float (&lqd)[7], float (&lqs)[7], float (&lm)[7]) {
+    const float (&inv)[Pat::N], const float (&ks)[Pat::N], const Sw& sw, float h,
+    float (&lq)[7], float (&lqd)[7], float (&lqs)[7], float (&lm)[7]) {
   constexpr int N = Pat::N;
   float mu[N], gq[N], gqd[N], gm[N];
 #pragma unroll
@@ -302,7 +342,7 @@ __device__ __forceinline__ void substep_adjoint_rec(
     mu[i] = lqd[i];        // qd' = qd + dqd
   }
   chol_apply(pat, M, inv, mu);
-  rnea_vjp(pat, rec, q, qd, acc, cq, sq, grav, mu, gq, gqd, gm);
+  rnea_vjp_rev(pat, rec, q, qd, cq, sq, sw, mu, gq, gqd, gm);
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     if (!pat.active(i)) continue;
@@ -326,7 +366,9 @@ __device__ __forceinline__ void substep_adjoint(const Pat& pat, const Rec& rec, 
   constexpr int N = Pat::N;
   float cq[N], sq[N], M[N][N], inv[N], acc[N], ks[N], dqd[N];
   substep_record(pat, rec, q, qd, qs, h, grav, cq, sq, M, inv, acc, ks, dqd);
-  substep_adjoint_rec(pat, rec, q, qd, cq, sq, M, inv, acc, ks, h, grav, lq, lqd, lqs, lm);
+  SweepArrays<N> sw;
+  id_sweeps(pat, rec, q, qd, acc, cq, sq, grav, sw);
+  substep_adjoint_sw(pat, rec, q, qd, cq, sq, M, inv, ks, sw, h, lq, lqd, lqs, lm);
 }
 
 }  // namespace sg

@@ -67,9 +67,10 @@ struct sg_ctx {
   // differentiable rollout: checkpoint scratch and the last forward's shape
   float* d_ckpt = nullptr;
   size_t ckpt_floats = 0;
-  float* d_replay = nullptr;       // warp-pair backward: two segments of substep records
+  float* d_replay = nullptr;       // pipelined backward: segment buffers of substep records
   size_t replay_floats = 0;
   bool use_replay = false;
+  bool replay_prefilled = false;   // replay buffer 0 holds the last forward's last segment
   bool diff_ready = false;
   int diff_T = 0, diff_substeps = 0, diff_every = 0;
   float diff_dt = 0.f;
@@ -741,7 +742,7 @@ sg_status sg_diff_forward(sg_ctx* ctx, const float* actions_dev, int32_t T, floa
     if (e != cudaSuccess) return cuda_err(ctx, e, "sg_diff_forward: checkpoint buffer");
     ctx->ckpt_floats = need;
   }
-  // replay buffers of the warp-pair backward (above the cap: the one-warp backward)
+  // replay buffers of the pipelined backward (above the cap: the one-warp backward)
   const size_t rneed = sg::replay_floats(ckpt_every, substeps, ctx->plan.num_slots);
   ctx->use_replay = rneed <= sg::kMaxReplayFloats;
   if (ctx->use_replay && rneed > ctx->replay_floats) {
@@ -764,6 +765,7 @@ sg_status sg_diff_forward(sg_ctx* ctx, const float* actions_dev, int32_t T, floa
   sg::DiffArgs a = diff_args(ctx);
   a.actions = actions_dev;
   a.ee = ee_dev;
+  ctx->replay_prefilled = ctx->use_replay;
   return cuda_err(ctx, sg::launch_diff_forward(a, ctx->stream), "sg_diff_forward");
 }
 
@@ -782,6 +784,10 @@ sg_status sg_diff_backward(sg_ctx* ctx, const float* actions_dev, const float* d
   a.dmass = dmass_dev;
   a.dq0 = dq0_dev;
   a.dqd0 = dqd0_dev;
+  // the first reverse pass after a forward starts from the records the forward
+  // left in buffer 0; later ones (which overwrote it) replay that segment too
+  a.prefilled = ctx->replay_prefilled ? 1 : 0;
+  ctx->replay_prefilled = false;
   return cuda_err(ctx, sg::launch_diff_backward(a, ctx->stream), "sg_diff_backward");
 }
 

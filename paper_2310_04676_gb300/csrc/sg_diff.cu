@@ -11,15 +11,18 @@
 // reversed substep by substep (the substep's input states are recomputed
 // from the step-start state), accumulating the cotangents of the targets and
 // of the link masses (see sg_adjoint.cuh for the substep adjoint).
-// Warp-pair backward: the same arithmetic split between two warps of one
-// block that share 32 chains.  The replay warp recomputes every substep of a
-// segment from its checkpoint -- state, joint trigonometry, Cholesky factor,
-// acceleration, drive stiffness -- into one of two global (L2-resident)
-// buffers, while the adjoint warp runs the reverse sweep of the previous
-// segment from the other buffer; mbarriers in shared memory hand the buffers
-// back and forth (bounded waits: a wait that runs out sets DEVERR_TIMEOUT and
-// both warps leave).  The adjoint warp's serial path per substep drops to
-// the triangular solve and the reverse RNEA.
+// Pipelined backward: the same arithmetic split between three warps that
+// share 32 chains.  Two replay warps recompute, segment by segment, every
+// substep from the segment's checkpoint -- state, joint trigonometry,
+// Cholesky factor, drive stiffness and the inverse-dynamics sweeps at the
+// substep's acceleration (the part of the substep adjoint that does not
+// depend on the cotangent) -- into global segment buffers; the adjoint warp
+// stages each substep's record in shared memory with one bulk copy and runs
+// only the triangular solve and the reversed sweeps.  mbarriers hand the
+// buffers back and forth (bounded waits: a wait that runs out sets
+// DEVERR_TIMEOUT and the warps leave).  With replay buffers the forward
+// kernel writes the last segment's records itself, so the first reverse pass
+// after it starts without waiting for a replay.
 #include <cuda_runtime.h>
 
 #include "sg_adjoint.cuh"
@@ -147,6 +150,131 @@ __device__ __forceinline__ void write_final_grads(const Pat& pat, const DiffArgs
   }
 }
 
+// ---- substep records of the pipelined backward (see below) --------------
+enum RecordField {
+  RF_Q = 0, RF_QD = 7, RF_CQ = 14, RF_SQ = 21, RF_KS = 28, RF_INV = 35, RF_L = 42,
+  RF_W = 63, RF_WD = 84, RF_ACC = 105, RF_F = 126, RF_NM = 147, RF_FL = 168, RF_NL = 189
+};
+static_assert(RF_NL + 3 * kMaxLinks == kReplayFields, "record layout");
+
+constexpr int kPipeWarps = kReplayWarps + 1;
+constexpr int kPipeBars = 3 + 2 * kReplayBufs;   // params, ready[B], freed[B], full[2]
+constexpr unsigned kRecordBytes = kReplayFields * kWarp * sizeof(float);
+constexpr unsigned long long kHandoffNs = 2000000000ull;   // bound of every wait (2 s)
+
+// strictly lower triangle of L, row by row: (i, j), i > j
+__device__ __forceinline__ constexpr int tri_lo(int i, int j) { return i * (i - 1) / 2 + j; }
+
+// record of buffer b, chain group g, substep j of the segment: [field][lane]
+__device__ __forceinline__ float* record_at(const DiffArgs& a, int b, int g, int j) {
+  const size_t per_seg = (size_t)a.ckpt_every * a.substeps;
+  return a.replay + (((size_t)b * a.num_warps + g) * per_seg + j) * (kReplayFields * kWarp);
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Wait for completion `m` (0-based) of a barrier's phases, i.e. parity m & 1,
+// bounded in time; warp-uniform verdict, DEVERR_TIMEOUT on failure.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, unsigned m, int* err, int lane) {
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_timed(bar, m & 1u, kHandoffNs));
+  if (!ok && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+  return ok;
+}
+
+// id_sweeps output written straight into a record (p: record + lane)
+struct RecordStore {
+  float* p;
+  __device__ __forceinline__ void put(int f, V3 v) const {
+    p[f * kWarp] = v.x;
+    p[(f + 1) * kWarp] = v.y;
+    p[(f + 2) * kWarp] = v.z;
+  }
+  __device__ __forceinline__ void fwd(int i, V3 w, V3 wd, V3 acc, V3 f, V3 n) const {
+    put(RF_W + 3 * i, w);
+    put(RF_WD + 3 * i, wd);
+    put(RF_ACC + 3 * i, acc);
+    put(RF_F + 3 * i, f);
+    put(RF_NM + 3 * i, n);
+  }
+  __device__ __forceinline__ void bwd(int i, V3 f, V3 n) const {
+    put(RF_FL + 3 * i, f);
+    put(RF_NL + 3 * i, n);
+  }
+};
+
+// the sweeps of a record in shared memory (p: record + lane), as read by
+// rnea_vjp_rev
+struct RecordView {
+  const float* p;
+  __device__ __forceinline__ V3 at(int f) const {
+    return V3{p[f * kWarp], p[(f + 1) * kWarp], p[(f + 2) * kWarp]};
+  }
+  __device__ __forceinline__ V3 w(int i) const { return at(RF_W + 3 * i); }
+  __device__ __forceinline__ V3 wd(int i) const { return at(RF_WD + 3 * i); }
+  __device__ __forceinline__ V3 acc(int i) const { return at(RF_ACC + 3 * i); }
+  __device__ __forceinline__ V3 f(int i) const { return at(RF_F + 3 * i); }
+  __device__ __forceinline__ V3 nm(int i) const { return at(RF_NM + 3 * i); }
+  __device__ __forceinline__ V3 fl(int i) const { return at(RF_FL + 3 * i); }
+  __device__ __forceinline__ V3 nl(int i) const { return at(RF_NL + 3 * i); }
+};
+
+template <class Pat>
+__device__ __forceinline__ void put_state(const Pat& pat, float* p, const float (&q)[7],
+                                          const float (&qd)[7], const float (&cq)[Pat::N],
+                                          const float (&sq)[Pat::N], const float (&ks)[Pat::N],
+                                          const float (&inv)[Pat::N],
+                                          const float (&M)[Pat::N][Pat::N]) {
+#pragma unroll
+  for (int i = 0; i < Pat::N; ++i) {
+    if (!pat.active(i)) continue;
+    p[(RF_Q + i) * kWarp] = q[i];
+    p[(RF_QD + i) * kWarp] = qd[i];
+    p[(RF_CQ + i) * kWarp] = cq[i];
+    p[(RF_SQ + i) * kWarp] = sq[i];
+    p[(RF_KS + i) * kWarp] = ks[i];
+    p[(RF_INV + i) * kWarp] = inv[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k)
+      if (pat.active(k)) p[(RF_L + tri_lo(i, k)) * kWarp] = M[i][k];
+  }
+}
+
+template <class Pat>
+__device__ __forceinline__ void get_state(const Pat& pat, const float* p, float (&q)[7],
+                                          float (&qd)[7], float (&cq)[Pat::N],
+                                          float (&sq)[Pat::N], float (&ks)[Pat::N],
+                                          float (&inv)[Pat::N], float (&M)[Pat::N][Pat::N]) {
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    q[i] = 0.f;
+    qd[i] = 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < Pat::N; ++i) {
+    cq[i] = 1.f;
+    sq[i] = 0.f;
+    ks[i] = 0.f;
+    inv[i] = 0.f;
+#pragma unroll
+    for (int k = 0; k < Pat::N; ++k) M[i][k] = 0.f;
+    if (!pat.active(i)) continue;
+    q[i] = p[(RF_Q + i) * kWarp];
+    qd[i] = p[(RF_QD + i) * kWarp];
+    cq[i] = p[(RF_CQ + i) * kWarp];
+    sq[i] = p[(RF_SQ + i) * kWarp];
+    ks[i] = p[(RF_KS + i) * kWarp];
+    inv[i] = p[(RF_INV + i) * kWarp];
+#pragma unroll
+    for (int k = 0; k < i; ++k)
+      if (pat.active(k)) M[i][k] = p[(RF_L + tri_lo(i, k)) * kWarp];
+  }
+}
+
 template <class Pat>
 __device__ __forceinline__ void diff_forward_chain(const DiffArgs& a, const Pat& pat,
                                                    const Rec& rec, int slot) {
@@ -163,14 +291,32 @@ __device__ __forceinline__ void diff_forward_chain(const DiffArgs& a, const Pat&
     q[i] = a.q[(size_t)i * a.num_slots + slot];
     qd[i] = a.qd[(size_t)i * a.num_slots + slot];
   }
+  constexpr int N = Pat::N;
   const size_t E = (size_t)a.num_envs;
-  float cq[Pat::N], sq[Pat::N];            // trigonometry of q, carried across substeps
+  // with replay buffers, the last segment's substep records go to buffer 0
+  // (the reverse pass starts from them instead of replaying that segment)
+  const int t_rec = a.replay ? (a.nseg - 1) * a.ckpt_every : a.T;
+  const int g = slot / kWarp, lane = slot % kWarp;
+  float cq[N], sq[N];                      // trigonometry of q, carried across substeps
   joint_sincos(pat, q, cq, sq);
   for (int t = 0; t < a.T; ++t) {
     if (t % a.ckpt_every == 0) put_ckpt(pat, a, t / a.ckpt_every, slot, q, qd);
     read_targets(pat, a, t, s, qs);
-    for (int k = 0; k < a.substeps; ++k)
-      chain_substep_trig(pat, rec, q, qd, qs, cq, sq, a.h, kGravity);
+    if (t < t_rec) {
+      for (int k = 0; k < a.substeps; ++k)
+        chain_substep_trig(pat, rec, q, qd, qs, cq, sq, a.h, kGravity);
+    } else {
+      for (int k = 0; k < a.substeps; ++k) {
+        float M[N][N], inv[N], acc[N], ks[N], dqd[N];
+        substep_record(pat, rec, q, qd, qs, a.h, kGravity, cq, sq, M, inv, acc, ks, dqd);
+        float* p = record_at(a, 0, g, (t - t_rec) * a.substeps + k) + lane;
+        put_state(pat, p, q, qd, cq, sq, ks, inv, M);
+        RecordStore st{p};
+        id_sweeps(pat, rec, q, qd, acc, cq, sq, kGravity, st);
+        integrate(pat, q, qd, dqd, a.h);
+      }
+      joint_sincos(pat, q, cq, sq);
+    }
     V3 tip, r0, r1, r2;
     chain_tip_trig(pat, rec, q, cq, sq, tip, r0, r1, r2);
     if (s.valid) {
@@ -308,91 +454,32 @@ __global__ void __launch_bounds__(kDiffThreads) diff_backward_kernel(DiffArgs a)
   diff_dispatch<true>(a);
 }
 
-// ---- warp-pair backward --------------------------------------------------
-enum ReplayField { RF_Q = 0, RF_QD = 7, RF_CQ = 14, RF_SQ = 21, RF_ACC = 28, RF_KS = 35,
-                   RF_INV = 42, RF_L = 49 };
-
-// strictly lower triangle of L, row by row: (i, j), i > j
-__device__ __forceinline__ constexpr int tri_lo(int i, int j) { return i * (i - 1) / 2 + j; }
-
-// buffer b, substep j of the segment, field f
-__device__ __forceinline__ float* replay_at(const DiffArgs& a, int b, int j, int f, int slot) {
-  return a.replay + (((size_t)b * a.ckpt_every * a.substeps + j) * kReplayFields + f) * a.num_slots +
-         slot;
-}
-
-template <class Pat>
-__device__ __forceinline__ void replay_put(const Pat& pat, const DiffArgs& a, int b, int j,
-                                           int slot, const float (&q)[7], const float (&qd)[7],
-                                           const float (&cq)[Pat::N], const float (&sq)[Pat::N],
-                                           const float (&M)[Pat::N][Pat::N],
-                                           const float (&inv)[Pat::N], const float (&acc)[Pat::N],
-                                           const float (&ks)[Pat::N]) {
-  const size_t NS = a.num_slots;
-  float* p = replay_at(a, b, j, 0, slot);
-#pragma unroll
-  for (int i = 0; i < Pat::N; ++i) {
-    if (!pat.active(i)) continue;
-    p[(RF_Q + i) * NS] = q[i];
-    p[(RF_QD + i) * NS] = qd[i];
-    p[(RF_CQ + i) * NS] = cq[i];
-    p[(RF_SQ + i) * NS] = sq[i];
-    p[(RF_ACC + i) * NS] = acc[i];
-    p[(RF_KS + i) * NS] = ks[i];
-    p[(RF_INV + i) * NS] = inv[i];
-#pragma unroll
-    for (int k = 0; k < i; ++k)
-      if (pat.active(k)) p[(RF_L + tri_lo(i, k)) * NS] = M[i][k];
-  }
-}
-
-template <class Pat>
-__device__ __forceinline__ void replay_get(const Pat& pat, const DiffArgs& a, int b, int j,
-                                           int slot, float (&q)[7], float (&qd)[7],
-                                           float (&cq)[Pat::N], float (&sq)[Pat::N],
-                                           float (&M)[Pat::N][Pat::N], float (&inv)[Pat::N],
-                                           float (&acc)[Pat::N], float (&ks)[Pat::N]) {
-  const size_t NS = a.num_slots;
-  const float* p = replay_at(a, b, j, 0, slot);   // read from L2 (__ldcg): written by the partner warp
-#pragma unroll
-  for (int i = 0; i < 7; ++i) {
-    q[i] = 0.f;
-    qd[i] = 0.f;
-  }
-#pragma unroll
-  for (int i = 0; i < Pat::N; ++i) {
-    cq[i] = 1.f;
-    sq[i] = 0.f;
-    acc[i] = 0.f;
-    ks[i] = 0.f;
-    inv[i] = 0.f;
-#pragma unroll
-    for (int k = 0; k < Pat::N; ++k) M[i][k] = 0.f;
-    if (!pat.active(i)) continue;
-    q[i] = __ldcg(p + (RF_Q + i) * NS);
-    qd[i] = __ldcg(p + (RF_QD + i) * NS);
-    cq[i] = __ldcg(p + (RF_CQ + i) * NS);
-    sq[i] = __ldcg(p + (RF_SQ + i) * NS);
-    acc[i] = __ldcg(p + (RF_ACC + i) * NS);
-    ks[i] = __ldcg(p + (RF_KS + i) * NS);
-    inv[i] = __ldcg(p + (RF_INV + i) * NS);
-#pragma unroll
-    for (int k = 0; k < i; ++k)
-      if (pat.active(k)) M[i][k] = __ldcg(p + (RF_L + tri_lo(i, k)) * NS);
-  }
-}
-
-// Replay warp: segments last first, each into buffer (order & 1).
+// ---- pipelined backward ----------------------------------------------------
+// kReplayWarps + 1 warps share a group of 32 chains: the replay warps and the
+// adjoint warp.  Replay warp r takes the segments of order r, r + R, ... (R
+// replay warps; order 0 = the last segment): from the segment's checkpoint
+// it recomputes every
+// substep -- start state, joint trigonometry, Cholesky factor, drive
+// stiffness -- and the inverse-dynamics sweeps at the substep's acceleration
+// (link velocities, accelerations, inertial and transmitted wrenches: the
+// part of the substep adjoint that does not depend on the cotangent), and
+// writes them as one record per substep into buffer order % (R + 1).  The adjoint
+// warp takes the orders in sequence; it copies each substep's record into
+// shared memory with one bulk copy, one substep ahead, and runs the solve and
+// the reversed sweeps only.
+// Replay warp r: segments of order r, r + R, ..., each into buffer order % (R + 1).
 template <class Pat>
 __device__ __forceinline__ void replay_role(const DiffArgs& a, const Pat& pat, const Rec& rec,
-                                            int slot, uint64_t* ready, uint64_t* freed, int lane) {
+                                            int g, int slot, int lane, int r, uint64_t* ready,
+                                            uint64_t* freed) {
   constexpr int N = Pat::N;
   const SlotInfo s = slot_info(a, slot);
-  unsigned ph_free[2] = {0u, 0u};
-  for (int order = 0; order < a.nseg; ++order) {
-    const int seg = a.nseg - 1 - order, b = order & 1;
-    if (order >= 2 && !pair_wait_long(freed + b, ph_free[b], a.err, lane)) return;
-    __threadfence();
+  // order 0 was written by the forward kernel when a.prefilled
+  for (int order = (a.prefilled ? 1 : 0) + r; order < a.nseg; order += kReplayWarps) {
+    const int seg = a.nseg - 1 - order, b = order % kReplayBufs;
+    // the buffer's previous segment (order - R - 1) has been consumed
+    if (order >= kReplayBufs && !wait_phase(freed + b, order / kReplayBufs - 1, a.err, lane))
+      return;
     const int t0 = seg * a.ckpt_every;
     const int t1 = min(a.T, t0 + a.ckpt_every);
     float q[7], qd[7], qs[7];
@@ -402,20 +489,26 @@ __device__ __forceinline__ void replay_role(const DiffArgs& a, const Pat& pat, c
       for (int k = 0; k < a.substeps; ++k) {
         float cq[N], sq[N], M[N][N], inv[N], acc[N], ks[N], dqd[N];
         substep_record(pat, rec, q, qd, qs, a.h, kGravity, cq, sq, M, inv, acc, ks, dqd);
-        replay_put(pat, a, b, (t - t0) * a.substeps + k, slot, q, qd, cq, sq, M, inv, acc, ks);
+        float* p = record_at(a, b, g, (t - t0) * a.substeps + k) + lane;
+        put_state(pat, p, q, qd, cq, sq, ks, inv, M);
+        RecordStore st{p};
+        id_sweeps(pat, rec, q, qd, acc, cq, sq, kGravity, st);
         integrate(pat, q, qd, dqd, a.h);
       }
     }
-    __threadfence();   // the buffer is in L2 before the partner is told
+    // the records are visible to the adjoint warp's bulk copies before it is told
+    fence_proxy_async_global();
+    __threadfence();
     mbar_arrive(ready + b);
   }
 }
 
-// Adjoint warp: the reverse sweep, segment by segment from the replay buffers.
+// Adjoint warp: the reverse sweep, segment by segment, substep records
+// staged in shared memory (two slots, one substep ahead).
 template <class Pat>
 __device__ __forceinline__ void adjoint_role(const DiffArgs& a, const Pat& pat, const Rec& rec,
-                                             int slot, uint64_t* ready, uint64_t* freed,
-                                             int lane) {
+                                             int g, int slot, int lane, uint64_t* ready,
+                                             uint64_t* freed, uint64_t* full, float* stage) {
   constexpr int N = Pat::N;
   const SlotInfo s = slot_info(a, slot);
   const size_t E = (size_t)a.num_envs;
@@ -427,31 +520,51 @@ __device__ __forceinline__ void adjoint_role(const DiffArgs& a, const Pat& pat, 
     lm[i] = 0.f;
   }
   get_ckpt(pat, a, a.nseg, slot, qn, qdn);     // state after the last step
-  unsigned ph_ready[2] = {0u, 0u};
+  // record (buffer b, substep j) into slot m & 1
+  auto fetch = [&](int b, int j, unsigned m) {
+    __syncwarp();                              // every lane is done with the slot
+    if (lane == 0) {
+      fence_proxy_async_shared();
+      mbar_expect_tx(full + (m & 1u), kRecordBytes);
+      bulk_g2s(stage + (m & 1u) * (kReplayFields * kWarp), record_at(a, b, g, j), kRecordBytes,
+               full + (m & 1u));
+    }
+  };
+  unsigned n = 0;                              // substeps consumed so far
+  if (a.prefilled) mbar_arrive(ready);         // buffer 0 holds order 0 already
   for (int order = 0; order < a.nseg; ++order) {
-    const int seg = a.nseg - 1 - order, b = order & 1;
-    if (!pair_wait_long(ready + b, ph_ready[b], a.err, lane)) return;
+    const int seg = a.nseg - 1 - order, b = order % kReplayBufs;
+    if (!wait_phase(ready + b, order / kReplayBufs, a.err, lane)) return;
     __threadfence();
+    fence_proxy_async_global();
     const int t0 = seg * a.ckpt_every;
     const int t1 = min(a.T, t0 + a.ckpt_every);
+    fetch(b, (t1 - t0) * a.substeps - 1, n);
     for (int t = t1 - 1; t >= t0; --t) {
       if (s.valid) {
-        const float* g = a.dl_dee + (((size_t)t * E + s.env) * kMaxChains + s.c) * 3;
+        const float* gp = a.dl_dee + (((size_t)t * E + s.env) * kMaxChains + s.c) * 3;
         float gq[N];
 #pragma unroll
         for (int i = 0; i < N; ++i) gq[i] = 0.f;
-        tip_vjp(pat, rec, qn, V3{g[0], g[1], g[2]}, gq);
+        tip_vjp(pat, rec, qn, V3{gp[0], gp[1], gp[2]}, gq);
 #pragma unroll
         for (int i = 0; i < N; ++i) lq[i] += gq[i];
       }
       float lqs[7];
 #pragma unroll
       for (int i = 0; i < 7; ++i) lqs[i] = 0.f;
-      for (int k = a.substeps - 1; k >= 0; --k) {
-        float q[7], qd[7], cq[N], sq[N], M[N][N], inv[N], acc[N], ks[N];
-        replay_get(pat, a, b, (t - t0) * a.substeps + k, slot, q, qd, cq, sq, M, inv, acc, ks);
-        substep_adjoint_rec(pat, rec, q, qd, cq, sq, M, inv, acc, ks, a.h, kGravity, lq, lqd, lqs,
-                            lm);
+      for (int k = a.substeps - 1; k >= 0; --k, ++n) {
+        const int j = (t - t0) * a.substeps + k;
+        if (!wait_phase(full + (n & 1u), n >> 1, a.err, lane)) {
+          mbar_wait_timed(full + (n & 1u), (n >> 1) & 1u, kHandoffNs);   // the copy in flight
+          return;
+        }
+        if (j > 0) fetch(b, j - 1, n + 1);
+        const float* p = stage + (n & 1u) * (kReplayFields * kWarp) + lane;
+        float q[7], qd[7], cq[N], sq[N], M[N][N], inv[N], ks[N];
+        get_state(pat, p, q, qd, cq, sq, ks, inv, M);
+        substep_adjoint_sw(pat, rec, q, qd, cq, sq, M, inv, ks, RecordView{p}, a.h, lq, lqd, lqs,
+                           lm);
         if (k == 0) {
 #pragma unroll
           for (int i = 0; i < 7; ++i) qn[i] = q[i];   // the state before step t
@@ -459,37 +572,41 @@ __device__ __forceinline__ void adjoint_role(const DiffArgs& a, const Pat& pat, 
       }
       write_action_grads(pat, a, s, t, lqs);
     }
-    __threadfence();
+    __syncwarp();
     mbar_arrive(freed + b);
   }
   write_final_grads(pat, a, s, lq, lqd, lm);
 }
 
-constexpr int kReplayBars = 5;   // tma, ready[2], free[2]
-
-__global__ void __launch_bounds__(kDiffPairThreads) diff_backward_pair_kernel(DiffArgs a) {
+__global__ void __launch_bounds__(kDiffPipeThreads) diff_backward_pipe_kernel(DiffArgs a) {
   extern __shared__ __align__(128) float smem[];
   const int w = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int pairs = blockDim.x >> 6;
-  const int pair = w >> 1, role = w & 1;
-  float* rec = smem + (size_t)pair * kRecordFloats;
-  uint64_t* bar0 = reinterpret_cast<uint64_t*>(smem + (size_t)pairs * kRecordFloats);
-  uint64_t* bars = bar0 + (size_t)pair * kReplayBars;
-  // start-up: warp 0 initialises every pair's barriers before any warp leaves
-  if (w == 0 && lane < pairs) {
-    uint64_t* b = bar0 + (size_t)lane * kReplayBars;
-    mbar_init(b + 0, 1);
-    for (int k = 1; k < kReplayBars; ++k) mbar_init(b + k, kWarp);
+  const int groups = blockDim.x / (kPipeWarps * kWarp);
+  // warps 0 .. groups-1: first replay warp of each group, then the second
+  // replay warps, ..., then the adjoint warps
+  const int grp = w % groups, role = w / groups;
+  float* rec = smem + (size_t)grp * kRecordFloats;
+  float* stage = smem + (size_t)groups * kRecordFloats + (size_t)grp * 2 * kReplayFields * kWarp;
+  uint64_t* bar0 = reinterpret_cast<uint64_t*>(
+      smem + (size_t)groups * (kRecordFloats + 2 * kReplayFields * kWarp));
+  uint64_t* bars = bar0 + (size_t)grp * kPipeBars;
+  // start-up: warp 0 initialises every group's barriers before any warp leaves
+  if (w == 0 && lane < groups) {
+    uint64_t* bb = bar0 + (size_t)lane * kPipeBars;
+    mbar_init(bb + 0, 1);
+    for (int k = 1; k < 1 + 2 * kReplayBufs; ++k) mbar_init(bb + k, kWarp);   // ready, freed
+    mbar_init(bb + 1 + 2 * kReplayBufs, 1);                                   // full[2]
+    mbar_init(bb + 2 + 2 * kReplayBufs, 1);
   }
   __syncthreads();
-  const int gw = blockIdx.x * pairs + pair;
-  if (gw >= a.num_warps) return;
-  const int wc = a.warp_class[gw];
+  const int g = blockIdx.x * groups + grp;
+  if (g >= a.num_warps) return;
+  const int wc = a.warp_class[g];
   if (role == 0 && lane == 0) {
     const unsigned bytes = (unsigned)record_bytes_dev(wc);
     mbar_expect_tx(bars, bytes);
-    bulk_g2s(rec, a.params + (size_t)gw * kRecordFloats, bytes, bars);
+    bulk_g2s(rec, a.params + (size_t)g * kRecordFloats, bytes, bars);
   }
   unsigned ph_tma = 0;
   if (!pair_wait(bars, ph_tma, a.err, lane)) {
@@ -497,10 +614,13 @@ __global__ void __launch_bounds__(kDiffPairThreads) diff_backward_pair_kernel(Di
     return;
   }
   const Rec r{rec + lane};
-  const int slot = gw * kWarp + lane;
+  const int slot = g * kWarp + lane;
   auto run = [&](const auto& pat) {
-    if (role == 0) replay_role(a, pat, r, slot, bars + 1, bars + 3, lane);
-    else adjoint_role(a, pat, r, slot, bars + 1, bars + 3, lane);
+    if (role < kReplayWarps)
+      replay_role(a, pat, r, g, slot, lane, role, bars + 1, bars + 1 + kReplayBufs);
+    else
+      adjoint_role(a, pat, r, g, slot, lane, bars + 1, bars + 1 + kReplayBufs,
+                   bars + 1 + 2 * kReplayBufs, stage);
   };
   switch (wc & 3) {
     case CLS_7R: run(Pat7R{}); break;
@@ -515,9 +635,10 @@ __global__ void __launch_bounds__(kDiffPairThreads) diff_backward_pair_kernel(Di
   }
 }
 
-size_t diff_pair_smem_bytes(int threads) {
-  const int pairs = threads / (2 * kWarp);
-  return (size_t)pairs * kRecordFloats * sizeof(float) + (size_t)pairs * kReplayBars * sizeof(uint64_t);
+size_t diff_pipe_smem_bytes(int threads) {
+  const int groups = threads / (kPipeWarps * kWarp);
+  return (size_t)groups * (kRecordFloats + 2 * kReplayFields * kWarp) * sizeof(float) +
+         (size_t)groups * kPipeBars * sizeof(uint64_t);
 }
 
 // link masses (and inertias, which scale with mass) from a caller array [E][J]
@@ -555,9 +676,9 @@ cudaError_t prepare_diff_kernels() {
   e = cudaFuncSetAttribute(diff_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)diff_smem_bytes(kDiffThreads));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(diff_backward_pair_kernel,
+  return cudaFuncSetAttribute(diff_backward_pipe_kernel,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)diff_pair_smem_bytes(kDiffPairThreads));
+                              (int)diff_pipe_smem_bytes(kDiffPipeThreads));
 }
 
 cudaError_t launch_diff_forward(const DiffArgs& a, cudaStream_t s) {
@@ -569,9 +690,9 @@ cudaError_t launch_diff_forward(const DiffArgs& a, cudaStream_t s) {
 
 cudaError_t launch_diff_backward(const DiffArgs& a, cudaStream_t s) {
   if (a.replay) {
-    const int pairs = kDiffPairThreads / (2 * kWarp);
-    diff_backward_pair_kernel<<<(a.num_warps + pairs - 1) / pairs, kDiffPairThreads,
-                                diff_pair_smem_bytes(kDiffPairThreads), s>>>(a);
+    const int groups = kDiffPipeThreads / (kPipeWarps * kWarp);
+    diff_backward_pipe_kernel<<<(a.num_warps + groups - 1) / groups, kDiffPipeThreads,
+                                diff_pipe_smem_bytes(kDiffPipeThreads), s>>>(a);
     return cudaGetLastError();
   }
   const int wpb = kDiffThreads / kWarp;

@@ -10,8 +10,12 @@
 namespace sg {
 
 constexpr int kDiffThreads = 128;
-constexpr int kDiffPairThreads = 128;  // two warp pairs per block (replay + adjoint warps)
-constexpr int kReplayFields = 70;      // per substep: q, qd, cos q, sin q, qdd, k_s, 1/L_ii (7 each), L (21)
+constexpr int kReplayWarps = 2;        // replay warps per group of 32 chains
+constexpr int kDiffPipeThreads = 2 * (kReplayWarps + 1) * 32;   // two groups (replay warps + adjoint)
+// per substep record: q, qd, cos q, sin q, k_s, 1/L_ii (7 each), L (21), and
+// per link the inverse-dynamics sweep quantities w, wd, acc, F, N, f, n (21 each)
+constexpr int kReplayFields = 210;
+constexpr int kReplayBufs = kReplayWarps + 1;   // segment buffers in flight
 constexpr int kMaxCkptEvery = 32;      // checkpoint interval limit (thread-local segment buffer)
 constexpr int kMaxDiffSubsteps = 16;   // substeps limit of the differentiable rollout
 
@@ -30,17 +34,18 @@ struct DiffArgs {
   float* dmass;            // [E][J]            (backward output)
   float* dq0;              // [E][J] or null    (backward output)
   float* dqd0;             // [E][J] or null    (backward output)
-  float* replay;           // [2][ckpt_every * substeps][kReplayFields][NS] or null
+  float* replay;           // [kReplayBufs][groups][ckpt_every * substeps][kReplayFields][32] or null
   int32_t* err;
+  int prefilled;           // backward: buffer 0 holds the last segment's records (forward wrote them)
   int num_warps, num_slots, num_envs, max_joints, T, substeps, ckpt_every, nseg;
   float h;
 };
 
 constexpr size_t kMaxReplayFloats = (size_t)1 << 28;   // 1 GiB of replay buffers at most
 
-// Floats of the replay buffers of the warp-pair backward kernel.
+// Floats of the replay buffers of the pipelined backward kernel.
 inline size_t replay_floats(int ckpt_every, int substeps, int num_slots) {
-  return (size_t)2 * ckpt_every * substeps * kReplayFields * num_slots;
+  return (size_t)kReplayBufs * ckpt_every * substeps * kReplayFields * num_slots;
 }
 
 struct MassArgs {
@@ -63,8 +68,8 @@ const std::vector<int32_t>& context_env_dof(sg_ctx* ctx);
 
 cudaError_t prepare_diff_kernels();
 cudaError_t launch_diff_forward(const DiffArgs& a, cudaStream_t s);
-// Reverse pass: with a.replay set, the warp-pair kernel (one warp replays
-// the next segment's substeps while its partner runs the adjoint of the
+// Reverse pass: with a.replay set, the pipelined kernel (kReplayWarps warps
+// replay the next segments' substeps while another runs the adjoint of the
 // current one); otherwise the one-warp kernel.
 cudaError_t launch_diff_backward(const DiffArgs& a, cudaStream_t s);
 cudaError_t launch_set_mass(const MassArgs& m, cudaStream_t s);

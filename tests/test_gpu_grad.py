@@ -107,6 +107,30 @@ def test_checkpoint_interval_does_not_change_gradients():
             assert rel_env(da, ref[0]) <= 1e-5 and rel_env(dm, ref[1]) <= 1e-5
 
 
+@pytest.mark.parametrize("T,every", [(16, 8), (13, 4), (5, 8)])
+def test_second_backward_after_one_forward(T, every):
+    """The first reverse pass after a forward starts from the last segment's
+    substep records written by the forward kernel; a second reverse pass
+    (which overwrote them) recomputes that segment from its checkpoint.  Both
+    give the same gradients to rounding (1e-5 relative: the forward and
+    backward kernels are compiled apart), for a last segment that is full,
+    partial, or the only one."""
+    desc = W.make_desc(["7R", "7P", "4R", "14B"] * 20)
+    S = 2
+    acts = W.joint_targets(desc, T)
+    tg = W.loss_targets(desc, T)
+    env = sg.Env(desc)
+    a = cuda(acts)
+    ee = env.diff_forward(a, DT, S, every)
+    nc = torch.as_tensor(desc["env_num_chains"], device="cuda")
+    chain_mask = (torch.arange(4, device="cuda")[None, :] < nc[:, None]).float()[None, :, :, None]
+    g = (2.0 * (ee - cuda(tg)) * chain_mask).contiguous()
+    da1, dm1 = [x.cpu().numpy() for x in env.diff_backward(a, g)]
+    da2, dm2 = [x.cpu().numpy() for x in env.diff_backward(a, g)]
+    assert np.isfinite(da1).all() and np.isfinite(dm1).all()
+    assert rel_env(da2, da1) <= 1e-5 and rel_env(dm2, dm1) <= 1e-5
+
+
 def test_diff_forward_leaves_state_and_matches_rollout():
     desc = W.make_desc(W.mixed_kinds(300, W.C3_FRACTIONS))
     T = 9
