@@ -109,7 +109,12 @@ KERNEL_SOURCES = {
                     "sg_device.cuh", "sg_kernels.cu"),
     "step_kernel_pair": ("sg_internal.h", "sg_kernels.h", "sg_rng.cuh", "sg_chain.cuh",
                          "sg_device.cuh", "sg_pair.cu"),
+    "diff_backward_pipe_kernel": ("sg_internal.h", "sg_chain.cuh", "sg_device.cuh",
+                                  "sg_adjoint.cuh", "sg_diff.h", "sg_diff.cu"),
 }
+# committed ncu summary holding each kernel's counters (default workload of its config)
+KERNEL_PROFILES = {"step_kernel": "step_kernel_c3.md", "step_kernel_pair": "step_kernel_c3.md",
+                   "diff_backward_pipe_kernel": "diff_backward_c4.md"}
 
 
 def kernel_source_hash(kernel):
@@ -126,8 +131,10 @@ def profiled_counter(kernel, name):
     """A per-launch counter (`traffic_bytes_per_launch`,
     `executed_flops_per_launch`) of `kernel` on the default workload, from the
     committed ncu summary, if it was taken from the current sources."""
-    p = os.path.join(ROOT, "profiles", "step_kernel_c3.md")
-    if not os.path.exists(p) or kernel not in KERNEL_SOURCES:
+    if kernel not in KERNEL_SOURCES:
+        return None
+    p = os.path.join(ROOT, "profiles", KERNEL_PROFILES[kernel])
+    if not os.path.exists(p):
         return None
     text = open(p).read()
     m = re.search(r"source_hash\[%s\]:\s*([0-9a-f]+)" % re.escape(kernel), text)
@@ -660,9 +667,11 @@ def run_adjoint_config(cx, with_error, name="C4", E=None, T=None, err_envs=16):
     peaks, src = load_peaks()
     props = cx.torch.cuda.get_device_properties(cx.dev)
     ms_b = sum(a["ms_bwd"]) / len(a["ms_bwd"])
-    rf = roofline("diff_backward_pipe_kernel", f_bwd, None, ms_b, props, peaks, src)
+    # the committed profile's counters belong to the C4 launch at its default size
+    profiled = name == "C4" and E is None and T is None and cx.args.gpus == 1
+    rf = roofline("diff_backward_pipe_kernel", f_bwd, None, ms_b, props, peaks, src,
+                  profiled=profiled)
     rf.pop("hbm_gbs", None), rf.pop("hbm_frac", None), rf.pop("algorithmic_bytes_per_launch", None)
-    rf["traffic"] = None
     out["roofline"] = rf
     out["flops_per_rollout"] = {"forward": f_fwd, "backward": f_bwd}
     out["ms_backward_kernel"] = ms_b
