@@ -108,9 +108,9 @@ KERNEL_SOURCES = {
     "step_kernel": ("sg_internal.h", "sg_kernels.h", "sg_rng.cuh", "sg_chain.cuh",
                     "sg_device.cuh", "sg_kernels.cu"),
     "step_kernel_pair": ("sg_internal.h", "sg_kernels.h", "sg_rng.cuh", "sg_chain.cuh",
-                         "sg_device.cuh", "sg_pair.cu"),
+                         "sg_device.cuh", "sg_pair.cuh", "sg_pair.cu"),
     "diff_backward_pipe_kernel": ("sg_internal.h", "sg_chain.cuh", "sg_device.cuh",
-                                  "sg_adjoint.cuh", "sg_diff.h", "sg_diff.cu"),
+                                  "sg_adjoint.cuh", "sg_pair.cuh", "sg_diff.h", "sg_diff.cu"),
 }
 # committed ncu summary holding each kernel's counters (default workload of its config)
 KERNEL_PROFILES = {"step_kernel": "step_kernel_c3.md", "step_kernel_pair": "step_kernel_c3.md",

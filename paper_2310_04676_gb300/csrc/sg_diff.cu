@@ -30,6 +30,7 @@
 #include "sg_device.cuh"
 #include "sg_diff.h"
 #include "sg_internal.h"
+#include "sg_pair.cuh"
 
 namespace sg {
 
@@ -331,6 +332,86 @@ __device__ __forceinline__ void diff_forward_chain(const DiffArgs& a, const Pat&
   put_ckpt(pat, a, a.nseg, slot, q, qd);
 }
 
+// Warp-pair forward (batches with a few warps of chains per SM): the substep
+// of every chain is split across two warps as in the warp-pair step kernel
+// (sg_pair.cuh).  Role 0 writes the checkpoints, role 1 the tool-tip
+// positions; with replay buffers, the last segment's substep records are
+// written as in the one-thread forward, role 1 the state part (state,
+// trigonometry, stiffness, factor) and role 0 the inverse-dynamics sweeps.
+template <class Pat>
+__device__ __forceinline__ void diff_forward_pair(const DiffArgs& a, const Pat& pat,
+                                                  const Rec& rec, int g, int lane, int role,
+                                                  float* xbuf, uint64_t* bar_x) {
+  constexpr int N = Pat::N;
+  const int slot = g * kWarp + lane;
+  const SlotInfo s = slot_info(a, slot);
+  float q[7], qd[7], qs[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    q[i] = 0.f;
+    qd[i] = 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (!pat.active(i)) continue;
+    q[i] = a.q[(size_t)i * a.num_slots + slot];
+    qd[i] = a.qd[(size_t)i * a.num_slots + slot];
+  }
+  const size_t E = (size_t)a.num_envs;
+  const int t_rec = a.replay ? (a.nseg - 1) * a.ckpt_every : a.T;
+  float cq[N], sq[N];
+  joint_sincos(pat, q, cq, sq);
+  unsigned ph_x = 0, xphase = 0;
+  for (int t = 0; t < a.T; ++t) {
+    if (role == 0 && t % a.ckpt_every == 0) put_ckpt(pat, a, t / a.ckpt_every, slot, q, qd);
+    read_targets(pat, a, t, s, qs);
+    for (int k = 0; k < a.substeps; ++k, ++xphase) {
+      float* xb = xbuf + (xphase & 1) * kXHalf;   // double-buffered exchange
+      float L[N][N], inv[N], dqd[N];
+      if (!pair_substep(pat, rec, q, qd, qs, cq, sq, a.h, xb, bar_x, ph_x, a.err, lane, role, L,
+                        inv, dqd))
+        return;
+      if (t >= t_rec) {
+        float* p = record_at(a, 0, g, (t - t_rec) * a.substeps + k) + lane;
+        if (role == 1) {
+          float ks[N];
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            ks[i] = 0.f;
+            if (!pat.active(i)) continue;
+            const float kp = rec.lf(i, LF_KP), kl = rec.lf(i, LF_KLIM);
+            const float lo = rec.lf(i, LF_QLO), hi = rec.lf(i, LF_QHI);
+            ks[i] = kp + ((q[i] > hi || q[i] < lo) ? kl : 0.f);
+          }
+          put_state(pat, p, q, qd, cq, sq, ks, inv, L);
+        } else {
+          const float hinv = 1.f / a.h;
+          float acc[N];
+#pragma unroll
+          for (int i = 0; i < N; ++i) acc[i] = pat.active(i) ? dqd[i] * hinv : 0.f;
+          RecordStore st{p};
+          id_sweeps(pat, rec, q, qd, acc, cq, sq, kGravity, st);
+        }
+      }
+      integrate(pat, q, qd, dqd, a.h);
+      joint_sincos(pat, q, cq, sq);
+    }
+    if (role == 1) {
+      V3 tip, r0, r1, r2;
+      chain_tip_trig(pat, rec, q, cq, sq, tip, r0, r1, r2);
+      if (s.valid) {
+        float* e = a.ee + (((size_t)t * E + s.env) * kMaxChains + s.c) * 3;
+        e[0] = tip.x;
+        e[1] = tip.y;
+        e[2] = tip.z;
+        if (s.c == 0)
+          for (int k = 3 * s.nc; k < 3 * kMaxChains; ++k) e[k] = 0.f;
+      }
+    }
+  }
+  if (role == 0) put_ckpt(pat, a, a.nseg, slot, q, qd);
+}
+
 template <class Pat>
 __device__ __forceinline__ void diff_backward_chain(const DiffArgs& a, const Pat& pat,
                                                     const Rec& rec, int slot) {
@@ -452,6 +533,58 @@ __global__ void __launch_bounds__(kDiffThreads) diff_forward_kernel(DiffArgs a) 
 
 __global__ void __launch_bounds__(kDiffThreads) diff_backward_kernel(DiffArgs a) {
   diff_dispatch<true>(a);
+}
+
+constexpr int kFwdPairBars = 2;   // params, exchange
+
+__global__ void __launch_bounds__(kDiffPairThreads) diff_forward_pair_kernel(DiffArgs a) {
+  extern __shared__ __align__(128) float smem[];
+  const int w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int pairs = blockDim.x >> 6;
+  // the first `pairs` warps take role 0, the rest role 1 (as in the step kernel)
+  const int pair = w % pairs, role = w / pairs;
+  float* rec = smem + (size_t)pair * kRecordFloats;
+  float* xbuf = smem + (size_t)pairs * kRecordFloats + (size_t)pair * kXFloats;
+  uint64_t* bar0 = reinterpret_cast<uint64_t*>(smem + (size_t)pairs * (kRecordFloats + kXFloats));
+  uint64_t* bars = bar0 + (size_t)pair * kFwdPairBars;
+  if (w == 0 && lane < pairs) {
+    mbar_init(bar0 + (size_t)lane * kFwdPairBars, 1);
+    mbar_init(bar0 + (size_t)lane * kFwdPairBars + 1, 2 * kWarp);
+  }
+  __syncthreads();
+  const int g = blockIdx.x * pairs + pair;
+  if (g >= a.num_warps) return;
+  const int wc = a.warp_class[g];
+  if (role == 0 && lane == 0) {
+    const unsigned bytes = (unsigned)record_bytes_dev(wc);
+    mbar_expect_tx(bars, bytes);
+    bulk_g2s(rec, a.params + (size_t)g * kRecordFloats, bytes, bars);
+  }
+  unsigned ph_tma = 0;
+  if (!pair_wait(bars, ph_tma, a.err, lane)) {
+    mbar_wait_bounded(bars, 0);   // second bounded chance for an in-flight copy
+    return;
+  }
+  const Rec r{rec + lane};
+  auto run = [&](const auto& pat) { diff_forward_pair(a, pat, r, g, lane, role, xbuf, bars + 1); };
+  switch (wc & 3) {
+    case CLS_7R: run(Pat7R{}); break;
+    case CLS_7P: run(Pat7P{}); break;
+    case CLS_4R: run(Pat4R{}); break;
+    default: {
+      int code;
+      const float cf = r.cf(CF_CODE);
+      memcpy(&code, &cf, 4);
+      run(PatGen{code, decode_slot(a.slot_info[g * kWarp + lane]).nchain});
+    }
+  }
+}
+
+size_t diff_fwd_pair_smem_bytes(int threads) {
+  const int pairs = threads / (2 * kWarp);
+  return (size_t)pairs * (kRecordFloats + kXFloats) * sizeof(float) +
+         (size_t)pairs * kFwdPairBars * sizeof(uint64_t);
 }
 
 // ---- pipelined backward ----------------------------------------------------
@@ -673,6 +806,9 @@ cudaError_t prepare_diff_kernels() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)diff_smem_bytes(kDiffThreads));
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(diff_forward_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)diff_fwd_pair_smem_bytes(kDiffPairThreads));
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(diff_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)diff_smem_bytes(kDiffThreads));
   if (e != cudaSuccess) return e;
@@ -682,6 +818,17 @@ cudaError_t prepare_diff_kernels() {
 }
 
 cudaError_t launch_diff_forward(const DiffArgs& a, cudaStream_t s) {
+  // a few warps of chains per SM: split each substep across a warp pair
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaGetLastError();
+  if (a.num_warps <= kDiffPairMaxWarpsPerSM * sms) {
+    const int pairs = kDiffPairThreads / (2 * kWarp);
+    diff_forward_pair_kernel<<<(a.num_warps + pairs - 1) / pairs, kDiffPairThreads,
+                               diff_fwd_pair_smem_bytes(kDiffPairThreads), s>>>(a);
+    return cudaGetLastError();
+  }
   const int wpb = kDiffThreads / kWarp;
   diff_forward_kernel<<<(a.num_warps + wpb - 1) / wpb, kDiffThreads, diff_smem_bytes(kDiffThreads),
                         s>>>(a);

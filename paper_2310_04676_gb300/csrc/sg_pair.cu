@@ -4,17 +4,14 @@
 // mixed envs are ~590 warps of chains for 608 schedulers), one thread per
 // chain leaves each scheduler with a single dependent instruction stream.
 // Here the substep of every chain is split across two warps that run
-// concurrently on the same SM:
-//   role 0 (dynamics): RNEA bias forces and the implicit drive right-hand side;
-//   role 1 (inertia):  composite-rigid-body mass matrix plus the drive
-//                      armature, then its Cholesky factorisation.
-// The two halves run concurrently; the roles then swap the right-hand side
-// and the factor through a double-buffered shared-memory exchange (one
-// mbarrier phase per substep, bounded waits: no block barrier after
-// start-up, and a wait that runs out sets DEVERR_TIMEOUT and the warp leaves,
-// so a partner is never left waiting forever).  Both roles then execute the
-// same triangular solve on the same operands and apply the same update, so
-// their copies of the chain state stay bit-identical.  The
+// concurrently on the same SM (sg_pair.cuh: role 0 the bias forces and the
+// drive right-hand side, role 1 the mass matrix and its Cholesky factor,
+// swapped through a double-buffered shared-memory exchange; bounded waits:
+// no block barrier after start-up, and a wait that runs out sets
+// DEVERR_TIMEOUT and the warp leaves, so a partner is never left waiting
+// forever).  Both roles then execute the same triangular solve on the same
+// operands and apply the same update, so their copies of the chain state
+// stay bit-identical.  The
 // observation rows are staged by both roles and written out half by each.
 // The arithmetic is that of the one-thread-per-chain kernel; the two kernels
 // agree to rounding (separately compiled code may contract multiply-adds
@@ -25,21 +22,14 @@
 #include "sg_device.cuh"
 #include "sg_internal.h"
 #include "sg_kernels.h"
+#include "sg_pair.cuh"
 #include "sg_rng.cuh"
 
 namespace sg {
 
 namespace {
 
-// exchange per pair and substep: the Cholesky factor (lower triangle with
-// 1/L_ii on the diagonal, packed row by row) and the right-hand side; two
-// buffers alternate between substeps
-constexpr int kTri = kMaxLinks * (kMaxLinks + 1) / 2;
-constexpr int kXHalf = (kTri + kMaxLinks) * kWarp;
-constexpr int kXFloats = 2 * kXHalf;
 constexpr int kPairBars = 3;                      // tma, exchange, stage
-
-__device__ __forceinline__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
 // kGlog: log2 of the lanes per env, a compile-time constant (see run_chain)
 template <int kGlog, class Pat>
@@ -103,43 +93,10 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
     }
     for (int k = 0; k < a.substeps; ++k, ++xphase) {
       float* xb = xbuf + (xphase & 1) * kXHalf;   // double-buffered exchange
-      if (role == 0) {
-        float bias[N], rhs[N], arm[N], Mdummy[N][N];
-        V3 F[N], Nm[N];
-        rnea_forward(pat, rec, q, qd, cq, sq, kGravity, F, Nm);
-        backward_sweep<Pat, true, false>(pat, rec, q, cq, sq, F, Nm, bias, Mdummy);
-        drive_terms(pat, rec, q, qd, qs, a.h, bias, rhs, arm);
-#pragma unroll
-        for (int i = 0; i < N; ++i)
-          if (pat.active(i)) xb[(kTri + i) * kWarp + lane] = rhs[i];
-      } else {
-        float M[N][N], inv[N], bias_dummy[N], rhs_dummy[N], arm[N];
-        V3 Fd[N], Nd[N];
-        backward_sweep<Pat, false, true>(pat, rec, q, cq, sq, Fd, Nd, bias_dummy, M);
-        drive_terms(pat, rec, q, qd, qs, a.h, bias_dummy, rhs_dummy, arm);
-        chol_factor(pat, M, arm, inv);
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          if (!pat.active(i)) continue;
-          xb[tri(i, i) * kWarp + lane] = inv[i];
-#pragma unroll
-          for (int j = 0; j < i; ++j) xb[tri(i, j) * kWarp + lane] = M[i][j];
-        }
-      }
-      mbar_arrive(bar_x);
-      if (!pair_wait(bar_x, ph_x, a.err, lane)) return;
-      // both roles run the same substitution on the same operands, so their
-      // copies of the state stay identical
       float L[N][N], inv[N], dqd[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        if (!pat.active(i)) continue;
-        dqd[i] = xb[(kTri + i) * kWarp + lane];
-        inv[i] = xb[tri(i, i) * kWarp + lane];
-#pragma unroll
-        for (int j = 0; j < i; ++j) L[i][j] = xb[tri(i, j) * kWarp + lane];
-      }
-      chol_apply(pat, L, inv, dqd);
+      if (!pair_substep(pat, rec, q, qd, qs, cq, sq, a.h, xb, bar_x, ph_x, a.err, lane, role, L,
+                        inv, dqd))
+        return;
       integrate(pat, q, qd, dqd, a.h);
       joint_sincos(pat, q, cq, sq);
     }

@@ -147,7 +147,9 @@ def test_diff_forward_leaves_state_and_matches_rollout():
         has = torch.as_tensor(desc["env_num_chains"] > c, device="cuda")
         cols = (2 * dof + 3 * c)[:, None] + torch.arange(3, device="cuda")[None]
         tip_obs = torch.gather(obs, 2, cols[None].expand(T, -1, -1))
-        assert torch.allclose(ee[:, has, c], tip_obs[:, has], atol=1e-6)
+        # small batches run the forward as warp pairs (sg_pair.cuh), so it
+        # agrees with the one-thread rollout to rounding, not bit for bit
+        assert torch.allclose(ee[:, has, c], tip_obs[:, has], atol=1e-5)
 
 
 def test_full_size_adjoint_sampled_against_oracle_and_central_differences():
