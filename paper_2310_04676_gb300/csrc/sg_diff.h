@@ -13,7 +13,7 @@ constexpr int kDiffThreads = 128;
 constexpr int kDiffPairThreads = 64;       // warp-pair forward: one pair per block
 constexpr int kDiffPairMaxWarpsPerSM = 2;  // warp-pair forward up to this many chain warps per SM
 constexpr int kReplayWarps = 2;        // replay warps per group of 32 chains
-constexpr int kDiffPipeThreads = 2 * (kReplayWarps + 1) * 32;   // two groups (replay warps + adjoint)
+constexpr int kDiffPipeThreads = 256;  // two groups (replay warps + adjoint) in 8 warp slots
 // per substep record: q, qd, cos q, sin q, k_s, 1/L_ii (7 each), L (21), and
 // per link the inverse-dynamics sweep quantities w, wd, acc, F, N, f, n (21 each)
 constexpr int kReplayFields = 210;
