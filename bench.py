@@ -61,6 +61,10 @@ W_HIDDEN = (256, 128, 64)   # hidden widths of the PPO networks
 # and the tool-tip Jacobian-transpose product.
 FLOP_SUBSTEP_ADJ = {"4R": 1460, "7R": 3278, "7P": 3070}
 FLOP_TIP_VJP = {"4R": 112, "7R": 238, "7P": 210}
+# the replay part of a substep adjoint (recomputed substep with its factor,
+# then the inverse-dynamics sweeps): with replay buffers, the forward kernel
+# does it for the last segment instead of the backward kernel
+FLOP_SUBSTEP_REPLAY = {"4R": 832, "7R": 1954, "7P": 1797}
 
 
 def env_step_flops(kinds, substeps, task=0):
@@ -79,16 +83,23 @@ def adjoint_flops(kinds, substeps, T, every, replay=True):
     every substep once, in a replay warp, with its inverse-dynamics sweeps
     (FLOP_SUBSTEP_ADJ counts the recomputed forward substep with its
     factorisation, the sweeps and their reverse), plus one tip product per
-    step; the one-warp backward also recomputes each segment from its
+    step -- except for the last segment, whose replay part
+    (FLOP_SUBSTEP_REPLAY) the forward kernel does in place of its own
+    substeps; the one-warp backward also recomputes each segment from its
     checkpoint and each step's substep start states."""
     fwd = bwd = 0
     seg_steps = [min(every, T - t0) for t0 in range(0, T, every)]
+    last = seg_steps[-1]
     for k in kinds:
         for c in (["7R", "7R"] if k == "14B" else [k]):
             sub = FLOP_SUBSTEP[c]
             fwd += T * (substeps * sub + FLOP_TIP[c])
             bwd += T * (FLOP_TIP_VJP[c] + substeps * FLOP_SUBSTEP_ADJ[c])
-            if not replay:
+            if replay:
+                rep = FLOP_SUBSTEP_REPLAY[c]
+                fwd += last * substeps * (rep - sub)
+                bwd -= last * substeps * rep
+            else:
                 bwd += sum(L - 1 for L in seg_steps) * substeps * sub
                 bwd += T * (substeps - 1) * sub
     return fwd, bwd

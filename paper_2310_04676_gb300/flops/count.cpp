@@ -117,13 +117,25 @@ void count(const char* name, P pat) {
   g = Cnt();
   substep_adjoint(pat, r, q, qd, qs, h, grav, lq, lqd, lqs, lm);
   const Cnt adj = g;
+  // the replay part of a substep adjoint: the recomputed substep with its
+  // factor, then the inverse-dynamics sweeps (replay warps, or the forward
+  // kernel for the last segment)
+  g = Cnt();
+  {
+    CF cq2[P::N], sq2[P::N], M[P::N][P::N], inv[P::N], acc[P::N], ks[P::N], dqd[P::N];
+    substep_record(pat, r, q, qd, qs, h, grav, cq2, sq2, M, inv, acc, ks, dqd);
+    SweepArrays<P::N> sw;
+    id_sweeps(pat, r, q, qd, acc, cq2, sq2, grav, sw);
+  }
+  const Cnt rp = g;
   g = Cnt();
   CF gq[P::N];
   for (int i = 0; i < P::N; ++i) gq[i] = CF::var(0.0);
   tip_vjp(pat, r, q, V3{CF::var(0.1), CF::var(0.2), CF::var(0.3)}, gq);
   const Cnt tv = g;
-  std::printf("%s substep %ld tip %ld substep_adjoint %ld tip_vjp %ld\n", name, sub.add + sub.mul,
-              tp.add + tp.mul, adj.add + adj.mul, tv.add + tv.mul);
+  std::printf("%s substep %ld tip %ld substep_adjoint %ld tip_vjp %ld substep_replay %ld\n", name,
+              sub.add + sub.mul, tp.add + tp.mul, adj.add + adj.mul, tv.add + tv.mul,
+              rp.add + rp.mul);
 }
 
 int main() {

@@ -4,7 +4,7 @@ numerator of bench.py).
 Makes host copies of csrc/sg_chain.cuh and csrc/sg_adjoint.cuh with `float`
 replaced by the counting scalar of flops/count.cpp, compiles that driver
 with the host C++ compiler and returns its counts:
-    {pattern: {"substep", "tip", "substep_adjoint", "tip_vjp"}}.
+    {pattern: {"substep", "tip", "substep_adjoint", "tip_vjp", "substep_replay"}}.
 
     python -m paper_2310_04676_gb300.flops.count
 """

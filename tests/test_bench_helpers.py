@@ -27,10 +27,17 @@ def test_adjoint_flops_by_hand():
     T, S, k = 20, 3, 8                       # segments of 8, 8, 4 steps
     f, b = bench.adjoint_flops(["7R"], S, T, k)
     sub, adj = bench.FLOP_SUBSTEP["7R"], bench.FLOP_SUBSTEP_ADJ["7R"]
-    assert f == T * (S * sub + bench.FLOP_TIP["7R"])
-    assert b == T * (bench.FLOP_TIP_VJP["7R"] + S * adj)
-    _, b1 = bench.adjoint_flops(["7R"], S, T, k, replay=False)
-    assert b1 - b == (7 + 7 + 3) * S * sub + T * (S - 1) * sub
+    rep = bench.FLOP_SUBSTEP_REPLAY["7R"]
+    # the forward does the last segment's (4 steps) replay part instead of its substeps
+    assert f == T * (S * sub + bench.FLOP_TIP["7R"]) + 4 * S * (rep - sub)
+    assert b == T * (bench.FLOP_TIP_VJP["7R"] + S * adj) - 4 * S * rep
+    # forward + backward together: every substep once forward, once as an adjoint
+    assert f + b == T * (S * sub + bench.FLOP_TIP["7R"] + bench.FLOP_TIP_VJP["7R"] + S * adj) \
+        - 4 * S * sub
+    f1, b1 = bench.adjoint_flops(["7R"], S, T, k, replay=False)
+    assert f1 == T * (S * sub + bench.FLOP_TIP["7R"])
+    assert b1 == T * (bench.FLOP_TIP_VJP["7R"] + S * adj) + (7 + 7 + 3) * S * sub \
+        + T * (S - 1) * sub
     # a two-arm env counts two chains
     assert bench.adjoint_flops(["14B"], S, T, k) == (2 * f, 2 * b)
 

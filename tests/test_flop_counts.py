@@ -20,6 +20,7 @@ def test_bench_constants_match_the_counted_chain_code():
         assert got[pat]["tip"] == bench.FLOP_TIP[pat], pat
         assert got[pat]["substep_adjoint"] == bench.FLOP_SUBSTEP_ADJ[pat], pat
         assert got[pat]["tip_vjp"] == bench.FLOP_TIP_VJP[pat], pat
+        assert got[pat]["substep_replay"] == bench.FLOP_SUBSTEP_REPLAY[pat], pat
 
 
 def test_counts_scale_with_the_chain():
@@ -30,4 +31,4 @@ def test_counts_scale_with_the_chain():
     got = C.count()
     assert got["4R"]["substep"] < got["7P"]["substep"] < got["7R"]["substep"]
     for pat in got:
-        assert got[pat]["substep_adjoint"] > got[pat]["substep"]
+        assert got[pat]["substep_adjoint"] > got[pat]["substep_replay"] > got[pat]["substep"]
