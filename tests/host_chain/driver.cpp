@@ -1,0 +1,118 @@
+// Host build of the device chain code in double precision, for the CPU tests
+// (test infrastructure, not part of the library).
+//
+// The device headers sg_chain.cuh and sg_adjoint.cuh are compiled for the
+// host with `float` replaced by `double` (the copies are made by
+// tests/test_host_chain.py); the parameter records are those of the
+// library's own host packer (sg_pack.cpp).  The entry points run one
+// substep, or one substep adjoint, of one chain of one env, so the device
+// algorithm can be compared with the FP64 oracle to double-precision
+// rounding, without a GPU.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+inline void __sincosf(double x, double* s, double* c) {
+  *s = std::sin(x);
+  *c = std::cos(x);
+}
+inline double rsqrtf(double x) { return 1.0 / std::sqrt(x); }
+inline double sqrtf(double x) { return std::sqrt(x); }
+inline double fminf(double a, double b) { return a < b ? a : b; }
+inline double fmaxf(double a, double b) { return a > b ? a : b; }
+
+#define __device__
+#define __forceinline__ inline
+#include "sg_internal.h"
+#include "chain_host.h"     // sg_chain.cuh with float -> double
+#include "adjoint_host.h"   // sg_adjoint.cuh with float -> double
+
+using namespace sg;
+
+namespace {
+
+Plan g_plan;
+double g_rec[kRecordFloats];
+constexpr double kGrav = 9.81;
+
+// Runs f(pattern, record view, number of joints) for chain c of env e.
+template <class F>
+int with_chain(int e, int c, F f) {
+  int s = -1;
+  for (int k = 0; k < g_plan.num_slots && s < 0; ++k)
+    if (g_plan.slot_env[k] == e && decode_slot(g_plan.slot_info[k]).c == c) s = k;
+  if (s < 0) return -1;
+  const int w = s / kWarp, lane = s % kWarp;
+  const float* src = g_plan.params.data() + (size_t)w * kRecordFloats;
+  for (int i = 0; i < kRecordFloats; ++i) g_rec[i] = src[i];
+  const Rec r{g_rec + lane};
+  const int n = decode_slot(g_plan.slot_info[s]).nchain;
+  switch (g_plan.warp_class[w] & 3) {
+    case CLS_7R: return f(Pat7R{}, r, n);
+    case CLS_7P: return f(Pat7P{}, r, n);
+    case CLS_4R: return f(Pat4R{}, r, n);
+    default: {
+      int code;
+      std::memcpy(&code, &src[CF_CODE * kWarp + lane], 4);
+      return f(PatGen{code, n}, r, n);
+    }
+  }
+}
+
+void load(const double* src, int n, double (&dst)[7]) {
+  for (int i = 0; i < 7; ++i) dst[i] = i < n ? src[i] : 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Pack a description with the library's packer; returns the slot count or -1.
+int host_plan(const sg_desc* d) {
+  std::string err;
+  return build_plan(d, &g_plan, &err) == SG_OK ? g_plan.num_slots : -1;
+}
+
+// One substep of chain c of env e from (q, qd) with commands qs: writes q',
+// qd'; returns the chain's joint count (or -1).
+int host_substep(int e, int c, const double* q_in, const double* qd_in, const double* qs_in,
+                 double h, double* q_out, double* qd_out) {
+  return with_chain(e, c, [&](auto pat, const Rec& r, int n) {
+    double q[7], qd[7], qs[7];
+    load(q_in, n, q);
+    load(qd_in, n, qd);
+    load(qs_in, n, qs);
+    chain_substep(pat, r, q, qd, qs, h, kGrav);
+    for (int i = 0; i < n; ++i) {
+      q_out[i] = q[i];
+      qd_out[i] = qd[i];
+    }
+    return n;
+  });
+}
+
+// Adjoint of that substep: lq, lqd hold the cotangents of (q', qd') on entry
+// and those of (q, qd) on exit; lqs, lm receive those of the commands and the
+// link masses.
+int host_substep_adjoint(int e, int c, const double* q_in, const double* qd_in,
+                         const double* qs_in, double h, double* lq_io, double* lqd_io,
+                         double* lqs_out, double* lm_out) {
+  return with_chain(e, c, [&](auto pat, const Rec& r, int n) {
+    double q[7], qd[7], qs[7], lq[7], lqd[7], lqs[7] = {0}, lm[7] = {0};
+    load(q_in, n, q);
+    load(qd_in, n, qd);
+    load(qs_in, n, qs);
+    load(lq_io, n, lq);
+    load(lqd_io, n, lqd);
+    substep_adjoint(pat, r, q, qd, qs, h, kGrav, lq, lqd, lqs, lm);
+    for (int i = 0; i < n; ++i) {
+      lq_io[i] = lq[i];
+      lqd_io[i] = lqd[i];
+      lqs_out[i] = lqs[i];
+      lm_out[i] = lm[i];
+    }
+    return n;
+  });
+}
+
+}  // extern "C"

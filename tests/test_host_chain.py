@@ -1,0 +1,173 @@
+"""The device chain code, compiled for the host in double precision, against
+the FP64 oracle (no GPU).
+
+tests/host_chain/driver.cpp runs sg_chain.cuh / sg_adjoint.cuh with `float`
+replaced by `double` on parameter records made by the library's own packer,
+one chain at a time.  In double precision the device algorithm (body-frame
+RNEA, composite-rigid-body mass matrix, in-register Cholesky, the adjoint's
+inverse-dynamics sweeps and their reverse) and the oracle's (spatial-algebra
+RNEA/CRBA, library Cholesky, autograd) differ only by rounding and by the
+packer's float32 sum kd + b (relative 6e-8), so one substep's state and its
+vector-Jacobian product must agree to 1e-6 relative (measured: 1e-9 to
+3e-8) -- a check of the device formulas a hundred times tighter than the
+FP32 parity tests, run on every CPU test pass.  A sign flipped in the
+Coriolis term, in the adjoint's prismatic-offset term or a dropped moment
+term in the mass cotangent moves the result by 1e-4 to 0.5.
+"""
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import dynamics as dyn
+from oracle.model import groups, make_params
+from paper_2310_04676_gb300 import sg, workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_2310_04676_gb300", "csrc")
+D64 = torch.float64
+H = 1.0 / 120.0
+TOL = 1e-6
+
+
+def _host_copy(src, dst, drop):
+    text = open(src).read()
+    for inc in drop:
+        text = text.replace(inc, "")
+    with open(dst, "w") as f:
+        f.write(re.sub(r"\bfloat\b", "double", text))
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("needs a host C++ compiler")
+    tmp = str(tmp_path_factory.mktemp("host_chain"))
+    _host_copy(os.path.join(CSRC, "sg_chain.cuh"), os.path.join(tmp, "chain_host.h"),
+               ["#include <cuda_runtime.h>"])
+    _host_copy(os.path.join(CSRC, "sg_adjoint.cuh"), os.path.join(tmp, "adjoint_host.h"),
+               ['#include "sg_chain.cuh"'])
+    so = os.path.join(tmp, "libhostchain.so")
+    cmd = [cxx, "-std=c++17", "-O1", "-shared", "-fPIC", "-I" + tmp, "-I" + CSRC,
+           "-I" + os.path.join(ROOT, "include"), os.path.join(HERE, "host_chain", "driver.cpp"),
+           os.path.join(CSRC, "sg_pack.cpp"), "-o", so]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    L = ctypes.CDLL(so)
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.host_plan.argtypes = [ctypes.c_void_p]
+    L.host_substep.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp, dp]
+    L.host_substep_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_double,
+                                       dp, dp, dp, dp]
+    return L
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _desc(kinds, variant):
+    """Six envs of `kinds`: position drives; position drives with limit
+    springs (k = 1e3); or the three command types mixed over the joints."""
+    desc = W.make_desc((kinds * 6)[:6], k_limit=1e3 if variant == "limits" else 0.0)
+    if variant == "drives":
+        E, J = desc["num_envs"], desc["max_joints"]
+        desc["joint_drive"] = ((np.arange(J)[None] + np.arange(E)[:, None]) % 3).astype(np.int32)
+    return desc
+
+
+def _plan(lib, desc):
+    cdesc, keep = sg.make_c_desc(desc)
+    n = lib.host_plan(ctypes.byref(cdesc))
+    assert n > 0
+    return keep
+
+
+def _state(desc, seed):
+    """Random joint positions inside (and, for limit springs, a little
+    beyond) the limits, velocities and commands, [E][J]."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.asarray(desc["q_lo"], np.float64), np.asarray(desc["q_hi"], np.float64)
+    span = hi - lo
+    q = lo - 0.1 * span + 1.2 * span * rng.random(lo.shape)
+    qd = rng.normal(0.0, 1.0, lo.shape)
+    qs = lo + span * rng.random(lo.shape)
+    return q, qd, qs
+
+
+def _chains(desc, e):
+    """(chain index, first joint, joints) of env e."""
+    out, jo = [], 0
+    for c in range(int(desc["env_num_chains"][e])):
+        n = int(desc["chain_num_joints"][e][c])
+        out.append((c, jo, n))
+        jo += n
+    return out
+
+
+KINDS = [["7R"], ["7P"], ["4R"], ["14B"], ["21T"], ["7R", "4R", "7P", "14B", "21T"]]
+
+
+@pytest.mark.parametrize("kinds", KINDS, ids=lambda k: "+".join(k))
+@pytest.mark.parametrize("variant", ["position", "limits", "drives"])
+def test_substep_matches_oracle(lib, kinds, variant):
+    desc = _desc(kinds, variant)
+    keep = _plan(lib, desc)
+    q, qd, qs = _state(desc, 1)
+    for idx, tree in groups(desc):
+        n = tree.n
+        P = make_params(tree, desc, idx)
+        t = lambda a: torch.as_tensor(a[idx, :n])
+        q1, qd1, _ = dyn.substep(tree, P, t(q), t(qd), t(qs), H)
+        for k, e in enumerate(idx):
+            for c, jo, nc in _chains(desc, e):
+                qo, qdo = np.zeros(7), np.zeros(7)
+                args = [np.ascontiguousarray(a[e, jo:jo + nc]) for a in (q, qd, qs)]
+                assert lib.host_substep(int(e), c, *map(_p, args), H, _p(qo), _p(qdo)) == nc
+                for got, ref in ((qo[:nc], q1[k, jo:jo + nc]), (qdo[:nc], qd1[k, jo:jo + nc])):
+                    ref = ref.numpy()
+                    assert np.linalg.norm(got - ref) <= TOL * max(np.linalg.norm(ref), 1.0), \
+                        (variant, kinds, e, c)
+    del keep
+
+
+@pytest.mark.parametrize("kinds", KINDS, ids=lambda k: "+".join(k))
+@pytest.mark.parametrize("variant", ["position", "limits", "drives"])
+def test_substep_adjoint_matches_oracle_autograd(lib, kinds, variant):
+    """Cotangents of (q, qd), the commands and the link masses of one
+    substep's output functional lq.q' + lqd.qd', against autograd through
+    the oracle's substep."""
+    desc = _desc(kinds, variant)
+    keep = _plan(lib, desc)
+    q, qd, qs = _state(desc, 2)
+    rng = np.random.default_rng(3)
+    lq, lqd = rng.normal(size=q.shape), rng.normal(size=q.shape)
+    mass = np.asarray(desc["link_mass"], np.float64)
+    for idx, tree in groups(desc):
+        n = tree.n
+        t = lambda a: torch.tensor(a[idx, :n], dtype=D64, requires_grad=True)
+        Q, QD, QS, M = t(q), t(qd), t(qs), t(mass)
+        P = make_params(tree, desc, idx, mass=M)
+        q1, qd1, _ = dyn.substep(tree, P, Q, QD, QS, H)
+        L = (torch.as_tensor(lq[idx, :n]) * q1).sum() + (torch.as_tensor(lqd[idx, :n]) * qd1).sum()
+        gq, gqd, gqs, gm = torch.autograd.grad(L, [Q, QD, QS, M])
+        for k, e in enumerate(idx):
+            for c, jo, nc in _chains(desc, e):
+                sl = slice(jo, jo + nc)
+                a_q, a_qd = np.ascontiguousarray(lq[e, sl]), np.ascontiguousarray(lqd[e, sl])
+                lqs, lm = np.zeros(nc), np.zeros(nc)
+                args = [np.ascontiguousarray(a[e, sl]) for a in (q, qd, qs)]
+                assert lib.host_substep_adjoint(int(e), c, *map(_p, args), H, _p(a_q), _p(a_qd),
+                                                _p(lqs), _p(lm)) == nc
+                for got, ref in ((a_q, gq), (a_qd, gqd), (lqs, gqs), (lm, gm)):
+                    ref = ref[k, sl].numpy()
+                    assert np.linalg.norm(got - ref) <= TOL * max(np.linalg.norm(ref), 1.0), \
+                        (variant, kinds, e, c)
+    del keep
