@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 
 inline void __sincosf(double x, double* s, double* c) {
   *s = std::sin(x);
@@ -111,6 +112,34 @@ int host_substep_adjoint(int e, int c, const double* q_in, const double* qd_in,
       lqs_out[i] = lqs[i];
       lm_out[i] = lm[i];
     }
+    return n;
+  });
+}
+
+// Tool-tip position and tip-frame quaternion (x, y, z, w) of chain c of env e.
+int host_tip(int e, int c, const double* q_in, double* tip_out, double* quat_out) {
+  return with_chain(e, c, [&](auto pat, const Rec& r, int n) {
+    double q[7];
+    load(q_in, n, q);
+    V3 tip, r0, r1, r2;
+    chain_tip(pat, r, q, tip, r0, r1, r2);
+    tip_out[0] = tip.x;
+    tip_out[1] = tip.y;
+    tip_out[2] = tip.z;
+    rot_to_quat(r0, r1, r2, quat_out);
+    return n;
+  });
+}
+
+// gq = J_tip(q)^T gbar for chain c of env e.
+int host_tip_vjp(int e, int c, const double* q_in, const double* gbar, double* gq_out) {
+  return with_chain(e, c, [&](auto pat, const Rec& r, int n) {
+    constexpr int N = std::decay_t<decltype(pat)>::N;
+    double q[7], gq[N];
+    load(q_in, n, q);
+    for (int i = 0; i < N; ++i) gq[i] = 0.0;
+    tip_vjp(pat, r, q, V3{gbar[0], gbar[1], gbar[2]}, gq);
+    for (int i = 0; i < n; ++i) gq_out[i] = gq[i];
     return n;
   });
 }

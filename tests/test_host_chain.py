@@ -10,7 +10,9 @@ RNEA/CRBA, library Cholesky, autograd) differ only by rounding and by the
 packer's float32 sum kd + b (relative 6e-8), so one substep's state and its
 vector-Jacobian product must agree to 1e-6 relative (measured: 1e-9 to
 3e-8) -- a check of the device formulas a hundred times tighter than the
-FP32 parity tests, run on every CPU test pass.  A sign flipped in the
+FP32 parity tests, run on every CPU test pass.  The tool-tip pose, the
+tip quaternion and the tip Jacobian-transpose product involve no packed sums
+and agree to 1e-12.  A sign flipped in the
 Coriolis term, in the adjoint's prismatic-offset term or a dropped moment
 term in the mass cotangent moves the result by 1e-4 to 0.5.
 """
@@ -25,6 +27,7 @@ import pytest
 import torch
 
 from oracle import dynamics as dyn
+from oracle.env import tip_quaternion
 from oracle.model import groups, make_params
 from paper_2310_04676_gb300 import sg, workloads as W
 
@@ -66,6 +69,8 @@ def lib(tmp_path_factory):
     L.host_substep.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp, dp]
     L.host_substep_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_double,
                                        dp, dp, dp, dp]
+    L.host_tip.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+    L.host_tip_vjp.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
     return L
 
 
@@ -170,4 +175,35 @@ def test_substep_adjoint_matches_oracle_autograd(lib, kinds, variant):
                     ref = ref[k, sl].numpy()
                     assert np.linalg.norm(got - ref) <= TOL * max(np.linalg.norm(ref), 1.0), \
                         (variant, kinds, e, c)
+    del keep
+
+
+@pytest.mark.parametrize("kinds", KINDS, ids=lambda k: "+".join(k))
+def test_tip_pose_and_jacobian_transpose_match_oracle(lib, kinds):
+    """Tool-tip position, tip quaternion (Shepperd on the device rotation,
+    against the oracle's product of joint quaternions, both with w >= 0) and
+    J_tip^T g (against autograd of g . tip) of every chain."""
+    desc = _desc(kinds, "position")
+    keep = _plan(lib, desc)
+    q, _, _ = _state(desc, 4)
+    rng = np.random.default_rng(5)
+    for idx, tree in groups(desc):
+        n = tree.n
+        P = make_params(tree, desc, idx)
+        Q = torch.tensor(q[idx, :n], dtype=D64, requires_grad=True)
+        tips, _ = dyn.end_effectors(tree, P, Q)
+        quats = tip_quaternion(tree, Q.detach())
+        g = torch.as_tensor(rng.normal(size=tips.shape))
+        (gq,) = torch.autograd.grad((g * tips).sum(), [Q])
+        for k, e in enumerate(idx):
+            for c, jo, nc in _chains(desc, e):
+                qa = np.ascontiguousarray(q[e, jo:jo + nc])
+                tip, quat, jt = np.zeros(3), np.zeros(4), np.zeros(nc)
+                assert lib.host_tip(int(e), c, _p(qa), _p(tip), _p(quat)) == nc
+                gb = np.ascontiguousarray(g[k, c].numpy())
+                assert lib.host_tip_vjp(int(e), c, _p(qa), _p(gb), _p(jt)) == nc
+                assert np.abs(tip - tips[k, c].detach().numpy()).max() <= 1e-12
+                assert np.abs(quat - quats[k, c].numpy()).max() <= 1e-12
+                ref = gq[k, jo:jo + nc].numpy()
+                assert np.abs(jt - ref).max() <= 1e-12 * max(np.abs(ref).max(), 1.0)
     del keep
