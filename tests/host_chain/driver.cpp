@@ -1,13 +1,14 @@
 // Host build of the device chain code in double precision, for the CPU tests
 // (test infrastructure, not part of the library).
 //
-// The device headers sg_chain.cuh and sg_adjoint.cuh are compiled for the
-// host with `float` replaced by `double` (the copies are made by
-// tests/test_host_chain.py); the parameter records are those of the
+// The device headers sg_chain.cuh, sg_adjoint.cuh and sg_rng.cuh are
+// compiled for the host with `float` replaced by `double` (the copies are
+// made by tests/test_host_chain.py); the parameter records are those of the
 // library's own host packer (sg_pack.cpp).  The entry points run one
-// substep, or one substep adjoint, of one chain of one env, so the device
-// algorithm can be compared with the FP64 oracle to double-precision
-// rounding, without a GPU.
+// substep, one substep adjoint, the tip kinematics of one chain of one env,
+// or one draw of the counter-based noise, so the device algorithm can be
+// compared with the FP64 oracle to double-precision rounding, without a
+// GPU.
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -21,12 +22,19 @@ inline double rsqrtf(double x) { return 1.0 / std::sqrt(x); }
 inline double sqrtf(double x) { return std::sqrt(x); }
 inline double fminf(double a, double b) { return a < b ? a : b; }
 inline double fmaxf(double a, double b) { return a > b ? a : b; }
+inline double logf(double x) { return std::log(x); }
+inline void sincospif(double x, double* s, double* c) {
+  const double pi = 3.14159265358979323846;
+  *s = std::sin(pi * x);
+  *c = std::cos(pi * x);
+}
 
 #define __device__
 #define __forceinline__ inline
 #include "sg_internal.h"
 #include "chain_host.h"     // sg_chain.cuh with float -> double
 #include "adjoint_host.h"   // sg_adjoint.cuh with float -> double
+#include "rng_host.h"       // sg_rng.cuh with float -> double
 
 using namespace sg;
 
@@ -142,6 +150,17 @@ int host_tip_vjp(int e, int c, const double* q_in, const double* gbar, double* g
     for (int i = 0; i < n; ++i) gq_out[i] = gq[i];
     return n;
   });
+}
+
+// Counter-based noise draws (tracking goals, policy exploration).
+void host_goal_noise(uint32_t seed, int env, int chain, int step, double* z) {
+  goal_noise(seed, env, chain, step, z[0], z[1], z[2]);
+}
+
+void host_action_noise(uint32_t seed, int env, int block, long long step, double* z) {
+  double zz[4];
+  action_noise(seed, env, block, step, zz);
+  for (int k = 0; k < 4; ++k) z[k] = zz[k];
 }
 
 }  // extern "C"

@@ -1,9 +1,9 @@
 """The device chain code, compiled for the host in double precision, against
 the FP64 oracle (no GPU).
 
-tests/host_chain/driver.cpp runs sg_chain.cuh / sg_adjoint.cuh with `float`
-replaced by `double` on parameter records made by the library's own packer,
-one chain at a time.  In double precision the device algorithm (body-frame
+tests/host_chain/driver.cpp runs sg_chain.cuh / sg_adjoint.cuh / sg_rng.cuh
+with `float` replaced by `double` on parameter records made by the library's
+own packer, one chain at a time.  In double precision the device algorithm (body-frame
 RNEA, composite-rigid-body mass matrix, in-register Cholesky, the adjoint's
 inverse-dynamics sweeps and their reverse) and the oracle's (spatial-algebra
 RNEA/CRBA, library Cholesky, autograd) differ only by rounding and by the
@@ -12,7 +12,8 @@ vector-Jacobian product must agree to 1e-6 relative (measured: 1e-9 to
 3e-8) -- a check of the device formulas a hundred times tighter than the
 FP32 parity tests, run on every CPU test pass.  The tool-tip pose, the
 tip quaternion and the tip Jacobian-transpose product involve no packed sums
-and agree to 1e-12.  A sign flipped in the
+and agree to 1e-12, as do the counter-based noise draws (exact integer
+key arithmetic, double-precision Box-Muller).  A sign flipped in the
 Coriolis term, in the adjoint's prismatic-offset term or a dropped moment
 term in the mass cotangent moves the result by 1e-4 to 0.5.
 """
@@ -29,6 +30,7 @@ import torch
 from oracle import dynamics as dyn
 from oracle.env import tip_quaternion
 from oracle.model import groups, make_params
+from oracle.rng import action_noise, goal_noise
 from paper_2310_04676_gb300 import sg, workloads as W
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -57,6 +59,7 @@ def lib(tmp_path_factory):
                ["#include <cuda_runtime.h>"])
     _host_copy(os.path.join(CSRC, "sg_adjoint.cuh"), os.path.join(tmp, "adjoint_host.h"),
                ['#include "sg_chain.cuh"'])
+    _host_copy(os.path.join(CSRC, "sg_rng.cuh"), os.path.join(tmp, "rng_host.h"), [])
     so = os.path.join(tmp, "libhostchain.so")
     cmd = [cxx, "-std=c++17", "-O1", "-shared", "-fPIC", "-I" + tmp, "-I" + CSRC,
            "-I" + os.path.join(ROOT, "include"), os.path.join(HERE, "host_chain", "driver.cpp"),
@@ -71,6 +74,9 @@ def lib(tmp_path_factory):
                                        dp, dp, dp, dp]
     L.host_tip.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
     L.host_tip_vjp.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+    L.host_goal_noise.argtypes = [ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+    L.host_action_noise.argtypes = [ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+                                    dp]
     return L
 
 
@@ -207,3 +213,20 @@ def test_tip_pose_and_jacobian_transpose_match_oracle(lib, kinds):
                 ref = gq[k, jo:jo + nc].numpy()
                 assert np.abs(jt - ref).max() <= 1e-12 * max(np.abs(ref).max(), 1.0)
     del keep
+
+
+def test_counter_based_noise_matches_oracle(lib):
+    """The device's key arithmetic (seed, env, chain or joint block, step;
+    shifts, masks, 64-bit step counts) and Box-Muller draw the oracle's
+    deviates: in double precision they agree to 1e-12."""
+    rng = np.random.default_rng(6)
+    for _ in range(200):
+        seed = int(rng.integers(0, 2**32))
+        env, c, blk = int(rng.integers(0, 2**20)), int(rng.integers(0, 4)), int(rng.integers(0, 7))
+        step = int(rng.integers(0, 2**28))
+        big = int(rng.integers(0, 2**50))
+        z3, z4 = np.zeros(3), np.zeros(4)
+        lib.host_goal_noise(seed, env, c, step, _p(z3))
+        assert np.abs(z3 - goal_noise(seed, env, c, step)).max() <= 1e-12
+        lib.host_action_noise(seed, env, blk, big, _p(z4))
+        assert np.abs(z4 - action_noise(seed, env, blk, big)).max() <= 1e-12
