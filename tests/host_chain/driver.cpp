@@ -152,6 +152,58 @@ int host_tip_vjp(int e, int c, const double* q_in, const double* gbar, double* g
   });
 }
 
+// Joint torques tau = ID(q, qd, qdd) of chain c of env e from the adjoint's
+// inverse-dynamics sweeps: the wrench each link transmits to its parent,
+// about the joint axis (revolute) or along it (prismatic).
+int host_inverse_dynamics(int e, int c, const double* q_in, const double* qd_in,
+                          const double* qdd_in, double* tau_out) {
+  return with_chain(e, c, [&](auto pat, const Rec& r, int n) {
+    constexpr int N = std::decay_t<decltype(pat)>::N;
+    double q[7], qd[7], qdd[N], cq[N], sq[N];
+    load(q_in, n, q);
+    load(qd_in, n, qd);
+    for (int i = 0; i < N; ++i) qdd[i] = i < n ? qdd_in[i] : 0.0;
+    joint_sincos(pat, q, cq, sq);
+    SweepArrays<N> sw;
+    id_sweeps(pat, r, q, qd, qdd, cq, sq, kGrav, sw);
+    for (int i = 0; i < n; ++i)
+      tau_out[i] = pat.type(i) == 1 ? sw.FL[i].z : compc(sw.NL[i], pat.axis(i));
+    return n;
+  });
+}
+
+// One substep computed as the warp pair splits it (role 0: bias forces and
+// right-hand side; role 1: mass matrix, armature and factor; then the shared
+// solve), run one role after the other.
+int host_substep_split(int e, int c, const double* q_in, const double* qd_in,
+                       const double* qs_in, double h, double* q_out, double* qd_out) {
+  return with_chain(e, c, [&](auto pat, const Rec& r, int n) {
+    constexpr int N = std::decay_t<decltype(pat)>::N;
+    double q[7], qd[7], qs[7], cq[N], sq[N];
+    load(q_in, n, q);
+    load(qd_in, n, qd);
+    load(qs_in, n, qs);
+    joint_sincos(pat, q, cq, sq);
+    double bias[N], rhs[N], arm[N], Mdummy[N][N];
+    V3 F[N], Nm[N];
+    rnea_forward(pat, r, q, qd, cq, sq, kGrav, F, Nm);
+    backward_sweep<decltype(pat), true, false>(pat, r, q, cq, sq, F, Nm, bias, Mdummy);
+    drive_terms(pat, r, q, qd, qs, h, bias, rhs, arm);
+    double M[N][N], inv[N], bias1[N] = {}, rhs1[N], arm1[N];
+    V3 Fd[N] = {}, Nd[N] = {};
+    backward_sweep<decltype(pat), false, true>(pat, r, q, cq, sq, Fd, Nd, bias1, M);
+    drive_terms(pat, r, q, qd, qs, h, bias1, rhs1, arm1);
+    chol_factor(pat, M, arm1, inv);
+    chol_apply(pat, M, inv, rhs);
+    integrate(pat, q, qd, rhs, h);
+    for (int i = 0; i < n; ++i) {
+      q_out[i] = q[i];
+      qd_out[i] = qd[i];
+    }
+    return n;
+  });
+}
+
 // Counter-based noise draws (tracking goals, policy exploration).
 void host_goal_noise(uint32_t seed, int env, int chain, int step, double* z) {
   goal_noise(seed, env, chain, step, z[0], z[1], z[2]);

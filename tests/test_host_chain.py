@@ -13,7 +13,10 @@ vector-Jacobian product must agree to 1e-6 relative (measured: 1e-9 to
 FP32 parity tests, run on every CPU test pass.  The tool-tip pose, the
 tip quaternion and the tip Jacobian-transpose product involve no packed sums
 and agree to 1e-12, as do the counter-based noise draws (exact integer
-key arithmetic, double-precision Box-Muller).  A sign flipped in the
+key arithmetic, double-precision Box-Muller); the adjoint's inverse-dynamics
+sweeps give the oracle's RNEA torques to 1e-10, and the warp pair's split
+of a substep (bias-only and mass-only sweeps, shared solve) equals the
+fused substep.  A sign flipped in the
 Coriolis term, in the adjoint's prismatic-offset term or a dropped moment
 term in the mass cotangent moves the result by 1e-4 to 0.5.
 """
@@ -74,6 +77,9 @@ def lib(tmp_path_factory):
                                        dp, dp, dp, dp]
     L.host_tip.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
     L.host_tip_vjp.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+    L.host_inverse_dynamics.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+    L.host_substep_split.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp,
+                                     dp]
     L.host_goal_noise.argtypes = [ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
     L.host_action_noise.argtypes = [ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                                     dp]
@@ -230,3 +236,45 @@ def test_counter_based_noise_matches_oracle(lib):
         assert np.abs(z3 - goal_noise(seed, env, c, step)).max() <= 1e-12
         lib.host_action_noise(seed, env, blk, big, _p(z4))
         assert np.abs(z4 - action_noise(seed, env, blk, big)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("kinds", KINDS, ids=lambda k: "+".join(k))
+def test_inverse_dynamics_sweeps_match_oracle_rnea(lib, kinds):
+    """The adjoint's inverse-dynamics sweeps (body-frame recursion, link
+    wrenches) give the oracle's spatial-algebra RNEA torques."""
+    desc = _desc(kinds, "position")
+    keep = _plan(lib, desc)
+    q, qd, _ = _state(desc, 7)
+    qdd = np.random.default_rng(8).normal(0.0, 3.0, q.shape)
+    for idx, tree in groups(desc):
+        n = tree.n
+        P = make_params(tree, desc, idx)
+        t = lambda a: torch.as_tensor(a[idx, :n])
+        tau = dyn.rnea(tree, P, t(q), t(qd), t(qdd)).numpy()
+        for k, e in enumerate(idx):
+            for c, jo, nc in _chains(desc, e):
+                args = [np.ascontiguousarray(a[e, jo:jo + nc]) for a in (q, qd, qdd)]
+                out = np.zeros(nc)
+                assert lib.host_inverse_dynamics(int(e), c, *map(_p, args), _p(out)) == nc
+                ref = tau[k, jo:jo + nc]
+                assert np.linalg.norm(out - ref) <= 1e-10 * max(np.linalg.norm(ref), 1.0)
+    del keep
+
+
+@pytest.mark.parametrize("kinds", KINDS, ids=lambda k: "+".join(k))
+@pytest.mark.parametrize("variant", ["position", "limits", "drives"])
+def test_warp_pair_split_equals_the_fused_substep(lib, kinds, variant):
+    """The warp pair's decomposition of a substep (bias-only and mass-only
+    backward sweeps in two roles, then the shared solve) computes the fused
+    one-thread substep."""
+    desc = _desc(kinds, variant)
+    keep = _plan(lib, desc)
+    q, qd, qs = _state(desc, 9)
+    for e in range(desc["num_envs"]):
+        for c, jo, nc in _chains(desc, e):
+            args = [np.ascontiguousarray(a[e, jo:jo + nc]) for a in (q, qd, qs)]
+            a1, b1, a2, b2 = np.zeros(7), np.zeros(7), np.zeros(7), np.zeros(7)
+            assert lib.host_substep(e, c, *map(_p, args), H, _p(a1), _p(b1)) == nc
+            assert lib.host_substep_split(e, c, *map(_p, args), H, _p(a2), _p(b2)) == nc
+            assert np.abs(a1 - a2).max() <= 1e-13 and np.abs(b1 - b2).max() <= 1e-11
+    del keep
