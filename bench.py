@@ -275,43 +275,60 @@ def cpu_baseline(wl, seconds=12.0, max_envs=2048):
                       % (n, E, steps, el)}
 
 
-def equal_accuracy(wl, launch, n_envs=64, steps=100):
-    """Joint positions of the first `n_envs` envs after `steps` control steps,
-    in the measured launch plan, as one persistent rollout and as one sg_step
-    call per step, against the FP64 oracle from the same initial state:
-    max over envs of ||q_gpu - q_ref|| / max(||q_ref||, 1e-3) (tolerance
-    1e-3, as in the parity tests)."""
+def sample_by_kind(kinds, per_kind, seed=12):
+    """`per_kind` env indices drawn at random from each kind of the batch."""
+    rng = np.random.default_rng(seed)
+    kinds = np.asarray(kinds)
+    pick = [rng.choice(np.flatnonzero(kinds == k), min(per_kind, int((kinds == k).sum())),
+                       replace=False) for k in sorted(set(kinds.tolist()))]
+    return np.sort(np.concatenate(pick))
+
+
+def sub_desc(desc, pick):
+    E = desc["num_envs"]
+    sub = {k: (v[pick] if isinstance(v, np.ndarray) and v.shape[:1] == (E,) else v)
+           for k, v in desc.items()}
+    sub["num_envs"] = len(pick)
+    return sub
+
+
+def equal_accuracy(wl, launch, per_kind=64, steps=100):
+    """The whole batch for `steps` control steps from the reset state, in the
+    measured launch plan, as one persistent rollout and as one sg_step call
+    per step; joint positions of `per_kind` envs drawn at random from each
+    kind against the FP64 oracle: max over the sampled envs of
+    ||q_gpu - q_ref|| / max(||q_ref||, 1e-3) (tolerance 1e-3, as in the
+    parity tests)."""
     import torch
     from oracle.env import OracleEnv
     from paper_2310_04676_gb300 import sg, workloads as W
-    E = wl.desc["num_envs"]
-    n = min(E, n_envs)
-    sub = {k: (v[:n] if isinstance(v, np.ndarray) and v.shape[:1] == (E,) else v)
-           for k, v in wl.desc.items()}
-    sub["num_envs"] = n
-    sub["episode_len"] = max(int(sub["episode_len"]), steps + 1)
-    acts = W.joint_targets(sub, steps)
-    ref = OracleEnv(sub)
+    desc = dict(wl.desc)
+    E = desc["num_envs"]
+    desc["episode_len"] = max(int(desc["episode_len"]), steps + 1)
+    pick = sample_by_kind(wl.kinds, per_kind)
+    acts = W.joint_targets(desc, steps)
+    ref = OracleEnv(sub_desc(desc, pick))
     for t in range(steps):
-        ref.step(acts[t], wl.dt, wl.substeps)
+        ref.step(acts[t][pick], wl.dt, wl.substeps)
     threads, mode, split = launch
     a = torch.as_tensor(acts, device="cuda")
     out = {}
     for form in ("rollout", "plain"):
-        env = sg.Env(sub)
+        env = sg.Env(desc)
         env.set_launch(threads, mode, split)
         if form == "rollout":
             env.rollout(a, wl.dt, wl.substeps)
         else:
             for t in range(steps):
                 env.step(a[t], wl.dt, wl.substeps)
-        q = env.get_state()[0].cpu().numpy().astype(np.float64)
+        q = env.get_state()[0].cpu().numpy().astype(np.float64)[pick]
         err = np.linalg.norm(q - ref.q, axis=1) / np.maximum(np.linalg.norm(ref.q, axis=1), 1e-3)
         out[form] = float(err.max())
         env.close()
     return {"q_rel_err_max": out, "tolerance": 1e-3, "within": max(out.values()) <= 1e-3,
-            "sample": "first %d of %d envs, %d steps from the initial state, measured launch "
-                      "plan; FP64 oracle" % (n, E, steps)}
+            "sample": "%d envs drawn at random across the %d kinds (%d each) of the whole "
+                      "%d-env batch, %d steps from the reset state, measured launch plan; "
+                      "FP64 oracle" % (len(pick), len(set(wl.kinds)), per_kind, E, steps)}
 
 
 def cpu_baseline_single_core(wl, seconds=6.0, max_envs=256):
@@ -619,11 +636,12 @@ def run_rollout_config(cx, name, E=None):
     nbytes = env_step_bytes(desc, r["obs_dim"]) * T
     ms_launch = sum(r["ms"]["ours"]) / len(r["ms"]["ours"])
     cfg = {"workload": wl.name, "envs_per_gpu": r["E"], "rollout_steps": T,
-           "substeps": wl.substeps, "dt": wl.dt, "form": "persistent kernel in a CUDA graph",
-           "launch": {"threads_per_block": threads, "mode": ["persistent", "step_graph"][mode],
-                      "chain_split": split},
+           "substeps": wl.substeps, "dt": wl.dt,
            "l2": "flushed (256 MiB write) before every timed step"}
     line = base_line(args, world, value, 1e3 * t["ours"] / args.steps, cfg)
+    line["form"] = "persistent kernel in a CUDA graph"
+    line["launch"] = {"threads_per_block": threads, "mode": ["persistent", "step_graph"][mode],
+                      "chain_split": split}
     line["us_per_control_step"] = 1e6 * t["ours"] / args.steps / T
     line["step_time_stats"] = stats(r["ms"]["ours"])
     for k, label in (("step_graph", "%d single-step kernels replayed from a CUDA graph" % T),
@@ -822,23 +840,39 @@ def run_ppo_config(cx, name="P1", E=None):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on the host cores,
+    on the default workload.  Every step is one bounded sample of the
+    workload (the first envs of the batch, as many control steps as fit in
+    its time slice); `value` is env-steps per second of the timed samples and
+    `ms_per_step` the measured wall time of one sample (not an extrapolation
+    to the whole batch)."""
     world, rank, local = dist_setup()
     if rank != 0:
         return
     from paper_2310_04676_gb300 import workloads as W
     wl = W.config("C3")
     per = max(2.0, 150.0 / max(1, args.steps + args.warmup))
-    runs = [cpu_baseline(wl, seconds=per) for _ in range(args.warmup + args.steps)]
-    v = float(np.median([r["value"] for r in runs[args.warmup:]]))
-    cb = dict(runs[-1])
+    runs = []
+    for _ in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = cpu_baseline(wl, seconds=per)
+        r["wall_s"] = time.perf_counter() - t0
+        runs.append(r)
+    timed = runs[args.warmup:]
+    v = float(np.median([r["value"] for r in timed]))
+    cb = dict(timed[-1])
     cb["value"] = v
+    wall = [r["wall_s"] for r in timed]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "env-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * ROLLOUT_T["C3"] * wl.desc["num_envs"] / v,
+            "ms_per_step": 1e3 * float(np.median(wall)),
+            "step_is": "one bounded sample of the workload (%s)" % cb["sample"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": wl.name, "rollout_steps": ROLLOUT_T["C3"],
-                       "substeps": wl.substeps, "dt": wl.dt},
+            "config": {"workload": wl.name, "envs_per_gpu": wl.desc["num_envs"],
+                       "rollout_steps": ROLLOUT_T["C3"], "substeps": wl.substeps, "dt": wl.dt,
+                       "l2": "not applicable (host run)"},
+            "form": "FP64 oracle (batched PyTorch, CPU) on the host cores",
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -915,7 +949,7 @@ def main():
             line["cpu_baseline"] = cpu_baseline(wl) if want_cpu else None
             if want_cpu:
                 line["cpu_baseline"]["single_core"] = cpu_baseline_single_core(wl)
-                launch = line["config"]["launch"]
+                launch = line["launch"]
                 line["equal_accuracy"] = equal_accuracy(
                     wl, (launch["threads_per_block"],
                          {"persistent": 0, "step_graph": 1}[launch["mode"]],

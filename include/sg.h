@@ -29,6 +29,12 @@
  *    sg_sync_status() reports.
  *  - No C++ exception crosses this ABI.  sg_last_error() describes the last
  *    failing call of a context.
+ *  - A context belongs to the CUDA device that was current at sg_create
+ *    (sg_device()).  Every call that enqueues work or reads device state
+ *    first checks that this device is current; if another device is current
+ *    it returns SG_ERR_INVALID_ARG (SG_ERR_CUDA if the current device cannot
+ *    be queried) and enqueues nothing.  sg_destroy releases the context on
+ *    its own device whatever device is current.
  */
 #ifndef SG_H
 #define SG_H
@@ -178,7 +184,10 @@ sg_status sg_create(const sg_desc *desc, void *stream, sg_ctx **out);
 /* Free a context and its device memory (synchronises its stream).  NULL is a no-op. */
 void sg_destroy(sg_ctx *ctx);
 
-/* Change the stream later calls enqueue on. */
+/* The CUDA device the context belongs to (current at sg_create); -1 for NULL. */
+int32_t sg_device(const sg_ctx *ctx);
+
+/* Change the stream later calls enqueue on (a stream of the context's device). */
 sg_status sg_set_stream(sg_ctx *ctx, void *stream);
 
 int32_t sg_obs_dim(const sg_ctx *ctx);
@@ -406,6 +415,29 @@ sg_status sg_sync_status(sg_ctx *ctx);
  * *tflops.  Synchronises the stream; allocates and frees a small buffer.
  * SG_ERR_INVALID_ARG for iters < 1, repeats < 1 or a NULL tflops. */
 sg_status sg_measure_fp32_fma_rate(void *stream, int32_t iters, int32_t repeats, float *tflops);
+
+/*
+ * Test hook (not part of the method): makes a bounded device-side wait run
+ * out, so that the give-up path of the step kernels can be exercised
+ * without a GPU fault or hang.  mode:
+ *   SG_FAULT_NONE            normal operation (the default);
+ *   SG_FAULT_SKIP_PARAM_COPY the one-thread step kernel (chain split 1) does
+ *                            not start the copy of each warp's parameter
+ *                            record, so every warp's wait for it runs out;
+ *   SG_FAULT_SKIP_PARTNER    in the warp-pair step kernel (chain split 2)
+ *                            the dynamics warp of every pair leaves out its
+ *                            first arrival at the pair's exchange, so both
+ *                            warps' waits for it run out.
+ * wait_limit_ns bounds every wait of the step kernels in wall-clock time
+ * (0 = the default, 2 s; at most 2e9).  A wait that runs out sets the
+ * context's timeout flag (sg_sync_status returns SG_ERR_TIMEOUT); the
+ * warps then leave the kernel without writing outputs or state, so the
+ * context's state and step counts are unchanged.  Applies to sg_step,
+ * sg_rollout (re-captured when the hook changes) and sg_observe.
+ * SG_ERR_INVALID_ARG for an unknown mode or a limit out of range.
+ */
+enum { SG_FAULT_NONE = 0, SG_FAULT_SKIP_PARAM_COPY = 1, SG_FAULT_SKIP_PARTNER = 2 };
+sg_status sg_debug_set_fault(sg_ctx *ctx, int32_t mode, int64_t wait_limit_ns);
 
 /* Message of the last failing call on ctx (never NULL; "" if none).
  * With ctx == NULL: the last sg_create failure of this thread. */

@@ -82,7 +82,9 @@ typedef struct sg_ppo_config {
 /* Create a PPO loop over the envs of `env` (which it uses, not owns; the env
  * must outlive it).  Allocates parameters, Adam moments, rollout buffers
  * ((n_steps + 1) x E x D observations and the per-step arrays), minibatch
- * activations and a cuBLAS handle on the current device.  Parameters start
+ * activations and a cuBLAS handle on the current device, which must be the
+ * env context's device (as for every sg_ppo_* call that enqueues work:
+ * otherwise SG_ERR_INVALID_ARG and nothing is enqueued).  Parameters start
  * at zero: set them with sg_ppo_set_params.  Invalid configurations return
  * SG_ERR_INVALID_ARG (message in sg_last_error(env)). */
 sg_status sg_ppo_create(sg_ctx *env, const sg_ppo_config *cfg, sg_ppo **out);

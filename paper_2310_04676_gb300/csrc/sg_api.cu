@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "sg.h"
+#include "sg_devcheck.h"
 #include "sg_internal.h"
 #include "sg_diff.h"
 #include "sg_kernels.h"
@@ -19,6 +20,7 @@
 
 struct sg_ctx {
   sg::Plan plan;
+  int device = -1;                 // CUDA device current at sg_create (owns everything below)
   cudaStream_t stream = nullptr;
   float* d_params = nullptr;
   float* d_q = nullptr;
@@ -35,6 +37,8 @@ struct sg_ctx {
   int rollout_mode = SG_ROLLOUT_PERSISTENT;
   int split = 1;
   int host_io = SG_HOST_IO_AUTO;
+  int fault = sg::FAULT_NONE;      // test hook (sg_debug_set_fault)
+  unsigned long long wait_ns = sg::kDefaultWaitNs;
   // pipelined host rollout: copy streams and events
   cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
   cudaEvent_t host_ev[2 + 2 * 8] = {};
@@ -47,12 +51,13 @@ struct sg_ctx {
     float* obs;
     float* reward;
     uint8_t* done;
-    int T, substeps, threads, mode, split;
+    int T, substeps, threads, mode, split, fault;
+    unsigned long long wait_ns;
     float dt;
     bool operator==(const Key& o) const {
       return actions == o.actions && obs == o.obs && reward == o.reward && done == o.done &&
              T == o.T && substeps == o.substeps && threads == o.threads && mode == o.mode &&
-             split == o.split && dt == o.dt;
+             split == o.split && fault == o.fault && wait_ns == o.wait_ns && dt == o.dt;
     }
   } graph_key{};
   // device staging for sg_rollout_host
@@ -91,6 +96,21 @@ sg_status set_err(sg_ctx* ctx, sg_status code, const std::string& msg) {
   if (ctx) ctx->last_error = msg;
   return code;
 }
+
+// SG_OK if the context's device is current, else an error naming entry point fn.
+sg_status on_device(sg_ctx* ctx, const char* fn) {
+  std::string msg;
+  const sg_status st = sg::check_device(
+      ctx->device, [](int* d) { return (int)cudaGetDevice(d); }, fn, &msg);
+  if (st != SG_OK) set_err(ctx, st, msg);
+  return st;
+}
+
+#define SG_CHECK_DEVICE(ctx, fn)                   \
+  do {                                             \
+    const sg_status st_dev_ = on_device(ctx, fn);  \
+    if (st_dev_ != SG_OK) return st_dev_;          \
+  } while (0)
 
 sg_status cuda_err(sg_ctx* ctx, cudaError_t e, const char* what) {
   if (e == cudaSuccess) return SG_OK;
@@ -183,6 +203,8 @@ sg::StepArgs step_args(sg_ctx* c, float dt, int substeps, int T) {
   a.substeps = substeps;
   a.T = T;
   a.h = dt / (float)substeps;
+  a.fault = c->fault;
+  a.wait_ns = c->wait_ns;
   return a;
 }
 
@@ -265,7 +287,7 @@ sg_status pipelined_host_rollout(sg_ctx* c, const float* act_h, int T, float dt,
 sg_status run_rollout(sg_ctx* c, const float* actions, int T, float dt, int substeps, float* obs,
                       float* rew, uint8_t* done) {
   const sg_ctx::Key key{actions, obs, rew, done, T, substeps, c->threads, c->rollout_mode,
-                        c->split, dt};
+                        c->split, c->fault, c->wait_ns, dt};
   if (!c->graph_exec || !(key == c->graph_key)) {
     if (c->graph_exec) {
       cudaGraphExecDestroy(c->graph_exec);
@@ -394,6 +416,12 @@ sg_status sg_create(const sg_desc* desc, void* stream, sg_ctx** out) {
     free_ctx(c);
     return st;
   }
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    g_create_error = "sg_create: no CUDA device is available";
+    free_ctx(c);
+    return SG_ERR_CUDA;
+  }
   c->stream = static_cast<cudaStream_t>(stream);
   const sg::Plan& P = c->plan;
   const size_t NS = P.num_slots;
@@ -450,9 +478,29 @@ sg_status sg_create(const sg_desc* desc, void* stream, sg_ctx** out) {
 
 void sg_destroy(sg_ctx* ctx) {
   if (!ctx) return;
+  // release on the owning device, then restore the caller's current device
+  int cur = -1;
+  const bool have = cudaGetDevice(&cur) == cudaSuccess;
+  const bool other = have && cur != ctx->device && ctx->device >= 0;
+  if (other) cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   free_ctx(ctx);
+  if (other) cudaSetDevice(cur);
 }
+
+sg_status sg_debug_set_fault(sg_ctx* ctx, int32_t mode, int64_t wait_limit_ns) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  if (mode != SG_FAULT_NONE && mode != SG_FAULT_SKIP_PARAM_COPY && mode != SG_FAULT_SKIP_PARTNER)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "sg_debug_set_fault: unknown mode");
+  if (wait_limit_ns < 0 || wait_limit_ns > (int64_t)sg::kDefaultWaitNs)
+    return set_err(ctx, SG_ERR_INVALID_ARG,
+                   "sg_debug_set_fault: wait_limit_ns must be 0 (default) .. 2e9");
+  ctx->fault = mode;
+  ctx->wait_ns = wait_limit_ns ? (unsigned long long)wait_limit_ns : sg::kDefaultWaitNs;
+  return SG_OK;
+}
+
+int32_t sg_device(const sg_ctx* ctx) { return ctx ? ctx->device : -1; }
 
 sg_status sg_set_stream(sg_ctx* ctx, void* stream) {
   if (!ctx) return SG_ERR_INVALID_ARG;
@@ -466,11 +514,14 @@ int32_t sg_max_joints(const sg_ctx* ctx) { return ctx ? ctx->plan.max_joints : 0
 
 sg_status sg_reset(sg_ctx* ctx, const uint8_t* env_mask_dev) {
   if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_reset");
   return cuda_err(ctx, sg::launch_reset(state_args(ctx), env_mask_dev, ctx->stream), "sg_reset");
 }
 
 sg_status sg_step(sg_ctx* ctx, const float* actions_dev, float dt, int32_t substeps,
                   float* obs_dev, float* reward_dev, uint8_t* done_dev) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_step");
   sg_status st = check_step_args(ctx, actions_dev, dt, substeps, obs_dev, reward_dev, done_dev);
   if (st != SG_OK) return st;
   sg::StepArgs a = step_args(ctx, dt, substeps, 1);
@@ -484,6 +535,7 @@ sg_status sg_step(sg_ctx* ctx, const float* actions_dev, float dt, int32_t subst
 sg_status sg_observe(sg_ctx* ctx, const float* targets_dev, const uint8_t* env_mask_dev,
                      float* obs_dev) {
   if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_observe");
   if (!targets_dev || !obs_dev)
     return set_err(ctx, SG_ERR_INVALID_ARG, "sg_observe: targets and obs must be non-NULL");
   sg::StepArgs a = step_args(ctx, 1.f, 1, 1);
@@ -497,6 +549,8 @@ sg_status sg_observe(sg_ctx* ctx, const float* targets_dev, const uint8_t* env_m
 
 sg_status sg_rollout(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt,
                      int32_t substeps, float* obs_dev, float* reward_dev, uint8_t* done_dev) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_rollout");
   sg_status st = check_rollout_args(ctx, actions_dev, T, dt, substeps, obs_dev, reward_dev, done_dev);
   if (st != SG_OK) return st;
   return run_rollout(ctx, actions_dev, T, dt, substeps, obs_dev, reward_dev, done_dev);
@@ -514,6 +568,8 @@ sg_status sg_set_host_io(sg_ctx* ctx, int32_t mode) {
 sg_status sg_rollout_host(sg_ctx* ctx, const float* actions_host, int32_t T, float dt,
                           int32_t substeps, float* obs_host, float* reward_host,
                           uint8_t* done_host) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_rollout_host");
   sg_status st =
       check_rollout_args(ctx, actions_host, T, dt, substeps, obs_host, reward_host, done_host);
   if (st != SG_OK) return st;
@@ -594,6 +650,8 @@ sg_status sg_get_launch(const sg_ctx* ctx, int32_t* threads_per_block, int32_t* 
 sg_status sg_autotune(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt,
                       int32_t substeps, float* obs_dev, float* reward_dev, uint8_t* done_dev,
                       int32_t repeats, float* best_ms) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_autotune");
   sg_status st = check_rollout_args(ctx, actions_dev, T, dt, substeps, obs_dev, reward_dev, done_dev);
   if (st != SG_OK) return st;
   if (repeats < 1 || repeats > 1000) return set_err(ctx, SG_ERR_INVALID_ARG, "repeats must be 1..1000");
@@ -655,6 +713,7 @@ sg_status sg_autotune(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt
 
 sg_status sg_get_state(sg_ctx* ctx, float* q_dev, float* qd_dev, int32_t* step_count_dev) {
   if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_get_state");
   return cuda_err(ctx, sg::launch_get_state(state_args(ctx), q_dev, qd_dev, step_count_dev,
                                             ctx->stream),
                   "sg_get_state");
@@ -663,6 +722,7 @@ sg_status sg_get_state(sg_ctx* ctx, float* q_dev, float* qd_dev, int32_t* step_c
 sg_status sg_set_state(sg_ctx* ctx, const float* q_dev, const float* qd_dev,
                        const int32_t* step_count_dev) {
   if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_set_state");
   return cuda_err(ctx, sg::launch_set_state(state_args(ctx), q_dev, qd_dev, step_count_dev,
                                             ctx->stream),
                   "sg_set_state");
@@ -714,6 +774,7 @@ DiffArgs context_diff_args(sg_ctx* c) {
   return a;
 }
 void context_set_error(sg_ctx* c, const char* msg) { c->last_error = msg; }
+sg_status context_check_device(sg_ctx* c, const char* fn) { return on_device(c, fn); }
 cudaStream_t context_stream(sg_ctx* c) { return c->stream; }
 const std::vector<int32_t>& context_env_dof(sg_ctx* c) { return c->plan.env_dof; }
 }  // namespace sg
@@ -723,6 +784,7 @@ extern "C" {
 sg_status sg_diff_forward(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt,
                           int32_t substeps, int32_t ckpt_every, float* ee_dev) {
   if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_diff_forward");
   if (!actions_dev || !ee_dev)
     return set_err(ctx, SG_ERR_INVALID_ARG, "actions and ee must be non-NULL");
   if (T < 1 || T > 4096) return set_err(ctx, SG_ERR_INVALID_ARG, "T must be 1..4096");
@@ -773,6 +835,7 @@ sg_status sg_diff_backward(sg_ctx* ctx, const float* actions_dev, const float* d
                            float* dactions_dev, float* dmass_dev, float* dq0_dev,
                            float* dqd0_dev) {
   if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_diff_backward");
   if (!ctx->diff_ready)
     return set_err(ctx, SG_ERR_INVALID_ARG, "sg_diff_backward needs a preceding sg_diff_forward");
   if (!actions_dev || !dl_dee_dev || !dactions_dev || !dmass_dev)
@@ -793,6 +856,7 @@ sg_status sg_diff_backward(sg_ctx* ctx, const float* actions_dev, const float* d
 
 sg_status sg_set_link_mass(sg_ctx* ctx, const float* mass_dev) {
   if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_set_link_mass");
   if (!mass_dev) return set_err(ctx, SG_ERR_INVALID_ARG, "mass must be non-NULL");
   sg::MassArgs m;
   m.params = ctx->d_params;
@@ -808,6 +872,7 @@ sg_status sg_set_link_mass(sg_ctx* ctx, const float* mass_dev) {
 
 sg_status sg_get_goal_state(sg_ctx* ctx, float* offset_dev, float* velocity_dev) {
   if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_get_goal_state");
   if (!ctx->d_track) return set_err(ctx, SG_ERR_INVALID_ARG, "goal state exists only for SG_TASK_TRACK");
   return cuda_err(ctx, sg::launch_goal_state(state_args(ctx), offset_dev, velocity_dev, nullptr,
                                              nullptr, ctx->stream),
@@ -816,6 +881,7 @@ sg_status sg_get_goal_state(sg_ctx* ctx, float* offset_dev, float* velocity_dev)
 
 sg_status sg_set_goal_state(sg_ctx* ctx, const float* offset_dev, const float* velocity_dev) {
   if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_set_goal_state");
   if (!ctx->d_track) return set_err(ctx, SG_ERR_INVALID_ARG, "goal state exists only for SG_TASK_TRACK");
   return cuda_err(ctx, sg::launch_goal_state(state_args(ctx), nullptr, nullptr, offset_dev,
                                              velocity_dev, ctx->stream),
@@ -825,6 +891,7 @@ sg_status sg_set_goal_state(sg_ctx* ctx, const float* offset_dev, const float* v
 sg_status sg_set_paths(sg_ctx* ctx, const float* ctrl_dev, int32_t K,
                        const uint8_t* env_mask_dev) {
   if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_set_paths");
   if (ctx->plan.task != SG_TASK_PATH)
     return set_err(ctx, SG_ERR_INVALID_ARG, "sg_set_paths: not a path-following context");
   if (!ctrl_dev) return set_err(ctx, SG_ERR_INVALID_ARG, "sg_set_paths: ctrl_dev is NULL");
@@ -838,6 +905,7 @@ sg_status sg_set_paths(sg_ctx* ctx, const float* ctrl_dev, int32_t K,
 
 sg_status sg_get_paths(sg_ctx* ctx, float* path_dev) {
   if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_get_paths");
   if (ctx->plan.task != SG_TASK_PATH)
     return set_err(ctx, SG_ERR_INVALID_ARG, "sg_get_paths: not a path-following context");
   if (!path_dev) return set_err(ctx, SG_ERR_INVALID_ARG, "sg_get_paths: path_dev is NULL");
@@ -849,6 +917,7 @@ sg_status sg_get_paths(sg_ctx* ctx, float* path_dev) {
 
 sg_status sg_sync_status(sg_ctx* ctx) {
   if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_sync_status");
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_err(ctx, e, "sg_sync_status");
   int32_t flags = 0;

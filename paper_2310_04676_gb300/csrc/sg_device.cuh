@@ -10,7 +10,9 @@
 namespace sg {
 
 constexpr float kGravity = 9.81f;
-constexpr int kWaitLimit = 1 << 20;   // bounded mbarrier polling
+// Default wall-clock bound of every device-side wait (2 s); a test hook can
+// shorten it per context (StepArgs::wait_ns).
+constexpr unsigned long long kWaitNs = kDefaultWaitNs;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -35,20 +37,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
+// One poll of a barrier phase; the thread may be suspended for at most
+// about 20 us (the suspend-time hint) while the phase is incomplete.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
       : "memory");
   return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  for (int it = 0; it < kWaitLimit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -57,17 +55,23 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// Wait that may legitimately last milliseconds (a partner warp's whole
-// segment of work): bounded by wall time (limit_ns) and, should the timer
-// not advance, by an iteration count.
+// Wait for a barrier phase, bounded by wall time (limit_ns, read from
+// %globaltimer after every unsuccessful poll) and, should the timer not
+// advance, by an iteration count.
 __device__ __forceinline__ bool mbar_wait_timed(uint64_t* bar, unsigned parity,
                                                 unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer_ns();
-  for (unsigned it = 0; it < (1u << 30); ++it) {
+  for (unsigned it = 0; it < (1u << 24); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63u) == 63u && globaltimer_ns() - t0 > limit_ns) return false;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
   return false;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity,
+                                                  unsigned long long limit_ns = kWaitNs) {
+  return mbar_wait_timed(bar, parity, limit_ns);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -75,17 +79,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // Bounded wait with a warp-uniform verdict; false (and the error flag set)
-// if the partner did not arrive in time.
-__device__ __forceinline__ bool pair_wait(uint64_t* bar, unsigned& parity, int* err, int lane) {
-  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity));
-  parity ^= 1u;
-  if (!ok && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
-  return ok;
-}
-
-// pair_wait for hand-offs of whole segments (limit 2 s)
-__device__ __forceinline__ bool pair_wait_long(uint64_t* bar, unsigned& parity, int* err, int lane) {
-  const bool ok = __all_sync(0xffffffffu, mbar_wait_timed(bar, parity, 2000000000ull));
+// if the partner did not arrive within limit_ns.
+__device__ __forceinline__ bool pair_wait(uint64_t* bar, unsigned& parity, int* err, int lane,
+                                          unsigned long long limit_ns = kWaitNs) {
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_timed(bar, parity, limit_ns));
   parity ^= 1u;
   if (!ok && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
   return ok;

@@ -64,6 +64,8 @@ struct MassArgs {
 // the context's parameter/state/slot pointers and sizes (shape fields zero).
 DiffArgs context_diff_args(sg_ctx* ctx);
 void context_set_error(sg_ctx* ctx, const char* msg);
+// SG_OK if the context's device is current; else an error (message set) naming fn
+sg_status context_check_device(sg_ctx* ctx, const char* fn);
 cudaStream_t context_stream(sg_ctx* ctx);
 // total joints of every env [E] (host copy of the description)
 const std::vector<int32_t>& context_env_dof(sg_ctx* ctx);

@@ -65,6 +65,9 @@ SG_HD inline SlotFields decode_slot(int info) {
 // Joint code of a generic chain: per joint 3 bits = axis (2 bits) | type << 2.
 SG_HD inline int joint_code_bits(int type, int axis) { return (axis & 3) | ((type & 1) << 2); }
 
+// Default wall-clock bound of every device-side wait (2 s)
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;
+
 // Device error flags
 constexpr int DEVERR_NONFINITE = 1;
 constexpr int DEVERR_TIMEOUT = 2;
@@ -124,6 +127,15 @@ struct StepArgs {
   float alpha, h;
   uint32_t seed;
   float track_sigma, track_limit;
+  // test hook (sg_debug_set_fault): FAULT_* mode and the wall-clock bound
+  // of every device-side wait of the step kernels
+  int fault;
+  unsigned long long wait_ns;
 };
+
+// Test-hook modes (sg.h, sg_debug_set_fault)
+constexpr int FAULT_NONE = 0;
+constexpr int FAULT_SKIP_PARAM_COPY = 1;   // step kernel: no parameter copy is started
+constexpr int FAULT_SKIP_PARTNER = 2;      // warp-pair kernel: role 0 skips its first arrival
 
 }  // namespace sg

@@ -17,20 +17,23 @@
 namespace sg {
 
 // Stage the warp's parameter record into shared memory; false if the copy
-// did not complete within the polling bound (error flag set).
+// did not complete within the wait bound (error flag set).  With the test
+// hook FAULT_SKIP_PARAM_COPY no copy is started, so the wait runs out.
 __device__ __forceinline__ bool stage_record(const StepArgs& a, int gw, int cls, float* rec,
                                              uint64_t* bar, int lane) {
   if (lane == 0) {
     mbar_init(bar, 1);
-    const unsigned bytes = (unsigned)record_bytes_dev(cls);
-    mbar_expect_tx(bar, bytes);
-    bulk_g2s(rec, a.params + (size_t)gw * kRecordFloats, bytes, bar);
+    if (a.fault != FAULT_SKIP_PARAM_COPY) {
+      const unsigned bytes = (unsigned)record_bytes_dev(cls);
+      mbar_expect_tx(bar, bytes);
+      bulk_g2s(rec, a.params + (size_t)gw * kRecordFloats, bytes, bar);
+    }
   }
   __syncwarp();
   // warp-uniform verdict: either every lane proceeds or the whole warp leaves
-  if (__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0))) return true;
+  if (__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0, a.wait_ns))) return true;
   if (lane == 0) atomicOr(a.err, DEVERR_TIMEOUT);
-  mbar_wait_bounded(bar, 0);   // give an in-flight copy a second bounded chance
+  mbar_wait_bounded(bar, 0, a.wait_ns);   // give an in-flight copy a second bounded chance
   __syncwarp();
   return false;
 }

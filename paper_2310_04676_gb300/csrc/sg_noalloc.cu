@@ -40,14 +40,25 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
 float* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (on the first call of the entry point on that device).
+// Device address of the scratch array on the current device, looked up on
+// the first call of the entry point on that device and cached.  The cached
+// address is checked against the runtime before use (it becomes invalid if
+// the program resets the device, which unloads the library's module); an
+// address the runtime no longer knows is looked up again.
 cudaError_t noalloc_scratch(float** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (g_scratch_ptr[dev]) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, g_scratch_ptr[dev]) != cudaSuccess ||
+        attr.type != cudaMemoryTypeDevice || attr.device != dev) {
+      cudaGetLastError();          // clear the error of an unknown pointer
+      g_scratch_ptr[dev] = nullptr;
+    }
+  }
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -96,6 +107,8 @@ extern "C" sg_status sg_diff_track_noalloc(sg_ctx* ctx, const float* actions_dev
                                            float* dmass_dev) {
   using namespace sg;
   if (!ctx) return SG_ERR_INVALID_ARG;
+  const sg_status st_dev = context_check_device(ctx, "sg_diff_track_noalloc");
+  if (st_dev != SG_OK) return st_dev;
   auto fail = [&](sg_status st, const char* msg) {
     context_set_error(ctx, msg);
     return st;

@@ -94,8 +94,9 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
     for (int k = 0; k < a.substeps; ++k, ++xphase) {
       float* xb = xbuf + (xphase & 1) * kXHalf;   // double-buffered exchange
       float L[N][N], inv[N], dqd[N];
+      const bool skip = a.fault == FAULT_SKIP_PARTNER && role == 0 && xphase == 0;
       if (!pair_substep(pat, rec, q, qd, qs, cq, sq, a.h, xb, bar_x, ph_x, a.err, lane, role, L,
-                        inv, dqd))
+                        inv, dqd, a.wait_ns, skip))
         return;
       integrate(pat, q, qd, dqd, a.h);
       joint_sincos(pat, q, cq, sq);
@@ -184,7 +185,7 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
       if (valid && c == 0) a.reward[(size_t)t * E + env] = reward;
     }
     mbar_arrive(bar_stage);
-    if (!pair_wait(bar_stage, ph_stage, a.err, lane)) return;
+    if (!pair_wait(bar_stage, ph_stage, a.err, lane, a.wait_ns)) return;
     // each role writes half of the staged rows
     constexpr int half = nrows >> 1;
     const int r0 = role * half;
@@ -245,8 +246,8 @@ __global__ void __launch_bounds__(kMaxThreads) step_kernel_pair(StepArgs a) {
     bulk_g2s(rec, a.params + (size_t)group * kRecordFloats, bytes, bars);
   }
   unsigned ph_tma = 0;
-  if (!pair_wait(bars, ph_tma, a.err, lane)) {
-    mbar_wait_bounded(bars, 0);   // second bounded chance for an in-flight copy
+  if (!pair_wait(bars, ph_tma, a.err, lane, a.wait_ns)) {
+    mbar_wait_bounded(bars, 0, a.wait_ns);   // second bounded chance for an in-flight copy
     return;
   }
   const Rec r{rec + lane};

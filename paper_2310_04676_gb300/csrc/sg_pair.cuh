@@ -27,7 +27,9 @@ __device__ __forceinline__ constexpr int tri(int i, int j) { return i * (i + 1) 
 // Computes this role's half of the substep from (q, qd, q*, cos q, sin q),
 // exchanges it through xb and returns in (L, inv, dqd) the factor, the
 // reciprocal diagonal and the solved velocity increment (state not yet
-// advanced).  False (error flag set) if the partner did not arrive in time.
+// advanced).  False (error flag set) if the partner did not arrive within
+// wait_ns.  skip_arrival (a test hook) leaves out this warp's arrival, so
+// that both warps' waits run out.
 template <class Pat>
 __device__ __forceinline__ bool pair_substep(const Pat& pat, const Rec& rec, const float (&q)[7],
                                              const float (&qd)[7], const float (&qs)[7],
@@ -35,7 +37,9 @@ __device__ __forceinline__ bool pair_substep(const Pat& pat, const Rec& rec, con
                                              float h, float* xb, uint64_t* bar_x, unsigned& ph_x,
                                              int* err, int lane, int role,
                                              float (&L)[Pat::N][Pat::N], float (&inv)[Pat::N],
-                                             float (&dqd)[Pat::N]) {
+                                             float (&dqd)[Pat::N],
+                                             unsigned long long wait_ns = kWaitNs,
+                                             bool skip_arrival = false) {
   constexpr int N = Pat::N;
   if (role == 0) {
     float bias[N], rhs[N], arm[N], Mdummy[N][N];
@@ -60,8 +64,8 @@ __device__ __forceinline__ bool pair_substep(const Pat& pat, const Rec& rec, con
       for (int j = 0; j < i; ++j) xb[tri(i, j) * kWarp + lane] = M[i][j];
     }
   }
-  mbar_arrive(bar_x);
-  if (!pair_wait(bar_x, ph_x, err, lane)) return false;
+  if (!skip_arrival) mbar_arrive(bar_x);
+  if (!pair_wait(bar_x, ph_x, err, lane, wait_ns)) return false;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     if (!pat.active(i)) continue;

@@ -708,12 +708,21 @@ sg_status enqueue_collect(sg_ppo* p) {
 
 }  // namespace
 
+// the environment context's device must be current (see sg_devcheck.h)
+#define SG_PPO_CHECK_DEVICE(p, fn)                                         \
+  do {                                                                     \
+    const sg_status st_dev_ = sg::context_check_device((p)->env, fn);      \
+    if (st_dev_ != SG_OK) return st_dev_;                                  \
+  } while (0)
+
 extern "C" {
 
 sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
   if (!out) return SG_ERR_INVALID_ARG;
   *out = nullptr;
   if (!env || !cfg) return SG_ERR_INVALID_ARG;
+  const sg_status st_dev = sg::context_check_device(env, "sg_ppo_create");
+  if (st_dev != SG_OK) return st_dev;
   sg_ppo* p = new (std::nothrow) sg_ppo();
   if (!p) return SG_ERR_OOM;
   p->env = env;
@@ -855,18 +864,25 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
 
 void sg_ppo_destroy(sg_ppo* p) {
   if (!p) return;
+  // release on the env context's device, then restore the caller's current device
+  const int owner = sg_device(p->env);
+  int cur = -1;
+  const bool other = cudaGetDevice(&cur) == cudaSuccess && owner >= 0 && cur != owner;
+  if (other) cudaSetDevice(owner);
   if (p->stream) cudaStreamSynchronize(p->stream);
   if (p->collect_exec) cudaGraphExecDestroy(p->collect_exec);
   if (p->blas) cublasDestroy(p->blas);
   if (p->blas_ws) cudaFree(p->blas_ws);
   for (void* a : p->allocs) cudaFree(a);
   delete p;
+  if (other) cudaSetDevice(cur);
 }
 
 int64_t sg_ppo_num_params(const sg_ppo* p) { return p ? (int64_t)p->public_params : 0; }
 
 sg_status sg_ppo_set_params(sg_ppo* p, const float* src) {
   if (!p || !src) return SG_ERR_INVALID_ARG;
+  SG_PPO_CHECK_DEVICE(p, "sg_ppo_set_params");
   bind_stream(p, sg::context_stream(p->env));
   cudaError_t e = cudaMemsetAsync(p->params, 0, p->L.total * 4, p->stream);   // padding stays 0
   const int n = (int)p->public_params;
@@ -879,6 +895,7 @@ sg_status sg_ppo_set_params(sg_ppo* p, const float* src) {
 
 sg_status sg_ppo_get_params(sg_ppo* p, float* dst) {
   if (!p || !dst) return SG_ERR_INVALID_ARG;
+  SG_PPO_CHECK_DEVICE(p, "sg_ppo_get_params");
   bind_stream(p, sg::context_stream(p->env));
   const int n = (int)p->public_params;
   sg::gather_params_kernel<<<sg::grid_for(n, 256), 256, 0, p->stream>>>(p->params, p->pub2int, n,
@@ -888,6 +905,7 @@ sg_status sg_ppo_get_params(sg_ppo* p, float* dst) {
 
 sg_status sg_ppo_reset(sg_ppo* p, int64_t step0) {
   if (!p) return SG_ERR_INVALID_ARG;
+  SG_PPO_CHECK_DEVICE(p, "sg_ppo_reset");
   bind_stream(p, sg::context_stream(p->env));
   sg_status st = sg_reset(p->env, nullptr);
   // the first observations go where a collect leaves its last ones
@@ -906,6 +924,7 @@ sg_status sg_ppo_reset(sg_ppo* p, int64_t step0) {
 
 sg_status sg_ppo_collect(sg_ppo* p) {
   if (!p) return SG_ERR_INVALID_ARG;
+  SG_PPO_CHECK_DEVICE(p, "sg_ppo_collect");
   cudaStream_t s = sg::context_stream(p->env);
   if (!p->collect_exec) {
     // capture on a private stream, then replay on the env's stream
@@ -937,6 +956,7 @@ sg_status sg_ppo_collect(sg_ppo* p) {
 
 sg_status sg_ppo_update(sg_ppo* p, const int32_t* perm, float* stats) {
   if (!p || !perm) return SG_ERR_INVALID_ARG;
+  SG_PPO_CHECK_DEVICE(p, "sg_ppo_update");
   bind_stream(p, sg::context_stream(p->env));
   const sg_ppo_config& c = p->cfg;
   const int M = p->M, A = p->A, D = p->D, E = p->E;
@@ -999,6 +1019,7 @@ bool buffer_of(sg_ppo* p, int which, void** ptr, size_t* bytes) {
 
 sg_status sg_ppo_get_buffer(sg_ppo* p, int32_t which, void* dst) {
   if (!p || !dst) return SG_ERR_INVALID_ARG;
+  SG_PPO_CHECK_DEVICE(p, "sg_ppo_get_buffer");
   void* ptr;
   size_t bytes;
   if (!buffer_of(p, which, &ptr, &bytes)) return fail(p, SG_ERR_INVALID_ARG, "unknown buffer");
@@ -1015,6 +1036,7 @@ sg_status sg_ppo_get_buffer(sg_ppo* p, int32_t which, void* dst) {
 
 sg_status sg_ppo_set_buffer(sg_ppo* p, int32_t which, const void* src) {
   if (!p || !src) return SG_ERR_INVALID_ARG;
+  SG_PPO_CHECK_DEVICE(p, "sg_ppo_set_buffer");
   void* ptr;
   size_t bytes;
   if (!buffer_of(p, which, &ptr, &bytes) || which == SG_PPO_GRAD)

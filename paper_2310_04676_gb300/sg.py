@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_CUDA", 3: "SG_ER
 DONE_TERMINATED, DONE_TIMEOUT, DONE_NONFINITE = 1, 2, 4
 HOST_IO_AUTO, HOST_IO_STAGED, HOST_IO_DIRECT = 0, 1, 2
 ROLLOUT_PERSISTENT, ROLLOUT_STEP_GRAPH = 0, 1
+FAULT_NONE, FAULT_SKIP_PARAM_COPY, FAULT_SKIP_PARTNER = 0, 1, 2
 DRIVE_POSITION, DRIVE_VELOCITY, DRIVE_TORQUE = 0, 1, 2
 MAX_CHAINS = 4                     # chains per env (SG_MAX_CHAINS)
 
@@ -91,6 +92,8 @@ def load_library(path=LIB_PATH):
         "sg_create": (i32, [ctypes.POINTER(SgDesc), vp, ctypes.POINTER(vp)]),
         "sg_destroy": (None, [vp]),
         "sg_set_stream": (i32, [vp, vp]),
+        "sg_device": (i32, [vp]),
+        "sg_debug_set_fault": (i32, [vp, i32, ctypes.c_int64]),
         "sg_obs_dim": (i32, [vp]),
         "sg_num_envs": (i32, [vp]),
         "sg_max_joints": (i32, [vp]),
@@ -461,6 +464,17 @@ class Env:
     def sync_status(self):
         """Synchronise and return the device status code (raises nothing)."""
         return self.lib.sg_sync_status(self.ctx)
+
+    @property
+    def cuda_device(self):
+        """The CUDA device the context belongs to."""
+        return self.lib.sg_device(self.ctx)
+
+    def debug_set_fault(self, mode, wait_limit_ns=0):
+        """Test hook: FAULT_SKIP_PARAM_COPY / FAULT_SKIP_PARTNER make the
+        step kernels' bounded waits run out (after ``wait_limit_ns``); see
+        sg_debug_set_fault in include/sg.h."""
+        self._check(self.lib.sg_debug_set_fault(self.ctx, int(mode), int(wait_limit_ns)))
 
 
 class PPO:

@@ -124,3 +124,95 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.sg_reset(None, None) == sg.SG_ERR_INVALID_ARG
     assert lib.sg_obs_dim(None) == 0
     lib.sg_destroy(None)
+
+
+# ---- device ownership of a context ------------------------------------------
+DEVCHECK_DRIVER = r'''
+#include "sg_devcheck.h"
+#include <cstring>
+// a stand-in for cudaGetDevice: returns `err`, reports device `cur`
+extern "C" int check(int owner, int cur, int err, char* msg, int len) {
+  std::string m;
+  const sg_status st = sg::check_device(
+      owner, [&](int* d) { *d = cur; return err; }, "sg_step", &m);
+  std::strncpy(msg, m.c_str(), (size_t)len - 1);
+  msg[len - 1] = 0;
+  return (int)st;
+}
+'''
+
+
+def test_device_check_reports_a_mismatched_current_device(tmp_path):
+    """The check every entry point runs before enqueuing work, compiled for
+    the host against a stand-in device query: the owner's device current ->
+    SG_OK; another device current -> SG_ERR_INVALID_ARG naming both devices
+    (the call then enqueues nothing); a failing query -> SG_ERR_CUDA."""
+    import shutil
+    import subprocess
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("needs a host C++ compiler")
+    src = tmp_path / "devcheck.cpp"
+    src.write_text(DEVCHECK_DRIVER)
+    so = tmp_path / "devcheck.so"
+    subprocess.run([cxx, "-std=c++17", "-shared", "-fPIC", "-O1",
+                    "-I" + os.path.join(ROOT, "include"),
+                    "-I" + os.path.join(ROOT, "paper_2310_04676_gb300", "csrc"),
+                    str(src), "-o", str(so)], check=True)
+    lib = ctypes.CDLL(str(so))
+    buf = ctypes.create_string_buffer(256)
+    assert lib.check(1, 1, 0, buf, 256) == sg.SG_OK and buf.value == b""
+    assert lib.check(1, 0, 0, buf, 256) == sg.SG_ERR_INVALID_ARG
+    assert b"device 1" in buf.value and b"device 0 is current" in buf.value
+    assert b"sg_step" in buf.value
+    assert lib.check(0, 3, 0, buf, 256) == sg.SG_ERR_INVALID_ARG
+    assert lib.check(2, 2, 100, buf, 256) == sg.SG_ERR_CUDA
+
+
+def _extern_c_functions(path):
+    """{name: body} of the functions of a source file that take a context."""
+    text = open(path).read()
+    out = {}
+    for m in re.finditer(r"\n(?:extern \"C\" )?(?:sg_status|void|int32_t|int64_t|const char\*) "
+                         r"(sg_\w+)\(([^)]*)\)\s*\{", text):
+        if "sg_ctx" not in m.group(2) and "sg_ppo*" not in m.group(2):
+            continue
+        depth, i = 1, m.end()
+        while depth:
+            depth += {"{": 1, "}": -1}.get(text[i], 0)
+            i += 1
+        out[m.group(1)] = (m.group(2), text[m.end():i])
+    return out
+
+
+# calls that touch no device state (host-side settings and queries), and the
+# two destructors, which switch to the owning device instead of refusing
+NO_DEVICE_WORK = {"sg_set_stream", "sg_set_launch", "sg_get_launch", "sg_set_host_io",
+                  "sg_debug_set_fault", "sg_obs_dim", "sg_num_envs", "sg_max_joints",
+                  "sg_last_error", "sg_device", "sg_ppo_num_params"}
+SWITCHING = {"sg_destroy", "sg_ppo_destroy"}
+
+
+def test_every_entry_point_checks_the_device():
+    """Every exported call that takes a context and enqueues work or reads
+    device state runs the device check before anything else reaches the
+    device; the destructors release on the owning device."""
+    csrc = os.path.join(ROOT, "paper_2310_04676_gb300", "csrc")
+    seen = {}
+    for f in ("sg_api.cu", "sg_ppo.cu", "sg_noalloc.cu"):
+        seen.update(_extern_c_functions(os.path.join(csrc, f)))
+    declared = set(declared_functions())
+    assert {"sg_step", "sg_rollout", "sg_ppo_update", "sg_diff_track_noalloc"} <= set(seen)
+    for name, (params, body) in seen.items():
+        if name not in declared or name in NO_DEVICE_WORK:
+            continue
+        if name in SWITCHING:
+            assert "cudaSetDevice" in body, name
+            continue
+        if name == "sg_create":               # records the owning device
+            assert "cudaGetDevice(&c->device)" in body
+            continue
+        first_cuda = re.search(r"\bcuda\w+\(|launch_|run_rollout|snapshot\(|pipelined_", body)
+        check = re.search(r"SG_CHECK_DEVICE|SG_PPO_CHECK_DEVICE|context_check_device", body)
+        assert check, "%s does not check the device" % name
+        assert first_cuda is None or check.start() < first_cuda.start(), name

@@ -304,6 +304,43 @@ def _sub_desc(desc, pick):
     return sub
 
 
+def _sample_by_kind(kinds, per_kind, seed):
+    """`per_kind` envs drawn at random from each kind of a mixed batch."""
+    rng = np.random.default_rng(seed)
+    kinds = np.asarray(kinds)
+    pick = [rng.choice(np.flatnonzero(kinds == k), per_kind, replace=False)
+            for k in sorted(set(kinds.tolist()))]
+    return np.sort(np.concatenate(pick))
+
+
+def test_full_c3_batch_100_damped_steps_sampled_in_autotuned_plan():
+    """The whole 16384-env mixed batch for 100 control steps in the launch
+    plan the autotuner picks (one 100-step rollout), from the reset state:
+    256 envs drawn at random across the four kinds (64 each) against the
+    oracle -- joint positions to 1e-3 relative after 100 steps and the
+    rewards of every step to 1e-3 relative."""
+    wl = W.config("C3")
+    desc = wl.desc
+    E, steps = desc["num_envs"], 100
+    acts = W.joint_targets(desc, steps)
+    env = sg.Env(desc)
+    a = cuda(acts)
+    plan = env.autotune(a[:32], wl.dt, wl.substeps, repeats=1)
+    obs, rew, done = env.rollout(a, wl.dt, wl.substeps)
+    q = env.get_state()[0].cpu().numpy().astype(np.float64)
+    assert env.sync_status() == sg.SG_OK
+    pick = _sample_by_kind(wl.kinds, 64, seed=12)
+    ref = OracleEnv(_sub_desc(desc, pick))
+    r_ref = np.zeros((steps, len(pick)))
+    for t in range(steps):
+        _, r_ref[t], _ = ref.step(acts[t][pick], wl.dt, wl.substeps)
+    rel_q = rel_rows(q[pick], ref.q)
+    assert rel_q.max() <= 1e-3, (plan, rel_q.max())
+    r_gpu = rew.cpu().numpy()[:, pick].astype(np.float64)
+    rel_r = np.abs(r_gpu - r_ref) / np.maximum(np.abs(r_ref), 1e-3)
+    assert rel_r.max() <= 1e-3, (plan, rel_r.max())
+
+
 def test_c1_latency_workload_trajectory():
     """64 envs of one shared 7-DOF arm: 100 steps as two 50-step rollouts in
     the autotuned plan; positions within 1e-3 and rewards within 1e-3 of the
