@@ -839,6 +839,79 @@ def run_ppo_config(cx, name="P1", E=None):
     return line
 
 
+def _compact_rollout(line):
+    """The figures of one rollout workload's line that the default line's
+    `configs` object carries."""
+    rf = line["roofline"]
+    out = {"workload": line["config"]["workload"], "envs": line["config"]["envs_per_gpu"],
+           "value": line["value"], "unit": line["unit"],
+           "ms_per_rollout": line["ms_per_step"],
+           "rollout_steps": line["config"]["rollout_steps"],
+           "substeps": line["config"]["substeps"],
+           "us_per_control_step": line["us_per_control_step"],
+           "step_time_stats": line["step_time_stats"],
+           "plain": {"value": line["plain"]["value"], "ms_per_rollout": line["plain"]["ms_per_step"]},
+           "step_graph": {"value": line["step_graph"]["value"]},
+           "batched_over_plain": line["batched_over_plain"],
+           "bitwise_equal_forms": line["bitwise_equal_forms"], "status": line["status"],
+           "roofline": {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac",
+                                           "frac_of_fma_probe", "kernel", "flops_per_launch",
+                                           "algorithmic_bytes_per_launch", "hbm_gbs",
+                                           "hbm_frac")},
+           "launch": line["launch"], "gpu_launches": line["gpu_launches"],
+           "clocks": line["clocks"]}
+    if "path_build" in line:
+        out["path_build"] = line["path_build"]
+    return out
+
+
+def _compact_adjoint(g):
+    keep = ("workload", "value", "unit", "ms_per_rollout", "rollout_time_stats",
+            "ms_backward_kernel", "flops_per_rollout", "rollout_tflops", "gpu_launches",
+            "clocks", "rel_err_actions", "rel_err_mass", "error_vs")
+    out = {k: g[k] for k in keep if k in g}
+    out["roofline"] = {k: g["roofline"][k] for k in ("bound", "achieved", "peak", "unit", "frac",
+                                                     "frac_of_fma_probe", "kernel",
+                                                     "flops_per_launch", "traffic")}
+    return out
+
+
+def _compact_ppo(line):
+    keep = ("value", "unit", "ms_per_step", "iteration_time_stats", "ms_collect", "ms_update",
+            "roofline", "tf32", "gpu_launches", "library_launches", "clocks", "status", "e2e")
+    out = {k: line[k] for k in keep if k in line}
+    out["workload"] = line["config"]["workload"]
+    out["config"] = line["config"]
+    return out
+
+
+def run_all_configs(cx, with_error):
+    """Every other workload of the benchmark set at its stated size, each
+    timed like the headline (W >= 3 warm-up steps, L2 flushed before every
+    timed step, CUDA events, its own clock record), with fewer timed steps:
+    C1 (64 envs, latency), C2 (8192 envs, path following, with the path
+    table rebuild), the C5 sweep (1024 .. 262144 envs, limit springs, 8
+    substeps) with its 4096-env, 128-step adjoint, and P1 (PPO with
+    learning)."""
+    args = cx.args
+    saved = (args.steps, args.warmup)
+    args.steps, args.warmup = min(args.steps, 10), 3
+    out = {"timed_steps_per_workload": args.steps, "warmup": args.warmup}
+    try:
+        line, _ = run_rollout_config(cx, "C1")
+        out["C1"] = _compact_rollout(line)
+        line, _ = run_rollout_config(cx, "C2")
+        out["C2"] = _compact_rollout(line)
+        out["C5"] = {"sweep": [_compact_rollout(run_rollout_config(cx, "C5", E)[0])
+                               for E in (1024, 4096, 16384, 65536, 262144)]}
+        out["C5"]["adjoint"] = _compact_adjoint(
+            run_adjoint_config(cx, with_error=with_error, name="C5", E=4096, T=128, err_envs=4))
+        out["P1"] = _compact_ppo(run_ppo_config(cx))
+    finally:
+        args.steps, args.warmup = saved
+    return out
+
+
 def run_reference(args):
     """The reference arm: the FP64 oracle as it stands, on the host cores,
     on the default workload.  Every step is one bounded sample of the
@@ -888,6 +961,8 @@ def main():
     ap.add_argument("--config", default="C3", choices=["C1", "C2", "C3", "C4", "C5", "P1"])
     ap.add_argument("--envs", type=int, nargs="*", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="default workload only (leave out the other workloads' `configs`)")
     ap.add_argument("--out-dir", default=None,
                     help="where the nvidia-smi clock samples go (default: a temporary directory)")
     ap.add_argument("--launch", default=None,
@@ -945,6 +1020,8 @@ def main():
         line, wl = run_rollout_config(cx, args.config)
         if args.config == "C3":
             line["grad"] = run_adjoint_config(cx, with_error=want_cpu)
+            if not args.headline_only:
+                line["configs"] = run_all_configs(cx, with_error=want_cpu)
         if rank == 0:
             line["cpu_baseline"] = cpu_baseline(wl) if want_cpu else None
             if want_cpu:

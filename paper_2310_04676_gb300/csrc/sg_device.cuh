@@ -124,6 +124,36 @@ __device__ __forceinline__ void write_rows(float* obs_t, const float* stage, int
   }
 }
 
+// The warp's kRows staged rows when they belong to consecutive envs (env0 ..
+// env0 + kRows - 1) and the stage pitch equals D: one contiguous block of
+// kRows * D floats in shared and in global memory, copied with all lanes on
+// consecutive addresses -- 16-byte vectors when both ends are 16-byte
+// aligned, else 4-byte words.  (Row by row, a single-arm env of odd width
+// D = 27 cost about 280 cycles per row; the block copy a few per row.)
+template <int kRows>
+__device__ __forceinline__ void write_block(float* obs_t, const float* stage, int env0, int D,
+                                            int lane) {
+  float* dst = obs_t + (size_t)env0 * D;
+  const int n = kRows * D;
+  if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(stage)) & 15) == 0 &&
+      (n & 3) == 0) {
+    const float4* s4 = reinterpret_cast<const float4*>(stage);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (int i = lane; i < (n >> 2); i += kWarp) d4[i] = s4[i];
+  } else {
+    for (int i = lane; i < n; i += kWarp) dst[i] = stage[i];
+  }
+}
+
+// Whether a warp's kRows observation rows (row r: env row_env of lane r,
+// -1 if not written) are consecutive envs whose staged rows are contiguous
+// (stage pitch D), i.e. can be written by write_block; warp-uniform.
+__device__ __forceinline__ bool rows_contiguous(int row_env, int nrows, int D, int DP, int lane) {
+  const int env0 = __shfl_sync(0xffffffffu, row_env, 0);
+  return DP == D && env0 >= 0 &&
+         __all_sync(0xffffffffu, lane >= nrows || row_env == env0 + lane);
+}
+
 // write_rows with the row count known at compile time (loop fully unrolled)
 template <int kRows>
 __device__ __forceinline__ void write_rows_n(float* obs_t, const float* stage, int row_env, int D,

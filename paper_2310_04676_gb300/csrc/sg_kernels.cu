@@ -43,8 +43,9 @@ __device__ __forceinline__ bool stage_record(const StepArgs& a, int gw, int cls,
 // warp writes each row to HBM with consecutive lanes on consecutive floats.
 // kGlog: log2 of the lanes per env (1, 2 or 4 chains in a lane group), a
 // compile-time constant so that the group reductions and the row write-out
-// unroll completely.
-template <int kGlog, class Pat>
+// unroll completely.  kBlock: the warp's rows belong to consecutive envs and
+// are written as one contiguous block (write_block), else row by row.
+template <int kGlog, bool kBlock, class Pat>
 __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, const Rec& rec,
                                           float* stage, int slot, int lane) {
   constexpr int glog = kGlog;
@@ -189,7 +190,9 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
       }
     }
     __syncwarp();
-    write_rows_n<nrows>(a.obs + (size_t)t * E * D, stage, row_env, D, DP, lane);
+    if (kBlock) write_block<nrows>(a.obs + (size_t)t * E * D, stage,
+                                   __shfl_sync(0xffffffffu, row_env, 0), D, lane);
+    else write_rows_n<nrows>(a.obs + (size_t)t * E * D, stage, row_env, D, DP, lane);
     __syncwarp();
   }
 
@@ -228,10 +231,22 @@ __global__ void __launch_bounds__(kMaxThreads) step_kernel(StepArgs a) {
   const Rec r{rec + lane};
   const int slot = gw * kWarp + lane;
   const int glog = group_log2(wc);
+  // rows of consecutive envs (homogeneous batches in caller order): block write
+  const int my_env = a.slot_env[slot];
+  const int my_row = (my_env >= 0 && (!a.obs_mask || a.obs_mask[my_env])) ? my_env : -1;
+  const int row_env = __shfl_sync(0xffffffffu, my_row, (lane << glog) & 31);
+  const bool block =
+      rows_contiguous(row_env, kWarp >> glog, a.obs_dim, stage_pitch(a.obs_dim), lane);
   auto run = [&](const auto& pat) {
-    if (glog == 0) run_chain<0>(a, pat, r, stage, slot, lane);
-    else if (glog == 1) run_chain<1>(a, pat, r, stage, slot, lane);
-    else run_chain<2>(a, pat, r, stage, slot, lane);
+    if (block) {
+      if (glog == 0) run_chain<0, true>(a, pat, r, stage, slot, lane);
+      else if (glog == 1) run_chain<1, true>(a, pat, r, stage, slot, lane);
+      else run_chain<2, true>(a, pat, r, stage, slot, lane);
+    } else {
+      if (glog == 0) run_chain<0, false>(a, pat, r, stage, slot, lane);
+      else if (glog == 1) run_chain<1, false>(a, pat, r, stage, slot, lane);
+      else run_chain<2, false>(a, pat, r, stage, slot, lane);
+    }
   };
   switch (wc & 3) {
     case CLS_7R: run(Pat7R{}); break;

@@ -31,8 +31,9 @@ namespace {
 
 constexpr int kPairBars = 3;                      // tma, exchange, stage
 
-// kGlog: log2 of the lanes per env, a compile-time constant (see run_chain)
-template <int kGlog, class Pat>
+// kGlog: log2 of the lanes per env, a compile-time constant; kBlock: rows of
+// consecutive envs, written as contiguous blocks (see run_chain)
+template <int kGlog, bool kBlock, class Pat>
 __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, const Rec& rec,
                                          float* stage, float* xbuf, uint64_t* bars, int group,
                                          int lane, int role) {
@@ -189,8 +190,13 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
     // each role writes half of the staged rows
     constexpr int half = nrows >> 1;
     const int r0 = role * half;
-    const int ev = __shfl_sync(0xffffffffu, row_env, (lane + r0) & 31);
-    write_rows_n<half>(a.obs + (size_t)t * E * D, stage + r0 * DP, ev, D, DP, lane);
+    if (kBlock) {
+      write_block<half>(a.obs + (size_t)t * E * D, stage + r0 * DP,
+                        __shfl_sync(0xffffffffu, row_env, 0) + r0, D, lane);
+    } else {
+      const int ev = __shfl_sync(0xffffffffu, row_env, (lane + r0) & 31);
+      write_rows_n<half>(a.obs + (size_t)t * E * D, stage + r0 * DP, ev, D, DP, lane);
+    }
   }
 
   if (valid && role == 0) {
@@ -252,10 +258,21 @@ __global__ void __launch_bounds__(kMaxThreads) step_kernel_pair(StepArgs a) {
   }
   const Rec r{rec + lane};
   const int glog = group_log2(wc);
+  // rows of consecutive envs (homogeneous batches in caller order): block writes
+  const int my_env = a.slot_env[group * kWarp + lane];
+  const int row_env = __shfl_sync(0xffffffffu, my_env, (lane << glog) & 31);
+  const bool block =
+      rows_contiguous(row_env, kWarp >> glog, a.obs_dim, stage_pitch(a.obs_dim), lane);
   auto run = [&](const auto& pat) {
-    if (glog == 0) run_pair<0>(a, pat, r, stage, xbuf, bars, group, lane, role);
-    else if (glog == 1) run_pair<1>(a, pat, r, stage, xbuf, bars, group, lane, role);
-    else run_pair<2>(a, pat, r, stage, xbuf, bars, group, lane, role);
+    if (block) {
+      if (glog == 0) run_pair<0, true>(a, pat, r, stage, xbuf, bars, group, lane, role);
+      else if (glog == 1) run_pair<1, true>(a, pat, r, stage, xbuf, bars, group, lane, role);
+      else run_pair<2, true>(a, pat, r, stage, xbuf, bars, group, lane, role);
+    } else {
+      if (glog == 0) run_pair<0, false>(a, pat, r, stage, xbuf, bars, group, lane, role);
+      else if (glog == 1) run_pair<1, false>(a, pat, r, stage, xbuf, bars, group, lane, role);
+      else run_pair<2, false>(a, pat, r, stage, xbuf, bars, group, lane, role);
+    }
   };
   switch (wc & 3) {
     case CLS_7R: run(Pat7R{}); break;

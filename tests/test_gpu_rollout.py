@@ -139,3 +139,40 @@ def test_rollout_argument_errors():
         env.set_launch(32, 0, 2)
     with pytest.raises(ValueError):
         env.rollout(torch.zeros(4, 8, 6, device="cuda"), DT, 2)
+
+
+@pytest.mark.parametrize("kind,E", [("7R", 100), ("7P", 64), ("4R", 96), ("14B", 70), ("21T", 40)])
+@pytest.mark.parametrize("split", [1, 2])
+def test_block_and_row_writes_agree(kind, E, split):
+    """Observation rows of a warp whose envs are consecutive are written as
+    one contiguous block, other warps' rows one by one.  The same envs in
+    caller order (block writes; the ragged last warp row by row) and
+    permuted (row by row) give the same rows, bit for bit, for odd and even
+    row widths, in the per-step and persistent forms."""
+    desc = W.make_desc([kind] * E)
+    perm = np.random.default_rng(5).permutation(E)
+    dp = {k: (v[perm] if isinstance(v, np.ndarray) and v.shape[:1] == (E,) else v)
+          for k, v in desc.items()}
+    acts = W.joint_targets(desc, 5)
+    a = torch.as_tensor(acts, device="cuda")
+    ap = torch.as_tensor(np.ascontiguousarray(acts[:, perm]), device="cuda")
+    threads = 64 * split
+    A, B = sg.Env(desc), sg.Env(dp)
+    A.set_launch(threads, sg.ROLLOUT_PERSISTENT, split)
+    B.set_launch(threads, sg.ROLLOUT_PERSISTENT, split)
+    oa, ra, da = A.rollout(a, DT, 2)
+    ob, rb, db = B.rollout(ap, DT, 2)
+    assert torch.equal(oa[:, perm], ob) and torch.equal(ra[:, perm], rb)
+    assert torch.equal(da[:, perm], db)
+    o1, r1, d1 = A.step(a[0], DT, 2)
+    o2, r2, d2 = B.step(ap[0], DT, 2)
+    assert torch.equal(o1[perm], o2) and torch.equal(r1[perm], r2)
+    # observe: all rows (block writes) and a masked subset (row by row)
+    full = A.observe(a[0])
+    mask = torch.zeros(E, dtype=torch.uint8, device="cuda")
+    mask[::3] = 1
+    part = torch.full_like(full, -7.0)
+    A.observe(a[0], mask, out=part)
+    m = mask.bool()
+    assert torch.equal(part[m], full[m]) and bool((part[~m] == -7.0).all())
+    assert A.sync_status() == sg.SG_OK and B.sync_status() == sg.SG_OK
