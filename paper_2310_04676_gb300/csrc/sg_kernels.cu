@@ -43,11 +43,13 @@ __device__ __forceinline__ bool stage_record(const StepArgs& a, int gw, int cls,
 // warp writes each row to HBM with consecutive lanes on consecutive floats.
 // kGlog: log2 of the lanes per env (1, 2 or 4 chains in a lane group), a
 // compile-time constant so that the group reductions and the row write-out
-// unroll completely.  kBlock: the warp's rows belong to consecutive envs and
-// are written as one contiguous block (write_block), else row by row.
-template <int kGlog, bool kBlock, class Pat>
+// unroll completely.  block: the warp's rows belong to consecutive envs and
+// are written as one contiguous block (write_block), else row by row -- a
+// run-time choice, so that the dynamics are compiled once and every warp
+// rounds alike whatever its env order (a permuted batch gives the same bits).
+template <int kGlog, class Pat>
 __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, const Rec& rec,
-                                          float* stage, int slot, int lane) {
+                                          float* stage, int slot, int lane, bool block) {
   constexpr int glog = kGlog;
   constexpr int N = Pat::N;
   const int env = a.slot_env[slot];
@@ -190,8 +192,8 @@ __device__ __forceinline__ void run_chain(const StepArgs& a, const Pat& pat, con
       }
     }
     __syncwarp();
-    if (kBlock) write_block<nrows>(a.obs + (size_t)t * E * D, stage,
-                                   __shfl_sync(0xffffffffu, row_env, 0), D, lane);
+    if (block) write_block<nrows>(a.obs + (size_t)t * E * D, stage,
+                                  __shfl_sync(0xffffffffu, row_env, 0), D, lane);
     else write_rows_n<nrows>(a.obs + (size_t)t * E * D, stage, row_env, D, DP, lane);
     __syncwarp();
   }
@@ -238,15 +240,9 @@ __global__ void __launch_bounds__(kMaxThreads) step_kernel(StepArgs a) {
   const bool block =
       rows_contiguous(row_env, kWarp >> glog, a.obs_dim, stage_pitch(a.obs_dim), lane);
   auto run = [&](const auto& pat) {
-    if (block) {
-      if (glog == 0) run_chain<0, true>(a, pat, r, stage, slot, lane);
-      else if (glog == 1) run_chain<1, true>(a, pat, r, stage, slot, lane);
-      else run_chain<2, true>(a, pat, r, stage, slot, lane);
-    } else {
-      if (glog == 0) run_chain<0, false>(a, pat, r, stage, slot, lane);
-      else if (glog == 1) run_chain<1, false>(a, pat, r, stage, slot, lane);
-      else run_chain<2, false>(a, pat, r, stage, slot, lane);
-    }
+    if (glog == 0) run_chain<0>(a, pat, r, stage, slot, lane, block);
+    else if (glog == 1) run_chain<1>(a, pat, r, stage, slot, lane, block);
+    else run_chain<2>(a, pat, r, stage, slot, lane, block);
   };
   switch (wc & 3) {
     case CLS_7R: run(Pat7R{}); break;

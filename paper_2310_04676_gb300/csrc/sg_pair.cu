@@ -31,12 +31,13 @@ namespace {
 
 constexpr int kPairBars = 3;                      // tma, exchange, stage
 
-// kGlog: log2 of the lanes per env, a compile-time constant; kBlock: rows of
-// consecutive envs, written as contiguous blocks (see run_chain)
-template <int kGlog, bool kBlock, class Pat>
+// kGlog: log2 of the lanes per env, a compile-time constant; block: rows of
+// consecutive envs, written as contiguous blocks (a run-time choice, see
+// run_chain)
+template <int kGlog, class Pat>
 __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, const Rec& rec,
                                          float* stage, float* xbuf, uint64_t* bars, int group,
-                                         int lane, int role) {
+                                         int lane, int role, bool block) {
   constexpr int glog = kGlog;
   constexpr int N = Pat::N;
   const int slot = group * kWarp + lane;
@@ -190,7 +191,7 @@ __device__ __forceinline__ void run_pair(const StepArgs& a, const Pat& pat, cons
     // each role writes half of the staged rows
     constexpr int half = nrows >> 1;
     const int r0 = role * half;
-    if (kBlock) {
+    if (block) {
       write_block<half>(a.obs + (size_t)t * E * D, stage + r0 * DP,
                         __shfl_sync(0xffffffffu, row_env, 0) + r0, D, lane);
     } else {
@@ -264,15 +265,9 @@ __global__ void __launch_bounds__(kMaxThreads) step_kernel_pair(StepArgs a) {
   const bool block =
       rows_contiguous(row_env, kWarp >> glog, a.obs_dim, stage_pitch(a.obs_dim), lane);
   auto run = [&](const auto& pat) {
-    if (block) {
-      if (glog == 0) run_pair<0, true>(a, pat, r, stage, xbuf, bars, group, lane, role);
-      else if (glog == 1) run_pair<1, true>(a, pat, r, stage, xbuf, bars, group, lane, role);
-      else run_pair<2, true>(a, pat, r, stage, xbuf, bars, group, lane, role);
-    } else {
-      if (glog == 0) run_pair<0, false>(a, pat, r, stage, xbuf, bars, group, lane, role);
-      else if (glog == 1) run_pair<1, false>(a, pat, r, stage, xbuf, bars, group, lane, role);
-      else run_pair<2, false>(a, pat, r, stage, xbuf, bars, group, lane, role);
-    }
+    if (glog == 0) run_pair<0>(a, pat, r, stage, xbuf, bars, group, lane, role, block);
+    else if (glog == 1) run_pair<1>(a, pat, r, stage, xbuf, bars, group, lane, role, block);
+    else run_pair<2>(a, pat, r, stage, xbuf, bars, group, lane, role, block);
   };
   switch (wc & 3) {
     case CLS_7R: run(Pat7R{}); break;
