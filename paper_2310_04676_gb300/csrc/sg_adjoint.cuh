@@ -140,7 +140,9 @@ struct SweepArrays {
 
 // Reverse of id_sweeps: given mu and the sweeps' quantities (accessor sw),
 // accumulates gq += (dID/dq)^T mu, gqd += (dID/dqd)^T mu and
-// gm += (dID/dm)^T mu.
+// gm += m (dID/dm)^T mu -- the mass cotangent times the link mass, since
+// ID is linear in m (F, N / m); callers divide by m once at the end of a
+// rollout (the masses are constant over it), not once per substep.
 template <class Pat, class Sw>
 __device__ __forceinline__ void rnea_vjp_rev(const Pat& pat, const Rec& rec, const float (&q)[7],
                                              const float (&qd)[7], const float (&cq)[Pat::N],
@@ -201,7 +203,7 @@ __device__ __forceinline__ void rnea_vjp_rev(const Pat& pat, const Rec& rec, con
       accb.y += m * Fb[i].y;
       accb.z += m * Fb[i].z;
       kz_adj(w, V3{m * c * Fb[i].x, m * c * Fb[i].y, m * c * Fb[i].z}, wb, wdb);
-      gm[i] += (dot3(Fb[i], sw.f(i)) + dot3(Nb[i], sw.nm(i))) / m;
+      gm[i] += dot3(Fb[i], sw.f(i)) + dot3(Nb[i], sw.nm(i));
       const V3 nb = Nb[i];
       wdb.x += Ix * nb.x;
       wdb.y += Iy * nb.y;
@@ -287,6 +289,63 @@ __device__ __forceinline__ void tip_vjp(const Pat& pat, const Rec& rec, const fl
   }
 }
 
+// World-frame tool-tip Jacobian of one chain, J_i = d(tip)/dq_i: z_i x
+// (tip - p_i) for a revolute joint i, z_i for a prismatic one (z_i its axis,
+// p_i its origin), given the joint trigonometry; out.jac(i, J_i).  Two
+// passes of the kinematics (the tip, then each joint's column as its frame
+// is reached) keep no per-link arrays.  J^T g is the tip cotangent's
+// contribution to the joint-position cotangent (tip_vjp computes it from q).
+template <class Pat>
+__device__ __forceinline__ void tip_frames_step(const Pat& pat, const Rec& rec, const float (&q)[7],
+                                                const float (&cq)[Pat::N],
+                                                const float (&sq)[Pat::N], int i, V3& p, V3& c0,
+                                                V3& c1, V3& c2) {
+  if (pat.type(i) == 1) {
+    p = V3{p.x + q[i] * c2.x, p.y + q[i] * c2.y, p.z + q[i] * c2.z};
+  } else {
+    const int a = pat.axis(i);
+    if (a == 2) rot_cols(c0, c1, cq[i], sq[i]);
+    else if (a == 1) rot_cols(c2, c0, cq[i], sq[i]);
+    else rot_cols(c1, c2, cq[i], sq[i]);
+  }
+}
+
+template <class Pat, class Out>
+__device__ __forceinline__ void tip_jacobian(const Pat& pat, const Rec& rec, const float (&q)[7],
+                                             const float (&cq)[Pat::N], const float (&sq)[Pat::N],
+                                             Out& out) {
+  constexpr int N = Pat::N;
+  const V3 base{rec.cf(CF_BX), rec.cf(CF_BY), rec.cf(CF_BZ)};
+  V3 tip = base;
+  {
+    V3 c0{1.f, 0.f, 0.f}, c1{0.f, 1.f, 0.f}, c2{0.f, 0.f, 1.f};
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      if (!pat.active(i)) continue;
+      tip_frames_step(pat, rec, q, cq, sq, i, tip, c0, c1, c2);
+      const float L = rec.lf(i, LF_L);
+      tip = V3{tip.x + L * c2.x, tip.y + L * c2.y, tip.z + L * c2.z};
+    }
+  }
+  V3 p = base;
+  V3 c0{1.f, 0.f, 0.f}, c1{0.f, 1.f, 0.f}, c2{0.f, 0.f, 1.f};
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (!pat.active(i)) continue;
+    tip_frames_step(pat, rec, q, cq, sq, i, p, c0, c1, c2);
+    if (pat.type(i) == 1) {
+      out.jac(i, c2);
+    } else {
+      const int a = pat.axis(i);
+      const V3 z = a == 0 ? c0 : (a == 1 ? c1 : c2);
+      const V3 r{tip.x - p.x, tip.y - p.y, tip.z - p.z};
+      out.jac(i, V3{z.y * r.z - z.z * r.y, z.z * r.x - z.x * r.z, z.x * r.y - z.y * r.x});
+    }
+    const float L = rec.lf(i, LF_L);
+    p = V3{p.x + L * c2.x, p.y + L * c2.y, p.z + L * c2.z};
+  }
+}
+
 // Forward substep that also returns the Cholesky factor (L in the lower
 // triangle of M, inv = 1 / L_ii), the velocity increment dqd, the
 // acceleration a = dqd / h and the drive stiffness k_s of every joint
@@ -356,7 +415,8 @@ __device__ __forceinline__ void substep_adjoint_sw(
 
 // Adjoint of one substep.  On entry lq, lqd are the cotangents of the
 // substep's outputs (q', qd'); on exit those of its inputs (q, qd).  lqs and
-// lm accumulate the cotangents of the targets q* and the link masses.
+// lm accumulate the cotangents of the targets q* and of the link masses,
+// the latter times the link mass (divide by m for dL/dm).
 template <class Pat>
 __device__ __forceinline__ void substep_adjoint(const Pat& pat, const Rec& rec, const float (&q)[7],
                                                 const float (&qd)[7], const float (&qs)[7],

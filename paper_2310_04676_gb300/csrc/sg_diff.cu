@@ -127,18 +127,20 @@ __device__ __forceinline__ void write_action_grads(const Pat& pat, const DiffArg
     for (int j = s.ntot; j < J; ++j) row[j] = 0.f;
 }
 
-// dL/d(link mass) and, when requested, dL/d(initial q, qd)
+// dL/d(link mass) (lm holds it times the mass, see rnea_vjp_rev) and, when
+// requested, dL/d(initial q, qd)
 template <class Pat>
 __device__ __forceinline__ void write_final_grads(const Pat& pat, const DiffArgs& a,
-                                                  const SlotInfo& s, const float (&lq)[7],
-                                                  const float (&lqd)[7], const float (&lm)[7]) {
+                                                  const Rec& rec, const SlotInfo& s,
+                                                  const float (&lq)[7], const float (&lqd)[7],
+                                                  const float (&lm)[7]) {
   if (!s.valid) return;
   const int J = a.max_joints;
   const size_t r = (size_t)s.env * J;
 #pragma unroll
   for (int i = 0; i < Pat::N; ++i) {
     if (!pat.active(i)) continue;
-    a.dmass[r + s.jo + i] = lm[i];
+    a.dmass[r + s.jo + i] = lm[i] / rec.lf(i, LF_M);
     if (a.dq0) a.dq0[r + s.jo + i] = lq[i];
     if (a.dqd0) a.dqd0[r + s.jo + i] = lqd[i];
   }
@@ -154,9 +156,11 @@ __device__ __forceinline__ void write_final_grads(const Pat& pat, const DiffArgs
 // ---- substep records of the pipelined backward (see below) --------------
 enum RecordField {
   RF_Q = 0, RF_QD = 7, RF_CQ = 14, RF_SQ = 21, RF_KS = 28, RF_INV = 35, RF_L = 42,
-  RF_W = 63, RF_WD = 84, RF_ACC = 105, RF_F = 126, RF_NM = 147, RF_FL = 168, RF_NL = 189
+  RF_W = 63, RF_WD = 84, RF_ACC = 105, RF_F = 126, RF_NM = 147, RF_FL = 168, RF_NL = 189,
+  RF_JT = 210
 };
-static_assert(RF_NL + 3 * kMaxLinks == kReplayFields, "record layout");
+static_assert(RF_JT + 3 * kMaxLinks == kReplayFields, "record layout");
+static_assert((kReplayFields * kWarp * sizeof(float)) % 16 == 0, "bulk copies of records");
 
 constexpr int kPipeGroups = 2;     // chain groups per block
 static_assert(kReplayWarps == 2 && kDiffPipeThreads == 8 * kWarp, "warp map of the block");
@@ -206,6 +210,16 @@ struct RecordStore {
   __device__ __forceinline__ void bwd(int i, V3 f, V3 n) const {
     put(RF_FL + 3 * i, f);
     put(RF_NL + 3 * i, n);
+  }
+};
+
+// tip_jacobian output written into a record (p: record + lane)
+struct JacStore {
+  float* p;
+  __device__ __forceinline__ void jac(int i, V3 v) const {
+    p[(RF_JT + 3 * i) * kWarp] = v.x;
+    p[(RF_JT + 3 * i + 1) * kWarp] = v.y;
+    p[(RF_JT + 3 * i + 2) * kWarp] = v.z;
   }
 };
 
@@ -318,6 +332,8 @@ __device__ __forceinline__ void diff_forward_chain(const DiffArgs& a, const Pat&
         integrate(pat, q, qd, dqd, a.h);
       }
       joint_sincos(pat, q, cq, sq);
+      JacStore js{record_at(a, 0, g, (t - t_rec + 1) * a.substeps - 1) + lane};
+      tip_jacobian(pat, rec, q, cq, sq, js);
     }
     V3 tip, r0, r1, r2;
     chain_tip_trig(pat, rec, q, cq, sq, tip, r0, r1, r2);
@@ -398,6 +414,10 @@ __device__ __forceinline__ void diff_forward_pair(const DiffArgs& a, const Pat& 
       joint_sincos(pat, q, cq, sq);
     }
     if (role == 1) {
+      if (t >= t_rec) {
+        JacStore js{record_at(a, 0, g, (t - t_rec + 1) * a.substeps - 1) + lane};
+        tip_jacobian(pat, rec, q, cq, sq, js);
+      }
       V3 tip, r0, r1, r2;
       chain_tip_trig(pat, rec, q, cq, sq, tip, r0, r1, r2);
       if (s.valid) {
@@ -494,7 +514,7 @@ __device__ __forceinline__ void diff_backward_chain(const DiffArgs& a, const Pat
       write_action_grads(pat, a, s, t, lqs);
     }
   }
-  write_final_grads(pat, a, s, lq, lqd, lm);
+  write_final_grads(pat, a, rec, s, lq, lqd, lm);
 }
 
 template <bool kBackward>
@@ -629,6 +649,11 @@ __device__ __forceinline__ void replay_role(const DiffArgs& a, const Pat& pat, c
         id_sweeps(pat, rec, q, qd, acc, cq, sq, kGravity, st);
         integrate(pat, q, qd, dqd, a.h);
       }
+      // tool-tip Jacobian of the state after step t (for the tip cotangent)
+      float cq[N], sq[N];
+      joint_sincos(pat, q, cq, sq);
+      JacStore js{record_at(a, b, g, (t - t0 + 1) * a.substeps - 1) + lane};
+      tip_jacobian(pat, rec, q, cq, sq, js);
     }
     // the records are visible to the adjoint warp's bulk copies before it is told
     fence_proxy_async_global();
@@ -646,14 +671,18 @@ __device__ __forceinline__ void adjoint_role(const DiffArgs& a, const Pat& pat, 
   constexpr int N = Pat::N;
   const SlotInfo s = slot_info(a, slot);
   const size_t E = (size_t)a.num_envs;
-  float lq[7], lqd[7], lm[7], qn[7], qdn[7];
+  float lq[7], lqd[7], lm[7];
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
     lq[i] = 0.f;
     lqd[i] = 0.f;
     lm[i] = 0.f;
   }
-  get_ckpt(pat, a, a.nseg, slot, qn, qdn);     // state after the last step
+  V3 gnext{0.f, 0.f, 0.f};                     // tip cotangent of the step about to be reversed
+  if (s.valid) {
+    const float* gp = a.dl_dee + (((size_t)(a.T - 1) * E + s.env) * kMaxChains + s.c) * 3;
+    gnext = V3{gp[0], gp[1], gp[2]};
+  }
   // record (buffer b, substep j) into slot m & 1
   auto fetch = [&](int b, int j, unsigned m) {
     __syncwarp();                              // every lane is done with the slot
@@ -675,15 +704,6 @@ __device__ __forceinline__ void adjoint_role(const DiffArgs& a, const Pat& pat, 
     const int t1 = min(a.T, t0 + a.ckpt_every);
     fetch(b, (t1 - t0) * a.substeps - 1, n);
     for (int t = t1 - 1; t >= t0; --t) {
-      if (s.valid) {
-        const float* gp = a.dl_dee + (((size_t)t * E + s.env) * kMaxChains + s.c) * 3;
-        float gq[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) gq[i] = 0.f;
-        tip_vjp(pat, rec, qn, V3{gp[0], gp[1], gp[2]}, gq);
-#pragma unroll
-        for (int i = 0; i < N; ++i) lq[i] += gq[i];
-      }
       float lqs[7];
 #pragma unroll
       for (int i = 0; i < 7; ++i) lqs[i] = 0.f;
@@ -695,21 +715,31 @@ __device__ __forceinline__ void adjoint_role(const DiffArgs& a, const Pat& pat, 
         }
         if (j > 0) fetch(b, j - 1, n + 1);
         const float* p = stage + (n & 1u) * (kReplayFields * kWarp) + lane;
+        if (k == a.substeps - 1 && s.valid) {
+          // tip cotangent of the state after step t: lq += J^T g
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            if (!pat.active(i)) continue;
+            lq[i] += gnext.x * p[(RF_JT + 3 * i) * kWarp] +
+                     gnext.y * p[(RF_JT + 3 * i + 1) * kWarp] +
+                     gnext.z * p[(RF_JT + 3 * i + 2) * kWarp];
+          }
+          if (t > 0) {                         // the next step's, loaded ahead
+            const float* gp = a.dl_dee + (((size_t)(t - 1) * E + s.env) * kMaxChains + s.c) * 3;
+            gnext = V3{gp[0], gp[1], gp[2]};
+          }
+        }
         float q[7], qd[7], cq[N], sq[N], M[N][N], inv[N], ks[N];
         get_state(pat, p, q, qd, cq, sq, ks, inv, M);
         substep_adjoint_sw(pat, rec, q, qd, cq, sq, M, inv, ks, RecordView{p}, a.h, lq, lqd, lqs,
                            lm);
-        if (k == 0) {
-#pragma unroll
-          for (int i = 0; i < 7; ++i) qn[i] = q[i];   // the state before step t
-        }
       }
       write_action_grads(pat, a, s, t, lqs);
     }
     __syncwarp();
     mbar_arrive(freed + b);
   }
-  write_final_grads(pat, a, s, lq, lqd, lm);
+  write_final_grads(pat, a, rec, s, lq, lqd, lm);
 }
 
 __global__ void __launch_bounds__(kDiffPipeThreads) diff_backward_pipe_kernel(DiffArgs a) {

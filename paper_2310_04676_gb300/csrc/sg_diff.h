@@ -14,9 +14,11 @@ constexpr int kDiffPairThreads = 64;       // warp-pair forward: one pair per bl
 constexpr int kDiffPairMaxWarpsPerSM = 2;  // warp-pair forward up to this many chain warps per SM
 constexpr int kReplayWarps = 2;        // replay warps per group of 32 chains
 constexpr int kDiffPipeThreads = 256;  // two groups (replay warps + adjoint) in 8 warp slots
-// per substep record: q, qd, cos q, sin q, k_s, 1/L_ii (7 each), L (21), and
-// per link the inverse-dynamics sweep quantities w, wd, acc, F, N, f, n (21 each)
-constexpr int kReplayFields = 210;
+// per substep record: q, qd, cos q, sin q, k_s, 1/L_ii (7 each), L (21), per
+// link the inverse-dynamics sweep quantities w, wd, acc, F, N, f, n (21 each),
+// and (in a step's last substep record) the tool-tip Jacobian of the state
+// after the step (21)
+constexpr int kReplayFields = 231;
 constexpr int kReplayBufs = kReplayWarps + 1;   // segment buffers in flight
 constexpr int kMaxCkptEvery = 32;      // checkpoint interval limit (thread-local segment buffer)
 constexpr int kMaxDiffSubsteps = 16;   // substeps limit of the differentiable rollout

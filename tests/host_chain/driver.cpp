@@ -118,7 +118,7 @@ int host_substep_adjoint(int e, int c, const double* q_in, const double* qd_in,
       lq_io[i] = lq[i];
       lqd_io[i] = lqd[i];
       lqs_out[i] = lqs[i];
-      lm_out[i] = lm[i];
+      lm_out[i] = lm[i] / r.lf(i, LF_M);   // lm holds dL/dm times the mass
     }
     return n;
   });
