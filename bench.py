@@ -804,7 +804,7 @@ def run_ppo_config(cx, name="P1", E=None):
     cfg = {"workload": wl.name, "envs_per_gpu": En, "n_steps": wl.steps, "epochs": 5,
            "minibatches": 4, "minibatch_rows": r["B"] // 4, "substeps": wl.substeps, "dt": wl.dt,
            "networks": "actor and critic MLP %d-256-128-64-{%d,1}, ELU" % (D, A),
-           "gemm": "cuBLAS FP32 SGEMM (tensor cores off)",
+           "gemm": "this library's tcgen05 contraction, FP32-grade split precision (3xTF32)",
            "l2": "flushed (256 MiB write) before every timed iteration"}
     line = base_line(args, cx.world, s32["value"], s32["ms_per_iteration"], cfg)
     line["metric"] = "with-learning frames/s (collect + PPO update), context for the step metric"
@@ -818,20 +818,23 @@ def run_ppo_config(cx, name="P1", E=None):
                         "kernel": "whole iteration (dense layers' FLOPs / iteration time)",
                         "peak_source": "SMs x 128 FP32 lanes x 2 x max SM clock",
                         "flops_per_iteration": {"collect": f_col, "update": f_upd}}
-    line["tf32"] = dict(stf, dtype="tf32", gemm="cuBLAS TF32 tensor cores",
+    line["tf32"] = dict(stf, dtype="tf32", gemm="this library's tcgen05 contraction, one TF32 product",
                         peak=tf32_peak, peak_source="measured bf16 burst x 1.1/2.25 (%s)" % src,
                         note="reduced-precision GEMM inputs (10-bit mantissa): context only")
     line["e2e"] = {"value": aggregate_rate(frames, sum(r["ms_e2e"]) / 1e3, world=cx.world,
                                            device=cx.dev),
                    "unit": "frames/s", "h2d_bytes_per_step": r["h2d"],
                    "d2h_bytes_per_step": r["d2h"]}
-    # kernels of this library per iteration: per collect step 8 bias/ELU, pad, sampling,
-    # the env step, bootstrap, reset, observe; then pad, 4 bias (last values), GAE,
-    # 2 moments, step counter; per minibatch gather, 8 bias/ELU, 2 loss-head,
-    # 6 ELU-backward + 6 bias-gradient sums, 2 norm, Adam
+    # kernels of this library per iteration: per collect step 8 layer products
+    # (bias + ELU fused), pad, sampling, the env step, bootstrap, reset, observe;
+    # then pad, 4 critic layers (last values), GAE, 2 moments, step counter; per
+    # minibatch gather, 8 forward layers, 2 loss-head, per network 4 weight
+    # gradients (product + fixed-order sum of the row splits), the output bias
+    # column sums (2), 3 input gradients with the ELU backward and 3 bias sums,
+    # then 2 norm, Adam
     n_mb = 5 * 4
-    line["gpu_launches"] = (wl.steps * 14 + 9 + n_mb * 26) * args.steps
-    line["library_launches"] = (wl.steps * 8 + 4 + n_mb * 24) * args.steps   # cuBLAS GEMM/GEMV
+    line["gpu_launches"] = (wl.steps * 14 + 9 + n_mb * 46) * args.steps
+    line["library_launches"] = 0
     line["clocks"] = r["clocks"]
     line["status"] = r["status"]
     line["paper_context"] = ("Table II: 6.8 s per 1M timesteps with learning (147,059 frames/s), "

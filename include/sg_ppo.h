@@ -47,9 +47,12 @@
  *   0.9 / 0.999, eps 1e-8, bias-corrected) takes one step of size lr.
  *
  * Threading and streams: all work goes to the env context's stream; the
- * collect loop is captured once into a CUDA graph and replayed.  GEMMs run
- * in cuBLAS (FP32, or TF32 tensor cores with tf32 = 1); every other step is
- * a kernel of this library.
+ * collect loop is captured once into a CUDA graph and replayed.  Every step
+ * is a kernel of this library; the dense layers run on its tensor-core
+ * contraction (sg_mlp_gemm below: FP32-grade split precision, or one TF32
+ * product per term with tf32 = 1), forward products with the bias and ELU in
+ * their epilogue, input gradients with the ELU derivative and the bias
+ * gradient's partial sums in theirs.
  */
 #ifndef SG_PPO_H
 #define SG_PPO_H
@@ -76,13 +79,15 @@ typedef struct sg_ppo_config {
   float dt;                 /* control step of the env, > 0 */
   int32_t substeps;         /* env substeps per step, 1..64 */
   uint32_t seed;            /* exploration-noise stream */
-  int32_t tf32;             /* 1: GEMMs on TF32 tensor cores, 0: FP32 */
+  int32_t tf32;             /* 1: one TF32 product per term (10-bit mantissas),
+                               0: split precision, FP32-grade (default) */
 } sg_ppo_config;
 
 /* Create a PPO loop over the envs of `env` (which it uses, not owns; the env
  * must outlive it).  Allocates parameters, Adam moments, rollout buffers
  * ((n_steps + 1) x E x D observations and the per-step arrays), minibatch
- * activations and a cuBLAS handle on the current device, which must be the
+ * activations and the partial sums of the weight gradients on the current
+ * device, which must be the
  * env context's device (as for every sg_ppo_* call that enqueues work:
  * otherwise SG_ERR_INVALID_ARG and nothing is enqueued).  Parameters start
  * at zero: set them with sg_ppo_set_params.  Invalid configurations return
@@ -137,6 +142,31 @@ sg_status sg_ppo_get_buffer(sg_ppo *ppo, int32_t which, void *dst_dev);
  * observations, actions, logp, values, advantages and returns are what the
  * update reads), e.g. to run the update on a batch collected elsewhere. */
 sg_status sg_ppo_set_buffer(sg_ppo *ppo, int32_t which, const void *src_dev);
+
+/*
+ * The dense contraction of the policy and value networks (Methods, "Policy
+ * learning and control": MLPs of 256, 128 and 64 ELU units), exposed as a
+ * building block: on `stream` (cudaStream_t, NULL = legacy default stream),
+ *   C[m * c_m + n] = act( sum_k A[m * a_m + k * a_k] * B[n * b_n + k * b_k] + bias[n] )
+ * for 0 <= m < M, 0 <= n < N, 0 <= k < K; all pointers are device float
+ * arrays, strides in elements (row- or column-major operands, transposes);
+ * bias [N] may be NULL; act is ELU when elu != 0, else the identity.  It
+ * runs on the tcgen05 tensor cores in kind::tf32 with FP32 accumulation;
+ * with split_tf32 != 0 every operand is split into two TF32 parts
+ * (x = hi + lo) and three products are accumulated (hi*hi + hi*lo + lo*hi:
+ * FP32-grade, about 2^-22 relative per product), else one TF32 product
+ * (10-bit mantissas).  For long contractions without bias or activation
+ * (c_m == N), `work` (device, work_floats floats, may be NULL) lets the
+ * library split K over more CTAs and add the partial sums in a fixed order
+ * afterwards (results do not depend on scheduling).  Asynchronous; C must not
+ * overlap A, B or work.  SG_ERR_INVALID_ARG for NULL operands or negative
+ * sizes; SG_ERR_CUDA if a launch fails.  A bounded device wait that runs out
+ * leaves C unspecified.
+ */
+sg_status sg_mlp_gemm(void *stream, const float *A, int64_t a_m, int64_t a_k, const float *B,
+                      int64_t b_n, int64_t b_k, const float *bias, int32_t elu, int32_t M,
+                      int32_t N, int32_t K, float *C, int64_t c_m, float *work,
+                      int64_t work_floats, int32_t split_tf32);
 
 #ifdef __cplusplus
 }

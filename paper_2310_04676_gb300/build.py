@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libsg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["sg_api.cu", "sg_kernels.cu", "sg_pair.cu", "sg_diff.cu", "sg_noalloc.cu", "sg_path.cu", "sg_peak.cu", "sg_ppo.cu", "sg_pack.cpp"]
+SOURCES = ["sg_api.cu", "sg_kernels.cu", "sg_pair.cu", "sg_diff.cu", "sg_noalloc.cu", "sg_path.cu", "sg_peak.cu", "sg_ppo.cu", "sg_mlp.cu", "sg_pack.cpp"]
 
 
 def nvcc():
@@ -55,7 +55,7 @@ def build(verbose=False):
             sys.stderr.write(log)
     tmp = LIB + ".tmp"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + [
-        "-lcudart_static", "-lcublas", "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
+        "-lcudart_static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (" ".join(cmd), r.stderr))

@@ -776,6 +776,7 @@ DiffArgs context_diff_args(sg_ctx* c) {
 void context_set_error(sg_ctx* c, const char* msg) { c->last_error = msg; }
 sg_status context_check_device(sg_ctx* c, const char* fn) { return on_device(c, fn); }
 cudaStream_t context_stream(sg_ctx* c) { return c->stream; }
+int32_t* context_err(sg_ctx* c) { return c->d_err; }
 const std::vector<int32_t>& context_env_dof(sg_ctx* c) { return c->plan.env_dof; }
 }  // namespace sg
 

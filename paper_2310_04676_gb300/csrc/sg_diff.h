@@ -69,6 +69,8 @@ void context_set_error(sg_ctx* ctx, const char* msg);
 // SG_OK if the context's device is current; else an error (message set) naming fn
 sg_status context_check_device(sg_ctx* ctx, const char* fn);
 cudaStream_t context_stream(sg_ctx* ctx);
+// the context's device error word (DEVERR_* flags, read by sg_sync_status)
+int32_t* context_err(sg_ctx* ctx);
 // total joints of every env [E] (host copy of the description)
 const std::vector<int32_t>& context_env_dof(sg_ctx* ctx);
 

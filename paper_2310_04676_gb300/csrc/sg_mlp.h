@@ -1,0 +1,50 @@
+// Dense contraction of the PPO networks on tcgen05 tensor cores (sg_mlp.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace sg {
+
+// C[m c_m + n] (+ split s at s c_split) = epilogue(sum_k A(m, k) B(n, k))
+// with A(m, k) = A[m a_m + k a_k], B(n, k) = B[n b_n + k b_k].
+struct MlpGemmArgs {
+  const float* A;
+  long long a_m, a_k;
+  const float* B;
+  long long b_n, b_k;
+  float* C;
+  long long c_m;
+  const float* bias;    // [N] or null: added to every row
+  int M, N, K;
+  int elu;              // 1: ELU after the bias
+  // input-gradient epilogue of an ELU layer: C = (A B^T) * ELU'(y) with
+  // y[m c_m + n] the layer's activated output (ELU'(y) = 1 for y > 0, else
+  // y + 1), and per CTA row tile the column sums of C (the bias gradient of
+  // that layer) into colsum[blockIdx.x][N]; both null otherwise
+  const float* act_y;
+  float* colsum;
+  int split_tf32;       // 1: three-product split precision (FP32-grade); 0: one TF32 product
+  int k_per_split;      // K per CTA layer when c_split != 0 (a multiple of 32)
+  long long c_split;    // 0: one output; else split s writes its partial sum at C + s c_split
+  int n_tile;           // 0: chosen by the launcher
+  int* err;             // device error word (bounded waits), or null
+};
+
+// output columns per CTA: up to 128; 64 for short contractions (K <= 32) or
+// when wider tiles would leave fewer than two CTAs per SM
+int mlp_tile_n(int M, int N, int K);
+size_t mlp_smem_bytes(int n_tile);
+cudaError_t prepare_mlp_kernels();
+cudaError_t launch_mlp_gemm(const MlpGemmArgs& a, cudaStream_t s);
+cudaError_t launch_mlp_split_reduce(const float* partial, int splits, long long split_len, float* C,
+                                    long long n_total, cudaStream_t s);
+// launch_mlp_gemm, splitting K over more CTAs (partial sums in `work`, then
+// a fixed-order reduction) when the product has few output tiles, no bias
+// and no activation, C is dense (c_m == N) and the partials fit in work.
+cudaError_t launch_mlp_gemm_split(const MlpGemmArgs& a, float* work, long long work_floats,
+                                  cudaStream_t s);
+
+}  // namespace sg

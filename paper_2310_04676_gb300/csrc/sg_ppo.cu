@@ -4,11 +4,15 @@
 //
 // Layout: activations are row-major [rows][width] (rows = envs while
 // collecting, minibatch rows while updating); weights row-major [out][in].
-// GEMMs are cuBLAS SGEMMs on the row-major data seen as column-major
-// transposes (FP32, or TF32 tensor cores); bias + ELU, the Gaussian head and
-// its gradient, GAE, the gathers, the reductions (fixed-order, so results do
-// not depend on scheduling) and Adam are the kernels below.
-#include <cublas_v2.h>
+// The dense layers run on this library's tensor-core contraction (sg_mlp.cu:
+// tcgen05 kind::tf32 with three-product split precision, FP32-grade; one
+// TF32 product per term with tf32 = 1): forward products with the bias and
+// ELU in their epilogue, input gradients with the ELU derivative and the
+// bias-gradient partial sums of the layer below in theirs, and weight
+// gradients split over the minibatch rows with a fixed-order sum of the
+// partials.  The Gaussian head and its gradient, GAE, the gathers, the
+// reductions (fixed-order, so results do not depend on scheduling) and Adam
+// are the kernels below.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,6 +25,7 @@
 #include "sg.h"
 #include "sg_diff.h"
 #include "sg_internal.h"
+#include "sg_mlp.h"
 #include "sg_ppo.h"
 #include "sg_rng.cuh"
 
@@ -68,58 +73,6 @@ Layout make_layout(int D, int A) {
 }
 
 // ---- kernels -----------------------------------------------------------------
-__device__ __forceinline__ float elu(float x) { return x > 0.f ? x : expm1f(x); }
-
-// Y[r][c] = act(Y[r][c] + b[c]) in place (width a multiple of 4: float4 path).
-// A thread owns 4 adjacent columns (its bias in registers) of every
-// `groups`-th row, two rows in flight, so no per-element index arithmetic is
-// needed.
-__device__ __forceinline__ float4 bias_act4(float4 z, float4 c, int do_elu) {
-  z.x += c.x;
-  z.y += c.y;
-  z.z += c.z;
-  z.w += c.w;
-  if (do_elu) {
-    z.x = elu(z.x);
-    z.y = elu(z.y);
-    z.z = elu(z.z);
-    z.w = elu(z.w);
-  }
-  return z;
-}
-
-__global__ void __launch_bounds__(256)
-bias_act4_kernel(float4* __restrict__ Y, const float4* __restrict__ b, int rows, int width4,
-                 int do_elu) {
-  const int groups = blockDim.x / width4;           // rows side by side (width4 | 256)
-  const int c4 = threadIdx.x % width4, g = threadIdx.x / width4;
-  if (g >= groups) return;
-  const float4 c = b[c4];
-  const int stride = gridDim.x * groups;
-  int r = blockIdx.x * groups + g;
-  for (; r + stride < rows; r += 2 * stride) {
-    const size_t k0 = (size_t)r * width4 + c4, k1 = k0 + (size_t)stride * width4;
-    const float4 z0 = Y[k0], z1 = Y[k1];
-    Y[k0] = bias_act4(z0, c, do_elu);
-    Y[k1] = bias_act4(z1, c, do_elu);
-  }
-  if (r < rows) {
-    const size_t k = (size_t)r * width4 + c4;
-    Y[k] = bias_act4(Y[k], c, do_elu);
-  }
-}
-
-__global__ void bias_act_kernel(float* __restrict__ Y, const float* __restrict__ b, int n,
-                                int width, int do_elu) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float z = Y[i] + b[i % width];
-    Y[i] = do_elu ? elu(z) : z;
-  }
-}
-
-// dY <- dY * ELU'(z), with ELU' from the stored output y: 1 for y > 0, y + 1 otherwise
-__device__ __forceinline__ float delu(float y) { return y > 0.f ? 1.f : y + 1.f; }
-
 // Zero-padded copy of rows [rows][w] -> [rows][wp]
 __global__ void pad_rows_kernel(const float* __restrict__ src, int rows, int w, int wp,
                                 float* __restrict__ dst) {
@@ -215,67 +168,28 @@ __device__ double block_sum(double v, double* sh) {
   return r;
 }
 
-// dZ = dY * ELU'(y) in place and per-block column sums of dZ (the bias
-// gradient of the layer that produced y).  Block b takes rows [b*chunk,
-// (b+1)*chunk); a thread owns 4 adjacent columns (float4) of every
-// `groups`-th row, four rows in flight per iteration.
+// blocks of the bias-gradient partial sums of the output layers
 constexpr int kBGradBlocks = 608;
-__device__ __forceinline__ float4 delu4(float4 d, float4 y) {
-  return make_float4(d.x * delu(y.x), d.y * delu(y.y), d.z * delu(y.z), d.w * delu(y.w));
-}
+
+// Per-block column sums of Y [rows][w] for narrow w (the output layers' bias
+// gradient): block b takes rows [b*chunk, (b+1)*chunk); thread t sums column
+// t % w over every (256 / w)-th row; partial sums then combine in thread order.
 __global__ void __launch_bounds__(256)
-elu_backward_bgrad_kernel(float* __restrict__ dY, const float* __restrict__ Y, int rows, int w,
-                          float* __restrict__ part) {
-  const int w4 = w >> 2;
-  const int groups = blockDim.x / w4;               // rows processed side by side (w | 1024)
-  const int c4 = threadIdx.x % w4, g = threadIdx.x / w4;
+colsum_partial_kernel(const float* __restrict__ Y, int rows, int w, float* __restrict__ part) {
+  __shared__ float sh[256];
+  const int groups = blockDim.x / w;
+  const int c = threadIdx.x % w, g = threadIdx.x / w;
   const int chunk = (rows + gridDim.x - 1) / gridDim.x;
   const int r0 = blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
-  float4* d4 = reinterpret_cast<float4*>(dY);
-  const float4* y4 = reinterpret_cast<const float4*>(Y);
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  auto add = [&](float4 v) {
-    acc.x += v.x;
-    acc.y += v.y;
-    acc.z += v.z;
-    acc.w += v.w;
-  };
-  int r = r0 + g;
-  for (; r + 3 * groups < r1; r += 4 * groups) {
-    size_t k[4];
-    float4 d[4], y[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      k[u] = (size_t)(r + u * groups) * w4 + c4;
-      d[u] = d4[k[u]];
-      y[u] = y4[k[u]];
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float4 z = delu4(d[u], y[u]);
-      d4[k[u]] = z;
-      add(z);
-    }
-  }
-  for (; r < r1; r += groups) {
-    const size_t k = (size_t)r * w4 + c4;
-    const float4 z = delu4(d4[k], y4[k]);
-    d4[k] = z;
-    add(z);
-  }
-  __shared__ float4 sh[256];
+  float acc = 0.f;
+  if (g < groups)
+    for (int r = r0 + g; r < r1; r += groups) acc += Y[(size_t)r * w + c];
   sh[threadIdx.x] = acc;
   __syncthreads();
-  if (g == 0) {
-    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int k = 0; k < groups; ++k) {
-      const float4 v = sh[k * w4 + c4];
-      t.x += v.x;
-      t.y += v.y;
-      t.z += v.z;
-      t.w += v.w;
-    }
-    reinterpret_cast<float4*>(part + (size_t)blockIdx.x * w)[c4] = t;
+  if (threadIdx.x < w) {
+    float t = 0.f;
+    for (int k = 0; k < groups; ++k) t += sh[k * w + threadIdx.x];
+    part[(size_t)blockIdx.x * w + threadIdx.x] = t;
   }
 }
 
@@ -531,9 +445,9 @@ struct sg_ppo {
   int32_t* pub2int = nullptr;          // [public_params] internal index of each public entry
   float* xin = nullptr;                // [E][Dp] padded observations of the collect step
   cudaStream_t stream = nullptr;       // the stream the collect graph was captured for
-  cublasHandle_t blas = nullptr;
-  void* blas_ws = nullptr;
-  float* ones = nullptr;               // [rows] for bias gradients
+  float* mlp_work = nullptr;           // partial sums of the row-split weight gradients
+  long long mlp_work_floats = 0;
+  int32_t* err = nullptr;              // the env context's device error word
   float *params = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
   long long adam_t = 0;
   long long* d_step = nullptr;         // global step of the exploration noise
@@ -549,7 +463,7 @@ struct sg_ppo {
   float *dmu = nullptr, *dv = nullptr;  // loss gradients w.r.t. the actor mean and the value
   sg::MiniBatch mb{};
   float* head_part = nullptr;
-  float* bgrad_part = nullptr;         // [kBGradBlocks][256] bias-gradient partial sums
+  float* bgrad_part = nullptr;         // [blocks or row tiles][256] bias-gradient partial sums
   double* red_part = nullptr;
   float* norm = nullptr;               // advantage mean, 1 / std
   float* clip_coef = nullptr;
@@ -577,46 +491,53 @@ cudaError_t dalloc(sg_ppo* p, T** ptr, size_t count) {
   return e;
 }
 
-bool blas_ok(cublasStatus_t s) { return s == CUBLAS_STATUS_SUCCESS; }
+sg::MlpGemmArgs gemm_args(const sg_ppo* p) {
+  sg::MlpGemmArgs g{};
+  g.split_tf32 = p->cfg.tf32 ? 0 : 1;
+  g.err = p->err;
+  return g;
+}
 
-// Y[rows][out] = X[rows][in] W^T
-bool gemm_fwd(sg_ppo* p, const float* X, int rows, const Layer& l, float* Y) {
-  const float one = 1.f, zero = 0.f;
-  return blas_ok(cublasSgemm(p->blas, CUBLAS_OP_T, CUBLAS_OP_N, l.out, rows, l.in, &one,
-                             p->params + l.w, l.in, X, l.in, &zero, Y, l.out));
+// Y[rows][out] = act(X[rows][in] W^T + b), act = ELU on hidden layers
+bool gemm_fwd(sg_ppo* p, const float* X, int rows, const Layer& l, float* Y, bool elu) {
+  sg::MlpGemmArgs g = gemm_args(p);
+  g.A = X, g.a_m = l.in, g.a_k = 1;
+  g.B = p->params + l.w, g.b_n = l.in, g.b_k = 1;
+  g.C = Y, g.c_m = l.out;
+  g.bias = p->params + l.b, g.elu = elu ? 1 : 0;
+  g.M = rows, g.N = l.out, g.K = l.in;
+  return sg::launch_mlp_gemm(g, p->stream) == cudaSuccess;
 }
-// dX[rows][in] = dY[rows][out] W
-bool gemm_bwd_data(sg_ppo* p, const float* dY, int rows, const Layer& l, float* dX) {
-  const float one = 1.f, zero = 0.f;
-  return blas_ok(cublasSgemm(p->blas, CUBLAS_OP_N, CUBLAS_OP_N, l.in, rows, l.out, &one,
-                             p->params + l.w, l.in, dY, l.out, &zero, dX, l.in));
+// dZ[rows][in] = (dY[rows][out] W) * ELU'(y), y [rows][in] the output of the
+// ELU layer below, and per 128-row tile the column sums of dZ (that layer's
+// bias gradient) into p->bgrad_part
+bool gemm_bwd_data_elu(sg_ppo* p, const float* dY, int rows, const Layer& l, const float* y,
+                       float* dZ) {
+  sg::MlpGemmArgs g = gemm_args(p);
+  g.A = dY, g.a_m = l.out, g.a_k = 1;
+  g.B = p->params + l.w, g.b_n = 1, g.b_k = l.in;       // B(n = in, k = out) = W[out][in]
+  g.C = dZ, g.c_m = l.in;
+  g.M = rows, g.N = l.in, g.K = l.out;
+  g.act_y = y;
+  g.colsum = p->bgrad_part;
+  return sg::launch_mlp_gemm(g, p->stream) == cudaSuccess;
 }
-// dW[out][in] = dY^T X ; with_bias: db[out] = dY^T 1
+// dW[out][in] = dY^T X (rows split over CTAs); with_bias: db[out] = dY^T 1
 bool gemm_bwd_weight(sg_ppo* p, const float* dY, const float* X, int rows, const Layer& l,
                      bool with_bias) {
-  const float one = 1.f, zero = 0.f;
-  if (!blas_ok(cublasSgemm(p->blas, CUBLAS_OP_N, CUBLAS_OP_T, l.in, l.out, rows, &one, X, l.in,
-                           dY, l.out, &zero, p->grad + l.w, l.in)))
+  sg::MlpGemmArgs g = gemm_args(p);
+  g.A = dY, g.a_m = 1, g.a_k = l.out;                   // A(m = out, k = row)
+  g.B = X, g.b_n = 1, g.b_k = l.in;                     // B(n = in, k = row)
+  g.C = p->grad + l.w, g.c_m = l.in;
+  g.M = l.out, g.N = l.in, g.K = rows;
+  if (sg::launch_mlp_gemm_split(g, p->mlp_work, p->mlp_work_floats, p->stream) != cudaSuccess)
     return false;
   if (!with_bias) return true;
-  return blas_ok(cublasSgemv(p->blas, CUBLAS_OP_N, l.out, rows, &one, dY, l.out, p->ones, 1, &zero,
-                             p->grad + l.b, 1));
-}
-
-cudaError_t bias_act(sg_ppo* p, float* Y, int rows, const Layer& l, bool elu) {
-  if (rows <= 0) return cudaSuccess;
-  const long long n = (long long)rows * l.out;
-  if (l.out % 4 == 0 && 256 % (l.out / 4) == 0) {
-    const int groups = 256 / (l.out / 4);
-    const int blocks = (int)std::min<long long>((rows + groups - 1) / groups, 152 * 8);
-    sg::bias_act4_kernel<<<blocks, 256, 0, p->stream>>>(
-        reinterpret_cast<float4*>(Y), reinterpret_cast<const float4*>(p->params + l.b), rows,
-        l.out / 4, elu ? 1 : 0);
-  } else {
-    sg::bias_act_kernel<<<sg::grid_for(n, 256), 256, 0, p->stream>>>(Y, p->params + l.b, (int)n,
-                                                                      l.out, elu ? 1 : 0);
-  }
-  return cudaGetLastError();
+  sg::colsum_partial_kernel<<<sg::kBGradBlocks, 256, 0, p->stream>>>(dY, rows, l.out,
+                                                                    p->bgrad_part);
+  sg::bgrad_final_kernel<<<l.out, 128, 0, p->stream>>>(p->bgrad_part, sg::kBGradBlocks, l.out,
+                                                      p->grad + l.b);
+  return cudaGetLastError() == cudaSuccess;
 }
 
 // Forward of one network over `rows` inputs; hidden outputs kept in h[0..2].
@@ -625,8 +546,7 @@ bool net_forward(sg_ppo* p, const Net& net, const float* X, int rows, float* con
   const float* in = X;
   for (int i = 0; i < 4; ++i) {
     float* y = i < 3 ? h[i] : out;
-    if (!gemm_fwd(p, in, rows, net.l[i], y)) return false;
-    if (bias_act(p, y, rows, net.l[i], i < 3) != cudaSuccess) return false;
+    if (!gemm_fwd(p, in, rows, net.l[i], y, i < 3)) return false;
     in = y;
   }
   return true;
@@ -643,11 +563,11 @@ bool net_backward(sg_ppo* p, const Net& net, const float* X, int rows, float* co
     if (!gemm_bwd_weight(p, dY, in, rows, net.l[i], i == 3)) return false;
     if (i == 0) break;
     float* dX = bufs[i & 1];
-    if (!gemm_bwd_data(p, dY, rows, net.l[i], dX)) return false;
-    const int w = net.l[i].in;                    // hidden widths 64, 128, 256 divide 256
-    sg::elu_backward_bgrad_kernel<<<sg::kBGradBlocks, 256, 0, p->stream>>>(dX, h[i - 1], rows, w,
-                                                                           p->bgrad_part);
-    sg::bgrad_final_kernel<<<w, 128, 0, p->stream>>>(p->bgrad_part, sg::kBGradBlocks, w,
+    // input gradient with the ELU backward and the bias-gradient partial sums
+    // of layer i - 1 in the product's epilogue
+    if (!gemm_bwd_data_elu(p, dY, rows, net.l[i], h[i - 1], dX)) return false;
+    const int w = net.l[i].in;
+    sg::bgrad_final_kernel<<<w, 128, 0, p->stream>>>(p->bgrad_part, (rows + 127) / 128, w,
                                                     p->grad + net.l[i - 1].b);
     if (cudaGetLastError() != cudaSuccess) return false;
     dY = dX;
@@ -657,7 +577,6 @@ bool net_backward(sg_ppo* p, const Net& net, const float* X, int rows, float* co
 
 sg_status bind_stream(sg_ppo* p, cudaStream_t s) {
   p->stream = s;
-  if (!blas_ok(cublasSetStream(p->blas, s))) return fail(p, SG_ERR_CUDA, "cublasSetStream failed");
   return SG_OK;
 }
 
@@ -790,7 +709,8 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
   step(dalloc(p, &p->dbuf1, (size_t)rows * sg::kH1));
   step(dalloc(p, &p->dmu, (size_t)p->M * p->Ap));
   step(dalloc(p, &p->dv, (size_t)p->M));
-  step(dalloc(p, &p->ones, (size_t)rows));
+  p->mlp_work_floats = (long long)2 * 152 * sg::kH1 * sg::kH2;   // row-split partial sums
+  step(dalloc(p, &p->mlp_work, (size_t)p->mlp_work_floats));
   step(dalloc(p, &p->mb.obs, (size_t)p->M * p->Dp));
   step(dalloc(p, &p->mb.act, (size_t)p->M * A));
   step(dalloc(p, &p->mb.mask, (size_t)p->M * A));
@@ -801,18 +721,18 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
   const int head_blocks = (p->M + sg::kRedThreads - 1) / sg::kRedThreads;
   step(dalloc(p, &p->head_part, (size_t)head_blocks * (2 + 2 * A)));
   step(dalloc(p, &p->red_part, (size_t)2 * sg::kRedBlocks));
-  step(dalloc(p, &p->bgrad_part, (size_t)sg::kBGradBlocks * sg::kH1));
+  const size_t part_rows = std::max<size_t>(sg::kBGradBlocks, ((size_t)rows + 127) / 128);
+  step(dalloc(p, &p->bgrad_part, part_rows * sg::kH1));
   step(dalloc(p, &p->norm, 2));
   step(dalloc(p, &p->clip_coef, 1));
-  const size_t ws_bytes = (size_t)32 << 20;
-  step(cudaMalloc(&p->blas_ws, ws_bytes));
+  step(sg::prepare_mlp_kernels());
   if (e != cudaSuccess) {
     sg_status st = cuda_fail(p, e, "sg_ppo_create");
     sg_ppo_destroy(p);
     return st;
   }
-  // host-built constants: joint mask, ones, zero targets, public -> internal parameter map
-  std::vector<float> jm((size_t)E * A, 0.f), ones((size_t)rows, 1.f);
+  // host-built constants: joint mask, zero targets, public -> internal parameter map
+  std::vector<float> jm((size_t)E * A, 0.f);
   std::vector<int32_t> map(p->public_params);
   {
     const Net* pn[2] = {&Lpub.actor, &Lpub.critic};
@@ -834,7 +754,6 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
     for (int j = 0; j < A && j < dof[k]; ++j) jm[(size_t)k * A + j] = 1.f;
   cudaStream_t s = sg::context_stream(env);
   step(cudaMemcpyAsync(p->jmask, jm.data(), jm.size() * 4, cudaMemcpyHostToDevice, s));
-  step(cudaMemcpyAsync(p->ones, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice, s));
   step(cudaMemsetAsync(p->zero_targets, 0, (size_t)E * A * 4, s));
   step(cudaMemsetAsync(p->params, 0, P * 4, s));
   step(cudaMemsetAsync(p->grad, 0, P * 4, s));
@@ -847,16 +766,7 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
     sg_ppo_destroy(p);
     return st;
   }
-  if (!blas_ok(cublasCreate(&p->blas)) ||
-      !blas_ok(cublasSetWorkspace(p->blas, p->blas_ws, ws_bytes)) ||
-      // FP32 mode: the default math mode, which never lowers FP32 products to TF32
-      !blas_ok(cublasSetMathMode(p->blas, c.tf32 ? CUBLAS_TF32_TENSOR_OP_MATH
-                                                 : CUBLAS_DEFAULT_MATH)) ||
-      !blas_ok(cublasSetPointerMode(p->blas, CUBLAS_POINTER_MODE_HOST))) {
-    fail(p, SG_ERR_CUDA, "sg_ppo_create: cuBLAS initialisation failed");
-    sg_ppo_destroy(p);
-    return SG_ERR_CUDA;
-  }
+  p->err = sg::context_err(env);
   bind_stream(p, s);
   *out = p;
   return SG_OK;
@@ -871,8 +781,6 @@ void sg_ppo_destroy(sg_ppo* p) {
   if (other) cudaSetDevice(owner);
   if (p->stream) cudaStreamSynchronize(p->stream);
   if (p->collect_exec) cudaGraphExecDestroy(p->collect_exec);
-  if (p->blas) cublasDestroy(p->blas);
-  if (p->blas_ws) cudaFree(p->blas_ws);
   for (void* a : p->allocs) cudaFree(a);
   delete p;
   if (other) cudaSetDevice(cur);

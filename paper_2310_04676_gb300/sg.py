@@ -128,6 +128,9 @@ def load_library(path=LIB_PATH):
         "sg_ppo_update": (i32, [vp, vp, vp]),
         "sg_ppo_get_buffer": (i32, [vp, i32, vp]),
         "sg_ppo_set_buffer": (i32, [vp, i32, vp]),
+        "sg_mlp_gemm": (i32, [vp, vp, ctypes.c_int64, ctypes.c_int64, vp, ctypes.c_int64,
+                             ctypes.c_int64, vp, i32, i32, i32, i32, vp, ctypes.c_int64, vp,
+                             ctypes.c_int64, i32]),
         "sg_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -216,6 +219,25 @@ def fp32_fma_rate(iters=4096, repeats=5, stream=None):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def mlp_gemm(A, a_strides, B, b_strides, M, N, K, out, c_m, bias=None, elu=False, work=None,
+             split=True, stream=None):
+    """sg_mlp_gemm: out[m * c_m + n] = act(sum_k A(m, k) B(n, k) + bias[n]) with
+    A(m, k) = A.flatten()[m * a_strides[0] + k * a_strides[1]] and
+    B(n, k) = B.flatten()[n * b_strides[0] + k * b_strides[1]] (tensor-core
+    split-precision contraction of the PPO networks)."""
+    import torch
+    lib = load_library()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = lib.sg_mlp_gemm(ctypes.c_void_p(s.cuda_stream), _ptr(A), int(a_strides[0]),
+                         int(a_strides[1]), _ptr(B), int(b_strides[0]), int(b_strides[1]),
+                         _ptr(bias), 1 if elu else 0, int(M), int(N), int(K), _ptr(out), int(c_m),
+                         _ptr(work), int(work.numel()) if work is not None else 0,
+                         1 if split else 0)
+    if st != SG_OK:
+        raise SgError(st, "sg_mlp_gemm failed")
+    return out
 
 
 class Env:

@@ -1,0 +1,103 @@
+"""The hand-written tensor-core contraction of the PPO networks (sg_mlp_gemm)
+against FP64 products of the same FP32 inputs.
+
+With the split-precision (3xTF32) products the result must carry FP32
+accuracy: max |C - C64| <= 2e-6 * sum_k |A(m,k) B(n,k)| (about twenty FP32
+roundings of the sum of magnitudes; one TF32 product would miss this by
+three orders of magnitude), widened by sqrt(K / 1024) for sums of more than
+1024 terms (FP32 accumulation error grows like the square root of the number
+of terms), for the three operand layouts of a layer -- forward (X W^T),
+input gradient (dY W) and weight gradient (dY^T X, K split over CTAs) -- at
+the networks' widths (28-wide inputs, 256, 128, 64 hidden, 8 and 1 outputs),
+with ragged M, N and K, bias and ELU.  The single-product TF32 mode must land
+within TF32 rounding (2^-9 relative to the magnitudes) and be measurably
+coarser than the split mode.
+"""
+import pytest
+import torch
+
+from paper_2310_04676_gb300 import sg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    sg.load_library()
+
+
+def _rand(shape, seed):
+    g = torch.Generator().manual_seed(seed)
+    return (torch.rand(shape, generator=g, dtype=torch.float64) * 2 - 1).float()
+
+
+def _check(C, A64, B64, bias=None, elu=False, tol=2e-6):
+    tol = tol * max(1.0, (A64.shape[1] / 1024) ** 0.5)
+    ref = A64 @ B64.T
+    mag = A64.abs() @ B64.abs().T
+    if bias is not None:
+        ref = ref + bias.double()[None, :]
+        mag = mag + bias.double().abs()[None, :]
+    if elu:
+        ref = torch.where(ref > 0, ref, torch.expm1(ref))
+    err = (C.double().cpu() - ref).abs()
+    assert (err <= tol * mag + 1e-30).all(), (err / mag.clamp_min(1e-30)).max().item()
+    return (err / mag.clamp_min(1e-30)).max().item()
+
+
+@pytest.mark.parametrize("rows,inp,out", [(300, 28, 256), (257, 256, 128), (129, 128, 64),
+                                          (200, 64, 8), (131, 64, 1), (1000, 256, 256)])
+def test_forward_layer(rows, inp, out):
+    X, W, b = _rand((rows, inp), 1), _rand((out, inp), 2), _rand((out,), 3)
+    Xd, Wd, bd = X.cuda(), W.cuda(), b.cuda()
+    for elu in (False, True):
+        Y = torch.empty(rows, out, device="cuda")
+        sg.mlp_gemm(Xd, (inp, 1), Wd, (inp, 1), rows, out, inp, Y, out, bias=bd, elu=elu)
+        torch.cuda.synchronize()
+        _check(Y, X.double(), W.double(), b, elu)
+    # ELU without a bias
+    Y = torch.empty(rows, out, device="cuda")
+    sg.mlp_gemm(Xd, (inp, 1), Wd, (inp, 1), rows, out, inp, Y, out, elu=True)
+    torch.cuda.synchronize()
+    _check(Y, X.double(), W.double(), None, True)
+
+
+@pytest.mark.parametrize("rows,inp,out", [(300, 256, 128), (257, 128, 64), (190, 64, 8),
+                                          (140, 256, 256)])
+def test_input_gradient(rows, inp, out):
+    dY, W = _rand((rows, out), 4), _rand((out, inp), 5)
+    dX = torch.empty(rows, inp, device="cuda")
+    # dX[r][i] = sum_o dY[r][o] W[o][i]: B(n = i, k = o) = W[o * inp + i]
+    sg.mlp_gemm(dY.cuda(), (out, 1), W.cuda(), (1, inp), rows, inp, out, dX, inp)
+    torch.cuda.synchronize()
+    _check(dX, dY.double(), W.double().T)
+
+
+@pytest.mark.parametrize("rows,inp,out", [(5000, 28, 256), (4099, 256, 128), (3000, 128, 64),
+                                          (2500, 64, 8), (777, 64, 1)])
+def test_weight_gradient_split(rows, inp, out):
+    dY, X = _rand((rows, out), 6), _rand((rows, inp), 7)
+    dW = torch.empty(out, inp, device="cuda")
+    work = torch.empty(400 * out * inp, device="cuda")
+    # dW[o][i] = sum_r dY[r][o] X[r][i]: A(m = o, k = r) = dY[r * out + o], B(n = i, k = r)
+    sg.mlp_gemm(dY.cuda(), (1, out), X.cuda(), (1, inp), out, inp, rows, dW, inp, work=work)
+    torch.cuda.synchronize()
+    _check(dW, dY.double().T, X.double().T)
+    # the same without a work buffer (one CTA per output tile) agrees to rounding
+    dW1 = torch.empty_like(dW)
+    sg.mlp_gemm(dY.cuda(), (1, out), X.cuda(), (1, inp), out, inp, rows, dW1, inp)
+    torch.cuda.synchronize()
+    _check(dW1, dY.double().T, X.double().T)
+
+
+def test_single_tf32_product_is_coarser():
+    X, W = _rand((256, 256), 8), _rand((128, 256), 9)
+    Y3, Y1 = (torch.empty(256, 128, device="cuda") for _ in range(2))
+    sg.mlp_gemm(X.cuda(), (256, 1), W.cuda(), (256, 1), 256, 128, 256, Y3, 128, split=True)
+    sg.mlp_gemm(X.cuda(), (256, 1), W.cuda(), (256, 1), 256, 128, 256, Y1, 128, split=False)
+    torch.cuda.synchronize()
+    e3 = _check(Y3, X.double(), W.double())
+    e1 = _check(Y1, X.double(), W.double(), tol=2.0 ** -9)
+    assert e1 > 20 * e3
