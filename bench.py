@@ -413,9 +413,12 @@ def measure_rollout(cx, wl, desc, T, with_e2e=True):
         env.set_launch(threads, mode, split)
     else:
         threads, mode, split, _ = env.autotune(acts, dt, S, out=out, repeats=3)
+    packing = env.packing
     sgraph, plain = sg.Env(desc), sg.Env(desc)
     sgraph.set_launch(threads, sg.ROLLOUT_STEP_GRAPH, split)
     plain.set_launch(threads, sg.ROLLOUT_PERSISTENT, split)
+    for e in (sgraph, plain):
+        e.set_packing(packing)
     out_g, out_p = sgraph.empty_outputs(T), plain.empty_outputs(T)
 
     def plain_rollout():
@@ -440,12 +443,14 @@ def measure_rollout(cx, wl, desc, T, with_e2e=True):
         qb, qdb, _ = other.get_state()
         same = same and bool(torch.equal(qa, qb) and torch.equal(qda, qdb)
                              and torch.equal(out[0], o2[0]))
-    res = {"T": T, "E": E, "ms": ms, "launch": (threads, mode, split), "same_bits": same,
+    res = {"T": T, "E": E, "ms": ms, "launch": (threads, mode, split), "packing": packing,
+           "same_bits": same,
            "status": sg.STATUS_NAMES.get(env.sync_status()), "clocks": clk.summary(),
            "obs_dim": env.obs_dim}
     if with_e2e:
         env_h = sg.Env(desc)
         env_h.set_launch(threads, mode, split)
+        env_h.set_packing(packing)
         a_h = acts.cpu().pin_memory()
         o_h = (torch.empty(T, E, env_h.obs_dim).pin_memory(), torch.empty(T, E).pin_memory(),
                torch.empty(T, E, dtype=torch.uint8).pin_memory())
@@ -641,7 +646,8 @@ def run_rollout_config(cx, name, E=None):
     line = base_line(args, world, value, 1e3 * t["ours"] / args.steps, cfg)
     line["form"] = "persistent kernel in a CUDA graph"
     line["launch"] = {"threads_per_block": threads, "mode": ["persistent", "step_graph"][mode],
-                      "chain_split": split}
+                      "chain_split": split,
+                      "packing": ["class-grouped", "interleaved"][r["packing"]]}
     line["us_per_control_step"] = 1e6 * t["ours"] / args.steps / T
     line["step_time_stats"] = stats(r["ms"]["ours"])
     for k, label in (("step_graph", "%d single-step kernels replayed from a CUDA graph" % T),
@@ -804,7 +810,8 @@ def run_ppo_config(cx, name="P1", E=None):
     cfg = {"workload": wl.name, "envs_per_gpu": En, "n_steps": wl.steps, "epochs": 5,
            "minibatches": 4, "minibatch_rows": r["B"] // 4, "substeps": wl.substeps, "dt": wl.dt,
            "networks": "actor and critic MLP %d-256-128-64-{%d,1}, ELU" % (D, A),
-           "gemm": "this library's tcgen05 contraction, FP32-grade split precision (3xTF32)",
+           "gemm": "this library's tcgen05 contraction, FP32-grade split precision (3xTF32), "
+                   "weights split once per update",
            "l2": "flushed (256 MiB write) before every timed iteration"}
     line = base_line(args, cx.world, s32["value"], s32["ms_per_iteration"], cfg)
     line["metric"] = "with-learning frames/s (collect + PPO update), context for the step metric"
@@ -825,15 +832,16 @@ def run_ppo_config(cx, name="P1", E=None):
                                            device=cx.dev),
                    "unit": "frames/s", "h2d_bytes_per_step": r["h2d"],
                    "d2h_bytes_per_step": r["d2h"]}
-    # kernels of this library per iteration: per collect step 8 layer products
-    # (bias + ELU fused), pad, sampling, the env step, bootstrap, reset, observe;
-    # then pad, 4 critic layers (last values), GAE, 2 moments, step counter; per
-    # minibatch gather, 8 forward layers, 2 loss-head, per network 4 weight
-    # gradients (product + fixed-order sum of the row splits), the output bias
-    # column sums (2), 3 input gradients with the ELU backward and 3 bias sums,
-    # then 2 norm, Adam
+    # kernels of this library per iteration: the weights' TF32 split, then per
+    # collect step 8 layer products (bias + ELU fused), pad, sampling, the env
+    # step, bootstrap, reset, observe; then pad, 4 critic layers (last values),
+    # GAE, 2 moments, step counter; per minibatch gather, the weights' TF32
+    # split, 8 forward layers, 2 loss-head, per network 4 weight gradients
+    # (product + fixed-order sum of the row splits), the output bias column
+    # sums (2), 3 input gradients with the ELU backward and 3 bias sums, then
+    # 2 norm, Adam
     n_mb = 5 * 4
-    line["gpu_launches"] = (wl.steps * 14 + 9 + n_mb * 46) * args.steps
+    line["gpu_launches"] = (1 + wl.steps * 14 + 9 + n_mb * 47) * args.steps
     line["library_launches"] = 0
     line["clocks"] = r["clocks"]
     line["status"] = r["status"]

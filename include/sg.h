@@ -279,13 +279,43 @@ sg_status sg_set_launch(sg_ctx *ctx, int32_t threads_per_block, int32_t rollout_
 sg_status sg_get_launch(const sg_ctx *ctx, int32_t *threads_per_block, int32_t *rollout_mode,
                         int32_t *chain_split);
 
-/* Autotuner: times every launch plan (threads per block x chain split x
- * rollout mode) on
+/* Packing: the order of the warps of chain slots (each warp holds 32 chains
+ * of one class; a block of the step kernel holds consecutive warps).
+ *   SG_PACK_CLASS       warps grouped by chain class, longest chains first
+ *                       (7R, 7P, generic, 4R), the order sg_create builds;
+ *   SG_PACK_INTERLEAVE  the classes interleaved in proportion: warp i of a
+ *                       class of n warps goes to the fractional position
+ *                       (2 i + 1) / (2 n) of the sequence (ties in class
+ *                       order), so every block holds a mix of long and short
+ *                       chains.
+ * Results do not depend on the packing (bit-identical).  sg_set_packing
+ * reorders the context's parameters, slot tables and state in place
+ * (a temporary device buffer; synchronises the stream) and discards a
+ * pending sg_diff_forward (the next sg_diff_backward then fails with
+ * SG_ERR_INVALID_ARG until sg_diff_forward runs again).  SG_ERR_INVALID_ARG
+ * for an unknown packing. */
+enum { SG_PACK_CLASS = 0, SG_PACK_INTERLEAVE = 1 };
+sg_status sg_set_packing(sg_ctx *ctx, int32_t packing);
+int32_t sg_get_packing(const sg_ctx *ctx);
+
+/* Host only, no CUDA call: the warp order of `packing` for a description,
+ * order[w] = the warp of the class-grouped order that position w holds, for
+ * w < num_warps = sg_plan_info.num_slots / 32 (num_warps must equal it).
+ * Errors as sg_plan (message in err), SG_ERR_INVALID_ARG for an unknown
+ * packing or a wrong num_warps. */
+sg_status sg_plan_packing(const sg_desc *desc, int32_t packing, int32_t *order,
+                          int32_t num_warps, char *err, int32_t err_len);
+
+/* Autotuner: times every launch plan (packing x threads per block x chain
+ * split x rollout mode) on
  * a rollout with the given arguments (CUDA events, median of `repeats`
  * timed runs after one warm-up run each), keeps the fastest and writes its
- * time per rollout to *best_ms (may be NULL).  The environment state and
- * step counts are restored afterwards; the output buffers hold the last
- * trial's results.  Synchronises the stream; allocates a state snapshot. */
+ * time per rollout to *best_ms (may be NULL).  The interleaved packing is
+ * tried only where it differs from the class-grouped one; the fastest
+ * packing is left in place (sg_get_packing), which discards a pending
+ * sg_diff_forward as sg_set_packing does.  The environment state and step
+ * counts are restored afterwards; the output buffers hold the last trial's
+ * results.  Synchronises the stream; allocates a state snapshot. */
 sg_status sg_autotune(sg_ctx *ctx, const float *actions_dev, int32_t T, float dt,
                       int32_t substeps, float *obs_dev, float *reward_dev, uint8_t *done_dev,
                       int32_t repeats, float *best_ms);

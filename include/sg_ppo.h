@@ -155,11 +155,17 @@ sg_status sg_ppo_set_buffer(sg_ppo *ppo, int32_t which, const void *src_dev);
  * with split_tf32 != 0 every operand is split into two TF32 parts
  * (x = hi + lo) and three products are accumulated (hi*hi + hi*lo + lo*hi:
  * FP32-grade, about 2^-22 relative per product), else one TF32 product
- * (10-bit mantissas).  For long contractions without bias or activation
- * (c_m == N), `work` (device, work_floats floats, may be NULL) lets the
- * library split K over more CTAs and add the partial sums in a fixed order
- * afterwards (results do not depend on scheduling).  Asynchronous; C must not
- * overlap A, B or work.  SG_ERR_INVALID_ARG for NULL operands or negative
+ * (10-bit mantissas).  `work` (device scratch of work_floats floats, may be
+ * NULL) serves two purposes.  A product with few output tiles (fewer than
+ * two 128 x 128 tiles per SM of 152), more than 32 terms, no bias or
+ * activation and a dense C (c_m == N) splits K over more CTAs, their partial
+ * sums in work, added in a fixed order afterwards (results do not depend on
+ * scheduling).  Any other product splits B into its TF32 parts once, into
+ * work, when work holds ceil(K / 16) * 2 * 16 * (N rounded up to 128)
+ * floats and is 16-byte aligned, and every CTA then copies its part of them
+ * instead of splitting B itself (the PPO networks' forward and
+ * input-gradient products take this path with their weights).
+ * Asynchronous; C must not overlap A, B or work.  SG_ERR_INVALID_ARG for NULL operands or negative
  * sizes; SG_ERR_CUDA if a launch fails.  A bounded device wait that runs out
  * leaves C unspecified.
  */

@@ -36,6 +36,8 @@ struct sg_ctx {
   int threads = 128;
   int rollout_mode = SG_ROLLOUT_PERSISTENT;
   int split = 1;
+  int packing = SG_PACK_CLASS;
+  std::vector<int32_t> warp_order;   // position w holds warp warp_order[w] of the plan's order
   int host_io = SG_HOST_IO_AUTO;
   int fault = sg::FAULT_NONE;      // test hook (sg_debug_set_fault)
   unsigned long long wait_ns = sg::kDefaultWaitNs;
@@ -364,9 +366,102 @@ cudaError_t snapshot(sg_ctx* c, bool save) {
   return e;
 }
 
+// Put the warps in `packing`'s order: the parameter records, slot tables,
+// per-slot state and the autotuner's state snapshot are gathered into a
+// temporary buffer and copied back in place (the pointers captured in a
+// rollout graph stay valid).  A pending differentiable forward refers to the
+// old order and is discarded.
+cudaError_t apply_packing(sg_ctx* c, int packing) {
+  const std::vector<int32_t> target = sg::packing_order(c->plan, packing);
+  const int NW = c->plan.num_warps;
+  std::vector<int32_t> inv(NW), rel(NW);
+  for (int w = 0; w < NW; ++w) inv[c->warp_order[w]] = w;
+  bool identity = true;
+  for (int w = 0; w < NW; ++w) {
+    rel[w] = inv[target[w]];
+    identity = identity && rel[w] == w;
+  }
+  c->packing = packing;
+  if (identity) return cudaSuccess;
+  struct Arr {
+    void* p;
+    int F, B;
+  };
+  const int W = sg::kWarp;
+  const Arr arrs[] = {{c->d_params, 1, sg::kRecordFloats}, {c->d_q, sg::kMaxLinks, W},
+                      {c->d_qd, sg::kMaxLinks, W},          {c->d_q0, sg::kMaxLinks, W},
+                      {c->d_slot_env, 1, W},                {c->d_slot_info, 1, W},
+                      {c->d_warp_class, 1, 1},              {c->d_track, 6, W},
+                      {c->d_mass0, sg::kMaxLinks, W},       {c->d_inertia0, 3 * sg::kMaxLinks, W},
+                      {c->d_snap_q, sg::kMaxLinks, W},      {c->d_snap_qd, sg::kMaxLinks, W}};
+  size_t words = 0;
+  for (const Arr& a : arrs) words = std::max(words, (size_t)a.F * NW * a.B);
+  void* tmp = nullptr;
+  int32_t* d_rel = nullptr;
+  cudaError_t e = cudaMalloc(&tmp, words * 4 + (size_t)NW * 4 + 16);
+  if (e != cudaSuccess) return e;
+  d_rel = reinterpret_cast<int32_t*>(static_cast<char*>(tmp) + words * 4);
+  e = cudaMemcpyAsync(d_rel, rel.data(), (size_t)NW * 4, cudaMemcpyHostToDevice, c->stream);
+  for (const Arr& a : arrs) {
+    if (!a.p || e != cudaSuccess) continue;
+    e = sg::launch_permute_warps(a.p, tmp, d_rel, a.F, NW, a.B, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(a.p, tmp, (size_t)a.F * NW * a.B * 4, cudaMemcpyDeviceToDevice,
+                          c->stream);
+  }
+  const cudaError_t es = cudaStreamSynchronize(c->stream);   // rel and tmp are released below
+  if (e == cudaSuccess) e = es;
+  cudaFree(tmp);
+  if (e == cudaSuccess) {
+    c->warp_order = target;
+    c->diff_ready = false;
+    c->replay_prefilled = false;
+  }
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
+
+sg_status sg_plan_packing(const sg_desc* desc, int32_t packing, int32_t* order,
+                          int32_t num_warps, char* err, int32_t err_len) {
+  sg::Plan p;
+  std::string msg;
+  sg_status st;
+  try {
+    st = sg::build_plan(desc, &p, &msg);
+    if (st == SG_OK && (packing != SG_PACK_CLASS && packing != SG_PACK_INTERLEAVE)) {
+      st = SG_ERR_INVALID_ARG;
+      msg = "packing must be SG_PACK_CLASS or SG_PACK_INTERLEAVE";
+    } else if (st == SG_OK && (!order || num_warps != p.num_warps)) {
+      st = SG_ERR_INVALID_ARG;
+      msg = "order must hold num_slots / 32 entries";
+    }
+    if (st == SG_OK) {
+      const std::vector<int32_t> o = sg::packing_order(p, packing);
+      std::copy(o.begin(), o.end(), order);
+    }
+  } catch (const std::bad_alloc&) {
+    st = SG_ERR_OOM;
+    msg = "host allocation failed";
+  }
+  if (err && err_len > 0) {
+    std::strncpy(err, msg.c_str(), (size_t)err_len - 1);
+    err[err_len - 1] = '\0';
+  }
+  return st;
+}
+
+sg_status sg_set_packing(sg_ctx* ctx, int32_t packing) {
+  if (!ctx) return SG_ERR_INVALID_ARG;
+  SG_CHECK_DEVICE(ctx, "sg_set_packing");
+  if (packing != SG_PACK_CLASS && packing != SG_PACK_INTERLEAVE)
+    return set_err(ctx, SG_ERR_INVALID_ARG, "sg_set_packing: unknown packing");
+  return cuda_err(ctx, apply_packing(ctx, packing), "sg_set_packing");
+}
+
+int32_t sg_get_packing(const sg_ctx* ctx) { return ctx ? ctx->packing : -1; }
 
 sg_status sg_plan(const sg_desc* desc, sg_plan_info* info, char* err, int32_t err_len) {
   sg::Plan p;
@@ -424,6 +519,7 @@ sg_status sg_create(const sg_desc* desc, void* stream, sg_ctx** out) {
   }
   c->stream = static_cast<cudaStream_t>(stream);
   const sg::Plan& P = c->plan;
+  c->warp_order = sg::packing_order(P, SG_PACK_CLASS);
   const size_t NS = P.num_slots;
   cudaError_t e = cudaSuccess;
   auto step = [&](cudaError_t r) {
@@ -665,44 +761,58 @@ sg_status sg_autotune(sg_ctx* ctx, const float* actions_dev, int32_t T, float dt
   const int modes[] = {SG_ROLLOUT_PERSISTENT, SG_ROLLOUT_STEP_GRAPH};
   float best = -1.f;
   int best_t = ctx->threads, best_m = ctx->rollout_mode, best_s = ctx->split;
-  for (int m : modes) {
-    for (int plan = 0; plan < 8; ++plan) {
-      const int th = threads_list[plan & 3], sp = 1 + (plan >> 2);
-      if (sp == 2 && th < 64) continue;
-      ctx->threads = th;
-      ctx->rollout_mode = m;
-      ctx->split = sp;
-      std::vector<float> times;
-      for (int r = -1; r < repeats && st == SG_OK; ++r) {
-        e = snapshot(ctx, false);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
-        if (e != cudaSuccess) break;
-        st = run_rollout(ctx, actions_dev, T, dt, substeps, obs_dev, reward_dev, done_dev);
-        if (st != SG_OK) break;
-        e = cudaEventRecord(e1, ctx->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) break;
-        if (r >= 0) times.push_back(ms);
-      }
-      if (e != cudaSuccess || st != SG_OK) break;
-      std::sort(times.begin(), times.end());
-      const float med = times[times.size() / 2];
-      if (best < 0.f || med < best) {
-        best = med;
-        best_t = th;
-        best_m = m;
-        best_s = sp;
+  int best_p = ctx->packing;
+  // time every launch plan of the current packing
+  auto time_plans = [&]() {
+    for (int m : modes) {
+      for (int plan = 0; plan < 8; ++plan) {
+        const int th = threads_list[plan & 3], sp = 1 + (plan >> 2);
+        if (sp == 2 && th < 64) continue;
+        ctx->threads = th;
+        ctx->rollout_mode = m;
+        ctx->split = sp;
+        std::vector<float> times;
+        for (int r = -1; r < repeats && st == SG_OK; ++r) {
+          e = snapshot(ctx, false);
+          if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+          if (e != cudaSuccess) break;
+          st = run_rollout(ctx, actions_dev, T, dt, substeps, obs_dev, reward_dev, done_dev);
+          if (st != SG_OK) break;
+          e = cudaEventRecord(e1, ctx->stream);
+          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+          if (e != cudaSuccess) break;
+          if (r >= 0) times.push_back(ms);
+        }
+        if (e != cudaSuccess || st != SG_OK) return;
+        std::sort(times.begin(), times.end());
+        const float med = times[times.size() / 2];
+        if (best < 0.f || med < best) {
+          best = med;
+          best_t = th;
+          best_m = m;
+          best_s = sp;
+          best_p = ctx->packing;
+        }
       }
     }
-    if (e != cudaSuccess || st != SG_OK) break;
+  };
+  const int packings[2] = {SG_PACK_CLASS, SG_PACK_INTERLEAVE};
+  const int npack = sg::packing_order(ctx->plan, SG_PACK_INTERLEAVE) !=
+                            sg::packing_order(ctx->plan, SG_PACK_CLASS)
+                        ? 2
+                        : 1;
+  for (int i = 0; i < npack && e == cudaSuccess && st == SG_OK; ++i) {
+    e = apply_packing(ctx, packings[i]);
+    if (e == cudaSuccess) time_plans();
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ctx->threads = best_t;
   ctx->rollout_mode = best_m;
   ctx->split = best_s;
+  if (e == cudaSuccess && ctx->packing != best_p) e = apply_packing(ctx, best_p);
   if (st != SG_OK) return st;
   if (e == cudaSuccess) e = snapshot(ctx, false);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

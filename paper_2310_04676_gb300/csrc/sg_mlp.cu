@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "sg.h"
 #include "sg_internal.h"
@@ -153,18 +154,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // Rows [r0, r0 + nrows) x K [k0, k0 + 16) of X(r, k) = X[r xr + k xk] (zero
 // outside R x K).  Raw chunks travel to shared memory by asynchronous
 // 16-byte copies (cp.async, zero-filled outside the operand), kRawStages - 1
-// chunks ahead, in whichever layout is contiguous in global memory:
-// row-major [r][16] when K is the contiguous direction (xk = 1), K-major
-// [16][nrows] when the rows are (xr = 1); other strides are read by plain
-// loads.  The conversion then cuts the chunk into 4-element units (row r, K
-// group kg) numbered core matrix by core matrix -- unit f has
-// r = 8 (f >> 5) + (f & 7), kg = (f >> 3) & 3, so eight consecutive threads
-// store the eight rows of one core matrix (conflict-free 16-byte stores) --
-// splits each value into its TF32 parts and stores them to the tiles.
+// chunks ahead.  When K is the contiguous direction (xk = 1) a 16-byte piece
+// is four K values of one row -- one row of a core matrix -- and lands at its
+// place in the tensor cores' layout, so the split into TF32 parts is an
+// elementwise pass over the chunk.  When the rows are contiguous (xr = 1) a
+// piece holds one K value of four rows: the chunk is kept K-major
+// ([16][nrows]) and the split also transposes it (4-element units numbered
+// core matrix by core matrix -- unit f has r = 8 (f >> 5) + (f & 7),
+// kg = (f >> 3) & 3 -- so eight consecutive threads store the eight rows of
+// one core matrix, conflict-free 16-byte stores).  Other strides are read by
+// plain loads during the split.  Every thread's pieces are the same in each
+// chunk, so their addresses are computed once (Loader) and advanced by one
+// chunk per step.
 constexpr int kRawStages = 3;
 constexpr int kMaxTileN = 128;
-constexpr int kUnitsA = kTileM * (kChunkK / 4) / kMlpThreads;      // 4 per thread
-constexpr int kUnitsB = kMaxTileN * (kChunkK / 4) / kMlpThreads;   // at most 4 per thread
+constexpr int kUnits = kTileM * (kChunkK / 4) / kMlpThreads;   // 16-byte pieces per thread, <= 4
 
 enum RawLayout { RAW_ROWS = 0, RAW_KMAJOR = 1, RAW_PLAIN = 2 };
 
@@ -183,8 +187,8 @@ __device__ __forceinline__ Operand make_operand(const float* X, long long xr, lo
   return o;
 }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
                "r"(src_bytes)
                : "memory");
 }
@@ -196,47 +200,115 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Issue the asynchronous copies of chunk k0 of an operand into raw.
-__device__ __forceinline__ void raw_issue(const Operand& o, int k0, float* raw, int tid) {
+// Per-thread copy state of one operand: up to kUnits 16-byte pieces per
+// chunk, each with its source address at chunk 0, its byte offset in a raw
+// stage and the bytes it holds (0: zero fill).  RAW_ROWS: piece j is row
+// r = (tid >> 2) + 32 j, K group tid & 3 (bytes shrink at the K tail);
+// RAW_KMAJOR: piece j is K row k_j, rows 4 q .. 4 q + 3 (q = tid % (nrows / 4)).
+struct Loader {
+  const float* src[kUnits];
+  unsigned dst[kUnits];
+  int bytes[kUnits];     // bytes of the piece inside the operand (rows / K range checks)
+  int kofs[kUnits];      // K offset of the piece within a chunk
+  int n;                 // pieces of this thread
+};
+
+__device__ __forceinline__ Loader make_loader(const Operand& o, int tid) {
+  Loader L{};
+  L.n = 0;
   if (o.layout == RAW_ROWS) {
-    for (int u = tid; u < o.nrows * 4; u += kMlpThreads) {
-      const int r = u >> 2, kg = u & 3;
-      const int gr = o.r0 + r, gk = k0 + 4 * kg;
-      const int nk = gr < o.R ? max(0, min(4, o.K - gk)) : 0;
-      const float* src = nk ? o.X + (long long)gr * o.xr + gk : o.X;
-      cp_async16(raw + r * kChunkK + 4 * kg, src, 4 * nk);
+    const int kg = tid & 3;
+#pragma unroll
+    for (int j = 0; j < kUnits; ++j) {
+      const int u = tid + j * kMlpThreads;
+      if (u >= o.nrows * 4) break;
+      const int r = u >> 2, gr = o.r0 + r;
+      L.src[j] = gr < o.R ? o.X + (long long)gr * o.xr + 4 * kg : o.X;
+      L.bytes[j] = gr < o.R ? 16 : 0;
+      L.kofs[j] = 4 * kg;
+      L.dst[j] = tile_off(r, 4 * kg);
+      L.n = j + 1;
     }
   } else if (o.layout == RAW_KMAJOR) {
     const int rg = o.nrows >> 2;
-    for (int u = tid; u < kChunkK * rg; u += kMlpThreads) {
+#pragma unroll
+    for (int j = 0; j < kUnits; ++j) {
+      const int u = tid + j * kMlpThreads;
+      if (u >= kChunkK * rg) break;
       const int k = u / rg, q = u - k * rg;
-      const int gk = k0 + k, gr = o.r0 + 4 * q;
-      const int nr = gk < o.K ? max(0, min(4, o.R - gr)) : 0;
-      const float* src = nr ? o.X + (long long)gk * o.xk + gr : o.X;
-      cp_async16(raw + k * o.nrows + 4 * q, src, 4 * nr);
+      const int gr = o.r0 + 4 * q;
+      const int nr = max(0, min(4, o.R - gr));
+      L.src[j] = nr ? o.X + (long long)k * o.xk + gr : o.X;
+      L.bytes[j] = 4 * nr;
+      L.kofs[j] = k;
+      L.dst[j] = (unsigned)(k * o.nrows + 4 * q) * 4u;
+      L.n = j + 1;
+    }
+  }
+  return L;
+}
+
+// Issue the copies of the chunk at K offset k0 into the raw stage at shared
+// address `raw`.
+__device__ __forceinline__ void raw_issue(const Operand& o, const Loader& L, int k0,
+                                          unsigned raw) {
+  const long long adv = (long long)k0 * o.xk;
+  if (o.layout == RAW_ROWS) {
+#pragma unroll
+    for (int j = 0; j < kUnits; ++j) {
+      if (j >= L.n) break;
+      const int nk = max(0, min(4, o.K - (k0 + L.kofs[j])));
+      const int b = L.bytes[j] ? 4 * nk : 0;
+      cp_async16(raw + L.dst[j], b ? L.src[j] + adv : o.X, b);
+    }
+  } else if (o.layout == RAW_KMAJOR) {
+#pragma unroll
+    for (int j = 0; j < kUnits; ++j) {
+      if (j >= L.n) break;
+      const int b = k0 + L.kofs[j] < o.K ? L.bytes[j] : 0;
+      cp_async16(raw + L.dst[j], b ? L.src[j] + adv : o.X, b);
     }
   }
 }
 
-// Convert chunk k0 (from raw, or read directly for RAW_PLAIN) into the
-// hi / lo tiles.
-template <int U>
+__device__ __forceinline__ void split4(const float (&v)[4], float4& h, float4& l) {
+  h.x = to_tf32(v[0]);
+  h.y = to_tf32(v[1]);
+  h.z = to_tf32(v[2]);
+  h.w = to_tf32(v[3]);
+  l.x = to_tf32(v[0] - h.x);
+  l.y = to_tf32(v[1] - h.y);
+  l.z = to_tf32(v[2] - h.z);
+  l.w = to_tf32(v[3] - h.w);
+}
+
+// Split chunk k0 (from raw, or read directly for RAW_PLAIN) into the hi / lo
+// tiles.
 __device__ __forceinline__ void convert(const Operand& o, int k0, const float* raw, int tid,
                                         char* hi, char* lo) {
   const int units = o.nrows * (kChunkK / 4);
+  if (o.layout == RAW_ROWS) {
+    // the raw chunk is already in the tiles' layout: elementwise
 #pragma unroll
-  for (int u = 0; u < U; ++u) {
+    for (int u = 0; u < kUnits; ++u) {
+      const int f = tid + u * kMlpThreads;
+      if (f >= units) break;
+      const float4 t = reinterpret_cast<const float4*>(raw)[f];
+      const float v[4] = {t.x, t.y, t.z, t.w};
+      float4 h, l;
+      split4(v, h, l);
+      reinterpret_cast<float4*>(hi)[f] = h;
+      reinterpret_cast<float4*>(lo)[f] = l;
+    }
+    return;
+  }
+#pragma unroll
+  for (int u = 0; u < kUnits; ++u) {
     const int f = tid + u * kMlpThreads;
-    if (f >= units) continue;
+    if (f >= units) break;
     const int r = ((f >> 5) << 3) + (f & 7), kg = (f >> 3) & 3;
     float v[4];
-    if (o.layout == RAW_ROWS) {
-      const float4 t = *reinterpret_cast<const float4*>(raw + r * kChunkK + 4 * kg);
-      v[0] = t.x;
-      v[1] = t.y;
-      v[2] = t.z;
-      v[3] = t.w;
-    } else if (o.layout == RAW_KMAJOR) {
+    if (o.layout == RAW_KMAJOR) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) v[j] = raw[(4 * kg + j) * o.nrows + r];
     } else {
@@ -249,14 +321,7 @@ __device__ __forceinline__ void convert(const Operand& o, int k0, const float* r
       }
     }
     float4 h, l;
-    h.x = to_tf32(v[0]);
-    h.y = to_tf32(v[1]);
-    h.z = to_tf32(v[2]);
-    h.w = to_tf32(v[3]);
-    l.x = to_tf32(v[0] - h.x);
-    l.y = to_tf32(v[1] - h.y);
-    l.z = to_tf32(v[2] - h.z);
-    l.w = to_tf32(v[3] - h.w);
+    split4(v, h, l);
     const unsigned off = tile_off(r, kg * 4);
     *reinterpret_cast<float4*>(hi + off) = h;
     *reinterpret_cast<float4*>(lo + off) = l;
@@ -272,7 +337,37 @@ enum EpiMode { EPI_PLAIN = 0, EPI_BIAS = 1, EPI_BIAS_ELU = 2, EPI_DELU_SUM = 3, 
 // about 1e-7 against expm1; the layers' activations are O(1))
 __device__ __forceinline__ float elu_fast(float x) { return x > 0.f ? x : __expf(x) - 1.f; }
 
-template <int kEpi>
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Pre-split B operand (the weights, split once per weight update by
+// mlp_presplit_kernel): chunk c, part p (0: hi, 1: lo) at
+// b_pre + (2 c + p) npad 16, its npad rows in the tiles' layout (tile_off), so
+// a CTA's Nt rows of one part are one contiguous block of Nt x 64 bytes and
+// arrive by one bulk copy.
+constexpr int kMmaBars = 3;     // MMA commits of chunk c signal barrier c % 3
+constexpr int kPreStages = 3;   // pre-split B stages (chunk c in stage c % 3)
+
+template <bool kPreB>
+__host__ __device__ constexpr size_t smem_bytes_for(int n_tile) {
+  // A tiles [2][hi, lo]; B tiles [kPreB ? 3 : 2][hi, lo]; raw A [3]; raw B [3]
+  // (not with kPreB); 6 barriers, the TMEM address and the abort flag
+  return (size_t)(2 * 2 + kRawStages) * kTileM * kChunkK * 4 +
+         (size_t)(kPreB ? 2 * kPreStages : 2 * 2 + kRawStages) * n_tile * kChunkK * 4 + 64;
+}
+
+template <int kEpi, bool kPreB>
 __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
   extern __shared__ __align__(1024) char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -280,21 +375,15 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
   const int m0 = blockIdx.x * kTileM, n0 = blockIdx.y * Nt;
   const int kbeg = blockIdx.z * g.k_per_split;
   const int kend = min(g.K, kbeg + g.k_per_split);
-  const int a_bytes = kTileM * kChunkK * 4, b_bytes = Nt * kChunkK * 4;
-  const int stage_bytes = 2 * (a_bytes + b_bytes);
-  // two tensor-core stages of (A hi, A lo, B hi, B lo), then kRawStages raw
-  // stages of (A, B)
-  auto a_hi = [&](int st) { return sm + st * stage_bytes; };
-  auto a_lo = [&](int st) { return sm + st * stage_bytes + a_bytes; };
-  auto b_hi = [&](int st) { return sm + st * stage_bytes + 2 * a_bytes; };
-  auto b_lo = [&](int st) { return sm + st * stage_bytes + 2 * a_bytes + b_bytes; };
-  char* raw0 = sm + 2 * stage_bytes;
-  auto raw_a = [&](int st) { return reinterpret_cast<float*>(raw0 + st * (a_bytes + b_bytes)); };
-  auto raw_b = [&](int st) {
-    return reinterpret_cast<float*>(raw0 + st * (a_bytes + b_bytes) + a_bytes);
-  };
-  uint64_t* bar = reinterpret_cast<uint64_t*>(raw0 + kRawStages * (a_bytes + b_bytes));   // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int a_part = kTileM * kChunkK * 4, b_part = Nt * kChunkK * 4;
+  char* const a_tiles = sm;
+  char* const b_tiles = sm + 2 * 2 * a_part;
+  char* const raw_a = b_tiles + (kPreB ? kPreStages : 2) * 2 * b_part;
+  char* const raw_b = raw_a + kRawStages * a_part;
+  uint64_t* const bars =
+      reinterpret_cast<uint64_t*>(raw_b + (kPreB ? 0 : kRawStages * b_part));   // [3] MMA, [3] B
+  uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bars + 6);
+  volatile int* const abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const uint32_t ncols = Nt <= 32 ? 32u : (Nt <= 64 ? 64u : 128u);
 
   if (warp == 0) {
@@ -305,8 +394,8 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init1(bar);
-    mbar_init1(bar + 1);
+    for (int b = 0; b < 6; ++b) mbar_init1(bars + b);
+    *abort_flag = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -314,75 +403,109 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = instr_desc(kTileM, Nt);
 
-  bool ok = true;
-  // commits issued and completions awaited per stage barrier; a barrier is
-  // awaited before its next commit, so it never holds two unawaited
-  // completions and a parity wait is unambiguous
-  int issued[2] = {0, 0}, waited[2] = {0, 0};
   const int nchunks = kbeg < kend ? (kend - kbeg + kChunkK - 1) / kChunkK : 0;
   const Operand opa = make_operand(g.A, g.a_m, g.a_k, g.M, g.K, m0, kTileM);
   const Operand opb = make_operand(g.B, g.b_n, g.b_k, g.N, g.K, n0, Nt);
+  const Loader la = make_loader(opa, tid);
+  Loader lb{};
+  if (!kPreB) lb = make_loader(opb, tid);
+  const unsigned raw_a_s = smem_addr(raw_a), raw_b_s = smem_addr(raw_b);
+  // thread 0's account of the pre-split B copies and of the MMA commits
+  int b_issued = 0, b_waited = 0, committed = 0;
+  auto issue_pre_b = [&](int c) {
+    uint64_t* full = bars + kMmaBars + c % kPreStages;
+    char* dst = b_tiles + (c % kPreStages) * 2 * b_part;
+    const float* src = g.b_pre + (long long)(kbeg / kChunkK + c) * 2 * g.b_npad * kChunkK +
+                       (long long)n0 * kChunkK;
+    mbar_expect_tx(full, 2u * b_part);
+    bulk_copy(dst, src, b_part, full);
+    bulk_copy(dst + b_part, src + (long long)g.b_npad * kChunkK, b_part, full);
+    ++b_issued;
+  };
+
+  bool ok = true;
   // prologue: the first kRawStages - 1 chunks in flight
 #pragma unroll
   for (int c = 0; c < kRawStages - 1; ++c) {
     if (c < nchunks) {
-      raw_issue(opa, kbeg + c * kChunkK, raw_a(c), tid);
-      raw_issue(opb, kbeg + c * kChunkK, raw_b(c), tid);
+      raw_issue(opa, la, kbeg + c * kChunkK, raw_a_s + c * a_part);
+      if (!kPreB) raw_issue(opb, lb, kbeg + c * kChunkK, raw_b_s + c * b_part);
+      if (kPreB && tid == 0) issue_pre_b(c);
     }
     cp_async_commit();
   }
   for (int c = 0; c < nchunks; ++c) {
-    const int st = c & 1, rs = c % kRawStages;
+    const int ts = c & 1, rs = c % kRawStages;
     cp_async_wait<kRawStages - 2>();              // this thread's copies of chunk c landed
-    __syncthreads();                              // ... and every thread's
+    __syncthreads();                              // ... and every thread's; raw stage of c - 1 free
+    if (*abort_flag) {
+      ok = false;
+      break;
+    }
     {
-      const int cn = c + kRawStages - 1;          // refill the stage chunk c - 1 came from
+      const int cn = c + kRawStages - 1;
       if (cn < nchunks) {
-        raw_issue(opa, kbeg + cn * kChunkK, raw_a(cn % kRawStages), tid);
-        raw_issue(opb, kbeg + cn * kChunkK, raw_b(cn % kRawStages), tid);
+        raw_issue(opa, la, kbeg + cn * kChunkK, raw_a_s + (cn % kRawStages) * a_part);
+        if (!kPreB) raw_issue(opb, lb, kbeg + cn * kChunkK, raw_b_s + (cn % kRawStages) * b_part);
       }
       cp_async_commit();
     }
-    // tensor-core stage st was read by the MMAs of chunk c - 2
-    if (waited[st] < issued[st]) {
-      const bool done = __syncthreads_and(mbar_wait(bar + st, (unsigned)waited[st] & 1u));
-      if (!done) {
-        ok = false;
-        break;
-      }
-      ++waited[st];
-    }
-    convert<kUnitsA>(opa, kbeg + c * kChunkK, raw_a(rs), tid, a_hi(st), a_lo(st));
-    convert<kUnitsB>(opb, kbeg + c * kChunkK, raw_b(rs), tid, b_hi(st), b_lo(st));
+    // the tiles of stage ts were read by the MMAs of chunk c - 2
+    if (c >= 2 && !mbar_wait(bars + (c - 2) % kMmaBars, (unsigned)((c - 2) / kMmaBars) & 1u))
+      *abort_flag = 1;
+    char* const ahi = a_tiles + ts * 2 * a_part;
+    convert(opa, kbeg + c * kChunkK, reinterpret_cast<const float*>(raw_a + rs * a_part), tid, ahi,
+            ahi + a_part);
+    char* const bhi = b_tiles + (kPreB ? c % kPreStages : ts) * 2 * b_part;
+    if (!kPreB)
+      convert(opb, kbeg + c * kChunkK, reinterpret_cast<const float*>(raw_b + rs * b_part), tid,
+              bhi, bhi + b_part);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int ks = 0; ks < kChunkK / 8; ++ks) {
-        const unsigned koff = (unsigned)ks * 2 * kLbo;   // two core matrices per K step
-        const uint64_t ah = smem_desc(smem_addr(a_hi(st)) + koff);
-        const uint64_t al = smem_desc(smem_addr(a_lo(st)) + koff);
-        const uint64_t bh = smem_desc(smem_addr(b_hi(st)) + koff);
-        const uint64_t bl = smem_desc(smem_addr(b_lo(st)) + koff);
-        mma_tf32(tmem, ah, bh, idesc, c > 0 || ks > 0);
-        if (g.split_tf32) {
-          mma_tf32(tmem, ah, bl, idesc, true);
-          mma_tf32(tmem, al, bh, idesc, true);
-        }
-      }
-      mma_commit(bar + st);
+    if (*abort_flag) {
+      ok = false;
+      break;
     }
-    ++issued[st];
+    if (tid == 0) {
+      bool bok = true;
+      if (kPreB) {
+        bok = mbar_wait(bars + kMmaBars + c % kPreStages, (unsigned)(c / kPreStages) & 1u);
+        if (bok) ++b_waited;
+      }
+      if (bok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int ks = 0; ks < kChunkK / 8; ++ks) {
+          const unsigned koff = (unsigned)ks * 2 * kLbo;   // two core matrices per K step
+          const uint64_t ah = smem_desc(smem_addr(ahi) + koff);
+          const uint64_t al = smem_desc(smem_addr(ahi + a_part) + koff);
+          const uint64_t bh = smem_desc(smem_addr(bhi) + koff);
+          const uint64_t bl = smem_desc(smem_addr(bhi + b_part) + koff);
+          mma_tf32(tmem, ah, bh, idesc, c > 0 || ks > 0);
+          if (g.split_tf32) {
+            mma_tf32(tmem, ah, bl, idesc, true);
+            mma_tf32(tmem, al, bh, idesc, true);
+          }
+        }
+        mma_commit(bars + c % kMmaBars);
+        ++committed;
+        if (kPreB && c + 2 < nchunks) {
+          // the B stage of chunk c + 2 was read by the MMAs of chunk c - 1
+          if (c == 0 || mbar_wait(bars + (c - 1) % kMmaBars, (unsigned)((c - 1) / kMmaBars) & 1u))
+            issue_pre_b(c + 2);
+          else
+            *abort_flag = 1;
+        }
+      } else {
+        *abort_flag = 1;
+      }
+    }
   }
   cp_async_wait<0>();
-  // every MMA has completed once both barriers' last commits have
-  for (int b = 0; b < 2 && ok; ++b) {
-    if (waited[b] < issued[b]) {
-      ok = __syncthreads_and(mbar_wait(bar + b, (unsigned)waited[b] & 1u));
-      if (ok) ++waited[b];
-    }
-  }
+  // every MMA has completed once the last chunk's commit has
+  if (ok && nchunks > 0)
+    ok = __syncthreads_and(
+        mbar_wait(bars + (nchunks - 1) % kMmaBars, (unsigned)((nchunks - 1) / kMmaBars) & 1u));
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   if (ok && nchunks > 0) {
@@ -403,6 +526,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
     const bool cvec = (g.c_m & 3) == 0 && (reinterpret_cast<uintptr_t>(cbase) & 15) == 0;
     const bool yvec = kEpi == EPI_DELU_SUM && (g.c_m & 3) == 0 &&
                       (reinterpret_cast<uintptr_t>(g.act_y) & 15) == 0;
+    const bool bvec = (reinterpret_cast<uintptr_t>(g.bias + n0) & 15) == 0;
     for (int c = 0; c < Nt; c += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
@@ -427,9 +551,15 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
         for (int j = 0; j < 16; ++j) v[j] *= y[j] > 0.f ? 1.f : y[j] + 1.f;
       }
       if (kEpi == EPI_BIAS || kEpi == EPI_BIAS_ELU) {
-        if (ncol == 16) {
+        if (ncol == 16 && bvec) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] += __ldg(g.bias + n0 + c + j);
+          for (int q = 0; q < 4; ++q) {
+            const float4 t = __ldg(reinterpret_cast<const float4*>(g.bias + n0 + c) + q);
+            v[4 * q] += t.x;
+            v[4 * q + 1] += t.y;
+            v[4 * q + 2] += t.z;
+            v[4 * q + 3] += t.w;
+          }
         } else {
 #pragma unroll
           for (int j = 0; j < 16; ++j) v[j] += j < ncol ? __ldg(g.bias + n0 + c + j) : 0.f;
@@ -467,7 +597,9 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
                 *reinterpret_cast<const float4*>(slab + rr * 20 + 4 * qq);
         }
       } else if (mrow) {
-        for (int j = 0; j < ncol; ++j) cbase[(long long)m * g.c_m + n0 + c + j] = v[j];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (j < ncol) cbase[(long long)m * g.c_m + n0 + c + j] = v[j];
       }
       __syncwarp();
     }
@@ -486,11 +618,16 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
     }
   }
   if (!ok) {
-    if (tid == 0 && g.err) atomicOr(g.err, DEVERR_TIMEOUT);
-    // MMAs may still be in flight: wait (bounded) once more for the
-    // outstanding commits before the tensor memory is released
-    for (int b = 0; b < 2; ++b)
-      if (waited[b] < issued[b]) mbar_wait(bar + b, (unsigned)waited[b] & 1u);
+    if (tid == 0) {
+      if (g.err) atomicOr(g.err, DEVERR_TIMEOUT);
+      // copies and MMAs may still be in flight: wait (bounded) for the
+      // outstanding B copies and the last commit before the shared and
+      // tensor memory are released
+      for (int j = b_waited; j < b_issued; ++j)
+        mbar_wait(bars + kMmaBars + j % kPreStages, (unsigned)(j / kPreStages) & 1u);
+      if (committed > 0)
+        mbar_wait(bars + (committed - 1) % kMmaBars, (unsigned)((committed - 1) / kMmaBars) & 1u);
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -499,14 +636,76 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
                  : "memory");
 }
 
-// Sum of the split partial outputs in split order: C[m][n] = sum_s P[s][m][n].
-__global__ void mlp_split_reduce_kernel(const float* __restrict__ P, int splits, long long split_len,
-                                        float* __restrict__ C, long long n_total) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_total;
-       i += (long long)gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < splits; ++k) s += P[(long long)k * split_len + i];
-    C[i] = s;
+// Sum of the split partial outputs in a fixed order: C[i] = sum_s P[s][i],
+// warp w of a block adding the splits s = w, w + 8, ... in increasing order
+// for 32 consecutive outputs (four floats per lane when kVec), then the
+// eight warp sums added in warp order.
+template <bool kVec>
+__global__ void __launch_bounds__(256) mlp_split_reduce_kernel(const float* __restrict__ P,
+                                                               int splits, long long split_len,
+                                                               float* __restrict__ C,
+                                                               long long n_total) {
+  using T = typename std::conditional<kVec, float4, float>::type;
+  __shared__ T sh[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long n = kVec ? n_total / 4 : n_total, len = kVec ? split_len / 4 : split_len;
+  const T* p = reinterpret_cast<const T*>(P);
+  T* c = reinterpret_cast<T*>(C);
+  auto add = [](T& a, const T& b) {
+    if constexpr (kVec) {
+      a.x += b.x;
+      a.y += b.y;
+      a.z += b.z;
+      a.w += b.w;
+    } else {
+      a += b;
+    }
+  };
+  for (long long base = blockIdx.x * 32LL; base < n; base += gridDim.x * 32LL) {
+    const long long i = base + lane;
+    T acc{};
+    if (i < n) {
+#pragma unroll 4
+      for (int s = warp; s < splits; s += 8) add(acc, __ldg(p + (long long)s * len + i));
+    }
+    sh[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && i < n) {
+      T t = sh[0][lane];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) add(t, sh[w][lane]);
+      c[i] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// Split W (B(n, k) = W[n wn + k wk], N x K) into the pre-split layout above:
+// dst[(2 c + p) npad 16 + e], e the float index of (n, k - 16 c) in the tiles'
+// layout; parts beyond N x K are zero; lo = 0 in the one-product mode.
+__global__ void mlp_presplit_kernel(PresplitJobs jobs, int split_tf32) {
+  long long base = 0;
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int j = 0; j < jobs.n; ++j) {
+    const PresplitJob& J = jobs.job[j];
+    const long long chunk = 2LL * J.npad * kChunkK;
+    const long long count = (long long)((J.K + kChunkK - 1) / kChunkK) * chunk;
+    long long i = i0 - base;
+    if (i < 0) i += (-i + stride - 1) / stride * stride;
+    for (; i < count; i += stride) {
+      const int c = (int)(i / chunk);
+      const long long rem = i - (long long)c * chunk;
+      const int p = (int)(rem / ((long long)J.npad * kChunkK));
+      const int e = (int)(rem - (long long)p * J.npad * kChunkK);
+      // e -> (n, kk): 128 floats per 8-row group, 32 per K group, 4 per row
+      const int n8 = e >> 7, w = e & 127, kg = w >> 5, w2 = w & 31;
+      const int n = n8 * 8 + (w2 >> 2), k = c * kChunkK + kg * 4 + (w2 & 3);
+      const float x = (n < J.N && k < J.K) ? J.W[(long long)n * J.wn + (long long)k * J.wk] : 0.f;
+      const float hi = to_tf32(x);
+      J.dst[i] = p == 0 ? hi : (split_tf32 ? to_tf32(x - hi) : 0.f);
+    }
+    base += count;
   }
 }
 
@@ -520,28 +719,63 @@ int mlp_tile_n(int M, int N, int K) {
   return nt;
 }
 
-size_t mlp_smem_bytes(int n_tile) {
-  const size_t ab = (size_t)(kTileM + n_tile) * kChunkK * 4;   // one chunk of A and B
-  return 2 * 2 * ab + kRawStages * ab + 64;
+size_t mlp_smem_bytes(int n_tile, bool pre_b) {
+  return pre_b ? smem_bytes_for<true>(n_tile) : smem_bytes_for<false>(n_tile);
 }
 
-cudaError_t prepare_mlp_kernels() {
-  const int smem = (int)mlp_smem_bytes(kMaxTileN);
-  cudaError_t e = cudaFuncSetAttribute(mlp_gemm_kernel<EPI_PLAIN>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mlp_gemm_kernel<EPI_BIAS>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mlp_gemm_kernel<EPI_BIAS_ELU>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mlp_gemm_kernel<EPI_DELU_SUM>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mlp_gemm_kernel<EPI_ELU>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+namespace {
+template <int kEpi, bool kPreB>
+cudaError_t allow_smem() {
+  return cudaFuncSetAttribute(mlp_gemm_kernel<kEpi, kPreB>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_bytes_for<kPreB>(kMaxTileN));
+}
+template <bool kPreB>
+cudaError_t allow_smem_all() {
+  cudaError_t e = allow_smem<EPI_PLAIN, kPreB>();
+  if (e == cudaSuccess) e = allow_smem<EPI_BIAS, kPreB>();
+  if (e == cudaSuccess) e = allow_smem<EPI_BIAS_ELU, kPreB>();
+  if (e == cudaSuccess) e = allow_smem<EPI_DELU_SUM, kPreB>();
+  if (e == cudaSuccess) e = allow_smem<EPI_ELU, kPreB>();
   return e;
+}
+template <bool kPreB>
+void launch_epi(const MlpGemmArgs& g, dim3 grid, size_t smem, cudaStream_t s) {
+  if (g.act_y) mlp_gemm_kernel<EPI_DELU_SUM, kPreB><<<grid, kMlpThreads, smem, s>>>(g);
+  else if (g.bias && g.elu) mlp_gemm_kernel<EPI_BIAS_ELU, kPreB><<<grid, kMlpThreads, smem, s>>>(g);
+  else if (g.bias) mlp_gemm_kernel<EPI_BIAS, kPreB><<<grid, kMlpThreads, smem, s>>>(g);
+  else if (g.elu) mlp_gemm_kernel<EPI_ELU, kPreB><<<grid, kMlpThreads, smem, s>>>(g);
+  else mlp_gemm_kernel<EPI_PLAIN, kPreB><<<grid, kMlpThreads, smem, s>>>(g);
+}
+}  // namespace
+
+cudaError_t prepare_mlp_kernels() {
+  cudaError_t e = allow_smem_all<false>();
+  if (e == cudaSuccess) e = allow_smem_all<true>();
+  return e;
+}
+
+int presplit_npad(int N) { return (N + kMaxTileN - 1) / kMaxTileN * kMaxTileN; }
+
+long long presplit_floats(int N, int K) {
+  return (long long)((K + kChunkK - 1) / kChunkK) * 2 * presplit_npad(N) * kChunkK;
+}
+
+cudaError_t launch_mlp_presplit(const PresplitJobs& jobs, int split_tf32, cudaStream_t s) {
+  if (jobs.n < 0 || jobs.n > kMaxPresplitJobs) return cudaErrorInvalidValue;
+  long long total = 0;
+  for (int j = 0; j < jobs.n; ++j) {
+    const PresplitJob& J = jobs.job[j];
+    if (!J.W || !J.dst || J.N <= 0 || J.K <= 0 || J.npad != presplit_npad(J.N) ||
+        (reinterpret_cast<uintptr_t>(J.dst) & 15))
+      return cudaErrorInvalidValue;
+    total += presplit_floats(J.N, J.K);
+  }
+  if (total == 0) return cudaSuccess;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  mlp_presplit_kernel<<<(int)blocks, 256, 0, s>>>(jobs, split_tf32);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_gemm(const MlpGemmArgs& a, cudaStream_t s) {
@@ -552,23 +786,37 @@ cudaError_t launch_mlp_gemm(const MlpGemmArgs& a, cudaStream_t s) {
   const int splits = g.c_split ? (a.K + g.k_per_split - 1) / g.k_per_split : 1;
   if (!g.c_split) g.k_per_split = a.K;
   if (g.k_per_split <= 0) return cudaErrorInvalidValue;
+  if (!g.act_y != !g.colsum) return cudaErrorInvalidValue;   // both or neither
+  const bool pre = g.b_pre != nullptr;
+  if (pre) {
+    // the CTAs' row blocks must lie inside the pre-split rows, the copies
+    // 16-byte aligned, and the K splits start at whole chunks
+    const int ntiles = (a.N + g.n_tile - 1) / g.n_tile;
+    if (g.b_npad != presplit_npad(a.N) || ntiles * g.n_tile > g.b_npad ||
+        (reinterpret_cast<uintptr_t>(g.b_pre) & 15) || (splits > 1 && g.k_per_split % kChunkK))
+      return cudaErrorInvalidValue;
+  }
   dim3 grid((a.M + kTileM - 1) / kTileM, (a.N + g.n_tile - 1) / g.n_tile, splits);
-  const size_t smem = mlp_smem_bytes(g.n_tile);
-  if (g.act_y && g.colsum) mlp_gemm_kernel<EPI_DELU_SUM><<<grid, kMlpThreads, smem, s>>>(g);
-  else if (g.act_y || g.colsum) return cudaErrorInvalidValue;   // both or neither
-  else if (g.bias && g.elu) mlp_gemm_kernel<EPI_BIAS_ELU><<<grid, kMlpThreads, smem, s>>>(g);
-  else if (g.bias) mlp_gemm_kernel<EPI_BIAS><<<grid, kMlpThreads, smem, s>>>(g);
-  else if (g.elu) mlp_gemm_kernel<EPI_ELU><<<grid, kMlpThreads, smem, s>>>(g);
-  else mlp_gemm_kernel<EPI_PLAIN><<<grid, kMlpThreads, smem, s>>>(g);
+  const size_t smem = mlp_smem_bytes(g.n_tile, pre);
+  if (pre) launch_epi<true>(g, grid, smem, s);
+  else launch_epi<false>(g, grid, smem, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_split_reduce(const float* partial, int splits, long long split_len,
                                     float* C, long long n_total, cudaStream_t s) {
-  long long blocks = (n_total + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  mlp_split_reduce_kernel<<<(int)(blocks > 0 ? blocks : 1), 256, 0, s>>>(partial, splits,
-                                                                        split_len, C, n_total);
+  const bool vec = (split_len & 3) == 0 && (n_total & 3) == 0 &&
+                   (reinterpret_cast<uintptr_t>(partial) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(C) & 15) == 0;
+  const long long n = vec ? n_total / 4 : n_total;
+  long long blocks = (n + 31) / 32;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  if (vec)
+    mlp_split_reduce_kernel<true><<<(int)blocks, 256, 0, s>>>(partial, splits, split_len, C, n_total);
+  else
+    mlp_split_reduce_kernel<false><<<(int)blocks, 256, 0, s>>>(partial, splits, split_len, C,
+                                                               n_total);
   return cudaGetLastError();
 }
 
@@ -590,6 +838,7 @@ cudaError_t launch_mlp_gemm_split(const MlpGemmArgs& a, float* work, long long w
   }
   if (splits <= 1) {
     g.c_split = 0;
+    g.n_tile = 0;
     return launch_mlp_gemm(g, s);
   }
   const long long chunks = (a.K + 31) / 32;
@@ -618,6 +867,7 @@ extern "C" sg_status sg_mlp_gemm(void* stream, const float* A, int64_t a_m, int6
     if (sg::prepare_mlp_kernels() != cudaSuccess) return SG_ERR_CUDA;
     prepared = true;
   }
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
   sg::MlpGemmArgs g{};
   g.A = A;
   g.a_m = a_m;
@@ -633,8 +883,19 @@ extern "C" sg_status sg_mlp_gemm(void* stream, const float* A, int64_t a_m, int6
   g.K = K;
   g.elu = elu ? 1 : 0;
   g.split_tf32 = split_tf32 ? 1 : 0;
-  return sg::launch_mlp_gemm_split(g, work, work_floats, static_cast<cudaStream_t>(stream)) ==
-                 cudaSuccess
-             ? SG_OK
-             : SG_ERR_CUDA;
+  // a product with enough row tiles to fill the GPU and a work buffer that
+  // holds B's TF32 parts: split B once, then every CTA copies its parts
+  const long long tiles = (long long)((M + 127) / 128) * ((N + 127) / 128);
+  const bool k_split = !bias && !elu && c_m == N && tiles < 2 * 152 && K > 32;
+  if (work && K > 0 && !k_split && work_floats >= sg::presplit_floats(N, K) &&
+      (reinterpret_cast<uintptr_t>(work) & 15) == 0) {
+    sg::PresplitJobs jobs{};
+    jobs.n = 1;
+    jobs.job[0] = sg::PresplitJob{B, b_n, b_k, N, K, sg::presplit_npad(N), work};
+    if (sg::launch_mlp_presplit(jobs, g.split_tf32, s) != cudaSuccess) return SG_ERR_CUDA;
+    g.b_pre = work;
+    g.b_npad = sg::presplit_npad(N);
+    return sg::launch_mlp_gemm(g, s) == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+  }
+  return sg::launch_mlp_gemm_split(g, work, work_floats, s) == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }

@@ -31,13 +31,37 @@ struct MlpGemmArgs {
   long long c_split;    // 0: one output; else split s writes its partial sum at C + s c_split
   int n_tile;           // 0: chosen by the launcher
   int* err;             // device error word (bounded waits), or null
+  // B already split into TF32 parts (launch_mlp_presplit), or null: b_pre
+  // holds presplit_floats(N, K) floats for b_npad = presplit_npad(N) rows
+  const float* b_pre;
+  int b_npad;
+};
+
+// One matrix to pre-split: B(n, k) = W[n wn + k wk], N x K, into dst
+// (presplit_floats(N, K) floats, 16-byte aligned; npad = presplit_npad(N)).
+struct PresplitJob {
+  const float* W;
+  long long wn, wk;
+  int N, K, npad;
+  float* dst;
+};
+constexpr int kMaxPresplitJobs = 16;
+struct PresplitJobs {
+  PresplitJob job[kMaxPresplitJobs];
+  int n;
 };
 
 // output columns per CTA: up to 128; 64 for short contractions (K <= 32) or
 // when wider tiles would leave fewer than two CTAs per SM
 int mlp_tile_n(int M, int N, int K);
-size_t mlp_smem_bytes(int n_tile);
+size_t mlp_smem_bytes(int n_tile, bool pre_b);
 cudaError_t prepare_mlp_kernels();
+// rows of a pre-split operand (N rounded up to the widest tile) and its size
+int presplit_npad(int N);
+long long presplit_floats(int N, int K);
+// split every job's matrix into its TF32 parts (lo = 0 unless split_tf32),
+// one launch for all jobs
+cudaError_t launch_mlp_presplit(const PresplitJobs& jobs, int split_tf32, cudaStream_t s);
 cudaError_t launch_mlp_gemm(const MlpGemmArgs& a, cudaStream_t s);
 cudaError_t launch_mlp_split_reduce(const float* partial, int splits, long long split_len, float* C,
                                     long long n_total, cudaStream_t s);

@@ -250,4 +250,35 @@ sg_status build_plan(const sg_desc* d, Plan* P, std::string* err) {
   return SG_OK;
 }
 
+std::vector<int32_t> packing_order(const Plan& P, int packing) {
+  const int NW = P.num_warps;
+  std::vector<int32_t> order(NW);
+  for (int w = 0; w < NW; ++w) order[w] = w;
+  if (packing != SG_PACK_INTERLEAVE) return order;
+  // the class-grouped order's runs of one warp class; warp i of a run of n
+  // warps goes to fractional position (2 i + 1) / (2 n), ties in run order
+  // (exact integer comparisons, so every platform builds the same order)
+  struct Key {
+    long long num, den;
+    int run, w;
+  };
+  std::vector<Key> keys;
+  keys.reserve(NW);
+  int run = 0;
+  for (int w0 = 0; w0 < NW;) {
+    int w1 = w0;
+    while (w1 < NW && P.warp_class[w1] == P.warp_class[w0]) ++w1;
+    const int n = w1 - w0;
+    for (int i = 0; i < n; ++i) keys.push_back(Key{2LL * i + 1, 2LL * n, run, w0 + i});
+    ++run;
+    w0 = w1;
+  }
+  std::stable_sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
+    const long long l = a.num * b.den, r = b.num * a.den;
+    return l < r || (l == r && a.run < b.run);
+  });
+  for (int w = 0; w < NW; ++w) order[w] = keys[w].w;
+  return order;
+}
+
 }  // namespace sg

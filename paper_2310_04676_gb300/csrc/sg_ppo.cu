@@ -41,6 +41,9 @@ constexpr float kHalfLog2Pi = 0.91893853320467274f;
 struct Layer {
   size_t w, b;       // offsets of W [out][in] and b [out]
   int in, out;
+  // offsets of W's TF32 parts in the pre-split buffer: as the forward
+  // product's B (n = out, k = in) and as the input gradient's (n = in, k = out)
+  size_t pre_fwd = 0, pre_dx = 0;
 };
 struct Net {
   Layer l[4];
@@ -447,6 +450,8 @@ struct sg_ppo {
   cudaStream_t stream = nullptr;       // the stream the collect graph was captured for
   float* mlp_work = nullptr;           // partial sums of the row-split weight gradients
   long long mlp_work_floats = 0;
+  float* pre = nullptr;                // the weights' TF32 parts (sg::launch_mlp_presplit)
+  sg::PresplitJobs pre_jobs{};
   int32_t* err = nullptr;              // the env context's device error word
   float *params = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
   long long adam_t = 0;
@@ -498,11 +503,18 @@ sg::MlpGemmArgs gemm_args(const sg_ppo* p) {
   return g;
 }
 
+// Split every layer's weights into their TF32 parts, in both operand roles
+// (one launch; after every change of the parameters, before the products)
+bool presplit_weights(sg_ppo* p) {
+  return sg::launch_mlp_presplit(p->pre_jobs, p->cfg.tf32 ? 0 : 1, p->stream) == cudaSuccess;
+}
+
 // Y[rows][out] = act(X[rows][in] W^T + b), act = ELU on hidden layers
 bool gemm_fwd(sg_ppo* p, const float* X, int rows, const Layer& l, float* Y, bool elu) {
   sg::MlpGemmArgs g = gemm_args(p);
   g.A = X, g.a_m = l.in, g.a_k = 1;
   g.B = p->params + l.w, g.b_n = l.in, g.b_k = 1;
+  g.b_pre = p->pre + l.pre_fwd, g.b_npad = sg::presplit_npad(l.out);
   g.C = Y, g.c_m = l.out;
   g.bias = p->params + l.b, g.elu = elu ? 1 : 0;
   g.M = rows, g.N = l.out, g.K = l.in;
@@ -516,6 +528,7 @@ bool gemm_bwd_data_elu(sg_ppo* p, const float* dY, int rows, const Layer& l, con
   sg::MlpGemmArgs g = gemm_args(p);
   g.A = dY, g.a_m = l.out, g.a_k = 1;
   g.B = p->params + l.w, g.b_n = 1, g.b_k = l.in;       // B(n = in, k = out) = W[out][in]
+  g.b_pre = p->pre + l.pre_dx, g.b_npad = sg::presplit_npad(l.in);
   g.C = dZ, g.c_m = l.in;
   g.M = rows, g.N = l.in, g.K = l.out;
   g.act_y = y;
@@ -589,6 +602,7 @@ sg_status enqueue_collect(sg_ppo* p) {
   cudaError_t ce = cudaMemcpyAsync(p->obs, p->obs + (size_t)n * E * D, (size_t)E * D * 4,
                                    cudaMemcpyDeviceToDevice, p->stream);
   if (ce != cudaSuccess) return cuda_fail(p, ce, "sg_ppo_collect");
+  if (!presplit_weights(p)) return fail(p, SG_ERR_CUDA, "sg_ppo_collect: weight split failed");
   for (int t = 0; t < n; ++t) {
     float* o_t = p->obs + (size_t)t * E * D;
     float* o_next = p->obs + (size_t)(t + 1) * E * D;
@@ -711,6 +725,33 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
   step(dalloc(p, &p->dv, (size_t)p->M));
   p->mlp_work_floats = (long long)2 * 152 * sg::kH1 * sg::kH2;   // row-split partial sums
   step(dalloc(p, &p->mlp_work, (size_t)p->mlp_work_floats));
+  {
+    // pre-split weights: every layer as a forward B, layers 2..4 as an input-gradient B
+    size_t off = 0;
+    Net* nets[2] = {&p->L.actor, &p->L.critic};
+    int nj = 0;
+    for (Net* net : nets)
+      for (int i = 0; i < 4; ++i) {
+        Layer& l = net->l[i];
+        l.pre_fwd = off;
+        off += (size_t)sg::presplit_floats(l.out, l.in);
+        if (i > 0) {
+          l.pre_dx = off;
+          off += (size_t)sg::presplit_floats(l.in, l.out);
+        }
+      }
+    step(dalloc(p, &p->pre, off));
+    for (Net* net : nets)
+      for (int i = 0; i < 4; ++i) {
+        const Layer& l = net->l[i];
+        p->pre_jobs.job[nj++] = sg::PresplitJob{p->params + l.w, l.in, 1, l.out, l.in,
+                                                sg::presplit_npad(l.out), p->pre + l.pre_fwd};
+        if (i > 0)
+          p->pre_jobs.job[nj++] = sg::PresplitJob{p->params + l.w, 1, l.in, l.in, l.out,
+                                                  sg::presplit_npad(l.in), p->pre + l.pre_dx};
+      }
+    p->pre_jobs.n = nj;
+  }
   step(dalloc(p, &p->mb.obs, (size_t)p->M * p->Dp));
   step(dalloc(p, &p->mb.act, (size_t)p->M * A));
   step(dalloc(p, &p->mb.mask, (size_t)p->M * A));
@@ -877,6 +918,7 @@ sg_status sg_ppo_update(sg_ppo* p, const int32_t* perm, float* stats) {
       float* st = stats ? stats + 4 * ((size_t)ep * c.minibatches + k) : nullptr;
       sg::gather_kernel<<<(int)(((long long)M * 32 + 255) / 256), 256, 0, p->stream>>>(
           src, p->mb, idx, M, E, D, p->Dp, A);
+      if (!presplit_weights(p)) return fail(p, SG_ERR_CUDA, "sg_ppo_update: weight split failed");
       if (!net_forward(p, p->L.actor, p->mb.obs, M, p->ha, p->mu) ||
           !net_forward(p, p->L.critic, p->mb.obs, M, p->hc, p->vout))
         return fail(p, SG_ERR_CUDA, "sg_ppo_update: forward failed");

@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_CUDA", 3: "SG_ER
 DONE_TERMINATED, DONE_TIMEOUT, DONE_NONFINITE = 1, 2, 4
 HOST_IO_AUTO, HOST_IO_STAGED, HOST_IO_DIRECT = 0, 1, 2
 ROLLOUT_PERSISTENT, ROLLOUT_STEP_GRAPH = 0, 1
+PACK_CLASS, PACK_INTERLEAVE = 0, 1
 FAULT_NONE, FAULT_SKIP_PARAM_COPY, FAULT_SKIP_PARTNER = 0, 1, 2
 DRIVE_POSITION, DRIVE_VELOCITY, DRIVE_TORQUE = 0, 1, 2
 MAX_CHAINS = 4                     # chains per env (SG_MAX_CHAINS)
@@ -109,6 +110,9 @@ def load_library(path=LIB_PATH):
         "sg_set_launch": (i32, [vp, i32, i32, i32]),
         "sg_get_launch": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "sg_autotune": (i32, [vp, vp, i32, f32, i32, vp, vp, u8p, i32, ctypes.POINTER(f32)]),
+        "sg_set_packing": (i32, [vp, i32]),
+        "sg_get_packing": (i32, [vp]),
+        "sg_plan_packing": (i32, [ctypes.POINTER(SgDesc), i32, vp, i32, ctypes.c_char_p, i32]),
         "sg_diff_forward": (i32, [vp, vp, i32, f32, i32, i32, vp]),
         "sg_diff_backward": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "sg_set_link_mass": (i32, [vp, vp]),
@@ -202,6 +206,26 @@ def plan(desc):
         raise SgError(st, buf.value.decode())
     return dict(obs_dim=info.obs_dim, num_slots=info.num_slots, num_chains=info.num_chains,
                 class_slots=list(info.class_slots))
+
+
+def plan_packing(desc, packing):
+    """Host-only warp order of a packing (no GPU): int32 array, entry w =
+    the warp of the class-grouped order that position w holds."""
+    import numpy as np
+    lib = load_library()
+    d, keep = make_c_desc(desc)
+    info = SgPlanInfo()
+    buf = ctypes.create_string_buffer(512)
+    st = lib.sg_plan(ctypes.byref(d), ctypes.byref(info), buf, 512)
+    if st != SG_OK:
+        raise SgError(st, buf.value.decode())
+    nw = info.num_slots // 32
+    order = np.zeros(nw, dtype=np.int32)
+    st = lib.sg_plan_packing(ctypes.byref(d), int(packing), order.ctypes.data_as(ctypes.c_void_p),
+                             nw, buf, 512)
+    if st != SG_OK:
+        raise SgError(st, buf.value.decode())
+    return order
 
 
 def fp32_fma_rate(iters=4096, repeats=5, stream=None):
@@ -374,10 +398,20 @@ class Env:
                                            ctypes.byref(sp)))
         return t.value, m.value, sp.value
 
+    def set_packing(self, packing):
+        """PACK_CLASS (warps grouped by chain class) or PACK_INTERLEAVE
+        (classes interleaved in proportion); results are bit-identical."""
+        self._sync_stream()
+        self._check(self.lib.sg_set_packing(self.ctx, int(packing)))
+
+    @property
+    def packing(self):
+        return int(self.lib.sg_get_packing(self.ctx))
+
     def autotune(self, actions, dt, substeps, out=None, repeats=3):
-        """Pick the fastest launch plan for this rollout shape; returns
-        (threads_per_block, mode, chain split, ms per rollout).  State is
-        preserved."""
+        """Pick the fastest launch plan (and packing, see `packing`) for this
+        rollout shape; returns (threads_per_block, mode, chain split, ms per
+        rollout).  State is preserved."""
         self._sync_stream()
         torch = self._torch
         T = int(actions.shape[0])

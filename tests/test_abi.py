@@ -189,7 +189,7 @@ def _extern_c_functions(path):
 # two destructors, which switch to the owning device instead of refusing
 NO_DEVICE_WORK = {"sg_set_stream", "sg_set_launch", "sg_get_launch", "sg_set_host_io",
                   "sg_debug_set_fault", "sg_obs_dim", "sg_num_envs", "sg_max_joints",
-                  "sg_last_error", "sg_device", "sg_ppo_num_params"}
+                  "sg_last_error", "sg_device", "sg_ppo_num_params", "sg_get_packing"}
 SWITCHING = {"sg_destroy", "sg_ppo_destroy"}
 
 

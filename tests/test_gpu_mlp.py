@@ -9,9 +9,11 @@ three orders of magnitude), widened by sqrt(K / 1024) for sums of more than
 of terms), for the three operand layouts of a layer -- forward (X W^T),
 input gradient (dY W) and weight gradient (dY^T X, K split over CTAs) -- at
 the networks' widths (28-wide inputs, 256, 128, 64 hidden, 8 and 1 outputs),
-with ragged M, N and K, bias and ELU.  The single-product TF32 mode must land
-within TF32 rounding (2^-9 relative to the magnitudes) and be measurably
-coarser than the split mode.
+with ragged M, N and K, bias and ELU -- both with B split into its TF32 parts
+by every CTA and with B split once beforehand (a work buffer that holds its
+parts: the path of the PPO networks' forward and input-gradient products).
+The single-product TF32 mode must land within TF32 rounding (2^-9 relative
+to the magnitudes) and be measurably coarser than the split mode.
 """
 import pytest
 import torch
@@ -47,21 +49,45 @@ def _check(C, A64, B64, bias=None, elu=False, tol=2e-6):
     return (err / mag.clamp_min(1e-30)).max().item()
 
 
+def _presplit_floats(N, K):
+    """Floats of B's pre-split TF32 parts: ceil(K/16) chunks x 2 parts x N
+    rounded up to 128 rows x 16."""
+    return -(-K // 16) * 2 * (-(-N // 128) * 128) * 16
+
+
+@pytest.mark.parametrize("presplit", [False, True])
 @pytest.mark.parametrize("rows,inp,out", [(300, 28, 256), (257, 256, 128), (129, 128, 64),
                                           (200, 64, 8), (131, 64, 1), (1000, 256, 256)])
-def test_forward_layer(rows, inp, out):
+def test_forward_layer(rows, inp, out, presplit):
     X, W, b = _rand((rows, inp), 1), _rand((out, inp), 2), _rand((out,), 3)
     Xd, Wd, bd = X.cuda(), W.cuda(), b.cuda()
+    work = torch.empty(_presplit_floats(out, inp), device="cuda") if presplit else None
     for elu in (False, True):
         Y = torch.empty(rows, out, device="cuda")
-        sg.mlp_gemm(Xd, (inp, 1), Wd, (inp, 1), rows, out, inp, Y, out, bias=bd, elu=elu)
+        sg.mlp_gemm(Xd, (inp, 1), Wd, (inp, 1), rows, out, inp, Y, out, bias=bd, elu=elu,
+                    work=work)
         torch.cuda.synchronize()
         _check(Y, X.double(), W.double(), b, elu)
     # ELU without a bias
     Y = torch.empty(rows, out, device="cuda")
-    sg.mlp_gemm(Xd, (inp, 1), Wd, (inp, 1), rows, out, inp, Y, out, elu=True)
+    sg.mlp_gemm(Xd, (inp, 1), Wd, (inp, 1), rows, out, inp, Y, out, elu=True, work=work)
     torch.cuda.synchronize()
     _check(Y, X.double(), W.double(), None, True)
+
+
+@pytest.mark.parametrize("rows,inp,out", [(40000, 256, 128), (39000, 64, 8), (38913, 128, 64)])
+def test_input_gradient_presplit(rows, inp, out):
+    """Enough row tiles that the library splits B = W^T once into the work
+    buffer (no K split), as the PPO update's input gradients do; a sample of
+    rows is checked against FP64."""
+    dY, W = _rand((rows, out), 10), _rand((out, inp), 11)
+    dX = torch.empty(rows, inp, device="cuda")
+    work = torch.empty(_presplit_floats(inp, out), device="cuda")
+    sg.mlp_gemm(dY.cuda(), (out, 1), W.cuda(), (1, inp), rows, inp, out, dX, inp, work=work)
+    torch.cuda.synchronize()
+    g = torch.Generator().manual_seed(12)
+    idx = torch.cat([torch.randperm(rows, generator=g)[:2000], torch.tensor([0, rows - 1])])
+    _check(dX.cpu()[idx], dY.double()[idx], W.double().T)
 
 
 @pytest.mark.parametrize("rows,inp,out", [(300, 256, 128), (257, 128, 64), (190, 64, 8),
@@ -92,12 +118,17 @@ def test_weight_gradient_split(rows, inp, out):
     _check(dW1, dY.double().T, X.double().T)
 
 
-def test_single_tf32_product_is_coarser():
-    X, W = _rand((256, 256), 8), _rand((128, 256), 9)
+@pytest.mark.parametrize("presplit", [False, True])
+def test_single_tf32_product_is_coarser(presplit):
+    X, W, b = _rand((256, 256), 8), _rand((128, 256), 9), _rand((128,), 13)
+    work = torch.empty(_presplit_floats(128, 256), device="cuda") if presplit else None
     Y3, Y1 = (torch.empty(256, 128, device="cuda") for _ in range(2))
-    sg.mlp_gemm(X.cuda(), (256, 1), W.cuda(), (256, 1), 256, 128, 256, Y3, 128, split=True)
-    sg.mlp_gemm(X.cuda(), (256, 1), W.cuda(), (256, 1), 256, 128, 256, Y1, 128, split=False)
+    bd = b.cuda()
+    sg.mlp_gemm(X.cuda(), (256, 1), W.cuda(), (256, 1), 256, 128, 256, Y3, 128, bias=bd,
+                work=work, split=True)
+    sg.mlp_gemm(X.cuda(), (256, 1), W.cuda(), (256, 1), 256, 128, 256, Y1, 128, bias=bd,
+                work=work, split=False)
     torch.cuda.synchronize()
-    e3 = _check(Y3, X.double(), W.double())
-    e1 = _check(Y1, X.double(), W.double(), tol=2.0 ** -9)
+    e3 = _check(Y3, X.double(), W.double(), b)
+    e1 = _check(Y1, X.double(), W.double(), b, tol=2.0 ** -9)
     assert e1 > 20 * e3

@@ -129,6 +129,71 @@ def test_autotune_keeps_state_and_picks_a_plan():
     assert torch.equal(oa, ob)
 
 
+@pytest.mark.parametrize("task", [0, 2])
+@pytest.mark.parametrize("threads,split", [(128, 1), (256, 1), (128, 2)])
+def test_packings_give_identical_bits(task, threads, split):
+    """The interleaved packing reorders whole warps: every env's outputs and
+    state are the same bits as with the class-grouped packing, for both
+    chain splits, the reach and the tracking task (per-slot goal state), and
+    after a masked reset and a change of link masses; switching back restores
+    the class-grouped order."""
+    kinds = W.mixed_kinds(3000, W.C3_FRACTIONS) + ["21T"] * 40
+    desc = W.make_desc(kinds, episode_len=12, task=task)
+    T = 16
+    acts = cuda(W.joint_targets(desc, T))
+    A, B = sg.Env(desc), sg.Env(desc)
+    for env in (A, B):
+        env.set_launch(threads, sg.ROLLOUT_PERSISTENT, split)
+    B.set_packing(sg.PACK_INTERLEAVE)
+    assert B.packing == sg.PACK_INTERLEAVE and A.packing == sg.PACK_CLASS
+    mass = cuda(np.asarray(desc["link_mass"], dtype=np.float32).reshape(A.num_envs, -1) * 1.3)
+    mask = cuda((np.arange(A.num_envs) % 3 == 0).astype(np.uint8))
+    for env in (A, B):
+        env.rollout(acts, DT, 2)
+        env.set_link_mass(mass)
+        env.reset(mask)
+    outs = [env.rollout(acts, DT, 2) for env in (A, B)]
+    for x, y in zip(*outs):
+        assert torch.equal(x, y)
+    for x, y in zip(A.get_state(), B.get_state()):
+        assert torch.equal(x, y)
+    if task == 2:
+        for x, y in zip(A.get_goal_state(), B.get_goal_state()):
+            assert torch.equal(x, y)
+    B.set_packing(sg.PACK_CLASS)
+    oa = A.rollout(acts, DT, 2)[0]
+    ob = B.rollout(acts, DT, 2)[0]
+    assert torch.equal(oa, ob)
+
+
+def test_packing_change_discards_a_pending_gradient_forward():
+    desc = W.make_desc(W.mixed_kinds(500, W.C3_FRACTIONS))
+    env = sg.Env(desc)
+    acts = cuda(W.joint_targets(desc, 8))
+    env.diff_forward(acts, DT, 2, ckpt_every=4)
+    env.set_packing(sg.PACK_INTERLEAVE)
+    with pytest.raises(sg.SgError) as e:
+        env.diff_backward(acts, torch.zeros(8, env.num_envs, 4, 3, device="cuda"))
+    assert e.value.status == sg.SG_ERR_INVALID_ARG
+    with pytest.raises(sg.SgError):
+        env.set_packing(9)
+
+
+def test_autotune_searches_the_packing():
+    """A mixed batch has two distinct packings; the autotuner leaves the
+    fastest in place and the results stay those of the class-grouped order."""
+    desc = W.make_desc(W.mixed_kinds(6000, W.C3_FRACTIONS))
+    T = 16
+    acts = cuda(W.joint_targets(desc, T))
+    A, B = sg.Env(desc), sg.Env(desc)
+    th, mode, split, ms = B.autotune(acts, DT, 2, repeats=2)
+    assert B.packing in (sg.PACK_CLASS, sg.PACK_INTERLEAVE) and ms > 0
+    A.set_launch(th, mode, split)
+    oa, _, _ = A.rollout(acts, DT, 2)
+    ob, _, _ = B.rollout(acts, DT, 2)
+    assert torch.equal(oa, ob)
+
+
 def test_rollout_argument_errors():
     env = sg.Env(W.make_desc(["7R"] * 8))
     with pytest.raises(sg.SgError):
