@@ -778,6 +778,55 @@ def measure_ppo(cx, wl, desc, tf32):
             "d2h": int(stats_h.numel() * 4)}
 
 
+def mlp_layer_times(cx, rows, D, A, repeats=10):
+    """Per-layer time of the networks' products at one minibatch of `rows`
+    rows, through sg_mlp_gemm with the PPO update's operand roles (forward
+    X W^T + b with ELU on hidden layers and input gradient dY W: weights
+    pre-split in a work buffer; weight gradient dY^T X: rows split over
+    CTAs), FP32-grade split mode; CUDA events, L2 flushed before each run,
+    median of `repeats`.  The update's input gradient also applies the ELU
+    derivative and sums bias gradients in its epilogue; this plain product
+    leaves those out."""
+    torch = cx.torch
+    from paper_2310_04676_gb300 import sg
+    dims = (D,) + W_HIDDEN
+    layers = [(dims[i], dims[i + 1] if i < 3 else A, i < 3) for i in range(4)]
+    work = torch.empty(2 * 152 * 256 * 128, device=cx.dev)
+    g = torch.Generator(device=cx.dev).manual_seed(5)
+    rnd = lambda *shape: torch.rand(*shape, device=cx.dev, generator=g) * 2 - 1
+    out = []
+    for i, (inp, o, elu) in enumerate(layers):
+        X, dY = rnd(rows, inp), rnd(rows, o)
+        Wt, b = rnd(o, inp) * 0.1, rnd(o)
+        Y, dX, dW = (torch.empty(rows, o, device=cx.dev), torch.empty(rows, inp, device=cx.dev),
+                     torch.empty(o, inp, device=cx.dev))
+        calls = {"forward": (lambda: sg.mlp_gemm(X, (inp, 1), Wt, (inp, 1), rows, o, inp, Y, o,
+                                                  bias=b, elu=elu, work=work), rows, o, inp),
+                 "weight_grad": (lambda: sg.mlp_gemm(dY, (1, o), X, (1, inp), o, inp, rows, dW,
+                                                      inp, work=work), o, inp, rows)}
+        if i > 0:
+            calls["input_grad"] = (lambda: sg.mlp_gemm(dY, (o, 1), Wt, (1, inp), rows, inp, o,
+                                                        dX, inp, work=work), rows, inp, o)
+        for kind, (f, M, N, K) in calls.items():
+            for _ in range(3):
+                f()
+            ts = []
+            for _ in range(repeats):
+                cx.flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                e = torch.cuda.Event(enable_timing=True)
+                a.record()
+                f()
+                e.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(e))
+            ms = float(np.median(ts))
+            out.append({"layer": "%d->%d" % (inp, o), "product": kind, "M": M, "N": N, "K": K,
+                        "ms": ms, "tflops": 2.0 * M * N * K / ms / 1e9})
+        del X, dY, Y, dX, dW
+    return out
+
+
 def run_ppo_config(cx, name="P1", E=None):
     """The with-learning workload: collect + update per iteration, with FP32
     GEMMs (the line's value) and with TF32 tensor-core GEMMs (beside it)."""
@@ -825,6 +874,11 @@ def run_ppo_config(cx, name="P1", E=None):
                         "kernel": "whole iteration (dense layers' FLOPs / iteration time)",
                         "peak_source": "SMs x 128 FP32 lanes x 2 x max SM clock",
                         "flops_per_iteration": {"collect": f_col, "update": f_upd}}
+    # the actor's products at one minibatch (inputs padded to 4 columns, as
+    # inside the library), outside the timed region
+    line["layers"] = {"rows": r["B"] // 4,
+                      "products": mlp_layer_times(cx, r["B"] // 4, (D + 3) // 4 * 4,
+                                                  (A + 3) // 4 * 4)}
     line["tf32"] = dict(stf, dtype="tf32", gemm="this library's tcgen05 contraction, one TF32 product",
                         peak=tf32_peak, peak_source="measured bf16 burst x 1.1/2.25 (%s)" % src,
                         note="reduced-precision GEMM inputs (10-bit mantissa): context only")
@@ -889,7 +943,8 @@ def _compact_adjoint(g):
 
 def _compact_ppo(line):
     keep = ("value", "unit", "ms_per_step", "iteration_time_stats", "ms_collect", "ms_update",
-            "roofline", "tf32", "gpu_launches", "library_launches", "clocks", "status", "e2e")
+            "roofline", "tf32", "gpu_launches", "library_launches", "clocks", "status", "e2e",
+            "layers")
     out = {k: line[k] for k in keep if k in line}
     out["workload"] = line["config"]["workload"]
     out["config"] = line["config"]

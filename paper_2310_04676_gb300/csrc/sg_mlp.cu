@@ -15,22 +15,26 @@
 //                                       then a fixed-order reduction: results do
 //                                       not depend on scheduling).
 //
-// Split precision (3xTF32): x = hi + lo with hi = tf32(x) and lo = tf32(x - hi);
+// Split precision (3xTF32): x = hi + lo with hi = tf32(x) and lo = tf32(x - hi)
+// (round to nearest);
 // a b ~ hi_a hi_b + hi_a lo_b + lo_a hi_b, the dropped lo_a lo_b term being
 // about 2^-22 of a b, so the products carry FP32 accuracy with FP32
 // accumulation (the published "3xTF32" emulation of FP32 matrix products).
 //
-// One CTA of 128 threads computes a 128 x Nt tile (Nt <= 128, a multiple of
+// One CTA of 256 threads computes a 128 x Nt tile (Nt <= 128, a multiple of
 // 16).  Raw FP32 operand chunks (16 wide in K) travel to shared memory by
-// asynchronous copies three chunks ahead; each chunk is then split into its
+// asynchronous copies two chunks ahead; each chunk is then split into its
 // TF32 parts and stored in the tensor cores' K-major layout without swizzle
-// (8-row x 16-byte core matrices).  One thread issues, per 8-wide K step, the
-// three tcgen05.mma of kind::tf32 into an FP32 accumulator in tensor memory
-// (TMEM lane = row, column = n) and commits them to an mbarrier; two
-// tensor-core stages alternate, a stage being refilled only after the
-// mbarrier of the MMAs that read it has completed (bounded wait).  The
-// epilogue reads the accumulator with tcgen05.ld (each warp its 32 TMEM
-// lanes), applies the epilogue and stores whole row segments.
+// (8-row x 16-byte core matrices), or, for pre-split weights, arrives
+// already split by bulk copies.  One CTA barrier per chunk; after it one
+// thread issues, per 8-wide K step, the three tcgen05.mma of kind::tf32 into
+// an FP32 accumulator in tensor memory (TMEM lane = row, column = n) and
+// commits them to an mbarrier, while the other threads split the next
+// chunk; two tensor-core stages alternate, a stage being refilled only after
+// the mbarrier of the MMAs that read it has completed (bounded wait).  The
+// epilogue reads the accumulator with tcgen05.ld (warps w and w + 4 share
+// the TMEM lanes 32 (w % 4) .., taking alternate 16-column blocks), applies
+// the epilogue and stores whole row segments.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -43,7 +47,7 @@
 namespace sg {
 namespace {
 
-constexpr int kMlpThreads = 128;
+constexpr int kMlpThreads = 256;
 constexpr int kTileM = 128;
 constexpr int kChunkK = 16;                       // K per shared-memory chunk (2 MMA K-steps)
 constexpr int kCoreBytes = 128;                   // one core matrix: 8 rows x 16 bytes
@@ -81,11 +85,6 @@ __device__ __forceinline__ uint32_t instr_desc(int M, int N) {
          ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
 
 __device__ __forceinline__ void mbar_init1(uint64_t* bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
@@ -168,7 +167,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // chunk per step.
 constexpr int kRawStages = 3;
 constexpr int kMaxTileN = 128;
-constexpr int kUnits = kTileM * (kChunkK / 4) / kMlpThreads;   // 16-byte pieces per thread, <= 4
+constexpr int kUnits = kTileM * (kChunkK / 4) / kMlpThreads;   // 16-byte pieces per thread, <= 2
 
 enum RawLayout { RAW_ROWS = 0, RAW_KMAJOR = 1, RAW_PLAIN = 2 };
 
@@ -203,7 +202,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // Per-thread copy state of one operand: up to kUnits 16-byte pieces per
 // chunk, each with its source address at chunk 0, its byte offset in a raw
 // stage and the bytes it holds (0: zero fill).  RAW_ROWS: piece j is row
-// r = (tid >> 2) + 32 j, K group tid & 3 (bytes shrink at the K tail);
+// r = (tid >> 2) + 64 j, K group tid & 3 (bytes shrink at the K tail);
 // RAW_KMAJOR: piece j is K row k_j, rows 4 q .. 4 q + 3 (q = tid % (nrows / 4)).
 struct Loader {
   const float* src[kUnits];
@@ -271,15 +270,25 @@ __device__ __forceinline__ void raw_issue(const Operand& o, const Loader& L, int
   }
 }
 
+// x rounded to the nearest TF32 value (10 mantissa bits), ties away from
+// zero: half a unit of the last kept bit added to the magnitude bits, the 13
+// dropped bits cleared.  For finite x below the largest TF32 value (a carry
+// out of the exponent would give infinity).
+__device__ __forceinline__ float round_tf32(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// TF32 parts: hi = round_tf32(x), lo = round_tf32(x - hi) (x - hi is exact in
+// FP32), so x = hi + lo within 2^-22 |x|.
 __device__ __forceinline__ void split4(const float (&v)[4], float4& h, float4& l) {
-  h.x = to_tf32(v[0]);
-  h.y = to_tf32(v[1]);
-  h.z = to_tf32(v[2]);
-  h.w = to_tf32(v[3]);
-  l.x = to_tf32(v[0] - h.x);
-  l.y = to_tf32(v[1] - h.y);
-  l.z = to_tf32(v[2] - h.z);
-  l.w = to_tf32(v[3] - h.w);
+  h.x = round_tf32(v[0]);
+  h.y = round_tf32(v[1]);
+  h.z = round_tf32(v[2]);
+  h.w = round_tf32(v[3]);
+  l.x = round_tf32(v[0] - h.x);
+  l.y = round_tf32(v[1] - h.y);
+  l.z = round_tf32(v[2] - h.z);
+  l.w = round_tf32(v[3] - h.w);
 }
 
 // Split chunk k0 (from raw, or read directly for RAW_PLAIN) into the hi / lo
@@ -424,25 +433,26 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
   };
 
   bool ok = true;
-  // prologue: the first kRawStages - 1 chunks in flight
+  // prologue: the raw copies of chunks 0 and 1 and the pre-split B of chunk 0
+  // in flight; chunk 0 landed before the loop starts
 #pragma unroll
   for (int c = 0; c < kRawStages - 1; ++c) {
     if (c < nchunks) {
       raw_issue(opa, la, kbeg + c * kChunkK, raw_a_s + c * a_part);
       if (!kPreB) raw_issue(opb, lb, kbeg + c * kChunkK, raw_b_s + c * b_part);
-      if (kPreB && tid == 0) issue_pre_b(c);
     }
     cp_async_commit();
   }
+  if (kPreB && tid == 0 && nchunks > 0) issue_pre_b(0);
+  cp_async_wait<kRawStages - 2>();
+  __syncthreads();
+  // One CTA barrier per chunk: after it, chunk c's tiles are split (every
+  // thread) and chunk c + 1's raw copies have landed; thread 0 then issues
+  // chunk c's MMAs while the others go on to split chunk c + 1.
   for (int c = 0; c < nchunks; ++c) {
     const int ts = c & 1, rs = c % kRawStages;
-    cp_async_wait<kRawStages - 2>();              // this thread's copies of chunk c landed
-    __syncthreads();                              // ... and every thread's; raw stage of c - 1 free
-    if (*abort_flag) {
-      ok = false;
-      break;
-    }
     {
+      // the raw stage of chunk c + 2 held chunk c - 1, split before the last barrier
       const int cn = c + kRawStages - 1;
       if (cn < nchunks) {
         raw_issue(opa, la, kbeg + cn * kChunkK, raw_a_s + (cn % kRawStages) * a_part);
@@ -450,9 +460,11 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
       }
       cp_async_commit();
     }
-    // the tiles of stage ts were read by the MMAs of chunk c - 2
+    // the tiles of stage ts (and the B stage of chunk c + 1) were read by
+    // the MMAs of chunk c - 2
     if (c >= 2 && !mbar_wait(bars + (c - 2) % kMmaBars, (unsigned)((c - 2) / kMmaBars) & 1u))
       *abort_flag = 1;
+    if (kPreB && tid == 0 && c + 1 < nchunks) issue_pre_b(c + 1);
     char* const ahi = a_tiles + ts * 2 * a_part;
     convert(opa, kbeg + c * kChunkK, reinterpret_cast<const float*>(raw_a + rs * a_part), tid, ahi,
             ahi + a_part);
@@ -461,6 +473,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
       convert(opb, kbeg + c * kChunkK, reinterpret_cast<const float*>(raw_b + rs * b_part), tid,
               bhi, bhi + b_part);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    cp_async_wait<kRawStages - 2>();              // this thread's copies of chunk c + 1 landed
     __syncthreads();
     if (*abort_flag) {
       ok = false;
@@ -489,13 +502,6 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
         }
         mma_commit(bars + c % kMmaBars);
         ++committed;
-        if (kPreB && c + 2 < nchunks) {
-          // the B stage of chunk c + 2 was read by the MMAs of chunk c - 1
-          if (c == 0 || mbar_wait(bars + (c - 1) % kMmaBars, (unsigned)((c - 1) / kMmaBars) & 1u))
-            issue_pre_b(c + 2);
-          else
-            *abort_flag = 1;
-        }
       } else {
         *abort_flag = 1;
       }
@@ -509,27 +515,29 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   if (ok && nchunks > 0) {
-    // epilogue: warp w holds rows m0 + 32 w + lane (TMEM lanes 32 w ..).
-    // Per 16 columns each thread finishes its row's values (bias, ELU, or the
-    // ELU derivative of the layer below) and parks them in a shared-memory
-    // slab of the warp (row pitch 20 floats).  From the slab the warp sums
-    // the columns (lane l: column l % 16 over 16 rows, then the two halves;
-    // fixed order) into its per-warp partials, and stores whole 64-byte row
-    // segments, four lanes per row, eight rows per instruction (scalar stores
-    // at ragged edges or unaligned outputs).  After the last slab the four
-    // warps' partials are added in order.
-    const int m = m0 + warp * 32 + lane;
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (its rows m0 + 32 (w % 4)
+    // + lane) and the 16-column blocks of parity w / 4.  Per block each
+    // thread finishes its row's values (bias, ELU, or the ELU derivative of
+    // the layer below) and parks them in a shared-memory slab of the warp
+    // (row pitch 20 floats).  From the slab the warp sums the columns (lane
+    // l: column l % 16 over 16 rows, then the two halves; fixed order) into
+    // the partials of its lane quarter, and stores whole 64-byte row
+    // segments, four lanes per row, eight rows per instruction (scalar
+    // stores at ragged edges or unaligned outputs).  After the last block the
+    // four lane quarters' partials are added in order.
+    const int lq = warp & 3, half = warp >> 2;
+    const int m = m0 + lq * 32 + lane;
     const bool mrow = m < g.M;
     float* cbase = g.C + (long long)blockIdx.z * g.c_split;
     float* slab = reinterpret_cast<float*>(sm) + warp * 32 * 20;
-    float* wsum = reinterpret_cast<float*>(sm) + 4 * 32 * 20;          // [4][128]
+    float* wsum = reinterpret_cast<float*>(sm) + 8 * 32 * 20;          // [4][128]
     const bool cvec = (g.c_m & 3) == 0 && (reinterpret_cast<uintptr_t>(cbase) & 15) == 0;
     const bool yvec = kEpi == EPI_DELU_SUM && (g.c_m & 3) == 0 &&
                       (reinterpret_cast<uintptr_t>(g.act_y) & 15) == 0;
     const bool bvec = (reinterpret_cast<uintptr_t>(g.bias + n0) & 15) == 0;
-    for (int c = 0; c < Nt; c += 16) {
+    for (int c = 16 * half; c < Nt; c += 32) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+      tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)c, v);
       const int ncol = min(16, g.N - (n0 + c));
       if (kEpi == EPI_DELU_SUM) {
         float y[16];
@@ -585,13 +593,13 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) t += slab[(r0 + r) * 20 + col];
         t += __shfl_xor_sync(0xffffffffu, t, 16);
-        if (lane < 16) wsum[warp * kMaxTileN + c + lane] = t;
+        if (lane < 16) wsum[lq * kMaxTileN + c + lane] = t;
       }
       if (cvec && ncol == 16) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int rr = 8 * i + (lane >> 2), qq = lane & 3;
-          const int mr = m0 + warp * 32 + rr;
+          const int mr = m0 + lq * 32 + rr;
           if (mr < g.M)
             *reinterpret_cast<float4*>(cbase + (long long)mr * g.c_m + n0 + c + 4 * qq) =
                 *reinterpret_cast<const float4*>(slab + rr * 20 + 4 * qq);
@@ -610,11 +618,13 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
             ((wsum[n] + wsum[kMaxTileN + n]) + wsum[2 * kMaxTileN + n]) + wsum[3 * kMaxTileN + n];
     }
   } else if (nchunks == 0 && g.c_split) {
-    // an empty split contributes zeros to the partial sums
-    const int m = m0 + warp * 32 + lane;
+    // an empty split contributes zeros to the partial sums: thread t takes
+    // row m0 + t % 128 and every other column from n0 + t / 128
+    const int m = m0 + (tid & (kTileM - 1));
     if (m < g.M) {
       float* crow = g.C + (long long)blockIdx.z * g.c_split + (long long)m * g.c_m;
-      for (int n = n0; n < min(g.N, n0 + Nt); ++n) crow[n] = 0.f;
+      for (int n = n0 + tid / kTileM; n < min(g.N, n0 + Nt); n += kMlpThreads / kTileM)
+        crow[n] = 0.f;
     }
   }
   if (!ok) {
@@ -702,8 +712,8 @@ __global__ void mlp_presplit_kernel(PresplitJobs jobs, int split_tf32) {
       const int n8 = e >> 7, w = e & 127, kg = w >> 5, w2 = w & 31;
       const int n = n8 * 8 + (w2 >> 2), k = c * kChunkK + kg * 4 + (w2 & 3);
       const float x = (n < J.N && k < J.K) ? J.W[(long long)n * J.wn + (long long)k * J.wk] : 0.f;
-      const float hi = to_tf32(x);
-      J.dst[i] = p == 0 ? hi : (split_tf32 ? to_tf32(x - hi) : 0.f);
+      const float hi = round_tf32(x);
+      J.dst[i] = p == 0 ? hi : (split_tf32 ? round_tf32(x - hi) : 0.f);
     }
     base += count;
   }
