@@ -783,10 +783,13 @@ def mlp_layer_times(cx, rows, D, A, repeats=10):
     rows, through sg_mlp_gemm with the PPO update's operand roles (forward
     X W^T + b with ELU on hidden layers and input gradient dY W: weights
     pre-split in a work buffer; weight gradient dY^T X: rows split over
-    CTAs), FP32-grade split mode; CUDA events, L2 flushed before each run,
-    median of `repeats`.  The update's input gradient also applies the ELU
-    derivative and sums bias gradients in its epilogue; this plain product
-    leaves those out."""
+    CTAs), in the update's mode: FP32-grade 3xTF32 on the tensor cores, the
+    narrow products (28 inputs, 8-wide outputs) as FP32 FMA loops; CUDA
+    events, L2 flushed before each run, median of `repeats`.  The update's
+    input gradient also applies the ELU derivative and sums bias gradients in
+    its epilogue; this plain product leaves those out, and each call here
+    splits its weights itself (the update splits all layers' weights in one
+    launch per minibatch)."""
     torch = cx.torch
     from paper_2310_04676_gb300 import sg
     dims = (D,) + W_HIDDEN
@@ -801,12 +804,14 @@ def mlp_layer_times(cx, rows, D, A, repeats=10):
         Y, dX, dW = (torch.empty(rows, o, device=cx.dev), torch.empty(rows, inp, device=cx.dev),
                      torch.empty(o, inp, device=cx.dev))
         calls = {"forward": (lambda: sg.mlp_gemm(X, (inp, 1), Wt, (inp, 1), rows, o, inp, Y, o,
-                                                  bias=b, elu=elu, work=work), rows, o, inp),
+                                                  bias=b, elu=elu, work=work, split=2),
+                             rows, o, inp),
                  "weight_grad": (lambda: sg.mlp_gemm(dY, (1, o), X, (1, inp), o, inp, rows, dW,
-                                                      inp, work=work), o, inp, rows)}
+                                                      inp, work=work, split=2), o, inp, rows)}
         if i > 0:
             calls["input_grad"] = (lambda: sg.mlp_gemm(dY, (o, 1), Wt, (1, inp), rows, inp, o,
-                                                        dX, inp, work=work), rows, inp, o)
+                                                        dX, inp, work=work, split=2),
+                                   rows, inp, o)
         for kind, (f, M, N, K) in calls.items():
             for _ in range(3):
                 f()
@@ -892,10 +897,10 @@ def run_ppo_config(cx, name="P1", E=None):
     # GAE, 2 moments, step counter; per minibatch gather, the weights' TF32
     # split, 8 forward layers, 2 loss-head, per network 4 weight gradients
     # (product + fixed-order sum of the row splits), the output bias column
-    # sums (2), 3 input gradients with the ELU backward and 3 bias sums, then
-    # 2 norm, Adam
+    # sums, 3 input gradients with the ELU backward and the hidden bias sums,
+    # one launch finishing the four bias gradients; then 2 norm, Adam
     n_mb = 5 * 4
-    line["gpu_launches"] = (1 + wl.steps * 14 + 9 + n_mb * 47) * args.steps
+    line["gpu_launches"] = (1 + wl.steps * 14 + 9 + n_mb * 41) * args.steps
     line["library_launches"] = 0
     line["clocks"] = r["clocks"]
     line["status"] = r["status"]

@@ -152,10 +152,14 @@ sg_status sg_ppo_set_buffer(sg_ppo *ppo, int32_t which, const void *src_dev);
  * arrays, strides in elements (row- or column-major operands, transposes);
  * bias [N] may be NULL; act is ELU when elu != 0, else the identity.  It
  * runs on the tcgen05 tensor cores in kind::tf32 with FP32 accumulation;
- * with split_tf32 != 0 every operand is split into two TF32 parts
+ * with split_tf32 = 1 every operand is split into two TF32 parts
  * (x = hi + lo) and three products are accumulated (hi*hi + hi*lo + lo*hi:
- * FP32-grade, about 2^-22 relative per product), else one TF32 product
- * (10-bit mantissas).  `work` (device scratch of work_floats floats, may be
+ * FP32-grade, about 2^-22 relative per product), with 0 one TF32 product
+ * (10-bit mantissas).  split_tf32 = 2 is FP32-grade as 1, except that
+ * narrow products with k-contiguous A (a_k = 1) run as FP32 FMA loops on
+ * the CUDA cores (exact FP32 products, fixed summation order): K <= 32 with
+ * K * N <= 2048, or N <= 16 with K <= 64 a multiple of 4 and A 16-byte
+ * aligned with a_m a multiple of 4.  `work` (device scratch of work_floats floats, may be
  * NULL) serves two purposes.  A product with few output tiles (fewer than
  * two 128 x 128 tiles per SM of 152), more than 32 terms, no bias or
  * activation and a dense C (c_m == N) splits K over more CTAs, their partial

@@ -14,6 +14,7 @@
 #include "sg.h"
 #include "sg_devcheck.h"
 #include "sg_internal.h"
+#include "sg_pack.h"
 #include "sg_diff.h"
 #include "sg_kernels.h"
 #include "sg_path.h"
@@ -366,6 +367,30 @@ cudaError_t snapshot(sg_ctx* c, bool save) {
   return e;
 }
 
+// dst[f][w][i] = src[f][perm[w]][i] over F x NW x B 32-bit words (the warp
+// reorder of a packing change); src and dst do not overlap
+__global__ void permute_warps_kernel(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
+                                     const int32_t* __restrict__ perm, int F, int NW, int B) {
+  const long long per = (long long)NW * B, n = (long long)F * per;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long f = idx / per, rem = idx - f * per;
+    const int w = (int)(rem / B), i = (int)(rem - (long long)w * B);
+    dst[idx] = src[f * per + (long long)perm[w] * B + i];
+  }
+}
+
+cudaError_t launch_permute_warps(const void* src, void* dst, const int32_t* perm, int F, int NW,
+                                 int B, cudaStream_t stream) {
+  const long long n = (long long)F * NW * B;
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  permute_warps_kernel<<<(int)blocks, 256, 0, stream>>>(static_cast<const uint32_t*>(src),
+                                                        static_cast<uint32_t*>(dst), perm, F, NW, B);
+  return cudaGetLastError();
+}
+
 // Put the warps in `packing`'s order: the parameter records, slot tables,
 // per-slot state and the autotuner's state snapshot are gathered into a
 // temporary buffer and copied back in place (the pointers captured in a
@@ -404,7 +429,7 @@ cudaError_t apply_packing(sg_ctx* c, int packing) {
   e = cudaMemcpyAsync(d_rel, rel.data(), (size_t)NW * 4, cudaMemcpyHostToDevice, c->stream);
   for (const Arr& a : arrs) {
     if (!a.p || e != cudaSuccess) continue;
-    e = sg::launch_permute_warps(a.p, tmp, d_rel, a.F, NW, a.B, c->stream);
+    e = launch_permute_warps(a.p, tmp, d_rel, a.F, NW, a.B, c->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(a.p, tmp, (size_t)a.F * NW * a.B * 4, cudaMemcpyDeviceToDevice,
                           c->stream);

@@ -95,10 +95,6 @@ struct Plan {
 // Validate `d` and build the packing plan; returns SG_OK or an error with *err set.
 sg_status build_plan(const sg_desc* d, Plan* plan, std::string* err);
 
-// Warp order of a packing (SG_PACK_*): order[w] = the warp of the plan's
-// class-grouped order that position w holds (the identity for SG_PACK_CLASS).
-std::vector<int32_t> packing_order(const Plan& plan, int packing);
-
 SG_HD inline int record_links(int warp_class) {
   return (warp_class & 3) == CLS_4R ? 4 : kMaxLinks;
 }

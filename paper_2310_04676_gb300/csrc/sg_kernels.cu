@@ -356,28 +356,6 @@ cudaError_t launch_step(const StepArgs& a, int threads, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-__global__ void permute_warps_kernel(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
-                                     const int32_t* __restrict__ perm, int F, int NW, int B) {
-  const long long per = (long long)NW * B, n = (long long)F * per;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long f = idx / per, rem = idx - f * per;
-    const int w = (int)(rem / B), i = (int)(rem - (long long)w * B);
-    dst[idx] = src[f * per + (long long)perm[w] * B + i];
-  }
-}
-
-cudaError_t launch_permute_warps(const void* src, void* dst, const int32_t* perm, int F, int NW,
-                                 int B, cudaStream_t stream) {
-  const long long n = (long long)F * NW * B;
-  if (n <= 0) return cudaSuccess;
-  long long blocks = (n + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  permute_warps_kernel<<<(int)blocks, 256, 0, stream>>>(static_cast<const uint32_t*>(src),
-                                                        static_cast<uint32_t*>(dst), perm, F, NW, B);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_reset(const StateArgs& s, const uint8_t* mask, cudaStream_t stream) {
   const int threads = 256, blocks = (s.num_slots + threads - 1) / threads;
   reset_kernel<<<blocks, threads, 0, stream>>>(s, mask);

@@ -36,10 +36,6 @@ size_t step_pair_smem_bytes(int threads, int obs_dim);
 cudaError_t prepare_step_pair_kernel();
 cudaError_t launch_step_pair(const StepArgs& a, int threads, cudaStream_t stream);
 cudaError_t launch_reset(const StateArgs& s, const uint8_t* mask, cudaStream_t stream);
-// dst[f][w][i] = src[f][perm[w]][i] over F x NW x B 32-bit words (the warp
-// reorder of a packing change); src and dst must not overlap
-cudaError_t launch_permute_warps(const void* src, void* dst, const int32_t* perm, int F, int NW,
-                                 int B, cudaStream_t stream);
 cudaError_t launch_get_state(const StateArgs& s, float* q, float* qd, int32_t* sc,
                              cudaStream_t stream);
 cudaError_t launch_set_state(const StateArgs& s, const float* q, const float* qd,

@@ -37,6 +37,7 @@
 // the epilogue and stores whole row segments.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -719,6 +720,146 @@ __global__ void mlp_presplit_kernel(PresplitJobs jobs, int split_tf32) {
   }
 }
 
+// ---- narrow products on the FP32 pipes ---------------------------------------
+// Products with a short inner dimension and few outputs per row (the input
+// gradient below an 8- or 1-wide output layer: K * N <= 2048) or an output of
+// at most 16 columns (the output layers) do a few FMAs per element they move:
+// a 128-row tensor-core tile is set up, filled and drained for one or two
+// chunks of work.  They run as plain FP32 FMA loops instead (exact FP32
+// products, accumulated in a fixed order), their operand rows staged in
+// shared memory by coalesced loads.
+constexpr int kNarrowRows = 128;      // rows per block (the bias-gradient partials' tile)
+constexpr int kNarrowMaxK = 32;
+
+__device__ __forceinline__ bool al16(const void* p) {
+  return (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
+// C[m][n] = epi(sum_{k < K} A[m a_m + k] B(n, k)), K <= 32, N <= 256.  Block:
+// 128 rows; warp w takes column strip w % S (S = ceil(N / 32)) and the rows
+// r = w / S (mod P = 8 / S) of them, lane l column 32 (w % S) + l with its K
+// weights in registers; A's rows broadcast from shared memory.  The input-
+// gradient epilogue also writes the block's column sums (fixed order: rows in
+// order per thread, then the P row classes in order).
+template <int kEpi>
+__global__ void __launch_bounds__(256) narrow_k_kernel(MlpGemmArgs g) {
+  __shared__ __align__(16) float As[kNarrowRows * kNarrowMaxK];
+  __shared__ float csum[8][256];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int K = g.K, N = g.N, K4 = (K + 3) & ~3;
+  const int m0 = blockIdx.x * kNarrowRows;
+  // stage A's rows [128][K4] (zero beyond M x K)
+  if (al16(g.A) && (g.a_m & 3) == 0 && (K & 3) == 0) {
+    const int q4 = K4 >> 2;
+    for (int u = tid; u < kNarrowRows * q4; u += 256) {
+      const int r = u / q4, q = u - r * q4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m0 + r < g.M) v = __ldg(reinterpret_cast<const float4*>(g.A + (long long)(m0 + r) * g.a_m) + q);
+      reinterpret_cast<float4*>(As)[r * q4 + q] = v;
+    }
+  } else {
+    for (int u = tid; u < kNarrowRows * K4; u += 256) {
+      const int r = u / K4, k = u - r * K4;
+      As[u] = (m0 + r < g.M && k < K) ? __ldg(g.A + (long long)(m0 + r) * g.a_m + k) : 0.f;
+    }
+  }
+  __syncthreads();
+  const int S = (N + 31) / 32, P = S >= 8 ? 1 : 8 / S;
+  for (int job = warp; job < S * P; job += 8) {
+    const int strip = job % S, phase = job / S;
+    const int n = strip * 32 + lane;
+    const bool nv = n < N;
+    float w[kNarrowMaxK];
+#pragma unroll
+    for (int k = 0; k < kNarrowMaxK; ++k)
+      w[k] = (nv && k < K) ? __ldg(g.B + (long long)n * g.b_n + (long long)k * g.b_k) : 0.f;
+    const float bn = ((kEpi == EPI_BIAS || kEpi == EPI_BIAS_ELU) && nv) ? __ldg(g.bias + n) : 0.f;
+    float cs = 0.f;
+    for (int r = phase; r < kNarrowRows; r += P) {
+      const int m = m0 + r;
+      if (m >= g.M) break;
+      const float4* x4 = reinterpret_cast<const float4*>(As + r * K4);
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < kNarrowMaxK / 4; ++q) {
+        if (4 * q >= K4) break;
+        const float4 x = x4[q];
+        acc = fmaf(x.x, w[4 * q], acc);
+        acc = fmaf(x.y, w[4 * q + 1], acc);
+        acc = fmaf(x.z, w[4 * q + 2], acc);
+        acc = fmaf(x.w, w[4 * q + 3], acc);
+      }
+      if (kEpi == EPI_BIAS || kEpi == EPI_BIAS_ELU) acc += bn;
+      if (kEpi == EPI_BIAS_ELU || kEpi == EPI_ELU) acc = elu_fast(acc);
+      if (kEpi == EPI_DELU_SUM) {
+        const float y = nv ? __ldg(g.act_y + (long long)m * g.c_m + n) : 0.f;
+        acc *= y > 0.f ? 1.f : y + 1.f;
+        cs += nv ? acc : 0.f;
+      }
+      if (nv) g.C[(long long)m * g.c_m + n] = acc;
+    }
+    if (kEpi == EPI_DELU_SUM && nv) csum[phase][n] = cs;
+  }
+  if (kEpi == EPI_DELU_SUM) {
+    __syncthreads();
+    for (int n = tid; n < N; n += 256) {
+      float t = 0.f;
+      for (int ph = 0; ph < P; ++ph) t += csum[ph][n];
+      g.colsum[(long long)blockIdx.x * N + n] = t;
+    }
+  }
+}
+
+// C[m][n] = epi(sum_k A[m a_m + k] B(n, k)), N <= 16, K <= 64 (a multiple of
+// 4): thread t of 128 takes row m0 + t with its N sums in registers; A's rows
+// staged with a pitch of K + 4 floats (conflict-free 16-byte reads), B in
+// shared memory (broadcast reads).
+constexpr int kNarrowMaxN = 16, kNarrowNMaxK = 64;
+template <int kEpi>
+__global__ void __launch_bounds__(128) narrow_n_kernel(MlpGemmArgs g) {
+  __shared__ __align__(16) float As[kNarrowRows * (kNarrowNMaxK + 4)];
+  __shared__ __align__(16) float Ws[kNarrowMaxN * kNarrowNMaxK];
+  const int tid = threadIdx.x;
+  const int K = g.K, N = g.N, q4 = K >> 2, pitch = K + 4;
+  const int m0 = blockIdx.x * kNarrowRows;
+  for (int u = tid; u < kNarrowRows * q4; u += kNarrowRows) {
+    const int r = u / q4, q = u - r * q4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m0 + r < g.M) v = __ldg(reinterpret_cast<const float4*>(g.A + (long long)(m0 + r) * g.a_m) + q);
+    *reinterpret_cast<float4*>(As + r * pitch + 4 * q) = v;
+  }
+  for (int u = tid; u < kNarrowMaxN * K; u += kNarrowRows) {
+    const int n = u / K, k = u - n * K;
+    Ws[u] = n < N ? __ldg(g.B + (long long)n * g.b_n + (long long)k * g.b_k) : 0.f;
+  }
+  __syncthreads();
+  const int m = m0 + tid;
+  if (m >= g.M) return;
+  float acc[kNarrowMaxN];
+#pragma unroll
+  for (int n = 0; n < kNarrowMaxN; ++n) acc[n] = 0.f;
+  for (int q = 0; q < q4; ++q) {
+    const float4 x = *reinterpret_cast<const float4*>(As + tid * pitch + 4 * q);
+#pragma unroll
+    for (int n = 0; n < kNarrowMaxN; ++n) {
+      if (n >= N) break;
+      const float4 w = *reinterpret_cast<const float4*>(Ws + n * K + 4 * q);
+      acc[n] = fmaf(x.x, w.x, acc[n]);
+      acc[n] = fmaf(x.y, w.y, acc[n]);
+      acc[n] = fmaf(x.z, w.z, acc[n]);
+      acc[n] = fmaf(x.w, w.w, acc[n]);
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < kNarrowMaxN; ++n) {
+    if (n >= N) break;
+    float v = acc[n];
+    if (kEpi == EPI_BIAS || kEpi == EPI_BIAS_ELU) v += __ldg(g.bias + n);
+    if (kEpi == EPI_BIAS_ELU || kEpi == EPI_ELU) v = elu_fast(v);
+    g.C[(long long)m * g.c_m + n] = v;
+  }
+}
+
 }  // namespace
 
 int mlp_tile_n(int M, int N, int K) {
@@ -788,15 +929,48 @@ cudaError_t launch_mlp_presplit(const PresplitJobs& jobs, int split_tf32, cudaSt
   return cudaGetLastError();
 }
 
+int mlp_narrow_kind(const MlpGemmArgs& g) {
+  if (!g.narrow || g.M <= 0 || g.N <= 0 || g.K <= 0 || g.c_split) return NARROW_NONE;
+  if (g.a_k != 1) return NARROW_NONE;
+  // a few FMAs per row: below that the tensor-core tile's setup and drain
+  // dominate, above it the FMA loops do
+  if (g.K <= kNarrowMaxK && g.N <= 256 && g.K * g.N <= 2048) return NARROW_K;
+  if (g.N <= kNarrowMaxN && g.K <= kNarrowNMaxK && (g.K & 3) == 0 && (g.a_m & 3) == 0 &&
+      (reinterpret_cast<uintptr_t>(g.A) & 15) == 0 && !g.act_y && !g.colsum)
+    return NARROW_N;
+  return NARROW_NONE;
+}
+
+namespace {
+template <int kEpi>
+void launch_narrow_rows(const MlpGemmArgs& g, int kind, cudaStream_t s) {
+  const int blocks = (g.M + kNarrowRows - 1) / kNarrowRows;
+  if (kind == NARROW_K) narrow_k_kernel<kEpi><<<blocks, 256, 0, s>>>(g);
+  else narrow_n_kernel<kEpi><<<blocks, kNarrowRows, 0, s>>>(g);
+}
+
+// the row kinds (forward and input gradient): one launch
+cudaError_t launch_narrow(const MlpGemmArgs& g, int kind, cudaStream_t s) {
+  if (g.act_y) launch_narrow_rows<EPI_DELU_SUM>(g, kind, s);
+  else if (g.bias && g.elu) launch_narrow_rows<EPI_BIAS_ELU>(g, kind, s);
+  else if (g.bias) launch_narrow_rows<EPI_BIAS>(g, kind, s);
+  else if (g.elu) launch_narrow_rows<EPI_ELU>(g, kind, s);
+  else launch_narrow_rows<EPI_PLAIN>(g, kind, s);
+  return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_mlp_gemm(const MlpGemmArgs& a, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0 || a.K <= 0) return cudaSuccess;
+  if (!a.act_y != !a.colsum) return cudaErrorInvalidValue;   // both or neither
+  const int nk = mlp_narrow_kind(a);
+  if (nk == NARROW_K || nk == NARROW_N) return launch_narrow(a, nk, s);
   MlpGemmArgs g = a;
   if (g.n_tile <= 0) g.n_tile = mlp_tile_n(a.M, a.N, a.K);
   if (g.n_tile > kMaxTileN || g.n_tile % 16) return cudaErrorInvalidValue;
   const int splits = g.c_split ? (a.K + g.k_per_split - 1) / g.k_per_split : 1;
   if (!g.c_split) g.k_per_split = a.K;
   if (g.k_per_split <= 0) return cudaErrorInvalidValue;
-  if (!g.act_y != !g.colsum) return cudaErrorInvalidValue;   // both or neither
   const bool pre = g.b_pre != nullptr;
   if (pre) {
     // the CTAs' row blocks must lie inside the pre-split rows, the copies
@@ -893,11 +1067,15 @@ extern "C" sg_status sg_mlp_gemm(void* stream, const float* A, int64_t a_m, int6
   g.K = K;
   g.elu = elu ? 1 : 0;
   g.split_tf32 = split_tf32 ? 1 : 0;
+  g.narrow = split_tf32 == 2 ? 1 : 0;
   // a product with enough row tiles to fill the GPU and a work buffer that
   // holds B's TF32 parts: split B once, then every CTA copies its parts
+  const int nk = sg::mlp_narrow_kind(g);
+  if (nk == sg::NARROW_K || nk == sg::NARROW_N)
+    return sg::launch_mlp_gemm(g, s) == cudaSuccess ? SG_OK : SG_ERR_CUDA;
   const long long tiles = (long long)((M + 127) / 128) * ((N + 127) / 128);
   const bool k_split = !bias && !elu && c_m == N && tiles < 2 * 152 && K > 32;
-  if (work && K > 0 && !k_split && work_floats >= sg::presplit_floats(N, K) &&
+  if (work && K > 0 && nk == sg::NARROW_NONE && !k_split && work_floats >= sg::presplit_floats(N, K) &&
       (reinterpret_cast<uintptr_t>(work) & 15) == 0) {
     sg::PresplitJobs jobs{};
     jobs.n = 1;

@@ -35,7 +35,15 @@ struct MlpGemmArgs {
   // holds presplit_floats(N, K) floats for b_npad = presplit_npad(N) rows
   const float* b_pre;
   int b_npad;
+  // 1: narrow products (K <= 32 with K N <= 2048, or N <= 16 with K <= 64)
+  // run as FP32 FMA loops on the CUDA cores instead (mlp_narrow_kind)
+  int narrow;
 };
+
+enum MlpNarrowKind { NARROW_NONE = 0, NARROW_K = 1, NARROW_N = 2 };
+// which FP32 kernel serves a product when a.narrow is set (NARROW_NONE: the
+// tensor-core contraction)
+int mlp_narrow_kind(const MlpGemmArgs& a);
 
 // One matrix to pre-split: B(n, k) = W[n wn + k wk], N x K, into dst
 // (presplit_floats(N, K) floats, 16-byte aligned; npad = presplit_npad(N)).

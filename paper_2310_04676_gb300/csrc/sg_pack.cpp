@@ -19,6 +19,7 @@
 #include <sstream>
 
 #include "sg_internal.h"
+#include "sg_pack.h"
 
 namespace sg {
 namespace {

@@ -196,15 +196,24 @@ colsum_partial_kernel(const float* __restrict__ Y, int rows, int w, float* __res
   }
 }
 
-// Bias gradient from the partials: grad[c] = sum_b part[b][c] (block per column).
-__global__ void __launch_bounds__(128)
-bgrad_final_kernel(const float* __restrict__ part, int nblk, int w, float* __restrict__ grad) {
+// The bias gradients of one network's four layers in one launch: job j
+// sums part_j[b][c] over b < nblk_j for its w_j columns (a block per column,
+// columns of the jobs in order).
+struct BGradJobs {
+  const float* part[4];
+  float* grad[4];
+  int nblk[4], w[4];
+};
+__global__ void __launch_bounds__(128) bgrad_final_multi_kernel(BGradJobs J) {
   __shared__ double sh[32];
-  const int c = blockIdx.x;
+  int c = blockIdx.x, j = 0;
+  while (j < 3 && c >= J.w[j]) c -= J.w[j++];
+  const float* part = J.part[j];
+  const int w = J.w[j];
   double s = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(size_t)b * w + c];
+  for (int b = threadIdx.x; b < J.nblk[j]; b += blockDim.x) s += part[(size_t)b * w + c];
   s = block_sum(s, sh);
-  if (threadIdx.x == 0) grad[c] = (float)s;
+  if (threadIdx.x == 0) J.grad[j][c] = (float)s;
 }
 
 // Stage 1: per-block sums of x and x^2 (fixed grid, fixed order).
@@ -468,7 +477,8 @@ struct sg_ppo {
   float *dmu = nullptr, *dv = nullptr;  // loss gradients w.r.t. the actor mean and the value
   sg::MiniBatch mb{};
   float* head_part = nullptr;
-  float* bgrad_part = nullptr;         // [blocks or row tiles][256] bias-gradient partial sums
+  float* bgrad_part = nullptr;         // bias-gradient partial sums, a region per layer:
+  size_t bgrad_off[4] = {0, 0, 0, 0};  // [row tiles][width] (hidden), [blocks][out] (output)
   double* red_part = nullptr;
   float* norm = nullptr;               // advantage mean, 1 / std
   float* clip_coef = nullptr;
@@ -496,9 +506,13 @@ cudaError_t dalloc(sg_ppo* p, T** ptr, size_t count) {
   return e;
 }
 
+// Products of the networks: tensor-core contraction (3xTF32, or one TF32
+// product in the tf32 mode); the narrow ones (the first layer's 28 inputs,
+// the output layers, their weight and input gradients) as FP32 FMA loops.
 sg::MlpGemmArgs gemm_args(const sg_ppo* p) {
   sg::MlpGemmArgs g{};
   g.split_tf32 = p->cfg.tf32 ? 0 : 1;
+  g.narrow = 1;
   g.err = p->err;
   return g;
 }
@@ -524,7 +538,7 @@ bool gemm_fwd(sg_ppo* p, const float* X, int rows, const Layer& l, float* Y, boo
 // ELU layer below, and per 128-row tile the column sums of dZ (that layer's
 // bias gradient) into p->bgrad_part
 bool gemm_bwd_data_elu(sg_ppo* p, const float* dY, int rows, const Layer& l, const float* y,
-                       float* dZ) {
+                       float* dZ, float* colsum) {
   sg::MlpGemmArgs g = gemm_args(p);
   g.A = dY, g.a_m = l.out, g.a_k = 1;
   g.B = p->params + l.w, g.b_n = 1, g.b_k = l.in;       // B(n = in, k = out) = W[out][in]
@@ -532,12 +546,13 @@ bool gemm_bwd_data_elu(sg_ppo* p, const float* dY, int rows, const Layer& l, con
   g.C = dZ, g.c_m = l.in;
   g.M = rows, g.N = l.in, g.K = l.out;
   g.act_y = y;
-  g.colsum = p->bgrad_part;
+  g.colsum = colsum;
   return sg::launch_mlp_gemm(g, p->stream) == cudaSuccess;
 }
-// dW[out][in] = dY^T X (rows split over CTAs); with_bias: db[out] = dY^T 1
+// dW[out][in] = dY^T X (rows split over CTAs); with a bias_part region:
+// the column sums of dY (db[out] = dY^T 1) per block of rows into it
 bool gemm_bwd_weight(sg_ppo* p, const float* dY, const float* X, int rows, const Layer& l,
-                     bool with_bias) {
+                     float* bias_part) {
   sg::MlpGemmArgs g = gemm_args(p);
   g.A = dY, g.a_m = 1, g.a_k = l.out;                   // A(m = out, k = row)
   g.B = X, g.b_n = 1, g.b_k = l.in;                     // B(n = in, k = row)
@@ -545,11 +560,8 @@ bool gemm_bwd_weight(sg_ppo* p, const float* dY, const float* X, int rows, const
   g.M = l.out, g.N = l.in, g.K = rows;
   if (sg::launch_mlp_gemm_split(g, p->mlp_work, p->mlp_work_floats, p->stream) != cudaSuccess)
     return false;
-  if (!with_bias) return true;
-  sg::colsum_partial_kernel<<<sg::kBGradBlocks, 256, 0, p->stream>>>(dY, rows, l.out,
-                                                                    p->bgrad_part);
-  sg::bgrad_final_kernel<<<l.out, 128, 0, p->stream>>>(p->bgrad_part, sg::kBGradBlocks, l.out,
-                                                      p->grad + l.b);
+  if (!bias_part) return true;
+  sg::colsum_partial_kernel<<<sg::kBGradBlocks, 256, 0, p->stream>>>(dY, rows, l.out, bias_part);
   return cudaGetLastError() == cudaSuccess;
 }
 
@@ -566,26 +578,39 @@ bool net_forward(sg_ppo* p, const Net& net, const float* X, int rows, float* con
 }
 
 // Backward of one network from dOut [rows][out]; weight gradients into p->grad.
-// Below the output layer the ELU backward also sums the bias gradient.
+// Below the output layer the ELU backward also sums the bias gradient (per
+// 128-row tile, each layer in its own region of p->bgrad_part); one launch
+// then finishes all four bias gradients.
 bool net_backward(sg_ppo* p, const Net& net, const float* X, int rows, float* const (&h)[3],
                   const float* dOut) {
   const float* dY = dOut;
   float* bufs[2] = {p->dbuf0, p->dbuf1};
+  const int tiles = (rows + 127) / 128;
+  sg::BGradJobs jobs{};
+  int cols = 0;
   for (int i = 3; i >= 0; --i) {
     const float* in = i > 0 ? h[i - 1] : X;
-    if (!gemm_bwd_weight(p, dY, in, rows, net.l[i], i == 3)) return false;
+    float* part = p->bgrad_part + p->bgrad_off[i];
+    if (!gemm_bwd_weight(p, dY, in, rows, net.l[i], i == 3 ? part : nullptr)) return false;
+    if (i == 3) {
+      jobs.part[0] = part, jobs.grad[0] = p->grad + net.l[3].b;
+      jobs.nblk[0] = sg::kBGradBlocks, jobs.w[0] = net.l[3].out;
+      cols += net.l[3].out;
+    }
     if (i == 0) break;
     float* dX = bufs[i & 1];
     // input gradient with the ELU backward and the bias-gradient partial sums
     // of layer i - 1 in the product's epilogue
-    if (!gemm_bwd_data_elu(p, dY, rows, net.l[i], h[i - 1], dX)) return false;
-    const int w = net.l[i].in;
-    sg::bgrad_final_kernel<<<w, 128, 0, p->stream>>>(p->bgrad_part, (rows + 127) / 128, w,
-                                                    p->grad + net.l[i - 1].b);
-    if (cudaGetLastError() != cudaSuccess) return false;
+    float* below = p->bgrad_part + p->bgrad_off[i - 1];
+    if (!gemm_bwd_data_elu(p, dY, rows, net.l[i], h[i - 1], dX, below)) return false;
+    const int j = 4 - i;
+    jobs.part[j] = below, jobs.grad[j] = p->grad + net.l[i - 1].b;
+    jobs.nblk[j] = tiles, jobs.w[j] = net.l[i].in;
+    cols += net.l[i].in;
     dY = dX;
   }
-  return true;
+  sg::bgrad_final_multi_kernel<<<cols, 128, 0, p->stream>>>(jobs);
+  return cudaGetLastError() == cudaSuccess;
 }
 
 sg_status bind_stream(sg_ppo* p, cudaStream_t s) {
@@ -763,7 +788,11 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
   step(dalloc(p, &p->head_part, (size_t)head_blocks * (2 + 2 * A)));
   step(dalloc(p, &p->red_part, (size_t)2 * sg::kRedBlocks));
   const size_t part_rows = std::max<size_t>(sg::kBGradBlocks, ((size_t)rows + 127) / 128);
-  step(dalloc(p, &p->bgrad_part, part_rows * sg::kH1));
+  p->bgrad_off[0] = 0;
+  p->bgrad_off[1] = part_rows * sg::kH1;
+  p->bgrad_off[2] = part_rows * (sg::kH1 + sg::kH2);
+  p->bgrad_off[3] = part_rows * (sg::kH1 + sg::kH2 + sg::kH3);
+  step(dalloc(p, &p->bgrad_part, p->bgrad_off[3] + part_rows * (size_t)p->Ap));
   step(dalloc(p, &p->norm, 2));
   step(dalloc(p, &p->clip_coef, 1));
   step(sg::prepare_mlp_kernels());

@@ -249,8 +249,10 @@ def mlp_gemm(A, a_strides, B, b_strides, M, N, K, out, c_m, bias=None, elu=False
              split=True, stream=None):
     """sg_mlp_gemm: out[m * c_m + n] = act(sum_k A(m, k) B(n, k) + bias[n]) with
     A(m, k) = A.flatten()[m * a_strides[0] + k * a_strides[1]] and
-    B(n, k) = B.flatten()[n * b_strides[0] + k * b_strides[1]] (tensor-core
-    split-precision contraction of the PPO networks)."""
+    B(n, k) = B.flatten()[n * b_strides[0] + k * b_strides[1]] (contraction of
+    the PPO networks).  split: True / 1 three TF32 products (FP32-grade),
+    False / 0 one TF32 product, 2 FP32-grade with narrow products as FP32
+    FMA loops on the CUDA cores."""
     import torch
     lib = load_library()
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -258,7 +260,7 @@ def mlp_gemm(A, a_strides, B, b_strides, M, N, K, out, c_m, bias=None, elu=False
                          int(a_strides[1]), _ptr(B), int(b_strides[0]), int(b_strides[1]),
                          _ptr(bias), 1 if elu else 0, int(M), int(N), int(K), _ptr(out), int(c_m),
                          _ptr(work), int(work.numel()) if work is not None else 0,
-                         1 if split else 0)
+                         int(split))
     if st != SG_OK:
         raise SgError(st, "sg_mlp_gemm failed")
     return out
