@@ -46,13 +46,18 @@
  *   its gradient is clipped to global norm max_grad_norm and Adam (beta
  *   0.9 / 0.999, eps 1e-8, bias-corrected) takes one step of size lr.
  *
- * Threading and streams: all work goes to the env context's stream; the
- * collect loop is captured once into a CUDA graph and replayed.  Every step
- * is a kernel of this library; the dense layers run on its tensor-core
- * contraction (sg_mlp_gemm below: FP32-grade split precision, or one TF32
- * product per term with tf32 = 1), forward products with the bias and ELU in
- * their epilogue, input gradients with the ELU derivative and the bias
- * gradient's partial sums in theirs.
+ * Threading and streams: all work is ordered on the env context's stream;
+ * the critic's products run on a private second stream of the handle,
+ * forked from and joined back to the context's stream by events around each
+ * network pass (the two networks are independent there), so every call's
+ * work is complete when the context's stream reaches its end.  The collect
+ * loop is captured once into a CUDA graph (the two networks as parallel
+ * branches) and replayed.  Every step is a kernel of this library; the dense
+ * layers run on its tensor-core contraction (sg_mlp_gemm below: FP32-grade
+ * split precision, or one TF32 product per term with tf32 = 1; the output
+ * layers and the input gradients below them as FP32 FMA loops), forward
+ * products with the bias and ELU in their epilogue, input gradients with the
+ * ELU derivative and the bias gradient's partial sums in theirs.
  */
 #ifndef SG_PPO_H
 #define SG_PPO_H

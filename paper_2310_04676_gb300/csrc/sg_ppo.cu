@@ -457,7 +457,20 @@ struct sg_ppo {
   int32_t* pub2int = nullptr;          // [public_params] internal index of each public entry
   float* xin = nullptr;                // [E][Dp] padded observations of the collect step
   cudaStream_t stream = nullptr;       // the stream the collect graph was captured for
-  float* mlp_work = nullptr;           // partial sums of the row-split weight gradients
+  // The actor's products run on `stream`, the critic's on `side`, forked
+  // from and joined back to `stream` by events: the networks are
+  // independent between the minibatch gather and the loss head, and between
+  // the head and the gradient norm.  Scratch per network: the row-split
+  // partial sums of the weight gradients, the bias-gradient partials, the
+  // input-gradient buffers.
+  struct Lane {
+    cudaStream_t s = nullptr;
+    float* work = nullptr;
+    float* bgrad_part = nullptr;
+    float* dbuf[2] = {nullptr, nullptr};
+  } lane[2];
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   long long mlp_work_floats = 0;
   float* pre = nullptr;                // the weights' TF32 parts (sg::launch_mlp_presplit)
   sg::PresplitJobs pre_jobs{};
@@ -473,12 +486,13 @@ struct sg_ppo {
   float* zero_targets = nullptr;       // [E][A]
   // activations and their gradients, [rows_max][width]
   float *ha[3] = {nullptr, nullptr, nullptr}, *hc[3] = {nullptr, nullptr, nullptr};
-  float *mu = nullptr, *vout = nullptr, *dbuf0 = nullptr, *dbuf1 = nullptr;
+  float *mu = nullptr, *vout = nullptr;
   float *dmu = nullptr, *dv = nullptr;  // loss gradients w.r.t. the actor mean and the value
   sg::MiniBatch mb{};
   float* head_part = nullptr;
-  float* bgrad_part = nullptr;         // bias-gradient partial sums, a region per layer:
-  size_t bgrad_off[4] = {0, 0, 0, 0};  // [row tiles][width] (hidden), [blocks][out] (output)
+  // bias-gradient partial sums (per network, Lane::bgrad_part), a region per
+  // layer: [row tiles][width] (hidden layers), [blocks][out] (output layer)
+  size_t bgrad_off[4] = {0, 0, 0, 0};
   double* red_part = nullptr;
   float* norm = nullptr;               // advantage mean, 1 / std
   float* clip_coef = nullptr;
@@ -524,7 +538,8 @@ bool presplit_weights(sg_ppo* p) {
 }
 
 // Y[rows][out] = act(X[rows][in] W^T + b), act = ELU on hidden layers
-bool gemm_fwd(sg_ppo* p, const float* X, int rows, const Layer& l, float* Y, bool elu) {
+bool gemm_fwd(sg_ppo* p, const sg_ppo::Lane& ln, const float* X, int rows, const Layer& l,
+              float* Y, bool elu) {
   sg::MlpGemmArgs g = gemm_args(p);
   g.A = X, g.a_m = l.in, g.a_k = 1;
   g.B = p->params + l.w, g.b_n = l.in, g.b_k = 1;
@@ -532,13 +547,13 @@ bool gemm_fwd(sg_ppo* p, const float* X, int rows, const Layer& l, float* Y, boo
   g.C = Y, g.c_m = l.out;
   g.bias = p->params + l.b, g.elu = elu ? 1 : 0;
   g.M = rows, g.N = l.out, g.K = l.in;
-  return sg::launch_mlp_gemm(g, p->stream) == cudaSuccess;
+  return sg::launch_mlp_gemm(g, ln.s) == cudaSuccess;
 }
 // dZ[rows][in] = (dY[rows][out] W) * ELU'(y), y [rows][in] the output of the
 // ELU layer below, and per 128-row tile the column sums of dZ (that layer's
-// bias gradient) into p->bgrad_part
-bool gemm_bwd_data_elu(sg_ppo* p, const float* dY, int rows, const Layer& l, const float* y,
-                       float* dZ, float* colsum) {
+// bias gradient) into colsum
+bool gemm_bwd_data_elu(sg_ppo* p, const sg_ppo::Lane& ln, const float* dY, int rows,
+                       const Layer& l, const float* y, float* dZ, float* colsum) {
   sg::MlpGemmArgs g = gemm_args(p);
   g.A = dY, g.a_m = l.out, g.a_k = 1;
   g.B = p->params + l.w, g.b_n = 1, g.b_k = l.in;       // B(n = in, k = out) = W[out][in]
@@ -547,31 +562,31 @@ bool gemm_bwd_data_elu(sg_ppo* p, const float* dY, int rows, const Layer& l, con
   g.M = rows, g.N = l.in, g.K = l.out;
   g.act_y = y;
   g.colsum = colsum;
-  return sg::launch_mlp_gemm(g, p->stream) == cudaSuccess;
+  return sg::launch_mlp_gemm(g, ln.s) == cudaSuccess;
 }
 // dW[out][in] = dY^T X (rows split over CTAs); with a bias_part region:
 // the column sums of dY (db[out] = dY^T 1) per block of rows into it
-bool gemm_bwd_weight(sg_ppo* p, const float* dY, const float* X, int rows, const Layer& l,
-                     float* bias_part) {
+bool gemm_bwd_weight(sg_ppo* p, const sg_ppo::Lane& ln, const float* dY, const float* X,
+                     int rows, const Layer& l, float* bias_part) {
   sg::MlpGemmArgs g = gemm_args(p);
   g.A = dY, g.a_m = 1, g.a_k = l.out;                   // A(m = out, k = row)
   g.B = X, g.b_n = 1, g.b_k = l.in;                     // B(n = in, k = row)
   g.C = p->grad + l.w, g.c_m = l.in;
   g.M = l.out, g.N = l.in, g.K = rows;
-  if (sg::launch_mlp_gemm_split(g, p->mlp_work, p->mlp_work_floats, p->stream) != cudaSuccess)
+  if (sg::launch_mlp_gemm_split(g, ln.work, p->mlp_work_floats, ln.s) != cudaSuccess)
     return false;
   if (!bias_part) return true;
-  sg::colsum_partial_kernel<<<sg::kBGradBlocks, 256, 0, p->stream>>>(dY, rows, l.out, bias_part);
+  sg::colsum_partial_kernel<<<sg::kBGradBlocks, 256, 0, ln.s>>>(dY, rows, l.out, bias_part);
   return cudaGetLastError() == cudaSuccess;
 }
 
 // Forward of one network over `rows` inputs; hidden outputs kept in h[0..2].
-bool net_forward(sg_ppo* p, const Net& net, const float* X, int rows, float* const (&h)[3],
-                 float* out) {
+bool net_forward(sg_ppo* p, const sg_ppo::Lane& ln, const Net& net, const float* X, int rows,
+                 float* const (&h)[3], float* out) {
   const float* in = X;
   for (int i = 0; i < 4; ++i) {
     float* y = i < 3 ? h[i] : out;
-    if (!gemm_fwd(p, in, rows, net.l[i], y, i < 3)) return false;
+    if (!gemm_fwd(p, ln, in, rows, net.l[i], y, i < 3)) return false;
     in = y;
   }
   return true;
@@ -579,19 +594,19 @@ bool net_forward(sg_ppo* p, const Net& net, const float* X, int rows, float* con
 
 // Backward of one network from dOut [rows][out]; weight gradients into p->grad.
 // Below the output layer the ELU backward also sums the bias gradient (per
-// 128-row tile, each layer in its own region of p->bgrad_part); one launch
-// then finishes all four bias gradients.
-bool net_backward(sg_ppo* p, const Net& net, const float* X, int rows, float* const (&h)[3],
-                  const float* dOut) {
+// 128-row tile, each layer in its own region of the lane's partials); one
+// launch then finishes all four bias gradients.
+bool net_backward(sg_ppo* p, const sg_ppo::Lane& ln, const Net& net, const float* X, int rows,
+                  float* const (&h)[3], const float* dOut) {
   const float* dY = dOut;
-  float* bufs[2] = {p->dbuf0, p->dbuf1};
+  float* const* bufs = ln.dbuf;
   const int tiles = (rows + 127) / 128;
   sg::BGradJobs jobs{};
   int cols = 0;
   for (int i = 3; i >= 0; --i) {
     const float* in = i > 0 ? h[i - 1] : X;
-    float* part = p->bgrad_part + p->bgrad_off[i];
-    if (!gemm_bwd_weight(p, dY, in, rows, net.l[i], i == 3 ? part : nullptr)) return false;
+    float* part = ln.bgrad_part + p->bgrad_off[i];
+    if (!gemm_bwd_weight(p, ln, dY, in, rows, net.l[i], i == 3 ? part : nullptr)) return false;
     if (i == 3) {
       jobs.part[0] = part, jobs.grad[0] = p->grad + net.l[3].b;
       jobs.nblk[0] = sg::kBGradBlocks, jobs.w[0] = net.l[3].out;
@@ -601,21 +616,34 @@ bool net_backward(sg_ppo* p, const Net& net, const float* X, int rows, float* co
     float* dX = bufs[i & 1];
     // input gradient with the ELU backward and the bias-gradient partial sums
     // of layer i - 1 in the product's epilogue
-    float* below = p->bgrad_part + p->bgrad_off[i - 1];
-    if (!gemm_bwd_data_elu(p, dY, rows, net.l[i], h[i - 1], dX, below)) return false;
+    float* below = ln.bgrad_part + p->bgrad_off[i - 1];
+    if (!gemm_bwd_data_elu(p, ln, dY, rows, net.l[i], h[i - 1], dX, below)) return false;
     const int j = 4 - i;
     jobs.part[j] = below, jobs.grad[j] = p->grad + net.l[i - 1].b;
     jobs.nblk[j] = tiles, jobs.w[j] = net.l[i].in;
     cols += net.l[i].in;
     dY = dX;
   }
-  sg::bgrad_final_multi_kernel<<<cols, 128, 0, p->stream>>>(jobs);
+  sg::bgrad_final_multi_kernel<<<cols, 128, 0, ln.s>>>(jobs);
   return cudaGetLastError() == cudaSuccess;
 }
 
 sg_status bind_stream(sg_ppo* p, cudaStream_t s) {
   p->stream = s;
+  p->lane[0].s = s;
+  p->lane[1].s = p->side;
   return SG_OK;
+}
+
+// The side stream waits for the work enqueued so far on p->stream.
+bool fork(sg_ppo* p) {
+  return cudaEventRecord(p->ev_fork, p->stream) == cudaSuccess &&
+         cudaStreamWaitEvent(p->side, p->ev_fork, 0) == cudaSuccess;
+}
+// p->stream waits for the work enqueued so far on the side stream.
+bool join(sg_ppo* p) {
+  return cudaEventRecord(p->ev_join, p->side) == cudaSuccess &&
+         cudaStreamWaitEvent(p->stream, p->ev_join, 0) == cudaSuccess;
 }
 
 // The collect loop as a sequence of launches on p->stream (captured once).
@@ -635,8 +663,9 @@ sg_status enqueue_collect(sg_ppo* p) {
     float* v_t = p->values + (size_t)t * E;
     sg::pad_rows_kernel<<<sg::grid_for((long long)E * p->Dp, 256), 256, 0, p->stream>>>(
         o_t, E, D, p->Dp, p->xin);
-    if (!net_forward(p, p->L.actor, p->xin, E, p->ha, p->mu) ||
-        !net_forward(p, p->L.critic, p->xin, E, p->hc, v_t))
+    // actor on this stream, critic on the side stream
+    if (!fork(p) || !net_forward(p, p->lane[0], p->L.actor, p->xin, E, p->ha, p->mu) ||
+        !net_forward(p, p->lane[1], p->L.critic, p->xin, E, p->hc, v_t) || !join(p))
       return fail(p, SG_ERR_CUDA, "sg_ppo_collect: network forward failed");
     sg::sample_kernel<<<eb, tb, 0, p->stream>>>(p->mu, p->params + p->L.log_std, p->jmask,
                                                p->d_step, t, c.seed, E, A, p->Ap, a_t,
@@ -652,7 +681,7 @@ sg_status enqueue_collect(sg_ppo* p) {
   }
   sg::pad_rows_kernel<<<sg::grid_for((long long)E * p->Dp, 256), 256, 0, p->stream>>>(
       p->obs + (size_t)n * E * D, E, D, p->Dp, p->xin);
-  if (!net_forward(p, p->L.critic, p->xin, E, p->hc, p->values + (size_t)n * E))
+  if (!net_forward(p, p->lane[0], p->L.critic, p->xin, E, p->hc, p->values + (size_t)n * E))
     return fail(p, SG_ERR_CUDA, "sg_ppo_collect: critic forward failed");
   sg::gae_kernel<<<eb, tb, 0, p->stream>>>(p->rewards, p->values, p->dones, n, E, c.gamma, c.lam,
                                           p->adv, p->ret);
@@ -744,12 +773,12 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
   step(dalloc(p, &p->xin, (size_t)E * p->Dp));
   step(dalloc(p, &p->pub2int, p->public_params));
   step(dalloc(p, &p->vout, (size_t)rows));
-  step(dalloc(p, &p->dbuf0, (size_t)rows * sg::kH1));
-  step(dalloc(p, &p->dbuf1, (size_t)rows * sg::kH1));
+  for (sg_ppo::Lane& ln : p->lane)
+    for (float*& d : ln.dbuf) step(dalloc(p, &d, (size_t)rows * sg::kH1));
   step(dalloc(p, &p->dmu, (size_t)p->M * p->Ap));
   step(dalloc(p, &p->dv, (size_t)p->M));
   p->mlp_work_floats = (long long)2 * 152 * sg::kH1 * sg::kH2;   // row-split partial sums
-  step(dalloc(p, &p->mlp_work, (size_t)p->mlp_work_floats));
+  for (sg_ppo::Lane& ln : p->lane) step(dalloc(p, &ln.work, (size_t)p->mlp_work_floats));
   {
     // pre-split weights: every layer as a forward B, layers 2..4 as an input-gradient B
     size_t off = 0;
@@ -792,7 +821,11 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
   p->bgrad_off[1] = part_rows * sg::kH1;
   p->bgrad_off[2] = part_rows * (sg::kH1 + sg::kH2);
   p->bgrad_off[3] = part_rows * (sg::kH1 + sg::kH2 + sg::kH3);
-  step(dalloc(p, &p->bgrad_part, p->bgrad_off[3] + part_rows * (size_t)p->Ap));
+  for (sg_ppo::Lane& ln : p->lane)
+    step(dalloc(p, &ln.bgrad_part, p->bgrad_off[3] + part_rows * (size_t)p->Ap));
+  step(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+  step(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+  step(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
   step(dalloc(p, &p->norm, 2));
   step(dalloc(p, &p->clip_coef, 1));
   step(sg::prepare_mlp_kernels());
@@ -850,8 +883,12 @@ void sg_ppo_destroy(sg_ppo* p) {
   const bool other = cudaGetDevice(&cur) == cudaSuccess && owner >= 0 && cur != owner;
   if (other) cudaSetDevice(owner);
   if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->side) cudaStreamSynchronize(p->side);
   if (p->collect_exec) cudaGraphExecDestroy(p->collect_exec);
   for (void* a : p->allocs) cudaFree(a);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->side) cudaStreamDestroy(p->side);
   delete p;
   if (other) cudaSetDevice(cur);
 }
@@ -948,8 +985,8 @@ sg_status sg_ppo_update(sg_ppo* p, const int32_t* perm, float* stats) {
       sg::gather_kernel<<<(int)(((long long)M * 32 + 255) / 256), 256, 0, p->stream>>>(
           src, p->mb, idx, M, E, D, p->Dp, A);
       if (!presplit_weights(p)) return fail(p, SG_ERR_CUDA, "sg_ppo_update: weight split failed");
-      if (!net_forward(p, p->L.actor, p->mb.obs, M, p->ha, p->mu) ||
-          !net_forward(p, p->L.critic, p->mb.obs, M, p->hc, p->vout))
+      if (!fork(p) || !net_forward(p, p->lane[0], p->L.actor, p->mb.obs, M, p->ha, p->mu) ||
+          !net_forward(p, p->lane[1], p->L.critic, p->mb.obs, M, p->hc, p->vout) || !join(p))
         return fail(p, SG_ERR_CUDA, "sg_ppo_update: forward failed");
       sg::HeadArgs h{p->mu, p->vout, p->params + p->L.log_std, p->mb, p->dmu, p->dv,
                      p->head_part, M, A, p->Ap, c.clip, c.value_coef};
@@ -957,8 +994,8 @@ sg_status sg_ppo_update(sg_ppo* p, const int32_t* perm, float* stats) {
       sg::head_final_kernel<<<1, sg::kRedThreads, 0, p->stream>>>(p->head_part, head_blocks, A, M,
                                                      p->params + p->L.log_std, c.entropy_coef,
                                                      p->grad + p->L.log_std, st);
-      if (!net_backward(p, p->L.actor, p->mb.obs, M, p->ha, p->dmu) ||
-          !net_backward(p, p->L.critic, p->mb.obs, M, p->hc, p->dv))
+      if (!fork(p) || !net_backward(p, p->lane[0], p->L.actor, p->mb.obs, M, p->ha, p->dmu) ||
+          !net_backward(p, p->lane[1], p->L.critic, p->mb.obs, M, p->hc, p->dv) || !join(p))
         return fail(p, SG_ERR_CUDA, "sg_ppo_update: backward failed");
       sg::sumsq_partial_kernel<<<sg::kRedBlocks, sg::kRedThreads, 0, p->stream>>>(p->grad, P,
                                                                                   p->red_part);
