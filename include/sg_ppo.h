@@ -49,8 +49,11 @@
  * Threading and streams: all work is ordered on the env context's stream;
  * the critic's products run on a private second stream of the handle,
  * forked from and joined back to the context's stream by events around each
- * network pass (the two networks are independent there), so every call's
- * work is complete when the context's stream reaches its end.  The collect
+ * network pass (the two networks are independent there), and within each
+ * network's backward pass the weight gradients run on a private stream of
+ * their own, each after its output gradient is ready; everything is joined
+ * back, so every call's work is complete when the context's stream reaches
+ * its end.  The collect
  * loop is captured once into a CUDA graph (the two networks as parallel
  * branches) and replayed.  Every step is a kernel of this library; the dense
  * layers run on its tensor-core contraction (sg_mlp_gemm below: FP32-grade

@@ -463,11 +463,15 @@ struct sg_ppo {
   // the head and the gradient norm.  Scratch per network: the row-split
   // partial sums of the weight gradients, the bias-gradient partials, the
   // input-gradient buffers.
+  // Within a network's backward the weight gradients run on a third stream
+  // (Lane::sw), each after the event that its output gradient is ready
+  // (Lane::ev_dy), joined back before the bias gradients are finished.
   struct Lane {
-    cudaStream_t s = nullptr;
+    cudaStream_t s = nullptr, sw = nullptr;
+    cudaEvent_t ev_dy[4] = {nullptr, nullptr, nullptr, nullptr}, ev_w = nullptr;
     float* work = nullptr;
     float* bgrad_part = nullptr;
-    float* dbuf[2] = {nullptr, nullptr};
+    float* dbuf[3] = {nullptr, nullptr, nullptr};   // input gradients of layers 3, 2, 1
   } lane[2];
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -595,25 +599,32 @@ bool net_forward(sg_ppo* p, const sg_ppo::Lane& ln, const Net& net, const float*
 // Backward of one network from dOut [rows][out]; weight gradients into p->grad.
 // Below the output layer the ELU backward also sums the bias gradient (per
 // 128-row tile, each layer in its own region of the lane's partials); one
-// launch then finishes all four bias gradients.
+// launch then finishes all four bias gradients.  The input gradients run in
+// order on ln.s, each layer's weight gradient on ln.sw once its output
+// gradient is ready; every input gradient has a buffer of its own, so none
+// is overwritten while a weight gradient still reads it.
 bool net_backward(sg_ppo* p, const sg_ppo::Lane& ln, const Net& net, const float* X, int rows,
                   float* const (&h)[3], const float* dOut) {
   const float* dY = dOut;
-  float* const* bufs = ln.dbuf;
   const int tiles = (rows + 127) / 128;
   sg::BGradJobs jobs{};
   int cols = 0;
+  sg_ppo::Lane wl = ln;
+  wl.s = ln.sw;                                // the weight gradients' stream
   for (int i = 3; i >= 0; --i) {
     const float* in = i > 0 ? h[i - 1] : X;
     float* part = ln.bgrad_part + p->bgrad_off[i];
-    if (!gemm_bwd_weight(p, ln, dY, in, rows, net.l[i], i == 3 ? part : nullptr)) return false;
+    if (cudaEventRecord(ln.ev_dy[i], ln.s) != cudaSuccess ||
+        cudaStreamWaitEvent(ln.sw, ln.ev_dy[i], 0) != cudaSuccess)
+      return false;
+    if (!gemm_bwd_weight(p, wl, dY, in, rows, net.l[i], i == 3 ? part : nullptr)) return false;
     if (i == 3) {
       jobs.part[0] = part, jobs.grad[0] = p->grad + net.l[3].b;
       jobs.nblk[0] = sg::kBGradBlocks, jobs.w[0] = net.l[3].out;
       cols += net.l[3].out;
     }
     if (i == 0) break;
-    float* dX = bufs[i & 1];
+    float* dX = ln.dbuf[3 - i];
     // input gradient with the ELU backward and the bias-gradient partial sums
     // of layer i - 1 in the product's epilogue
     float* below = ln.bgrad_part + p->bgrad_off[i - 1];
@@ -624,6 +635,9 @@ bool net_backward(sg_ppo* p, const sg_ppo::Lane& ln, const Net& net, const float
     cols += net.l[i].in;
     dY = dX;
   }
+  if (cudaEventRecord(ln.ev_w, ln.sw) != cudaSuccess ||
+      cudaStreamWaitEvent(ln.s, ln.ev_w, 0) != cudaSuccess)
+    return false;
   sg::bgrad_final_multi_kernel<<<cols, 128, 0, ln.s>>>(jobs);
   return cudaGetLastError() == cudaSuccess;
 }
@@ -773,8 +787,12 @@ sg_status sg_ppo_create(sg_ctx* env, const sg_ppo_config* cfg, sg_ppo** out) {
   step(dalloc(p, &p->xin, (size_t)E * p->Dp));
   step(dalloc(p, &p->pub2int, p->public_params));
   step(dalloc(p, &p->vout, (size_t)rows));
-  for (sg_ppo::Lane& ln : p->lane)
+  for (sg_ppo::Lane& ln : p->lane) {
     for (float*& d : ln.dbuf) step(dalloc(p, &d, (size_t)rows * sg::kH1));
+    step(cudaStreamCreateWithFlags(&ln.sw, cudaStreamNonBlocking));
+    for (cudaEvent_t& ev : ln.ev_dy) step(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    step(cudaEventCreateWithFlags(&ln.ev_w, cudaEventDisableTiming));
+  }
   step(dalloc(p, &p->dmu, (size_t)p->M * p->Ap));
   step(dalloc(p, &p->dv, (size_t)p->M));
   p->mlp_work_floats = (long long)2 * 152 * sg::kH1 * sg::kH2;   // row-split partial sums
@@ -882,13 +900,22 @@ void sg_ppo_destroy(sg_ppo* p) {
   int cur = -1;
   const bool other = cudaGetDevice(&cur) == cudaSuccess && owner >= 0 && cur != owner;
   if (other) cudaSetDevice(owner);
+  // every stream of the handle finished before its memory is released
   if (p->stream) cudaStreamSynchronize(p->stream);
   if (p->side) cudaStreamSynchronize(p->side);
+  for (sg_ppo::Lane& ln : p->lane)
+    if (ln.sw) cudaStreamSynchronize(ln.sw);
   if (p->collect_exec) cudaGraphExecDestroy(p->collect_exec);
   for (void* a : p->allocs) cudaFree(a);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->side) cudaStreamDestroy(p->side);
+  for (sg_ppo::Lane& ln : p->lane) {
+    if (ln.sw) cudaStreamDestroy(ln.sw);
+    for (cudaEvent_t ev : ln.ev_dy)
+      if (ev) cudaEventDestroy(ev);
+    if (ln.ev_w) cudaEventDestroy(ln.ev_w);
+  }
   delete p;
   if (other) cudaSetDevice(cur);
 }
