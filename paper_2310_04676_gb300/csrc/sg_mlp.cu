@@ -280,20 +280,24 @@ __device__ __forceinline__ float round_tf32(float x) {
 }
 
 // TF32 parts: hi = round_tf32(x), lo = round_tf32(x - hi) (x - hi is exact in
-// FP32), so x = hi + lo within 2^-22 |x|.
+// FP32), so x = hi + lo within 2^-22 |x|; the one-product mode needs hi only.
+template <bool kSplit>
 __device__ __forceinline__ void split4(const float (&v)[4], float4& h, float4& l) {
   h.x = round_tf32(v[0]);
   h.y = round_tf32(v[1]);
   h.z = round_tf32(v[2]);
   h.w = round_tf32(v[3]);
-  l.x = round_tf32(v[0] - h.x);
-  l.y = round_tf32(v[1] - h.y);
-  l.z = round_tf32(v[2] - h.z);
-  l.w = round_tf32(v[3] - h.w);
+  if (kSplit) {
+    l.x = round_tf32(v[0] - h.x);
+    l.y = round_tf32(v[1] - h.y);
+    l.z = round_tf32(v[2] - h.z);
+    l.w = round_tf32(v[3] - h.w);
+  }
 }
 
 // Split chunk k0 (from raw, or read directly for RAW_PLAIN) into the hi / lo
-// tiles.
+// tiles (hi only in the one-product mode).
+template <bool kSplit>
 __device__ __forceinline__ void convert(const Operand& o, int k0, const float* raw, int tid,
                                         char* hi, char* lo) {
   const int units = o.nrows * (kChunkK / 4);
@@ -306,9 +310,9 @@ __device__ __forceinline__ void convert(const Operand& o, int k0, const float* r
       const float4 t = reinterpret_cast<const float4*>(raw)[f];
       const float v[4] = {t.x, t.y, t.z, t.w};
       float4 h, l;
-      split4(v, h, l);
+      split4<kSplit>(v, h, l);
       reinterpret_cast<float4*>(hi)[f] = h;
-      reinterpret_cast<float4*>(lo)[f] = l;
+      if (kSplit) reinterpret_cast<float4*>(lo)[f] = l;
     }
     return;
   }
@@ -331,10 +335,10 @@ __device__ __forceinline__ void convert(const Operand& o, int k0, const float* r
       }
     }
     float4 h, l;
-    split4(v, h, l);
+    split4<kSplit>(v, h, l);
     const unsigned off = tile_off(r, kg * 4);
     *reinterpret_cast<float4*>(hi + off) = h;
-    *reinterpret_cast<float4*>(lo + off) = l;
+    if (kSplit) *reinterpret_cast<float4*>(lo + off) = l;
   }
 }
 
@@ -377,7 +381,7 @@ __host__ __device__ constexpr size_t smem_bytes_for(int n_tile) {
          (size_t)(kPreB ? 2 * kPreStages : 2 * 2 + kRawStages) * n_tile * kChunkK * 4 + 64;
 }
 
-template <int kEpi, bool kPreB>
+template <int kEpi, bool kPreB, bool kSplit>
 __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
   extern __shared__ __align__(1024) char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -467,11 +471,13 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
       *abort_flag = 1;
     if (kPreB && tid == 0 && c + 1 < nchunks) issue_pre_b(c + 1);
     char* const ahi = a_tiles + ts * 2 * a_part;
-    convert(opa, kbeg + c * kChunkK, reinterpret_cast<const float*>(raw_a + rs * a_part), tid, ahi,
+    convert<kSplit>(opa, kbeg + c * kChunkK, reinterpret_cast<const float*>(raw_a + rs * a_part),
+                    tid, ahi,
             ahi + a_part);
     char* const bhi = b_tiles + (kPreB ? c % kPreStages : ts) * 2 * b_part;
     if (!kPreB)
-      convert(opb, kbeg + c * kChunkK, reinterpret_cast<const float*>(raw_b + rs * b_part), tid,
+      convert<kSplit>(opb, kbeg + c * kChunkK,
+                      reinterpret_cast<const float*>(raw_b + rs * b_part), tid,
               bhi, bhi + b_part);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     cp_async_wait<kRawStages - 2>();              // this thread's copies of chunk c + 1 landed
@@ -496,7 +502,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
           const uint64_t bh = smem_desc(smem_addr(bhi) + koff);
           const uint64_t bl = smem_desc(smem_addr(bhi + b_part) + koff);
           mma_tf32(tmem, ah, bh, idesc, c > 0 || ks > 0);
-          if (g.split_tf32) {
+          if (kSplit) {
             mma_tf32(tmem, ah, bl, idesc, true);
             mma_tf32(tmem, al, bh, idesc, true);
           }
@@ -875,34 +881,42 @@ size_t mlp_smem_bytes(int n_tile, bool pre_b) {
 }
 
 namespace {
-template <int kEpi, bool kPreB>
+template <int kEpi, bool kPreB, bool kSplit>
 cudaError_t allow_smem() {
-  return cudaFuncSetAttribute(mlp_gemm_kernel<kEpi, kPreB>,
+  return cudaFuncSetAttribute(mlp_gemm_kernel<kEpi, kPreB, kSplit>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_bytes_for<kPreB>(kMaxTileN));
 }
-template <bool kPreB>
+template <bool kPreB, bool kSplit>
 cudaError_t allow_smem_all() {
-  cudaError_t e = allow_smem<EPI_PLAIN, kPreB>();
-  if (e == cudaSuccess) e = allow_smem<EPI_BIAS, kPreB>();
-  if (e == cudaSuccess) e = allow_smem<EPI_BIAS_ELU, kPreB>();
-  if (e == cudaSuccess) e = allow_smem<EPI_DELU_SUM, kPreB>();
-  if (e == cudaSuccess) e = allow_smem<EPI_ELU, kPreB>();
+  cudaError_t e = allow_smem<EPI_PLAIN, kPreB, kSplit>();
+  if (e == cudaSuccess) e = allow_smem<EPI_BIAS, kPreB, kSplit>();
+  if (e == cudaSuccess) e = allow_smem<EPI_BIAS_ELU, kPreB, kSplit>();
+  if (e == cudaSuccess) e = allow_smem<EPI_DELU_SUM, kPreB, kSplit>();
+  if (e == cudaSuccess) e = allow_smem<EPI_ELU, kPreB, kSplit>();
   return e;
+}
+template <bool kPreB, bool kSplit>
+void launch_epi2(const MlpGemmArgs& g, dim3 grid, size_t smem, cudaStream_t s) {
+  if (g.act_y) mlp_gemm_kernel<EPI_DELU_SUM, kPreB, kSplit><<<grid, kMlpThreads, smem, s>>>(g);
+  else if (g.bias && g.elu)
+    mlp_gemm_kernel<EPI_BIAS_ELU, kPreB, kSplit><<<grid, kMlpThreads, smem, s>>>(g);
+  else if (g.bias) mlp_gemm_kernel<EPI_BIAS, kPreB, kSplit><<<grid, kMlpThreads, smem, s>>>(g);
+  else if (g.elu) mlp_gemm_kernel<EPI_ELU, kPreB, kSplit><<<grid, kMlpThreads, smem, s>>>(g);
+  else mlp_gemm_kernel<EPI_PLAIN, kPreB, kSplit><<<grid, kMlpThreads, smem, s>>>(g);
 }
 template <bool kPreB>
 void launch_epi(const MlpGemmArgs& g, dim3 grid, size_t smem, cudaStream_t s) {
-  if (g.act_y) mlp_gemm_kernel<EPI_DELU_SUM, kPreB><<<grid, kMlpThreads, smem, s>>>(g);
-  else if (g.bias && g.elu) mlp_gemm_kernel<EPI_BIAS_ELU, kPreB><<<grid, kMlpThreads, smem, s>>>(g);
-  else if (g.bias) mlp_gemm_kernel<EPI_BIAS, kPreB><<<grid, kMlpThreads, smem, s>>>(g);
-  else if (g.elu) mlp_gemm_kernel<EPI_ELU, kPreB><<<grid, kMlpThreads, smem, s>>>(g);
-  else mlp_gemm_kernel<EPI_PLAIN, kPreB><<<grid, kMlpThreads, smem, s>>>(g);
+  if (g.split_tf32) launch_epi2<kPreB, true>(g, grid, smem, s);
+  else launch_epi2<kPreB, false>(g, grid, smem, s);
 }
 }  // namespace
 
 cudaError_t prepare_mlp_kernels() {
-  cudaError_t e = allow_smem_all<false>();
-  if (e == cudaSuccess) e = allow_smem_all<true>();
+  cudaError_t e = allow_smem_all<false, true>();
+  if (e == cudaSuccess) e = allow_smem_all<true, true>();
+  if (e == cudaSuccess) e = allow_smem_all<false, false>();
+  if (e == cudaSuccess) e = allow_smem_all<true, false>();
   return e;
 }
 
