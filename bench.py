@@ -598,6 +598,11 @@ def roofline(kernel_name, flops_launch, bytes_launch, ms_per_launch, props, peak
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
             "traffic": profiled_traffic(kernel_name) if profiled else None,
+            # bytes the kernel wrote into L2 (ncu lts__t_sectors_op_write x 32):
+            # DRAM writes undercount them when written lines are still in L2
+            # as the kernel ends
+            "l2_write_bytes": (profiled_counter(kernel_name, "l2_write_bytes_per_launch")
+                               if profiled else None),
             "fma_probe_tflops": fma, "frac_of_fma_probe": achieved / fma,
             "kernel": kernel_name,
             "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s max SM clock)"
@@ -942,7 +947,8 @@ def _compact_adjoint(g):
     out = {k: g[k] for k in keep if k in g}
     out["roofline"] = {k: g["roofline"][k] for k in ("bound", "achieved", "peak", "unit", "frac",
                                                      "frac_of_fma_probe", "kernel",
-                                                     "flops_per_launch", "traffic")}
+                                                     "flops_per_launch", "traffic",
+                                                     "l2_write_bytes")}
     return out
 
 
