@@ -86,11 +86,15 @@ def test_profile_counters_only_for_the_profiled_launch():
     peaks = {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0}
     bench._FMA_RATE["v"] = 78.0          # no GPU here: a stand-in for the probe
     r = bench.roofline("step_kernel", 1.5e9, 1.3e8, 0.12, P, peaks, "measured", profiled=False)
-    assert r["traffic"] is None and r["executed_tflops"] is None
+    assert r["traffic"] is None and r["executed_tflops"] is None and r["l2_write_bytes"] is None
     assert np.isclose(r["peak"], 152 * 128 * 2 * 2070e6 / 1e12)
     assert np.isclose(r["frac"], 1.5e9 / 0.12e-3 / 1e12 / r["peak"])
     r = bench.roofline("step_kernel", 1.5e9, 1.3e8, 0.12, P, peaks, "measured", profiled=True)
     if bench.profiled_traffic("step_kernel") is not None:      # summary matches the sources
         assert r["traffic"] == bench.profiled_traffic("step_kernel")
         assert r["executed_tflops"] > 0
+        # the L2 write sectors: at least the DRAM writes, at most all L2 sector traffic
+        assert r["l2_write_bytes"] == bench.profiled_counter("step_kernel",
+                                                             "l2_write_bytes_per_launch")
+        assert r["l2_write_bytes"] > 0
     bench._FMA_RATE.clear()
