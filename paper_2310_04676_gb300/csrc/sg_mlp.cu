@@ -34,7 +34,10 @@
 // the mbarrier of the MMAs that read it has completed (bounded wait).  The
 // epilogue reads the accumulator with tcgen05.ld (warps w and w + 4 share
 // the TMEM lanes 32 (w % 4) .., taking alternate 16-column blocks), applies
-// the epilogue and stores whole row segments.
+// the epilogue and stores whole row segments.  Products with pre-split
+// weights and at least two chunks run persistent CTAs (about two per SM)
+// that take the output tiles in turn, the copies of a tile's first chunks
+// overlapping the previous tile's epilogue.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -386,7 +389,10 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
   extern __shared__ __align__(1024) char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Nt = g.n_tile;                         // multiple of 16, <= 128
-  const int m0 = blockIdx.x * kTileM, n0 = blockIdx.y * Nt;
+  // output tiles, row-major (consecutive tiles share A's rows); this CTA
+  // takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int tiles_n = (g.N + Nt - 1) / Nt;
+  const int ntiles = ((g.M + kTileM - 1) / kTileM) * tiles_n;
   const int kbeg = blockIdx.z * g.k_per_split;
   const int kend = min(g.K, kbeg + g.k_per_split);
   const int a_part = kTileM * kChunkK * 4, b_part = Nt * kChunkK * 4;
@@ -418,19 +424,37 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
   const uint32_t idesc = instr_desc(kTileM, Nt);
 
   const int nchunks = kbeg < kend ? (kend - kbeg + kChunkK - 1) / kChunkK : 0;
-  const Operand opa = make_operand(g.A, g.a_m, g.a_k, g.M, g.K, m0, kTileM);
-  const Operand opb = make_operand(g.B, g.b_n, g.b_k, g.N, g.K, n0, Nt);
-  const Loader la = make_loader(opa, tid);
+  auto tile_m0 = [&](int t) { return (t / tiles_n) * kTileM; };
+  auto tile_n0 = [&](int t) { return (t % tiles_n) * Nt; };
+  int tile = blockIdx.x;
+  // the chunk pipeline runs across this CTA's tiles (chunk G of the CTA's
+  // stream: stage G & 1, raw stage G % 3, barriers G % 3): the copies of the
+  // next tile's first two chunks start during the current tile's last two,
+  // and so overlap its epilogue.  A tile boundary is crossed at most once by
+  // a two-chunk lookahead only with two or more chunks per tile; shorter
+  // products take one tile per CTA (the launcher's grid).
+  int nxt = tile + (int)gridDim.x;
+  bool has_next = kPreB && nxt < ntiles && nchunks >= 2;   // the launcher's persistent grids
+  Operand opa = make_operand(g.A, g.a_m, g.a_k, g.M, g.K, tile_m0(tile), kTileM);
+  const Operand opb = make_operand(g.B, g.b_n, g.b_k, g.N, g.K, tile_n0(tile), Nt);
+  Loader la = make_loader(opa, tid);
   Loader lb{};
   if (!kPreB) lb = make_loader(opb, tid);
+  Operand opa_n = opa;
+  Loader la_n = la;
+  if (has_next) {
+    opa_n = make_operand(g.A, g.a_m, g.a_k, g.M, g.K, tile_m0(nxt), kTileM);
+    la_n = make_loader(opa_n, tid);
+  }
   const unsigned raw_a_s = smem_addr(raw_a), raw_b_s = smem_addr(raw_b);
   // thread 0's account of the pre-split B copies and of the MMA commits
   int b_issued = 0, b_waited = 0, committed = 0;
-  auto issue_pre_b = [&](int c) {
-    uint64_t* full = bars + kMmaBars + c % kPreStages;
-    char* dst = b_tiles + (c % kPreStages) * 2 * b_part;
+  // B of stream chunk G: chunk c of the tile at column n0x
+  auto issue_pre_b = [&](int G, int n0x, int c) {
+    uint64_t* full = bars + kMmaBars + G % kPreStages;
+    char* dst = b_tiles + (G % kPreStages) * 2 * b_part;
     const float* src = g.b_pre + (long long)(kbeg / kChunkK + c) * 2 * g.b_npad * kChunkK +
-                       (long long)n0 * kChunkK;
+                       (long long)n0x * kChunkK;
     mbar_expect_tx(full, 2u * b_part);
     bulk_copy(dst, src, b_part, full);
     bulk_copy(dst + b_part, src + (long long)g.b_npad * kChunkK, b_part, full);
@@ -448,192 +472,222 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
     }
     cp_async_commit();
   }
-  if (kPreB && tid == 0 && nchunks > 0) issue_pre_b(0);
+  if (kPreB && tid == 0 && nchunks > 0) issue_pre_b(0, tile_n0(tile), 0);
   cp_async_wait<kRawStages - 2>();
   __syncthreads();
-  // One CTA barrier per chunk: after it, chunk c's tiles are split (every
-  // thread) and chunk c + 1's raw copies have landed; thread 0 then issues
-  // chunk c's MMAs while the others go on to split chunk c + 1.
-  for (int c = 0; c < nchunks; ++c) {
-    const int ts = c & 1, rs = c % kRawStages;
-    {
-      // the raw stage of chunk c + 2 held chunk c - 1, split before the last barrier
-      const int cn = c + kRawStages - 1;
-      if (cn < nchunks) {
-        raw_issue(opa, la, kbeg + cn * kChunkK, raw_a_s + (cn % kRawStages) * a_part);
-        if (!kPreB) raw_issue(opb, lb, kbeg + cn * kChunkK, raw_b_s + (cn % kRawStages) * b_part);
+  int G0 = 0;                                     // stream index of the tile's chunk 0
+  for (;;) {
+    const int m0 = tile_m0(tile), n0 = tile_n0(tile);
+    // One CTA barrier per chunk: after it, chunk c's tiles are split (every
+    // thread) and chunk c + 1's raw copies have landed; thread 0 then issues
+    // chunk c's MMAs while the others go on to split chunk c + 1.
+    for (int c = 0; c < nchunks; ++c) {
+      const int G = G0 + c, ts = G & 1, rs = G % kRawStages;
+      {
+        // the raw stage of chunk G + 2 held chunk G - 1, split before the last barrier
+        const int cn = c + kRawStages - 1, Gn = G + kRawStages - 1;
+        if (cn < nchunks) {
+          raw_issue(opa, la, kbeg + cn * kChunkK, raw_a_s + (Gn % kRawStages) * a_part);
+          if (!kPreB)
+            raw_issue(opb, lb, kbeg + cn * kChunkK, raw_b_s + (Gn % kRawStages) * b_part);
+        } else if (has_next) {
+          raw_issue(opa_n, la_n, kbeg + (cn - nchunks) * kChunkK,
+                    raw_a_s + (Gn % kRawStages) * a_part);
+        }
+        cp_async_commit();
       }
-      cp_async_commit();
-    }
-    // the tiles of stage ts (and the B stage of chunk c + 1) were read by
-    // the MMAs of chunk c - 2
-    if (c >= 2 && !mbar_wait(bars + (c - 2) % kMmaBars, (unsigned)((c - 2) / kMmaBars) & 1u))
-      *abort_flag = 1;
-    if (kPreB && tid == 0 && c + 1 < nchunks) issue_pre_b(c + 1);
-    char* const ahi = a_tiles + ts * 2 * a_part;
-    convert<kSplit>(opa, kbeg + c * kChunkK, reinterpret_cast<const float*>(raw_a + rs * a_part),
-                    tid, ahi,
-            ahi + a_part);
-    char* const bhi = b_tiles + (kPreB ? c % kPreStages : ts) * 2 * b_part;
-    if (!kPreB)
-      convert<kSplit>(opb, kbeg + c * kChunkK,
-                      reinterpret_cast<const float*>(raw_b + rs * b_part), tid,
-              bhi, bhi + b_part);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    cp_async_wait<kRawStages - 2>();              // this thread's copies of chunk c + 1 landed
-    __syncthreads();
-    if (*abort_flag) {
-      ok = false;
-      break;
-    }
-    if (tid == 0) {
-      bool bok = true;
-      if (kPreB) {
-        bok = mbar_wait(bars + kMmaBars + c % kPreStages, (unsigned)(c / kPreStages) & 1u);
-        if (bok) ++b_waited;
+      // the tiles of stage ts (and the B stage of chunk G + 1) were read by
+      // the MMAs of chunk G - 2
+      if (G >= 2 && !mbar_wait(bars + (G - 2) % kMmaBars, (unsigned)((G - 2) / kMmaBars) & 1u))
+        *abort_flag = 1;
+      if (kPreB && tid == 0) {
+        if (c + 1 < nchunks) issue_pre_b(G + 1, n0, c + 1);
+        else if (has_next) issue_pre_b(G + 1, tile_n0(nxt), 0);
       }
-      if (bok) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      char* const ahi = a_tiles + ts * 2 * a_part;
+      convert<kSplit>(opa, kbeg + c * kChunkK, reinterpret_cast<const float*>(raw_a + rs * a_part),
+                      tid, ahi, ahi + a_part);
+      char* const bhi = b_tiles + (kPreB ? G % kPreStages : ts) * 2 * b_part;
+      if (!kPreB)
+        convert<kSplit>(opb, kbeg + c * kChunkK,
+                        reinterpret_cast<const float*>(raw_b + rs * b_part), tid, bhi,
+                        bhi + b_part);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      cp_async_wait<kRawStages - 2>();            // this thread's copies of chunk G + 1 landed
+      __syncthreads();
+      if (*abort_flag) {
+        ok = false;
+        break;
+      }
+      if (tid == 0) {
+        bool bok = true;
+        if (kPreB) {
+          bok = mbar_wait(bars + kMmaBars + G % kPreStages, (unsigned)(G / kPreStages) & 1u);
+          if (bok) ++b_waited;
+        }
+        if (bok) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int ks = 0; ks < kChunkK / 8; ++ks) {
-          const unsigned koff = (unsigned)ks * 2 * kLbo;   // two core matrices per K step
-          const uint64_t ah = smem_desc(smem_addr(ahi) + koff);
-          const uint64_t al = smem_desc(smem_addr(ahi + a_part) + koff);
-          const uint64_t bh = smem_desc(smem_addr(bhi) + koff);
-          const uint64_t bl = smem_desc(smem_addr(bhi + b_part) + koff);
-          mma_tf32(tmem, ah, bh, idesc, c > 0 || ks > 0);
-          if (kSplit) {
-            mma_tf32(tmem, ah, bl, idesc, true);
-            mma_tf32(tmem, al, bh, idesc, true);
+          for (int ks = 0; ks < kChunkK / 8; ++ks) {
+            const unsigned koff = (unsigned)ks * 2 * kLbo;   // two core matrices per K step
+            const uint64_t ah = smem_desc(smem_addr(ahi) + koff);
+            const uint64_t al = smem_desc(smem_addr(ahi + a_part) + koff);
+            const uint64_t bh = smem_desc(smem_addr(bhi) + koff);
+            const uint64_t bl = smem_desc(smem_addr(bhi + b_part) + koff);
+            mma_tf32(tmem, ah, bh, idesc, c > 0 || ks > 0);
+            if (kSplit) {
+              mma_tf32(tmem, ah, bl, idesc, true);
+              mma_tf32(tmem, al, bh, idesc, true);
+            }
+          }
+          mma_commit(bars + G % kMmaBars);
+          ++committed;
+        } else {
+          *abort_flag = 1;
+        }
+      }
+    }
+    if (!ok) break;
+    G0 += nchunks;
+    // the tile's accumulator is complete once its last chunk's commit is
+    if (nchunks > 0)
+      ok = __syncthreads_and(
+          mbar_wait(bars + (G0 - 1) % kMmaBars, (unsigned)((G0 - 1) / kMmaBars) & 1u));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) break;
+
+    if (nchunks > 0) {
+      // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (its rows m0 + 32 (w % 4)
+      // + lane) and the 16-column blocks of parity w / 4.  Per block each
+      // thread finishes its row's values (bias, ELU, or the ELU derivative of
+      // the layer below) and parks them in a shared-memory slab of the warp
+      // (row pitch 20 floats; the slabs overlap the split tiles, which no
+      // copy writes and no MMA reads at this point).  From the slab the warp
+      // sums the columns (lane l: column l % 16 over 16 rows, then the two
+      // halves; fixed order) into the partials of its lane quarter, and
+      // stores whole 64-byte row segments, four lanes per row, eight rows
+      // per instruction (scalar stores at ragged edges or unaligned
+      // outputs).  After the last block the four lane quarters' partials are
+      // added in order (per 128-row tile of the output).
+      const int lq = warp & 3, half = warp >> 2;
+      const int m = m0 + lq * 32 + lane;
+      const bool mrow = m < g.M;
+      float* cbase = g.C + (long long)blockIdx.z * g.c_split;
+      float* slab = reinterpret_cast<float*>(sm) + warp * 32 * 20;
+      float* wsum = reinterpret_cast<float*>(sm) + 8 * 32 * 20;          // [4][128]
+      const bool cvec = (g.c_m & 3) == 0 && (reinterpret_cast<uintptr_t>(cbase) & 15) == 0;
+      const bool yvec = kEpi == EPI_DELU_SUM && (g.c_m & 3) == 0 &&
+                        (reinterpret_cast<uintptr_t>(g.act_y) & 15) == 0;
+      const bool bvec = (reinterpret_cast<uintptr_t>(g.bias + n0) & 15) == 0;
+      for (int c = 16 * half; c < Nt; c += 32) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)c, v);
+        const int ncol = min(16, g.N - (n0 + c));
+        if (kEpi == EPI_DELU_SUM) {
+          float y[16];
+          const float* yr = g.act_y + (long long)m * g.c_m + n0 + c;
+          if (yvec && mrow && ncol == 16) {
+  #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float4 t = __ldg(reinterpret_cast<const float4*>(yr) + q);
+              y[4 * q] = t.x;
+              y[4 * q + 1] = t.y;
+              y[4 * q + 2] = t.z;
+              y[4 * q + 3] = t.w;
+            }
+          } else {
+  #pragma unroll
+            for (int j = 0; j < 16; ++j) y[j] = (mrow && j < ncol) ? yr[j] : 0.f;
+          }
+  #pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] *= y[j] > 0.f ? 1.f : y[j] + 1.f;
+        }
+        if (kEpi == EPI_BIAS || kEpi == EPI_BIAS_ELU) {
+          if (ncol == 16 && bvec) {
+  #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float4 t = __ldg(reinterpret_cast<const float4*>(g.bias + n0 + c) + q);
+              v[4 * q] += t.x;
+              v[4 * q + 1] += t.y;
+              v[4 * q + 2] += t.z;
+              v[4 * q + 3] += t.w;
+            }
+          } else {
+  #pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] += j < ncol ? __ldg(g.bias + n0 + c + j) : 0.f;
           }
         }
-        mma_commit(bars + c % kMmaBars);
-        ++committed;
-      } else {
-        *abort_flag = 1;
+        if (kEpi == EPI_BIAS_ELU || kEpi == EPI_ELU) {
+  #pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = elu_fast(v[j]);
+        }
+        if (kEpi == EPI_DELU_SUM) {
+          // rows and columns outside C add nothing to the column sums
+  #pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = (mrow && j < ncol) ? v[j] : 0.f;
+        }
+  #pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<float4*>(slab + lane * 20 + 4 * q) =
+              make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        __syncwarp();
+        if (kEpi == EPI_DELU_SUM) {
+          const int col = lane & 15, r0 = (lane >> 4) * 16;
+          float t = 0.f;
+  #pragma unroll
+          for (int r = 0; r < 16; ++r) t += slab[(r0 + r) * 20 + col];
+          t += __shfl_xor_sync(0xffffffffu, t, 16);
+          if (lane < 16) wsum[lq * kMaxTileN + c + lane] = t;
+        }
+        if (cvec && ncol == 16) {
+  #pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int rr = 8 * i + (lane >> 2), qq = lane & 3;
+            const int mr = m0 + lq * 32 + rr;
+            if (mr < g.M)
+              *reinterpret_cast<float4*>(cbase + (long long)mr * g.c_m + n0 + c + 4 * qq) =
+                  *reinterpret_cast<const float4*>(slab + rr * 20 + 4 * qq);
+          }
+        } else if (mrow) {
+  #pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (j < ncol) cbase[(long long)m * g.c_m + n0 + c + j] = v[j];
+        }
+        __syncwarp();
       }
+      if (kEpi == EPI_DELU_SUM) {
+        __syncthreads();
+        for (int n = tid; n < Nt && n0 + n < g.N; n += kMlpThreads)
+          g.colsum[(long long)(m0 / kTileM) * g.N + n0 + n] =
+              ((wsum[n] + wsum[kMaxTileN + n]) + wsum[2 * kMaxTileN + n]) + wsum[3 * kMaxTileN + n];
+      }
+    } else if (g.c_split) {
+      // an empty split contributes zeros to the partial sums: thread t takes
+      // row m0 + t % 128 and every other column from n0 + t / 128
+      const int m = m0 + (tid & (kTileM - 1));
+      if (m < g.M) {
+        float* crow = g.C + (long long)blockIdx.z * g.c_split + (long long)m * g.c_m;
+        for (int n = n0 + tid / kTileM; n < min(g.N, n0 + Nt); n += kMlpThreads / kTileM)
+          crow[n] = 0.f;
+      }
+    }
+    if (!has_next) break;
+    // the next tile's MMAs overwrite the accumulator and its splits reuse the
+    // slabs' shared memory: every thread done with both first
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tile = nxt;
+    opa = opa_n;
+    la = la_n;
+    nxt = tile + (int)gridDim.x;
+    has_next = kPreB && nxt < ntiles;
+    if (has_next) {
+      opa_n = make_operand(g.A, g.a_m, g.a_k, g.M, g.K, tile_m0(nxt), kTileM);
+      la_n = make_loader(opa_n, tid);
     }
   }
   cp_async_wait<0>();
-  // every MMA has completed once the last chunk's commit has
-  if (ok && nchunks > 0)
-    ok = __syncthreads_and(
-        mbar_wait(bars + (nchunks - 1) % kMmaBars, (unsigned)((nchunks - 1) / kMmaBars) & 1u));
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-  if (ok && nchunks > 0) {
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (its rows m0 + 32 (w % 4)
-    // + lane) and the 16-column blocks of parity w / 4.  Per block each
-    // thread finishes its row's values (bias, ELU, or the ELU derivative of
-    // the layer below) and parks them in a shared-memory slab of the warp
-    // (row pitch 20 floats).  From the slab the warp sums the columns (lane
-    // l: column l % 16 over 16 rows, then the two halves; fixed order) into
-    // the partials of its lane quarter, and stores whole 64-byte row
-    // segments, four lanes per row, eight rows per instruction (scalar
-    // stores at ragged edges or unaligned outputs).  After the last block the
-    // four lane quarters' partials are added in order.
-    const int lq = warp & 3, half = warp >> 2;
-    const int m = m0 + lq * 32 + lane;
-    const bool mrow = m < g.M;
-    float* cbase = g.C + (long long)blockIdx.z * g.c_split;
-    float* slab = reinterpret_cast<float*>(sm) + warp * 32 * 20;
-    float* wsum = reinterpret_cast<float*>(sm) + 8 * 32 * 20;          // [4][128]
-    const bool cvec = (g.c_m & 3) == 0 && (reinterpret_cast<uintptr_t>(cbase) & 15) == 0;
-    const bool yvec = kEpi == EPI_DELU_SUM && (g.c_m & 3) == 0 &&
-                      (reinterpret_cast<uintptr_t>(g.act_y) & 15) == 0;
-    const bool bvec = (reinterpret_cast<uintptr_t>(g.bias + n0) & 15) == 0;
-    for (int c = 16 * half; c < Nt; c += 32) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)c, v);
-      const int ncol = min(16, g.N - (n0 + c));
-      if (kEpi == EPI_DELU_SUM) {
-        float y[16];
-        const float* yr = g.act_y + (long long)m * g.c_m + n0 + c;
-        if (yvec && mrow && ncol == 16) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 t = __ldg(reinterpret_cast<const float4*>(yr) + q);
-            y[4 * q] = t.x;
-            y[4 * q + 1] = t.y;
-            y[4 * q + 2] = t.z;
-            y[4 * q + 3] = t.w;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) y[j] = (mrow && j < ncol) ? yr[j] : 0.f;
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] *= y[j] > 0.f ? 1.f : y[j] + 1.f;
-      }
-      if (kEpi == EPI_BIAS || kEpi == EPI_BIAS_ELU) {
-        if (ncol == 16 && bvec) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 t = __ldg(reinterpret_cast<const float4*>(g.bias + n0 + c) + q);
-            v[4 * q] += t.x;
-            v[4 * q + 1] += t.y;
-            v[4 * q + 2] += t.z;
-            v[4 * q + 3] += t.w;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] += j < ncol ? __ldg(g.bias + n0 + c + j) : 0.f;
-        }
-      }
-      if (kEpi == EPI_BIAS_ELU || kEpi == EPI_ELU) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = elu_fast(v[j]);
-      }
-      if (kEpi == EPI_DELU_SUM) {
-        // rows and columns outside C add nothing to the column sums
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = (mrow && j < ncol) ? v[j] : 0.f;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<float4*>(slab + lane * 20 + 4 * q) =
-            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-      __syncwarp();
-      if (kEpi == EPI_DELU_SUM) {
-        const int col = lane & 15, r0 = (lane >> 4) * 16;
-        float t = 0.f;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) t += slab[(r0 + r) * 20 + col];
-        t += __shfl_xor_sync(0xffffffffu, t, 16);
-        if (lane < 16) wsum[lq * kMaxTileN + c + lane] = t;
-      }
-      if (cvec && ncol == 16) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int rr = 8 * i + (lane >> 2), qq = lane & 3;
-          const int mr = m0 + lq * 32 + rr;
-          if (mr < g.M)
-            *reinterpret_cast<float4*>(cbase + (long long)mr * g.c_m + n0 + c + 4 * qq) =
-                *reinterpret_cast<const float4*>(slab + rr * 20 + 4 * qq);
-        }
-      } else if (mrow) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (j < ncol) cbase[(long long)m * g.c_m + n0 + c + j] = v[j];
-      }
-      __syncwarp();
-    }
-    if (kEpi == EPI_DELU_SUM) {
-      __syncthreads();
-      for (int n = tid; n < Nt && n0 + n < g.N; n += kMlpThreads)
-        g.colsum[(long long)blockIdx.x * g.N + n0 + n] =
-            ((wsum[n] + wsum[kMaxTileN + n]) + wsum[2 * kMaxTileN + n]) + wsum[3 * kMaxTileN + n];
-    }
-  } else if (nchunks == 0 && g.c_split) {
-    // an empty split contributes zeros to the partial sums: thread t takes
-    // row m0 + t % 128 and every other column from n0 + t / 128
-    const int m = m0 + (tid & (kTileM - 1));
-    if (m < g.M) {
-      float* crow = g.C + (long long)blockIdx.z * g.c_split + (long long)m * g.c_m;
-      for (int n = n0 + tid / kTileM; n < min(g.N, n0 + Nt); n += kMlpThreads / kTileM)
-        crow[n] = 0.f;
-    }
-  }
   if (!ok) {
     if (tid == 0) {
       if (g.err) atomicOr(g.err, DEVERR_TIMEOUT);
@@ -994,7 +1048,16 @@ cudaError_t launch_mlp_gemm(const MlpGemmArgs& a, cudaStream_t s) {
         (reinterpret_cast<uintptr_t>(g.b_pre) & 15) || (splits > 1 && g.k_per_split % kChunkK))
       return cudaErrorInvalidValue;
   }
-  dim3 grid((a.M + kTileM - 1) / kTileM, (a.N + g.n_tile - 1) / g.n_tile, splits);
+  // tiles in one dimension; products with pre-split weights and two or more
+  // chunks per tile run persistent CTAs (about two per SM) that take the
+  // tiles in turn, the others one CTA per tile
+  const long long ntiles =
+      (long long)((a.M + kTileM - 1) / kTileM) * ((a.N + g.n_tile - 1) / g.n_tile);
+  const int kchunks = (g.k_per_split + kChunkK - 1) / kChunkK;
+  const long long ctas = (pre && splits == 1 && kchunks >= 2) ? std::min<long long>(ntiles, 2 * 152)
+                                                             : ntiles;
+  if (ctas > 0x7fffffffLL) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)ctas, 1, splits);
   const size_t smem = mlp_smem_bytes(g.n_tile, pre);
   if (pre) launch_epi<true>(g, grid, smem, s);
   else launch_epi<false>(g, grid, smem, s);

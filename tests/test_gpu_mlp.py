@@ -83,6 +83,24 @@ def test_forward_layer(rows, inp, out, presplit):
     _check(Y, X.double(), W.double(), None, True)
 
 
+@pytest.mark.parametrize("rows,inp,out", [(70001, 28, 256), (65537, 256, 128), (40000, 128, 64)])
+def test_forward_persistent_tiles(rows, inp, out):
+    """More output tiles than persistent CTAs (pre-split weights): each CTA
+    takes several tiles in turn, the next tile's first chunks copied during
+    the current tile's epilogue; a sample of rows, the first and the last
+    (ragged) tile against FP64."""
+    X, W, b = _rand((rows, inp), 21), _rand((out, inp), 22), _rand((out,), 23)
+    Y = torch.empty(rows, out, device="cuda")
+    work = torch.empty(_presplit_floats(out, inp), device="cuda")
+    sg.mlp_gemm(X.cuda(), (inp, 1), W.cuda(), (inp, 1), rows, out, inp, Y, out, bias=b.cuda(),
+                elu=True, work=work)
+    torch.cuda.synchronize()
+    g = torch.Generator().manual_seed(24)
+    idx = torch.cat([torch.randperm(rows, generator=g)[:3000], torch.arange(128),
+                     torch.arange(rows - 200, rows)])
+    _check(Y.cpu()[idx], X.double()[idx], W.double(), b, True)
+
+
 @pytest.mark.parametrize("rows,inp,out", [(40000, 256, 128), (39000, 64, 8), (38913, 128, 64)])
 def test_input_gradient_presplit(rows, inp, out):
     """Enough row tiles that the library splits B = W^T once into the work
