@@ -21,16 +21,17 @@
 // about 2^-22 of a b, so the products carry FP32 accuracy with FP32
 // accumulation (the published "3xTF32" emulation of FP32 matrix products).
 //
-// One CTA of 256 threads computes a 128 x Nt tile (Nt <= 128, a multiple of
-// 16).  Raw FP32 operand chunks (16 wide in K) travel to shared memory by
-// asynchronous copies two chunks ahead; each chunk is then split into its
-// TF32 parts and stored in the tensor cores' K-major layout without swizzle
-// (8-row x 16-byte core matrices), or, for pre-split weights, arrives
-// already split by bulk copies.  One CTA barrier per chunk; after it one
-// thread issues, per 8-wide K step, the three tcgen05.mma of kind::tf32 into
-// an FP32 accumulator in tensor memory (TMEM lane = row, column = n) and
-// commits them to an mbarrier, while the other threads split the next
-// chunk; two tensor-core stages alternate, a stage being refilled only after
+// One CTA computes a 128 x Nt tile (Nt <= 128, a multiple of 16): eight
+// warps copy, split and drain; lane 0 of a ninth warp issues the bulk copies
+// of pre-split weights and the MMAs.  Raw FP32 operand chunks (16 wide in K)
+// travel to shared memory by asynchronous copies two chunks ahead; each
+// chunk is then split into its TF32 parts and stored in the tensor cores'
+// K-major layout without swizzle (8-row x 16-byte core matrices), or, for
+// pre-split weights, arrives already split by bulk copies.  One CTA barrier
+// per chunk; after it the issuing lane issues, per 8-wide K step, the three
+// tcgen05.mma of kind::tf32 into an FP32 accumulator in tensor memory (TMEM
+// lane = row, column = n) and commits them to an mbarrier, while the eight
+// warps split the next chunk; two tensor-core stages alternate, a stage being refilled only after
 // the mbarrier of the MMAs that read it has completed (bounded wait).  The
 // epilogue reads the accumulator with tcgen05.ld (warps w and w + 4 share
 // the TMEM lanes 32 (w % 4) .., taking alternate 16-column blocks), applies
@@ -51,7 +52,8 @@
 namespace sg {
 namespace {
 
-constexpr int kMlpThreads = 256;
+constexpr int kMlpThreads = 256;                  // threads that copy, split and drain
+constexpr int kMlpBlock = kMlpThreads + 32;       // ... plus one warp that issues the MMAs
 constexpr int kTileM = 128;
 constexpr int kChunkK = 16;                       // K per shared-memory chunk (2 MMA K-steps)
 constexpr int kCoreBytes = 128;                   // one core matrix: 8 rows x 16 bytes
@@ -385,9 +387,12 @@ __host__ __device__ constexpr size_t smem_bytes_for(int n_tile) {
 }
 
 template <int kEpi, bool kPreB, bool kSplit>
-__global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
+__global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
   extern __shared__ __align__(1024) char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // warps 0-7 copy and split the operands and drain the accumulator; lane 0
+  // of warp 8 alone issues the pre-split B copies, the MMAs and their commits
+  const bool conv = tid < kMlpThreads, issuer = tid == kMlpThreads;
   const int Nt = g.n_tile;                         // multiple of 16, <= 128
   // output tiles, row-major (consecutive tiles share A's rows); this CTA
   // takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...
@@ -437,17 +442,17 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
   bool has_next = kPreB && nxt < ntiles && nchunks >= 2;   // the launcher's persistent grids
   Operand opa = make_operand(g.A, g.a_m, g.a_k, g.M, g.K, tile_m0(tile), kTileM);
   const Operand opb = make_operand(g.B, g.b_n, g.b_k, g.N, g.K, tile_n0(tile), Nt);
-  Loader la = make_loader(opa, tid);
-  Loader lb{};
-  if (!kPreB) lb = make_loader(opb, tid);
+  Loader la{}, lb{};
+  if (conv) la = make_loader(opa, tid);
+  if (!kPreB && conv) lb = make_loader(opb, tid);
   Operand opa_n = opa;
   Loader la_n = la;
   if (has_next) {
     opa_n = make_operand(g.A, g.a_m, g.a_k, g.M, g.K, tile_m0(nxt), kTileM);
-    la_n = make_loader(opa_n, tid);
+    if (conv) la_n = make_loader(opa_n, tid);
   }
   const unsigned raw_a_s = smem_addr(raw_a), raw_b_s = smem_addr(raw_b);
-  // thread 0's account of the pre-split B copies and of the MMA commits
+  // the issuer's account of the pre-split B copies and of the MMA commits
   int b_issued = 0, b_waited = 0, committed = 0;
   // B of stream chunk G: chunk c of the tile at column n0x
   auto issue_pre_b = [&](int G, int n0x, int c) {
@@ -472,15 +477,15 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
     }
     cp_async_commit();
   }
-  if (kPreB && tid == 0 && nchunks > 0) issue_pre_b(0, tile_n0(tile), 0);
+  if (kPreB && issuer && nchunks > 0) issue_pre_b(0, tile_n0(tile), 0);
   cp_async_wait<kRawStages - 2>();
   __syncthreads();
   int G0 = 0;                                     // stream index of the tile's chunk 0
   for (;;) {
     const int m0 = tile_m0(tile), n0 = tile_n0(tile);
-    // One CTA barrier per chunk: after it, chunk c's tiles are split (every
-    // thread) and chunk c + 1's raw copies have landed; thread 0 then issues
-    // chunk c's MMAs while the others go on to split chunk c + 1.
+    // One CTA barrier per chunk: after it, chunk c's tiles are split (warps
+    // 0-7) and chunk c + 1's raw copies have landed; the issuer then issues
+    // chunk c's MMAs while the other warps go on to split chunk c + 1.
     for (int c = 0; c < nchunks; ++c) {
       const int G = G0 + c, ts = G & 1, rs = G % kRawStages;
       {
@@ -500,18 +505,21 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
       // the MMAs of chunk G - 2
       if (G >= 2 && !mbar_wait(bars + (G - 2) % kMmaBars, (unsigned)((G - 2) / kMmaBars) & 1u))
         *abort_flag = 1;
-      if (kPreB && tid == 0) {
+      if (kPreB && issuer) {
         if (c + 1 < nchunks) issue_pre_b(G + 1, n0, c + 1);
         else if (has_next) issue_pre_b(G + 1, tile_n0(nxt), 0);
       }
       char* const ahi = a_tiles + ts * 2 * a_part;
-      convert<kSplit>(opa, kbeg + c * kChunkK, reinterpret_cast<const float*>(raw_a + rs * a_part),
-                      tid, ahi, ahi + a_part);
       char* const bhi = b_tiles + (kPreB ? G % kPreStages : ts) * 2 * b_part;
-      if (!kPreB)
-        convert<kSplit>(opb, kbeg + c * kChunkK,
-                        reinterpret_cast<const float*>(raw_b + rs * b_part), tid, bhi,
-                        bhi + b_part);
+      if (conv) {
+        convert<kSplit>(opa, kbeg + c * kChunkK,
+                        reinterpret_cast<const float*>(raw_a + rs * a_part), tid, ahi,
+                        ahi + a_part);
+        if (!kPreB)
+          convert<kSplit>(opb, kbeg + c * kChunkK,
+                          reinterpret_cast<const float*>(raw_b + rs * b_part), tid, bhi,
+                          bhi + b_part);
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       cp_async_wait<kRawStages - 2>();            // this thread's copies of chunk G + 1 landed
       __syncthreads();
@@ -519,7 +527,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
         ok = false;
         break;
       }
-      if (tid == 0) {
+      if (issuer) {
         bool bok = true;
         if (kPreB) {
           bok = mbar_wait(bars + kMmaBars + G % kPreStages, (unsigned)(G / kPreStages) & 1u);
@@ -579,7 +587,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
       const bool yvec = kEpi == EPI_DELU_SUM && (g.c_m & 3) == 0 &&
                         (reinterpret_cast<uintptr_t>(g.act_y) & 15) == 0;
       const bool bvec = (reinterpret_cast<uintptr_t>(g.bias + n0) & 15) == 0;
-      for (int c = 16 * half; c < Nt; c += 32) {
+      for (int c = 16 * half; conv && c < Nt; c += 32) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)c, v);
         const int ncol = min(16, g.N - (n0 + c));
@@ -665,7 +673,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
       // an empty split contributes zeros to the partial sums: thread t takes
       // row m0 + t % 128 and every other column from n0 + t / 128
       const int m = m0 + (tid & (kTileM - 1));
-      if (m < g.M) {
+      if (conv && m < g.M) {
         float* crow = g.C + (long long)blockIdx.z * g.c_split + (long long)m * g.c_m;
         for (int n = n0 + tid / kTileM; n < min(g.N, n0 + Nt); n += kMlpThreads / kTileM)
           crow[n] = 0.f;
@@ -684,12 +692,12 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_gemm_kernel(MlpGemmArgs g) {
     has_next = kPreB && nxt < ntiles;
     if (has_next) {
       opa_n = make_operand(g.A, g.a_m, g.a_k, g.M, g.K, tile_m0(nxt), kTileM);
-      la_n = make_loader(opa_n, tid);
+      if (conv) la_n = make_loader(opa_n, tid);
     }
   }
   cp_async_wait<0>();
   if (!ok) {
-    if (tid == 0) {
+    if (issuer) {
       if (g.err) atomicOr(g.err, DEVERR_TIMEOUT);
       // copies and MMAs may still be in flight: wait (bounded) for the
       // outstanding B copies and the last commit before the shared and
@@ -952,12 +960,12 @@ cudaError_t allow_smem_all() {
 }
 template <bool kPreB, bool kSplit>
 void launch_epi2(const MlpGemmArgs& g, dim3 grid, size_t smem, cudaStream_t s) {
-  if (g.act_y) mlp_gemm_kernel<EPI_DELU_SUM, kPreB, kSplit><<<grid, kMlpThreads, smem, s>>>(g);
+  if (g.act_y) mlp_gemm_kernel<EPI_DELU_SUM, kPreB, kSplit><<<grid, kMlpBlock, smem, s>>>(g);
   else if (g.bias && g.elu)
-    mlp_gemm_kernel<EPI_BIAS_ELU, kPreB, kSplit><<<grid, kMlpThreads, smem, s>>>(g);
-  else if (g.bias) mlp_gemm_kernel<EPI_BIAS, kPreB, kSplit><<<grid, kMlpThreads, smem, s>>>(g);
-  else if (g.elu) mlp_gemm_kernel<EPI_ELU, kPreB, kSplit><<<grid, kMlpThreads, smem, s>>>(g);
-  else mlp_gemm_kernel<EPI_PLAIN, kPreB, kSplit><<<grid, kMlpThreads, smem, s>>>(g);
+    mlp_gemm_kernel<EPI_BIAS_ELU, kPreB, kSplit><<<grid, kMlpBlock, smem, s>>>(g);
+  else if (g.bias) mlp_gemm_kernel<EPI_BIAS, kPreB, kSplit><<<grid, kMlpBlock, smem, s>>>(g);
+  else if (g.elu) mlp_gemm_kernel<EPI_ELU, kPreB, kSplit><<<grid, kMlpBlock, smem, s>>>(g);
+  else mlp_gemm_kernel<EPI_PLAIN, kPreB, kSplit><<<grid, kMlpBlock, smem, s>>>(g);
 }
 template <bool kPreB>
 void launch_epi(const MlpGemmArgs& g, dim3 grid, size_t smem, cudaStream_t s) {
