@@ -152,6 +152,29 @@ sg_status sg_ppo_get_buffer(sg_ppo *ppo, int32_t which, void *dst_dev);
 sg_status sg_ppo_set_buffer(sg_ppo *ppo, int32_t which, const void *src_dev);
 
 /*
+ * Test hook (not part of the method): makes a bounded wait of the
+ * tensor-core contraction run out, so that its give-up path can be
+ * exercised without a GPU fault or hang.  mode:
+ *   SG_FAULT_NONE              normal operation (the default);
+ *   SG_FAULT_SKIP_WEIGHT_COPY  every CTA of a product with pre-split weights
+ *                              (the hidden layers' forward and input-gradient
+ *                              products) leaves out the bulk copy of its first
+ *                              weight chunk, so the issuing thread's wait for
+ *                              it runs out.
+ * wait_limit_ns bounds every wait of the contraction in wall-clock time (0 =
+ * the default, 2 s; at most 2e9).  A wait that runs out sets the env
+ * context's timeout flag (sg_sync_status(env) returns SG_ERR_TIMEOUT); the
+ * CTA then waits, bounded, for its copies and tensor-core operations in
+ * flight, releases its tensor memory and leaves without writing its output
+ * tile, so the outputs of those products -- and whatever the collect or
+ * update computes from them -- are unspecified until the next collect and
+ * update with the hook off.  The collect graph is captured again.
+ * SG_ERR_INVALID_ARG for an unknown mode or a limit out of range.
+ */
+enum { SG_FAULT_SKIP_WEIGHT_COPY = 3 };
+sg_status sg_ppo_debug_set_fault(sg_ppo *ppo, int32_t mode, int64_t wait_limit_ns);
+
+/*
  * The dense contraction of the policy and value networks (Methods, "Policy
  * learning and control": MLPs of 256, 128 and 64 ELU units), exposed as a
  * building block: on `stream` (cudaStream_t, NULL = legacy default stream),

@@ -115,12 +115,13 @@ __device__ __forceinline__ unsigned long long gtimer() {
 }
 
 // Bounded wait for phase `parity` (wall-clock limit, iteration cap).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity,
+                                          unsigned long long limit_ns) {
   if (mbar_poll(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
   for (unsigned it = 0; it < (1u << 24); ++it) {
     if (mbar_poll(bar, parity)) return true;
-    if (gtimer() - t0 > kMmaWaitNs) return false;
+    if (gtimer() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -393,6 +394,7 @@ __global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
   // warps 0-7 copy and split the operands and drain the accumulator; lane 0
   // of warp 8 alone issues the pre-split B copies, the MMAs and their commits
   const bool conv = tid < kMlpThreads, issuer = tid == kMlpThreads;
+  const unsigned long long lim = g.wait_ns ? g.wait_ns : kMmaWaitNs;   // bound of every wait
   const int Nt = g.n_tile;                         // multiple of 16, <= 128
   // output tiles, row-major (consecutive tiles share A's rows); this CTA
   // takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...
@@ -456,6 +458,12 @@ __global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
   int b_issued = 0, b_waited = 0, committed = 0;
   // B of stream chunk G: chunk c of the tile at column n0x
   auto issue_pre_b = [&](int G, int n0x, int c) {
+    if (g.fault && G == 0) {
+      // test hook: the copy of the stream's first weight chunk is left out
+      // (but counted, so that an abort waits for every later copy)
+      ++b_issued;
+      return;
+    }
     uint64_t* full = bars + kMmaBars + G % kPreStages;
     char* dst = b_tiles + (G % kPreStages) * 2 * b_part;
     const float* src = g.b_pre + (long long)(kbeg / kChunkK + c) * 2 * g.b_npad * kChunkK +
@@ -503,7 +511,8 @@ __global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
       }
       // the tiles of stage ts (and the B stage of chunk G + 1) were read by
       // the MMAs of chunk G - 2
-      if (G >= 2 && !mbar_wait(bars + (G - 2) % kMmaBars, (unsigned)((G - 2) / kMmaBars) & 1u))
+      if (G >= 2 &&
+          !mbar_wait(bars + (G - 2) % kMmaBars, (unsigned)((G - 2) / kMmaBars) & 1u, lim))
         *abort_flag = 1;
       if (kPreB && issuer) {
         if (c + 1 < nchunks) issue_pre_b(G + 1, n0, c + 1);
@@ -530,7 +539,7 @@ __global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
       if (issuer) {
         bool bok = true;
         if (kPreB) {
-          bok = mbar_wait(bars + kMmaBars + G % kPreStages, (unsigned)(G / kPreStages) & 1u);
+          bok = mbar_wait(bars + kMmaBars + G % kPreStages, (unsigned)(G / kPreStages) & 1u, lim);
           if (bok) ++b_waited;
         }
         if (bok) {
@@ -560,7 +569,7 @@ __global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
     // the tile's accumulator is complete once its last chunk's commit is
     if (nchunks > 0)
       ok = __syncthreads_and(
-          mbar_wait(bars + (G0 - 1) % kMmaBars, (unsigned)((G0 - 1) / kMmaBars) & 1u));
+          mbar_wait(bars + (G0 - 1) % kMmaBars, (unsigned)((G0 - 1) / kMmaBars) & 1u, lim));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) break;
 
@@ -703,9 +712,10 @@ __global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
       // outstanding B copies and the last commit before the shared and
       // tensor memory are released
       for (int j = b_waited; j < b_issued; ++j)
-        mbar_wait(bars + kMmaBars + j % kPreStages, (unsigned)(j / kPreStages) & 1u);
+        mbar_wait(bars + kMmaBars + j % kPreStages, (unsigned)(j / kPreStages) & 1u, lim);
       if (committed > 0)
-        mbar_wait(bars + (committed - 1) % kMmaBars, (unsigned)((committed - 1) / kMmaBars) & 1u);
+        mbar_wait(bars + (committed - 1) % kMmaBars, (unsigned)((committed - 1) / kMmaBars) & 1u,
+                  lim);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -38,6 +38,10 @@ struct MlpGemmArgs {
   // 1: narrow products (K <= 32 with K N <= 2048, or N <= 16 with K <= 64)
   // run as FP32 FMA loops on the CUDA cores instead (mlp_narrow_kind)
   int narrow;
+  // test hook: 1 = every CTA of a product with pre-split B leaves out the
+  // copy of its first weight chunk, so the wait for it runs out
+  int fault;
+  unsigned long long wait_ns;   // bound of every wait, 0 = the default (2 s)
 };
 
 enum MlpNarrowKind { NARROW_NONE = 0, NARROW_K = 1, NARROW_N = 2 };

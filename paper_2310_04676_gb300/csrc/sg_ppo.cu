@@ -501,6 +501,8 @@ struct sg_ppo {
   float* norm = nullptr;               // advantage mean, 1 / std
   float* clip_coef = nullptr;
   cudaGraphExec_t collect_exec = nullptr;
+  int fault = 0;                       // test hook (sg_ppo_debug_set_fault)
+  unsigned long long wait_ns = 0;      // bound of the contraction's waits, 0 = default
   std::vector<void*> allocs;
 };
 
@@ -532,6 +534,8 @@ sg::MlpGemmArgs gemm_args(const sg_ppo* p) {
   g.split_tf32 = p->cfg.tf32 ? 0 : 1;
   g.narrow = 1;
   g.err = p->err;
+  g.fault = p->fault == SG_FAULT_SKIP_WEIGHT_COPY ? 1 : 0;
+  g.wait_ns = p->wait_ns;
   return g;
 }
 
@@ -994,6 +998,26 @@ sg_status sg_ppo_collect(sg_ppo* p) {
   }
   bind_stream(p, s);
   return cuda_fail(p, cudaGraphLaunch(p->collect_exec, s), "sg_ppo_collect");
+}
+
+sg_status sg_ppo_debug_set_fault(sg_ppo* p, int32_t mode, int64_t wait_limit_ns) {
+  if (!p) return SG_ERR_INVALID_ARG;
+  SG_PPO_CHECK_DEVICE(p, "sg_ppo_debug_set_fault");
+  if (mode != SG_FAULT_NONE && mode != SG_FAULT_SKIP_WEIGHT_COPY)
+    return fail(p, SG_ERR_INVALID_ARG, "sg_ppo_debug_set_fault: unknown mode");
+  if (wait_limit_ns < 0 || wait_limit_ns > 2000000000LL)
+    return fail(p, SG_ERR_INVALID_ARG,
+                "sg_ppo_debug_set_fault: wait_limit_ns must be 0 (default) .. 2e9");
+  // the collect graph holds the products' arguments: capture it again
+  if (p->collect_exec) {
+    const cudaError_t e = cudaStreamSynchronize(sg::context_stream(p->env));
+    if (e != cudaSuccess) return cuda_fail(p, e, "sg_ppo_debug_set_fault");
+    cudaGraphExecDestroy(p->collect_exec);
+    p->collect_exec = nullptr;
+  }
+  p->fault = mode;
+  p->wait_ns = (unsigned long long)wait_limit_ns;
+  return SG_OK;
 }
 
 sg_status sg_ppo_update(sg_ppo* p, const int32_t* perm, float* stats) {

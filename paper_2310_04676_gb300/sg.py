@@ -21,7 +21,7 @@ DONE_TERMINATED, DONE_TIMEOUT, DONE_NONFINITE = 1, 2, 4
 HOST_IO_AUTO, HOST_IO_STAGED, HOST_IO_DIRECT = 0, 1, 2
 ROLLOUT_PERSISTENT, ROLLOUT_STEP_GRAPH = 0, 1
 PACK_CLASS, PACK_INTERLEAVE = 0, 1
-FAULT_NONE, FAULT_SKIP_PARAM_COPY, FAULT_SKIP_PARTNER = 0, 1, 2
+FAULT_NONE, FAULT_SKIP_PARAM_COPY, FAULT_SKIP_PARTNER, FAULT_SKIP_WEIGHT_COPY = 0, 1, 2, 3
 DRIVE_POSITION, DRIVE_VELOCITY, DRIVE_TORQUE = 0, 1, 2
 MAX_CHAINS = 4                     # chains per env (SG_MAX_CHAINS)
 
@@ -128,6 +128,7 @@ def load_library(path=LIB_PATH):
         "sg_ppo_set_params": (i32, [vp, vp]),
         "sg_ppo_get_params": (i32, [vp, vp]),
         "sg_ppo_reset": (i32, [vp, ctypes.c_int64]),
+        "sg_ppo_debug_set_fault": (i32, [vp, i32, ctypes.c_int64]),
         "sg_ppo_collect": (i32, [vp]),
         "sg_ppo_update": (i32, [vp, vp, vp]),
         "sg_ppo_get_buffer": (i32, [vp, i32, vp]),
@@ -626,6 +627,14 @@ class PPO:
         shape, dt = self._shape(which)
         self.env._want(src, dt, shape, "buffer")
         self._check(self.lib.sg_ppo_set_buffer(self.h, int(which), _ptr(src)))
+
+    def debug_set_fault(self, mode, wait_limit_ns=0):
+        """Test hook: FAULT_SKIP_WEIGHT_COPY makes the tensor-core
+        contraction's wait for its first weight chunk run out (bounded by
+        wait_limit_ns, 0 = 2 s); see sg_ppo_debug_set_fault in
+        include/sg_ppo.h."""
+        self.env._sync_stream()
+        self._check(self.lib.sg_ppo_debug_set_fault(self.h, int(mode), int(wait_limit_ns)))
 
 
 def _autograd_function():

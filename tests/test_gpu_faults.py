@@ -83,3 +83,57 @@ def test_hook_validates_its_arguments():
         env.debug_set_fault(sg.FAULT_NONE, -1)
     env.debug_set_fault(sg.FAULT_NONE, 0)
     assert env.cuda_device == torch.cuda.current_device()
+
+
+def _ppo_run(env, ppo, perms):
+    ppo.set_params(torch.as_tensor(W.ppo_init_params(env.obs_dim, env.max_joints, seed=5),
+                                   device="cuda"))
+    ppo.reset(step0=0)
+    ppo.collect()
+    stats = ppo.update(perms)
+    return stats
+
+
+def test_contraction_wait_runs_out_and_ppo_recovers():
+    """The tensor-core contraction's bounded waits (hook
+    sg_ppo_debug_set_fault): with the copy of each CTA's first weight chunk
+    left out, every product with pre-split weights gives up after the bound
+    (its CTAs wait, bounded, for their copies in flight and release their
+    tensor memory), the collect and the update return, and the env context
+    reports SG_ERR_TIMEOUT.  With the hook off the same handles collect and
+    update bit-identically to fresh ones."""
+    cfg = dict(n_steps=4, epochs=2, minibatches=2, gamma=0.99, lam=0.95, clip=0.2,
+               value_coef=1.0, entropy_coef=0.0, lr=3e-4, max_grad_norm=1.0, dt=DT, substeps=2)
+    desc = W.make_desc(["7P"] * 300, episode_len=50)     # 1200 collect rows: 10 row tiles
+    env = sg.Env(desc)
+    ppo = sg.PPO(env, **cfg)
+    perms = torch.as_tensor(W.ppo_perms(ppo.B, cfg["epochs"]), device="cuda")
+    assert env.sync_status() == sg.SG_OK
+    ppo.debug_set_fault(sg.FAULT_SKIP_WEIGHT_COPY, LIMIT_NS)
+    t0 = time.perf_counter()
+    ppo.set_params(torch.as_tensor(W.ppo_init_params(env.obs_dim, env.max_joints, seed=5),
+                                   device="cuda"))
+    ppo.reset(step0=0)
+    ppo.collect()
+    st = env.sync_status()
+    assert st == sg.SG_ERR_TIMEOUT, sg.STATUS_NAMES.get(st)
+    ppo.update(perms)
+    st = env.sync_status()
+    assert st == sg.SG_ERR_TIMEOUT, sg.STATUS_NAMES.get(st)
+    elapsed = time.perf_counter() - t0
+    # about 60 products, each a few waits of 2 ms (all CTAs wait together)
+    assert elapsed < 10.0, elapsed
+    # hook off: the same handles work like fresh ones
+    ppo.debug_set_fault(sg.FAULT_NONE, 0)
+    stats = _ppo_run(env, ppo, perms)
+    ref_env = sg.Env(desc)
+    ref = sg.PPO(ref_env, **cfg)
+    ref_stats = _ppo_run(ref_env, ref, perms)
+    assert env.sync_status() == sg.SG_OK and ref_env.sync_status() == sg.SG_OK
+    assert torch.equal(stats, ref_stats)
+    assert torch.equal(ppo.get_params(), ref.get_params())
+    assert torch.equal(ppo.get_buffer(sg.PPO_VALUES), ref.get_buffer(sg.PPO_VALUES))
+    with pytest.raises(sg.SgError):
+        ppo.debug_set_fault(1, 0)                      # a step-kernel mode: not this hook's
+    with pytest.raises(sg.SgError):
+        ppo.debug_set_fault(sg.FAULT_SKIP_WEIGHT_COPY, 3_000_000_000)
