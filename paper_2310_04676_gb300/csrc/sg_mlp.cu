@@ -853,28 +853,42 @@ __global__ void __launch_bounds__(256) narrow_k_kernel(MlpGemmArgs g) {
       w[k] = (nv && k < K) ? __ldg(g.B + (long long)n * g.b_n + (long long)k * g.b_k) : 0.f;
     const float bn = ((kEpi == EPI_BIAS || kEpi == EPI_BIAS_ELU) && nv) ? __ldg(g.bias + n) : 0.f;
     float cs = 0.f;
-    for (int r = phase; r < kNarrowRows; r += P) {
-      const int m = m0 + r;
-      if (m >= g.M) break;
-      const float4* x4 = reinterpret_cast<const float4*>(As + r * K4);
-      float acc = 0.f;
+    // rows phase, phase + P, ... in order, four at a time so that the four
+    // rows' activation loads are in flight together
+    const int nrows = min(kNarrowRows, g.M - m0);
+    constexpr int kU = 4;
+    for (int r0 = phase; r0 < nrows; r0 += kU * P) {
+      float y[kU];
 #pragma unroll
-      for (int q = 0; q < kNarrowMaxK / 4; ++q) {
-        if (4 * q >= K4) break;
-        const float4 x = x4[q];
-        acc = fmaf(x.x, w[4 * q], acc);
-        acc = fmaf(x.y, w[4 * q + 1], acc);
-        acc = fmaf(x.z, w[4 * q + 2], acc);
-        acc = fmaf(x.w, w[4 * q + 3], acc);
+      for (int u = 0; u < kU; ++u) {
+        const int r = r0 + u * P;
+        y[u] = (kEpi == EPI_DELU_SUM && nv && r < nrows)
+                   ? __ldg(g.act_y + (long long)(m0 + r) * g.c_m + n)
+                   : 0.f;
       }
-      if (kEpi == EPI_BIAS || kEpi == EPI_BIAS_ELU) acc += bn;
-      if (kEpi == EPI_BIAS_ELU || kEpi == EPI_ELU) acc = elu_fast(acc);
-      if (kEpi == EPI_DELU_SUM) {
-        const float y = nv ? __ldg(g.act_y + (long long)m * g.c_m + n) : 0.f;
-        acc *= y > 0.f ? 1.f : y + 1.f;
-        cs += nv ? acc : 0.f;
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int r = r0 + u * P;
+        if (r >= nrows) break;
+        const float4* x4 = reinterpret_cast<const float4*>(As + r * K4);
+        float acc = 0.f;
+#pragma unroll
+        for (int q = 0; q < kNarrowMaxK / 4; ++q) {
+          if (4 * q >= K4) break;
+          const float4 x = x4[q];
+          acc = fmaf(x.x, w[4 * q], acc);
+          acc = fmaf(x.y, w[4 * q + 1], acc);
+          acc = fmaf(x.z, w[4 * q + 2], acc);
+          acc = fmaf(x.w, w[4 * q + 3], acc);
+        }
+        if (kEpi == EPI_BIAS || kEpi == EPI_BIAS_ELU) acc += bn;
+        if (kEpi == EPI_BIAS_ELU || kEpi == EPI_ELU) acc = elu_fast(acc);
+        if (kEpi == EPI_DELU_SUM) {
+          acc *= y[u] > 0.f ? 1.f : y[u] + 1.f;
+          cs += nv ? acc : 0.f;
+        }
+        if (nv) g.C[(long long)(m0 + r) * g.c_m + n] = acc;
       }
-      if (nv) g.C[(long long)m * g.c_m + n] = acc;
     }
     if (kEpi == EPI_DELU_SUM && nv) csum[phase][n] = cs;
   }

@@ -83,12 +83,14 @@ def test_forward_layer(rows, inp, out, presplit):
     _check(Y, X.double(), W.double(), None, True)
 
 
-@pytest.mark.parametrize("rows,inp,out", [(70001, 28, 256), (65537, 256, 128), (40000, 128, 64)])
+@pytest.mark.parametrize("rows,inp,out", [(70001, 28, 256), (65537, 256, 128), (40000, 128, 64),
+                                          (50001, 40, 64), (45000, 33, 128)])
 def test_forward_persistent_tiles(rows, inp, out):
     """More output tiles than persistent CTAs (pre-split weights): each CTA
     takes several tiles in turn, the next tile's first chunks copied during
-    the current tile's epilogue; a sample of rows, the first and the last
-    (ragged) tile against FP64."""
+    the current tile's epilogue (the two-chunk lookahead crosses each tile
+    boundary; K = 33 and 40 end in a ragged K chunk); a sample of rows, the
+    first and the last (ragged) tile against FP64."""
     X, W, b = _rand((rows, inp), 21), _rand((out, inp), 22), _rand((out,), 23)
     Y = torch.empty(rows, out, device="cuda")
     work = torch.empty(_presplit_floats(out, inp), device="cuda")
