@@ -189,7 +189,7 @@ __device__ __forceinline__ Operand make_operand(const float* X, long long xr, lo
   Operand o{X, xr, xk, R, K, r0, nrows, RAW_PLAIN};
   const bool al = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
   if (al && xk == 1 && (xr & 3) == 0) o.layout = RAW_ROWS;
-  else if (al && xr == 1 && (xk & 3) == 0 && (nrows & 3) == 0) o.layout = RAW_KMAJOR;
+  else if (al && xr == 1 && (xk & 3) == 0 && (nrows & 15) == 0) o.layout = RAW_KMAJOR;
   return o;
 }
 
@@ -208,9 +208,17 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Per-thread copy state of one operand: up to kUnits 16-byte pieces per
 // chunk, each with its source address at chunk 0, its byte offset in a raw
-// stage and the bytes it holds (0: zero fill).  RAW_ROWS: piece j is row
-// r = (tid >> 2) + 64 j, K group tid & 3 (bytes shrink at the K tail);
-// RAW_KMAJOR: piece j is K row k_j, rows 4 q .. 4 q + 3 (q = tid % (nrows / 4)).
+// stage and the bytes it holds (0: zero fill).  RAW_ROWS: piece j (u = tid +
+// 256 j) is row r = 8 (u >> 5) + (u & 7), K group (u >> 3) & 3 (bytes shrink
+// at the K tail); RAW_KMAJOR: piece j is K row k_j, rows 4 q .. 4 q + 3
+// (q = tid % (nrows / 4)), stored at row position 4 q ^ kmajor_swz(k_j).
+// In the K-major stage, row k holds its nrows values with the 8-row groups
+// permuted by kmajor_swz(k) (an XOR of bits 3-4 of the row index), so that
+// the split's reads -- 32 threads reading rows 8 w .. 8 w + 7 of the four K
+// groups -- hit 32 different banks.
+__device__ __forceinline__ int kmajor_swz(int k, int nrows) {
+  return 8 * ((k >> 2) & ((nrows & 31) ? 1 : 3));
+}
 struct Loader {
   const float* src[kUnits];
   unsigned dst[kUnits];
@@ -223,12 +231,15 @@ __device__ __forceinline__ Loader make_loader(const Operand& o, int tid) {
   Loader L{};
   L.n = 0;
   if (o.layout == RAW_ROWS) {
-    const int kg = tid & 3;
 #pragma unroll
     for (int j = 0; j < kUnits; ++j) {
       const int u = tid + j * kMlpThreads;
       if (u >= o.nrows * 4) break;
-      const int r = u >> 2, gr = o.r0 + r;
+      // eight consecutive threads take the eight rows of one core matrix
+      // (16-byte pieces 16 bytes apart: conflict-free shared-memory writes);
+      // a warp still reads eight whole 64-byte row segments
+      const int kg = (u >> 3) & 3;
+      const int r = ((u >> 5) << 3) + (u & 7), gr = o.r0 + r;
       L.src[j] = gr < o.R ? o.X + (long long)gr * o.xr + 4 * kg : o.X;
       L.bytes[j] = gr < o.R ? 16 : 0;
       L.kofs[j] = 4 * kg;
@@ -247,7 +258,7 @@ __device__ __forceinline__ Loader make_loader(const Operand& o, int tid) {
       L.src[j] = nr ? o.X + (long long)k * o.xk + gr : o.X;
       L.bytes[j] = 4 * nr;
       L.kofs[j] = k;
-      L.dst[j] = (unsigned)(k * o.nrows + 4 * q) * 4u;
+      L.dst[j] = (unsigned)(k * o.nrows + ((4 * q) ^ kmajor_swz(k, o.nrows))) * 4u;
       L.n = j + 1;
     }
   }
@@ -330,7 +341,8 @@ __device__ __forceinline__ void convert(const Operand& o, int k0, const float* r
     float v[4];
     if (o.layout == RAW_KMAJOR) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = raw[(4 * kg + j) * o.nrows + r];
+      for (int j = 0; j < 4; ++j)
+        v[j] = raw[(4 * kg + j) * o.nrows + (r ^ kmajor_swz(4 * kg + j, o.nrows))];
     } else {
       const int gr = o.r0 + r;
       const float* row = o.X + (long long)gr * o.xr;
