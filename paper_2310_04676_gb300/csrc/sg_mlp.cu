@@ -24,21 +24,23 @@
 // One CTA computes a 128 x Nt tile (Nt <= 128, a multiple of 16): eight
 // warps copy, split and drain; lane 0 of a ninth warp issues the bulk copies
 // of pre-split weights and the MMAs.  Raw FP32 operand chunks (16 wide in K)
-// travel to shared memory by asynchronous copies two chunks ahead; each
-// chunk is then split into its TF32 parts and stored in the tensor cores'
-// K-major layout without swizzle (8-row x 16-byte core matrices), or, for
-// pre-split weights, arrives already split by bulk copies.  One CTA barrier
-// per chunk; after it the issuing lane issues, per 8-wide K step, the three
-// tcgen05.mma of kind::tf32 into an FP32 accumulator in tensor memory (TMEM
-// lane = row, column = n) and commits them to an mbarrier, while the eight
-// warps split the next chunk; two tensor-core stages alternate, a stage being refilled only after
-// the mbarrier of the MMAs that read it has completed (bounded wait).  The
-// epilogue reads the accumulator with tcgen05.ld (warps w and w + 4 share
-// the TMEM lanes 32 (w % 4) .., taking alternate 16-column blocks), applies
-// the epilogue and stores whole row segments.  Products with pre-split
-// weights and at least two chunks run persistent CTAs (about two per SM)
-// that take the output tiles in turn, the copies of a tile's first chunks
-// overlapping the previous tile's epilogue.
+// travel to shared memory by asynchronous copies two chunks ahead.  Each
+// chunk of A is then split into its TF32 parts and stored in tensor memory
+// (TMEM lane = row, one column per K value: the MMAs read A from there);
+// each chunk of B is split into the tensor cores' K-major shared-memory
+// layout without swizzle (8-row x 16-byte core matrices), or, for pre-split
+// weights, arrives already split by bulk copies.  One CTA barrier per chunk;
+// after it the issuing lane issues, per 8-wide K step, the three
+// tcgen05.mma of kind::tf32 into an FP32 accumulator in tensor memory
+// (column = n) and commits them to an mbarrier, while the eight warps split
+// the next chunk; two operand stages alternate, a stage being refilled only
+// after the mbarrier of the MMAs that read it has completed (bounded wait).
+// The epilogue reads the accumulator with tcgen05.ld (warps w and w + 4
+// share the TMEM lanes 32 (w % 4) .., taking alternate 16-column blocks),
+// applies the epilogue and stores whole row segments.  Products with
+// pre-split weights and at least two chunks run persistent CTAs (about two
+// per SM) that take the output tiles in turn, the copies of a tile's first
+// chunks overlapping the previous tile's epilogue.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -126,12 +128,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity,
   return false;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         bool accumulate) {
+// D (+)= A B^T with A (128 rows x 8 K, TF32) in tensor memory: row r in
+// lane r, K value k in column a_tmem + k.
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
+                                            uint32_t idesc, bool accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate ? 1 : 0)
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate ? 1 : 0)
       : "memory");
 }
 
@@ -154,6 +158,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Eight consecutive 32-bit columns of this thread's TMEM lane (warp w may
+// address lanes 32 (w % 4) .. 32 (w % 4) + 31 only).
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+      : "memory");
 }
 
 // ---- operand chunks ---------------------------------------------------------
@@ -360,6 +374,57 @@ __device__ __forceinline__ void convert(const Operand& o, int k0, const float* r
   }
 }
 
+// Split chunk k0 of A (128 rows: raw stage in the tiles' layout or K-major,
+// or read directly for RAW_PLAIN) into its TF32 parts in tensor memory:
+// warp w < 8 takes the rows of its TMEM lane quarter, 32 (w % 4) + lane, and
+// the K values 8 (w / 4) .. 8 (w / 4) + 7 of the chunk; hi goes to columns
+// t_hi + 8 (w / 4) .., lo to t_lo + 8 (w / 4) .. (hi only in the one-product
+// mode).  The caller waits for the stores (tcgen05.wait::st).
+template <bool kSplit>
+__device__ __forceinline__ void split_a_tmem(const Operand& o, int k0, const char* raw, int warp,
+                                             int lane, uint32_t t_hi, uint32_t t_lo) {
+  const int lq = warp & 3, half = warp >> 2;
+  const int r = lq * 32 + lane;
+  float v[8];
+  if (o.layout == RAW_ROWS) {
+    const float4 a = *reinterpret_cast<const float4*>(raw + tile_off(r, 8 * half));
+    const float4 b = *reinterpret_cast<const float4*>(raw + tile_off(r, 8 * half + 4));
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+    v[4] = b.x;
+    v[5] = b.y;
+    v[6] = b.z;
+    v[7] = b.w;
+  } else if (o.layout == RAW_KMAJOR) {
+    const float* rf = reinterpret_cast<const float*>(raw);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = 8 * half + j;
+      v[j] = rf[k * o.nrows + (r ^ kmajor_swz(k, o.nrows))];
+    }
+  } else {
+    const int gr = o.r0 + r;
+    const float* row = o.X + (long long)gr * o.xr;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gk = k0 + 8 * half + j;
+      v[j] = (gr < o.R && gk < o.K) ? __ldg(row + (long long)gk * o.xk) : 0.f;
+    }
+  }
+  uint32_t h[8], l[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float hf = round_tf32(v[j]);
+    h[j] = __float_as_uint(hf);
+    l[j] = kSplit ? __float_as_uint(round_tf32(v[j] - hf)) : 0u;
+  }
+  const uint32_t lane_base = (uint32_t)(lq * 32) << 16;
+  tmem_st8(t_hi + lane_base + 8u * (uint32_t)half, h);
+  if (kSplit) tmem_st8(t_lo + lane_base + 8u * (uint32_t)half, l);
+}
+
 // Epilogue modes (compile-time, no per-element branches): plain product,
 // bias (+ ELU), ELU only, or the ELU derivative of the layer below with
 // column sums.
@@ -389,14 +454,18 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
 // a CTA's Nt rows of one part are one contiguous block of Nt x 64 bytes and
 // arrive by one bulk copy.
 constexpr int kMmaBars = 3;     // MMA commits of chunk c signal barrier c % 3
+// epilogue: per warp a 32 x 20-float slab, then [4][128] column partials
+constexpr size_t kSlabBytes = (8 * 32 * 20 + 4 * 128) * sizeof(float);
 constexpr int kPreStages = 3;   // pre-split B stages (chunk c in stage c % 3)
 
 template <bool kPreB>
 __host__ __device__ constexpr size_t smem_bytes_for(int n_tile) {
-  // A tiles [2][hi, lo]; B tiles [kPreB ? 3 : 2][hi, lo]; raw A [3]; raw B [3]
-  // (not with kPreB); 6 barriers, the TMEM address and the abort flag
-  return (size_t)(2 * 2 + kRawStages) * kTileM * kChunkK * 4 +
-         (size_t)(kPreB ? 2 * kPreStages : 2 * 2 + kRawStages) * n_tile * kChunkK * 4 + 64;
+  // B tiles [kPreB ? 3 : 2][hi, lo]; raw A [3]; raw B [3] (not with kPreB);
+  // the epilogue's slabs; 6 barriers, the TMEM address and the abort flag
+  // (A's split parts live in tensor memory)
+  return (size_t)kRawStages * kTileM * kChunkK * 4 +
+         (size_t)(kPreB ? 2 * kPreStages : 2 * 2 + kRawStages) * n_tile * kChunkK * 4 +
+         kSlabBytes + 64;
 }
 
 template <int kEpi, bool kPreB, bool kSplit>
@@ -415,15 +484,17 @@ __global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
   const int kbeg = blockIdx.z * g.k_per_split;
   const int kend = min(g.K, kbeg + g.k_per_split);
   const int a_part = kTileM * kChunkK * 4, b_part = Nt * kChunkK * 4;
-  char* const a_tiles = sm;
-  char* const b_tiles = sm + 2 * 2 * a_part;
+  char* const b_tiles = sm;
   char* const raw_a = b_tiles + (kPreB ? kPreStages : 2) * 2 * b_part;
   char* const raw_b = raw_a + kRawStages * a_part;
-  uint64_t* const bars =
-      reinterpret_cast<uint64_t*>(raw_b + (kPreB ? 0 : kRawStages * b_part));   // [3] MMA, [3] B
+  char* const slabs = raw_b + (kPreB ? 0 : kRawStages * b_part);
+  uint64_t* const bars = reinterpret_cast<uint64_t*>(slabs + kSlabBytes);   // [3] MMA, [3] B
   uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bars + 6);
   volatile int* const abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  const uint32_t ncols = Nt <= 32 ? 32u : (Nt <= 64 ? 64u : 128u);
+  // tensor memory: the accumulator in columns 0 .. Nt - 1, then A's split
+  // parts, stage s: hi at a_col0 + 32 s, lo 16 columns further
+  const uint32_t a_col0 = Nt <= 64 ? 64u : 128u;
+  const uint32_t ncols = Nt <= 64 ? 128u : 256u;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -530,18 +601,21 @@ __global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
         if (c + 1 < nchunks) issue_pre_b(G + 1, n0, c + 1);
         else if (has_next) issue_pre_b(G + 1, tile_n0(nxt), 0);
       }
-      char* const ahi = a_tiles + ts * 2 * a_part;
+      const uint32_t a_hi = tmem + a_col0 + 32u * (uint32_t)ts;
       char* const bhi = b_tiles + (kPreB ? G % kPreStages : ts) * 2 * b_part;
       if (conv) {
-        convert<kSplit>(opa, kbeg + c * kChunkK,
-                        reinterpret_cast<const float*>(raw_a + rs * a_part), tid, ahi,
-                        ahi + a_part);
+        // after the wait above: the MMAs of chunk G - 2 no longer read the stage
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        split_a_tmem<kSplit>(opa, kbeg + c * kChunkK, raw_a + rs * a_part, warp, lane, a_hi,
+                             a_hi + 16u);
         if (!kPreB)
           convert<kSplit>(opb, kbeg + c * kChunkK,
                           reinterpret_cast<const float*>(raw_b + rs * b_part), tid, bhi,
                           bhi + b_part);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       cp_async_wait<kRawStages - 2>();            // this thread's copies of chunk G + 1 landed
       __syncthreads();
       if (*abort_flag) {
@@ -559,14 +633,14 @@ __global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
 #pragma unroll
           for (int ks = 0; ks < kChunkK / 8; ++ks) {
             const unsigned koff = (unsigned)ks * 2 * kLbo;   // two core matrices per K step
-            const uint64_t ah = smem_desc(smem_addr(ahi) + koff);
-            const uint64_t al = smem_desc(smem_addr(ahi + a_part) + koff);
+            const uint32_t ah = a_hi + 8u * (uint32_t)ks;    // eight TMEM columns per K step
+            const uint32_t al = ah + 16u;
             const uint64_t bh = smem_desc(smem_addr(bhi) + koff);
             const uint64_t bl = smem_desc(smem_addr(bhi + b_part) + koff);
-            mma_tf32(tmem, ah, bh, idesc, c > 0 || ks > 0);
+            mma_tf32_ta(tmem, ah, bh, idesc, c > 0 || ks > 0);
             if (kSplit) {
-              mma_tf32(tmem, ah, bl, idesc, true);
-              mma_tf32(tmem, al, bh, idesc, true);
+              mma_tf32_ta(tmem, ah, bl, idesc, true);
+              mma_tf32_ta(tmem, al, bh, idesc, true);
             }
           }
           mma_commit(bars + G % kMmaBars);
@@ -590,8 +664,7 @@ __global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
       // + lane) and the 16-column blocks of parity w / 4.  Per block each
       // thread finishes its row's values (bias, ELU, or the ELU derivative of
       // the layer below) and parks them in a shared-memory slab of the warp
-      // (row pitch 20 floats; the slabs overlap the split tiles, which no
-      // copy writes and no MMA reads at this point).  From the slab the warp
+      // (row pitch 20 floats, a region of its own).  From the slab the warp
       // sums the columns (lane l: column l % 16 over 16 rows, then the two
       // halves; fixed order) into the partials of its lane quarter, and
       // stores whole 64-byte row segments, four lanes per row, eight rows
@@ -602,8 +675,8 @@ __global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
       const int m = m0 + lq * 32 + lane;
       const bool mrow = m < g.M;
       float* cbase = g.C + (long long)blockIdx.z * g.c_split;
-      float* slab = reinterpret_cast<float*>(sm) + warp * 32 * 20;
-      float* wsum = reinterpret_cast<float*>(sm) + 8 * 32 * 20;          // [4][128]
+      float* slab = reinterpret_cast<float*>(slabs) + warp * 32 * 20;
+      float* wsum = reinterpret_cast<float*>(slabs) + 8 * 32 * 20;       // [4][128]
       const bool cvec = (g.c_m & 3) == 0 && (reinterpret_cast<uintptr_t>(cbase) & 15) == 0;
       const bool yvec = kEpi == EPI_DELU_SUM && (g.c_m & 3) == 0 &&
                         (reinterpret_cast<uintptr_t>(g.act_y) & 15) == 0;
@@ -701,8 +774,8 @@ __global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
       }
     }
     if (!has_next) break;
-    // the next tile's MMAs overwrite the accumulator and its splits reuse the
-    // slabs' shared memory: every thread done with both first
+    // the next tile's MMAs overwrite the accumulator: every thread done
+    // reading it (and with the slabs) first
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
