@@ -592,8 +592,8 @@ __global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
         }
         cp_async_commit();
       }
-      // the tiles of stage ts (and the B stage of chunk G + 1) were read by
-      // the MMAs of chunk G - 2
+      // stage ts (A's tensor-memory columns, B's split tiles) and the B stage
+      // of chunk G + 1 were read by the MMAs of chunk G - 2
       if (G >= 2 &&
           !mbar_wait(bars + (G - 2) % kMmaBars, (unsigned)((G - 2) / kMmaBars) & 1u, lim))
         *abort_flag = 1;
