@@ -612,11 +612,12 @@ __global__ void __launch_bounds__(kMlpBlock, 2) mlp_gemm_kernel(MlpGemmArgs g) {
           convert<kSplit>(opb, kbeg + c * kChunkK,
                           reinterpret_cast<const float*>(raw_b + rs * b_part), tid, bhi,
                           bhi + b_part);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      // B's split tiles (written by these threads) are read by the MMAs
+      if (!kPreB) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       cp_async_wait<kRawStages - 2>();            // this thread's copies of chunk G + 1 landed
+      if (conv) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
       if (*abort_flag) {
         ok = false;
