@@ -326,8 +326,9 @@ __device__ __forceinline__ void split4(const float (&v)[4], float4& h, float4& l
   }
 }
 
-// Split chunk k0 (from raw, or read directly for RAW_PLAIN) into the hi / lo
-// tiles (hi only in the one-product mode).
+// Split chunk k0 of B (from raw, or read directly for RAW_PLAIN) into the
+// hi / lo shared-memory tiles the MMAs read (hi only in the one-product
+// mode); used when B is not pre-split.
 template <bool kSplit>
 __device__ __forceinline__ void convert(const Operand& o, int k0, const float* raw, int tid,
                                         char* hi, char* lo) {
